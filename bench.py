@@ -1,0 +1,368 @@
+"""Benchmark of the fused double-MRT thermal LBM step on GB300.
+
+Workload: a 128^3 cavity of Type 2 (hot / cold y walls, linear-profile x and z
+walls), Ra = 1e5, Pr = 0.71, Ma = 0.1, starting from rest.  One benchmark
+step = 100 fused LBM time steps + the convergence residual + the hot-wall
+Nusselt numbers, i.e. one pass of the whole hot path.  Throughput is MLUPS
+(million coupled D3Q19 + D3Q7 cell updates per second).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl dmrt|reference]
+
+With N > 1 (launched by torchrun) every rank runs an independent replica of
+the same cavity ("replicas only": a single cavity is not sharded); the
+reported value is the total cell updates of all ranks over the slowest
+rank's time.  Rank 0 prints one JSON line.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+GRID = (128, 128, 128)
+WALL = 2
+RA, PR, MA = 1e5, 0.71, 0.1
+LBM_STEPS_PER_STEP = 100
+BYTES_PER_CELL = 208  # 26 float32 populations read + written per cell update
+METRIC = "MLUPS and % HBM roofline per coupled step"
+WORKLOAD = ("128^3 cavity, Type 2 (linear side walls), Ra=1e5, Pr=0.71, Ma=0.1, from rest; "
+            "one step = 100 fused LBM steps + residual + hot-wall Nu")
+STEP_KERNEL_SOURCES = ["paper_1511_04633_gb300/csrc/step.cu",
+                       "paper_1511_04633_gb300/csrc/lattice.cuh"]
+
+
+# ---------------------------------------------------------------- distributed plumbing
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, local, world
+
+
+def init_dist(world: int, backend: str):
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+    os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+    dist.init_process_group(backend=backend)
+    return dist
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def reduce_max(dist, value: float, device=None) -> float:
+    """Maximum of `value` over all ranks (the slowest rank's time)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate(units_per_rank: float, world: int, seconds_max: float) -> float:
+    """Whole-job throughput in MLUPS: all ranks' cell updates / slowest time."""
+    return units_per_rank * world / seconds_max / 1e6
+
+
+# ---------------------------------------------------------------- clocks and peaks
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        max_mhz = max(r[1] for r in rows)
+        loaded = [r for r in rows if r[0] > 0.5 * max_mhz] or rows
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in loaded for k, v in enumerate(r[2]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in loaded), "sm_max_mhz": max_mhz,
+                "reasons": reasons, "samples": len(loaded)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def step_kernel_digest() -> str:
+    h = hashlib.sha256()
+    for rel in STEP_KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per step-kernel launch from the committed ncu summary, only
+    if it was taken on the current kernel sources."""
+    path = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
+    try:
+        with open(path) as fh:
+            t = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    if t.get("source_digest") != step_kernel_digest():
+        return None
+    return t.get("dram_bytes_per_launch")
+
+
+# ---------------------------------------------------------------- CPU oracle legs
+
+def oracle_sample(seconds: float = 12.0, max_steps: int = 400):
+    """Time the FP64 oracle on the benchmark cavity: steps from rest until
+    `seconds` of CPU work (at least 2).  Returns (MLUPS, cores, steps)."""
+    import oracle
+    o = oracle.Oracle.physical(GRID, WALL, RA, PR, MA)
+    o.step(1)  # first touch of the buffers
+    cells = GRID[0] * GRID[1] * GRID[2]
+    n = 0
+    t0 = time.perf_counter()
+    while n < 2 or (time.perf_counter() - t0 < seconds and n < max_steps):
+        o.step(1)
+        n += 1
+    dt = time.perf_counter() - t0
+    o.close()
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return cells * n / dt / 1e6, cores, n
+
+
+def run_reference(args, rank, world):
+    """The oracle as the reference arm: each benchmark step is a bounded
+    sample of the same workload (a few oracle LBM steps) on the host cores."""
+    if rank != 0:
+        return
+    import oracle
+    o = oracle.Oracle.physical(GRID, WALL, RA, PR, MA)
+    cells = GRID[0] * GRID[1] * GRID[2]
+    per_step = args.ref_lbm_steps
+    for _ in range(args.warmup):
+        o.step(per_step)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.step(per_step)
+    dt = time.perf_counter() - t0
+    o.close()
+    value = cells * per_step * args.steps / dt / 1e6
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    sample = f"{per_step} oracle LBM steps of the 128^3 Type 2 cavity per benchmark step"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": list(GRID), "wall_type": WALL, "Ra": RA,
+                   "parallelism": "replicas"},
+        "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU arm
+
+def run_dmrt(args, rank, local, world):
+    import torch
+    from paper_1511_04633_gb300 import dmrt
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dist = init_dist(world, "nccl")
+    device = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(device)
+    dmrt.load()
+
+    cells = GRID[0] * GRID[1] * GRID[2]
+    cav = dmrt.Cavity(GRID, RA, PR, MA, WALL)
+    dmrt.dmrt_set_stream(cav.h, stream)
+    inner = args.inner
+
+    def one_step():
+        dmrt.dmrt_step(cav.h, inner)
+        return dmrt.dmrt_nusselt(cav.h, 0)
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+
+    # timed region: device-resident state, CUDA events on the launch stream
+    dmrt.dmrt_get_stats(cav.h, reset=True)
+    dmrt.dmrt_set_timing(cav.h, True)
+    barrier(dist)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            one_step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier(dist)
+    ms = ev0.elapsed_time(ev1)
+    stats = dmrt.dmrt_get_stats(cav.h, reset=True)
+    dmrt.dmrt_set_timing(cav.h, False)
+    secs = reduce_max(dist, ms / 1e3, device)
+    units = cells * inner * args.steps
+    value = aggregate(units, world, secs)
+
+    # roofline of the dominant kernel (the fused step), from its own events
+    launch_s = stats["step_ms"] / 1e3 / max(stats["timed_steps"], 1)
+    achieved = BYTES_PER_CELL * cells / launch_s / 1e9
+    peak, peak_src = measured_peaks()
+    traffic = profiled_traffic()
+
+    # end to end through the C ABI with host buffers: upload the start fields
+    # from pinned memory, step, read the fields and Nu back
+    rho_h = torch.ones(GRID[::-1], dtype=torch.float32).pin_memory()
+    u_h = torch.zeros((3,) + GRID[::-1], dtype=torch.float32).pin_memory()
+    th_h = torch.zeros(GRID[::-1], dtype=torch.float32).pin_memory()
+    rho_o = torch.empty_like(rho_h).pin_memory()
+    u_o = torch.empty_like(u_h).pin_memory()
+    th_o = torch.empty_like(th_h).pin_memory()
+    dmrt.dmrt_fields(cav.h, rho_h, u_h, th_h)  # the current state as the start fields
+
+    def e2e_step():
+        dmrt.dmrt_init_fields(cav.h, rho_h, u_h, th_h)
+        dmrt.dmrt_step(cav.h, inner)
+        dmrt.dmrt_fields(cav.h, rho_o, u_o, th_o)
+        return dmrt.dmrt_nusselt(cav.h, 0)
+
+    for _ in range(2):
+        e2e_step()
+    e2e_steps = max(3, args.steps // 4)
+    barrier(dist)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_secs = reduce_max(dist, time.perf_counter() - t0, device)
+    e2e_value = aggregate(cells * inner * e2e_steps, world, e2e_secs)
+    h2d = 5 * 4 * cells
+    d2h = 5 * 4 * cells + 3 * 8
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        mlups, cores, n = oracle_sample(args.cpu_seconds)
+        cpu = {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+               "sample": f"{n} FP64 oracle LBM steps of the 128^3 Type 2 cavity from rest"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": list(GRID), "wall_type": WALL, "Ra": RA, "Pr": PR,
+                   "Ma": MA, "lbm_steps_per_step": inner, "storage": "f32 deviations",
+                   "l2": "inputs larger than L2 (two 218 MB population buffers)",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
+                     "kernel": "step_kernel<2>", "bytes_per_cell": BYTES_PER_CELL,
+                     "launch_us": launch_s * 1e6},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": stats["total_launches"],
+        "clocks": clocks.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["dmrt", "reference"], default="dmrt")
+    ap.add_argument("--inner", type=int, default=LBM_STEPS_PER_STEP,
+                    help="LBM time steps per benchmark step")
+    ap.add_argument("--ref-lbm-steps", type=int, default=1,
+                    help="oracle LBM steps per reference benchmark step")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    rank, local, world = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    run_dmrt(args, rank, local, world)
+
+
+if __name__ == "__main__":
+    main()

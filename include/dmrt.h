@@ -1,0 +1,191 @@
+/*
+ * dmrt.h -- C ABI of the GB300 double-MRT thermal lattice Boltzmann library.
+ *
+ * Method: "LBM Simulation of 3-D Natural Convection with Double MRT Model"
+ * (arXiv:1511.04633).  Flow: D3Q19 MRT (Sec. 3.1, Eqs. (11)-(26)); energy:
+ * D3Q7 MRT (Sec. 3.2, Eqs. (27)-(37)); coupling: Boussinesq buoyancy force
+ * (Eqs. (15)-(17)); problem: a box of nx*ny*nz cells with the hot wall at
+ * y = 0 and the cold wall at y = H = ny (Sec. 2, Eqs. (6)-(10)); lattice
+ * units and Nusselt numbers: Sec. 4, Eqs. (38)-(41).
+ *
+ * Conventions shared by every call:
+ *  - Temperatures are theta = (T - T_c)/(T_h - T_c) - 1/2, so the hot wall is
+ *    +1/2 and the cold wall -1/2.  Velocities are lattice units (c = 1).
+ *  - Field arrays are float32 in [z][y][x] order, x fastest; the velocity is
+ *    three such planes [3][z][y][x] (u_x, u_y, u_z).  Population arrays are
+ *    [q][z][y][x] with q in the velocity order of Eq. (12) (D3Q19) or
+ *    Eq. (28) (D3Q7).
+ *  - `on_device` = 1: the pointer is CUDA device memory (e.g. a torch
+ *    tensor's data_ptr) on the handle's device; 0: host memory.  The caller
+ *    owns every array it passes; the library copies and never keeps it.
+ *  - Every call returns a dmrt_status; none throws or aborts.  After an error
+ *    dmrt_last_error() describes it.  Work is queued on the handle's stream;
+ *    calls that return data to the host synchronise that stream.
+ *  - The handle owns all device memory it allocates; dmrt_destroy frees it.
+ *  - A handle is not thread-safe: one host thread at a time.
+ */
+#ifndef DMRT_H
+#define DMRT_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dmrt dmrt_t;
+
+typedef enum {
+    DMRT_OK = 0,
+    DMRT_ERR_ARG = 1,      /* invalid argument; nothing was changed */
+    DMRT_ERR_CUDA = 2,     /* a CUDA call failed; see dmrt_last_error */
+    DMRT_ERR_OOM = 3,      /* device allocation failed */
+    DMRT_ERR_DIVERGED = 4, /* a NaN/Inf was found in the fields */
+    DMRT_ERR_TIMEOUT = 5,  /* a step budget ran out before convergence */
+} dmrt_status;
+
+/* Wall types (Sec. 2).  All walls are no-slip (Eq. (8)); y = 0 is hot and
+ * y = H cold (Eqs. (6),(7)).
+ *  TYPE1: the x and z walls adiabatic.
+ *  TYPE2: the x and z walls carry the linear profile of Eq. (9).
+ *  TYPE3: the x walls linear, the z walls adiabatic (Eq. (10)).
+ *  PERIODIC: no walls at all (a test configuration for conservation laws). */
+typedef enum {
+    DMRT_WALL_PERIODIC = 0,
+    DMRT_WALL_TYPE1 = 1,
+    DMRT_WALL_TYPE2 = 2,
+    DMRT_WALL_TYPE3 = 3,
+} dmrt_wall;
+
+/* Population storage format in HBM.  F32 stores f_i - w_i and g_i in float32
+ * (208 bytes moved per cell update). */
+typedef enum {
+    DMRT_STORE_F32 = 0,
+} dmrt_storage;
+
+/* Optional creation settings; pass NULL for the defaults. */
+typedef struct dmrt_opts {
+    int storage;           /* dmrt_storage; default DMRT_STORE_F32 */
+    int residual_interval; /* K of the convergence residual; default 100 */
+} dmrt_opts;
+
+/* Derived lattice parameters of a handle (read-only view). */
+typedef struct dmrt_params {
+    int nx, ny, nz, wall_type, storage, residual_interval;
+    double nu, alpha, gbeta;   /* lattice viscosity, diffusivity, g*beta*dT */
+    double tau_nu, tau_alpha;  /* 3 nu + 1/2 (Eq. (26)); 1/2 + 4 alpha (Eq. (36)) */
+    long steps;                /* time steps taken since creation / last reset */
+} dmrt_params;
+
+/* Counters for profiling and for the benchmark's launch count. */
+typedef struct dmrt_stats {
+    long step_launches;    /* fused step kernels launched */
+    long total_launches;   /* every kernel this handle launched */
+    double step_ms;        /* summed CUDA-event time of timed step-kernel runs */
+    long timed_steps;      /* step kernels inside those timed runs */
+    double bytes_per_cell; /* algorithmic HBM bytes per cell update */
+} dmrt_stats;
+
+/* Create a cavity of grid[0]*grid[1]*grid[2] = nx*ny*nz cells from the
+ * physical numbers of Sec. 4: Rayleigh Ra > 0, Prandtl Pr > 0 and Mach
+ * 0 < Ma < 0.3.  Lattice parameters follow Eq. (38) with H = ny, dT = 1:
+ * u_c = Ma/sqrt(3), nu = u_c H sqrt(Pr/Ra), alpha = nu/Pr, g*beta = u_c^2/H.
+ * The fluid starts at rest: rho = 1, u = 0, theta = 0 (populations at the
+ * equilibrium of Eq. (17), energy populations zero).  Runs on the current
+ * CUDA device.  Every grid dimension must be >= 2 (>= 1 for PERIODIC) and
+ * nx*ny*nz < 2^31.  On error *out is NULL. */
+dmrt_status dmrt_create(dmrt_t **out, const int grid[3], double Ra, double Pr, double Ma,
+                        int wall_type);
+
+/* dmrt_create with settings (opts may be NULL). */
+dmrt_status dmrt_create_ex(dmrt_t **out, const int grid[3], double Ra, double Pr, double Ma,
+                           int wall_type, const dmrt_opts *opts);
+
+/* Create from lattice parameters directly: viscosity nu > 0, diffusivity
+ * alpha > 0 and buoyancy g*beta*dT (any finite value; 0 decouples the flow
+ * from the temperature).  Same start state as dmrt_create. */
+dmrt_status dmrt_create_lattice(dmrt_t **out, const int grid[3], double nu, double alpha,
+                                double gbeta, int wall_type, const dmrt_opts *opts);
+
+/* Free every resource of the handle (NULL is a no-op).  Synchronises. */
+void dmrt_destroy(dmrt_t *h);
+
+/* Use this CUDA stream (a cudaStream_t; NULL = the handle's own stream) for
+ * all later work.  The caller keeps the stream alive while it is set. */
+dmrt_status dmrt_set_stream(dmrt_t *h, void *stream);
+
+/* Advance n >= 0 time steps (Eqs. (14), (19), (29)): each step is one fused
+ * kernel that, for every cell, pulls the D3Q19 and D3Q7 populations from its
+ * neighbours (bounce-back / anti-bounce-back at walls), collides them in
+ * moment space, adds the buoyancy force and stores them.  After every K-th
+ * step (K = residual_interval) the convergence residual is computed on the
+ * device.  Asynchronous: returns once the work is queued. */
+dmrt_status dmrt_step(dmrt_t *h, long n);
+
+/* Wait for the handle's queued work; reports deferred CUDA errors. */
+dmrt_status dmrt_sync(dmrt_t *h);
+
+/* Fields at the current step: the moments of the pulled (pre-collision)
+ * populations, Eqs. (20),(30): rho, u = j/rho ([3][z][y][x]) and theta.
+ * Any pointer may be NULL to skip that field.  Synchronises. */
+dmrt_status dmrt_fields(dmrt_t *h, float *rho, float *u, float *theta, int on_device);
+
+/* Nusselt numbers on wall 0 (hot, y = 0) or 1 (cold, y = H), Eqs. (39)-(41):
+ * out[0] = Nu_3D (mean over the wall), out[1] = Nu_2D (mean over z at
+ * X = 1/2: the two centre x columns for even nx, the centre one for odd nx),
+ * out[2] = Nu_max.  The local Nu uses the second-order one-sided difference
+ * (-8 theta_w + 9 theta_1 - theta_2)/3 with cells 1/2 and 3/2 from the wall;
+ * sums are accumulated in FP64 in a fixed order.  `out` is host memory.
+ * Requires ny >= 2.  Synchronises. */
+dmrt_status dmrt_nusselt(dmrt_t *h, int wall, double out[3]);
+
+/* The local Nusselt number of wall 0 or 1 as a float32 [z][x] map. */
+dmrt_status dmrt_nusselt_local(dmrt_t *h, int wall, float *local, int on_device);
+
+/* The convergence residual from the last two residual points (K steps
+ * apart): r = max(|theta^n - theta^{n-K}|_2 / |theta^n|_2,
+ * |u^n - u^{n-K}|_2 / |u^n|_2) / K, in FP64.  +inf until two points exist.
+ * Returns DMRT_ERR_DIVERGED if the fields hold a NaN or Inf.  Synchronises. */
+dmrt_status dmrt_residual(dmrt_t *h, double *r);
+
+/* Step until the residual falls below tol or max_steps more steps are taken
+ * (then DMRT_ERR_TIMEOUT).  *steps_taken and *r (either may be NULL) receive
+ * the steps run by this call and the last residual. */
+dmrt_status dmrt_run_to_steady(dmrt_t *h, double tol, long max_steps, long *steps_taken,
+                               double *r);
+
+/* Replace the stored (post-collision) populations: f is [19][z][y][x], g is
+ * [7][z][y][x], float32.  Resets the residual history. */
+dmrt_status dmrt_set_populations(dmrt_t *h, const float *f, const float *g, int on_device);
+
+/* Copy out the stored populations in the layout of dmrt_set_populations.
+ * Either pointer may be NULL.  Synchronises. */
+dmrt_status dmrt_get_populations(dmrt_t *h, float *f, float *g, int on_device);
+
+/* Set the state to the equilibrium of given fields: f = f_eq(rho, u) of
+ * Eq. (17), g = w_T theta (1 + 4 e.u), the D3Q7 equilibrium of Eq. (33).
+ * Resets the residual history (used for warm starts). */
+dmrt_status dmrt_init_fields(dmrt_t *h, const float *rho, const float *u, const float *theta,
+                             int on_device);
+
+/* Read the derived lattice parameters. */
+dmrt_status dmrt_get_params(const dmrt_t *h, dmrt_params *out);
+
+/* Enable (1) or disable (0) CUDA-event timing of the step kernels. */
+dmrt_status dmrt_set_timing(dmrt_t *h, int enabled);
+
+/* Read the launch counters and the event timing (synchronises when timing
+ * is on).  reset = 1 zeroes them afterwards. */
+dmrt_status dmrt_get_stats(dmrt_t *h, dmrt_stats *out, int reset);
+
+/* Text of the last error on this handle ("" if none; static if h is NULL). */
+const char *dmrt_last_error(const dmrt_t *h);
+
+/* Name of a status code. */
+const char *dmrt_status_string(int status);
+
+/* Library version string. */
+const char *dmrt_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DMRT_H */

@@ -1,0 +1,639 @@
+// api.cu -- host implementation of the C ABI declared in include/dmrt.h.
+//
+// The handle owns two population buffers (A-B ping-pong, 26 planes each), the
+// residual snapshot and the reduction scratch.  Every entry point validates
+// its arguments, queues work on the handle's stream and converts CUDA errors
+// into a dmrt_status plus a message; nothing throws across the ABI.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "dmrt.h"
+#include "internal.h"
+
+using lbm::CollideParams;
+using lbm::Geometry;
+
+struct dmrt {
+    int device = 0;
+    int wall = 1;
+    int storage = DMRT_STORE_F32;
+    int K = 100;
+    double nu = 0, alpha = 0, gbeta = 0;
+    Geometry G{};
+    CollideParams C{};
+    lbm::BlockShape block{32, 4};
+
+    float *buf[2] = {nullptr, nullptr};  // ping-pong population buffers
+    int cur = 0;                          // buffer holding the current state
+    float *snap = nullptr;                // residual snapshot: theta, u (4 planes)
+    double *partials = nullptr;           // reduction scratch
+    size_t npartials = 0;
+    double *dres = nullptr;               // residual result (8 doubles)
+    double *dnu = nullptr;                // Nusselt result (3 doubles)
+    float *staging = nullptr;             // device staging for host transfers
+    size_t staging_floats = 0;
+
+    cudaStream_t own = nullptr;
+    cudaStream_t stream = nullptr;
+
+    long steps = 0;
+    int snaps = 0;  // residual points taken since the last reset (capped at 2)
+
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
+    std::vector<long> ev_counts;
+    long step_launches = 0, total_launches = 0, timed_steps = 0;
+    double step_ms = 0.0;
+
+    std::string err;
+};
+
+namespace {
+
+const char *kStatusNames[] = {"DMRT_OK", "DMRT_ERR_ARG", "DMRT_ERR_CUDA", "DMRT_ERR_OOM",
+                              "DMRT_ERR_DIVERGED", "DMRT_ERR_TIMEOUT"};
+
+dmrt_status fail(dmrt_t *h, dmrt_status st, const char *fmt, ...)
+    __attribute__((format(printf, 3, 4)));
+
+dmrt_status fail(dmrt_t *h, dmrt_status st, const char *fmt, ...)
+{
+    if (h) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        h->err = buf;
+    }
+    return st;
+}
+
+dmrt_status cuda_fail(dmrt_t *h, cudaError_t e, const char *what)
+{
+    return fail(h, e == cudaErrorMemoryAllocation ? DMRT_ERR_OOM : DMRT_ERR_CUDA, "%s: %s (%s)",
+                what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+#define CK(h, call, what)                                   \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return cuda_fail(h, e_, what); \
+    } while (0)
+
+// Keeps the handle's device current for the duration of a call.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+long long cell_count(const Geometry &G)
+{
+    return static_cast<long long>(G.nx) * G.ny * G.nz;
+}
+
+// Relaxation rates of Eq. (26) (flow) and Eqs. (35),(36) (energy), folded with
+// the squared norms of the moment basis.
+void fill_rates(dmrt_t *h)
+{
+    const double s_nu = 1.0 / (3.0 * h->nu + 0.5);
+    double s[19];
+    for (int k = 0; k < 19; ++k) s[k] = 1.0;
+    s[1] = 1.19;
+    s[2] = s[10] = s[12] = 1.4;
+    s[4] = s[6] = s[8] = 1.2;
+    s[16] = s[17] = s[18] = 1.98;
+    s[9] = s[11] = s[13] = s[14] = s[15] = s_nu;
+    for (int k = 0; k < 19; ++k) h->C.rs[k] = static_cast<float>(s[k] / lbm::m19_norm2(k));
+    const double tau_a = 0.5 + 4.0 * h->alpha;  // eps = 1/4, dt = dx = 1
+    double q[7] = {1.0, 1.0 / tau_a, 1.0 / tau_a, 1.0 / tau_a, 1.0, 1.0, 1.0};
+    for (int k = 0; k < 7; ++k) h->C.rq[k] = static_cast<float>(q[k] / lbm::m7_norm2(k));
+    h->C.gbeta = static_cast<float>(h->gbeta);
+    h->C.theta_ref = 0.0f;  // T_l = (T_h + T_c)/2
+}
+
+dmrt_status ensure_staging(dmrt_t *h, size_t floats)
+{
+    if (h->staging_floats >= floats) return DMRT_OK;
+    if (h->staging) cudaFree(h->staging);
+    h->staging = nullptr;
+    h->staging_floats = 0;
+    CK(h, cudaMalloc(&h->staging, floats * sizeof(float)), "cudaMalloc(staging)");
+    h->staging_floats = floats;
+    return DMRT_OK;
+}
+
+cudaEvent_t take_event(dmrt_t *h)
+{
+    if (!h->ev_pool.empty()) {
+        cudaEvent_t e = h->ev_pool.back();
+        h->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+dmrt_status collect_timing(dmrt_t *h)
+{
+    for (size_t k = 0; k < h->ev_pending.size(); ++k) {
+        auto &p = h->ev_pending[k];
+        CK(h, cudaEventSynchronize(p.second), "cudaEventSynchronize");
+        float ms = 0.f;
+        CK(h, cudaEventElapsedTime(&ms, p.first, p.second), "cudaEventElapsedTime");
+        h->step_ms += ms;
+        h->timed_steps += h->ev_counts[k];
+        h->ev_pool.push_back(p.first);
+        h->ev_pool.push_back(p.second);
+    }
+    h->ev_pending.clear();
+    h->ev_counts.clear();
+    return DMRT_OK;
+}
+
+dmrt_status run_residual(dmrt_t *h)
+{
+    CK(h,
+       lbm::launch_residual(h->wall, h->buf[h->cur], h->G, h->snap, h->snaps > 0 ? 1 : 0, h->K,
+                             h->partials, h->dres, h->stream),
+       "residual kernel");
+    h->total_launches += 2;
+    if (h->snaps < 2) h->snaps++;
+    return DMRT_OK;
+}
+
+// Launch n fused steps, taking a residual point after every K-th step.
+dmrt_status run_steps(dmrt_t *h, long n)
+{
+    long done = 0;
+    while (done < n) {
+        long until_res = h->K - (h->steps % h->K);
+        long chunk = std::min(n - done, until_res);
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (h->timing) {
+            e0 = take_event(h);
+            e1 = take_event(h);
+            if (!e0 || !e1) return fail(h, DMRT_ERR_CUDA, "cudaEventCreate failed");
+            CK(h, cudaEventRecord(e0, h->stream), "cudaEventRecord");
+        }
+        for (long s = 0; s < chunk; ++s) {
+            float *src = h->buf[h->cur];
+            float *dst = h->buf[h->cur ^ 1];
+            CK(h, lbm::launch_step(h->wall, src, dst, h->G, h->C, h->block, h->stream),
+               "step kernel");
+            h->cur ^= 1;
+            h->steps++;
+            h->step_launches++;
+            h->total_launches++;
+        }
+        if (h->timing) {
+            CK(h, cudaEventRecord(e1, h->stream), "cudaEventRecord");
+            h->ev_pending.emplace_back(e0, e1);
+            h->ev_counts.push_back(chunk);
+        }
+        done += chunk;
+        if (h->steps % h->K == 0) {
+            dmrt_status st = run_residual(h);
+            if (st != DMRT_OK) return st;
+        }
+    }
+    return DMRT_OK;
+}
+
+dmrt_status create_common(dmrt_t **out, const int grid[3], double nu, double alpha, double gbeta,
+                          int wall_type, const dmrt_opts *opts)
+{
+    if (!out) return DMRT_ERR_ARG;
+    *out = nullptr;
+    if (!grid) return DMRT_ERR_ARG;
+    if (wall_type < 0 || wall_type > 3) return DMRT_ERR_ARG;
+    const int minext = wall_type == DMRT_WALL_PERIODIC ? 1 : 2;
+    for (int a = 0; a < 3; ++a)
+        if (grid[a] < minext || grid[a] > 65535) return DMRT_ERR_ARG;
+    const long long cells = static_cast<long long>(grid[0]) * grid[1] * grid[2];
+    if (cells >= (1LL << 31)) return DMRT_ERR_ARG;
+    if (!(nu > 0.0) || !(alpha > 0.0) || !std::isfinite(nu) || !std::isfinite(alpha) ||
+        !std::isfinite(gbeta))
+        return DMRT_ERR_ARG;
+    int storage = DMRT_STORE_F32, K = 100;
+    if (opts) {
+        storage = opts->storage;
+        if (opts->residual_interval > 0) K = opts->residual_interval;
+        if (opts->residual_interval < 0) return DMRT_ERR_ARG;
+    }
+    if (storage != DMRT_STORE_F32) return DMRT_ERR_ARG;
+
+    dmrt_t *h = new (std::nothrow) dmrt();
+    if (!h) return DMRT_ERR_OOM;
+    if (cudaGetDevice(&h->device) != cudaSuccess) {
+        delete h;
+        return DMRT_ERR_CUDA;
+    }
+    h->wall = wall_type;
+    h->storage = storage;
+    h->K = K;
+    h->nu = nu;
+    h->alpha = alpha;
+    h->gbeta = gbeta;
+    h->G.nx = grid[0];
+    h->G.ny = grid[1];
+    h->G.nz = grid[2];
+    h->G.pad = 0;
+    // pad each plane to a whole number of 128-byte lines (and 256-byte
+    // alignment of every plane start)
+    h->G.plane = (cells + 63) / 64 * 64;
+    h->G.inv_ny = 1.0f / static_cast<float>(grid[1]);
+    fill_rates(h);
+    if (grid[0] >= 128) h->block = {128, 1};
+    else if (grid[0] >= 64) h->block = {64, 2};
+    else h->block = {32, 4};
+
+    auto bail = [&](dmrt_status st) {
+        dmrt_destroy(h);
+        return st;
+    };
+    cudaError_t e;
+    const size_t buf_bytes = static_cast<size_t>(h->G.plane) * lbm::kPlanes * sizeof(float);
+    for (int b = 0; b < 2; ++b) {
+        e = cudaMalloc(&h->buf[b], buf_bytes);
+        if (e != cudaSuccess) return bail(e == cudaErrorMemoryAllocation ? DMRT_ERR_OOM : DMRT_ERR_CUDA);
+    }
+    e = cudaMalloc(&h->snap, static_cast<size_t>(cells) * 4 * sizeof(float));
+    if (e != cudaSuccess) return bail(DMRT_ERR_OOM);
+    h->npartials = lbm::residual_partials(h->G) * 4;
+    if (h->npartials < 3 * static_cast<size_t>(grid[2])) h->npartials = 3 * grid[2];
+    e = cudaMalloc(&h->partials, h->npartials * sizeof(double));
+    if (e != cudaSuccess) return bail(DMRT_ERR_OOM);
+    e = cudaMalloc(&h->dres, 16 * sizeof(double));
+    if (e != cudaSuccess) return bail(DMRT_ERR_OOM);
+    h->dnu = h->dres + 8;
+    e = cudaStreamCreateWithFlags(&h->own, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return bail(DMRT_ERR_CUDA);
+    h->stream = h->own;
+    // start from rest: f = w (zero deviations), g = 0 (theta = 0)
+    e = cudaMemsetAsync(h->buf[0], 0, buf_bytes, h->stream);
+    if (e != cudaSuccess) return bail(DMRT_ERR_CUDA);
+    e = cudaMemsetAsync(h->buf[1], 0, buf_bytes, h->stream);
+    if (e != cudaSuccess) return bail(DMRT_ERR_CUDA);
+    e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return bail(DMRT_ERR_CUDA);
+    *out = h;
+    return DMRT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+dmrt_status dmrt_create(dmrt_t **out, const int grid[3], double Ra, double Pr, double Ma,
+                        int wall_type)
+{
+    return dmrt_create_ex(out, grid, Ra, Pr, Ma, wall_type, nullptr);
+}
+
+dmrt_status dmrt_create_ex(dmrt_t **out, const int grid[3], double Ra, double Pr, double Ma,
+                           int wall_type, const dmrt_opts *opts)
+{
+    if (out) *out = nullptr;
+    if (!grid || !(Ra > 0.0) || !(Pr > 0.0) || !(Ma > 0.0) || !(Ma < 0.3) || !std::isfinite(Ra) ||
+        !std::isfinite(Pr))
+        return DMRT_ERR_ARG;
+    if (grid[1] < 2) return DMRT_ERR_ARG;
+    // Eq. (38) with H = ny, dT = 1, c = 1: Ma = u_c / c_s, u_c^2 = g beta dT H,
+    // Ra = g beta dT H^3 Pr / nu^2, Pr = nu / alpha.
+    const double H = static_cast<double>(grid[1]);
+    const double uc = Ma / std::sqrt(3.0);
+    const double gbeta = uc * uc / H;
+    const double nu = uc * H * std::sqrt(Pr / Ra);
+    const double alpha = nu / Pr;
+    return create_common(out, grid, nu, alpha, gbeta, wall_type, opts);
+}
+
+dmrt_status dmrt_create_lattice(dmrt_t **out, const int grid[3], double nu, double alpha,
+                                double gbeta, int wall_type, const dmrt_opts *opts)
+{
+    return create_common(out, grid, nu, alpha, gbeta, wall_type, opts);
+}
+
+void dmrt_destroy(dmrt_t *h)
+{
+    if (!h) return;
+    DeviceGuard dg(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    for (auto &p : h->ev_pending) {
+        cudaEventDestroy(p.first);
+        cudaEventDestroy(p.second);
+    }
+    for (auto e : h->ev_pool) cudaEventDestroy(e);
+    for (int b = 0; b < 2; ++b)
+        if (h->buf[b]) cudaFree(h->buf[b]);
+    if (h->snap) cudaFree(h->snap);
+    if (h->partials) cudaFree(h->partials);
+    if (h->dres) cudaFree(h->dres);
+    if (h->staging) cudaFree(h->staging);
+    if (h->own) cudaStreamDestroy(h->own);
+    delete h;
+}
+
+dmrt_status dmrt_set_stream(dmrt_t *h, void *stream)
+{
+    if (!h) return DMRT_ERR_ARG;
+    DeviceGuard dg(h->device);
+    // order the new stream after everything queued so far
+    CK(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    h->stream = stream ? static_cast<cudaStream_t>(stream) : h->own;
+    return DMRT_OK;
+}
+
+dmrt_status dmrt_step(dmrt_t *h, long n)
+{
+    if (!h) return DMRT_ERR_ARG;
+    if (n < 0) return fail(h, DMRT_ERR_ARG, "dmrt_step: n = %ld < 0", n);
+    DeviceGuard dg(h->device);
+    return run_steps(h, n);
+}
+
+dmrt_status dmrt_sync(dmrt_t *h)
+{
+    if (!h) return DMRT_ERR_ARG;
+    DeviceGuard dg(h->device);
+    CK(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    return DMRT_OK;
+}
+
+dmrt_status dmrt_fields(dmrt_t *h, float *rho, float *u, float *theta, int on_device)
+{
+    if (!h) return DMRT_ERR_ARG;
+    DeviceGuard dg(h->device);
+    const size_t cells = static_cast<size_t>(cell_count(h->G));
+    float *drho = rho, *du = u, *dth = theta;
+    if (!on_device) {
+        dmrt_status st = ensure_staging(h, 5 * cells);
+        if (st != DMRT_OK) return st;
+        drho = rho ? h->staging : nullptr;
+        du = u ? h->staging + cells : nullptr;
+        dth = theta ? h->staging + 4 * cells : nullptr;
+    }
+    CK(h, lbm::launch_fields(h->wall, h->buf[h->cur], h->G, drho, du, dth, h->stream),
+       "fields kernel");
+    h->total_launches++;
+    if (!on_device) {
+        if (rho)
+            CK(h, cudaMemcpyAsync(rho, drho, cells * sizeof(float), cudaMemcpyDeviceToHost, h->stream),
+               "copy rho");
+        if (u)
+            CK(h, cudaMemcpyAsync(u, du, 3 * cells * sizeof(float), cudaMemcpyDeviceToHost, h->stream),
+               "copy u");
+        if (theta)
+            CK(h, cudaMemcpyAsync(theta, dth, cells * sizeof(float), cudaMemcpyDeviceToHost, h->stream),
+               "copy theta");
+    }
+    CK(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    return DMRT_OK;
+}
+
+dmrt_status dmrt_nusselt(dmrt_t *h, int wall, double out[3])
+{
+    if (!h || !out) return DMRT_ERR_ARG;
+    if (wall != 0 && wall != 1) return fail(h, DMRT_ERR_ARG, "dmrt_nusselt: wall must be 0 or 1");
+    if (h->G.ny < 2) return fail(h, DMRT_ERR_ARG, "dmrt_nusselt: needs ny >= 2");
+    DeviceGuard dg(h->device);
+    CK(h,
+       lbm::launch_nusselt(h->wall, h->buf[h->cur], h->G, wall, nullptr, h->partials, h->dnu,
+                            h->stream),
+       "nusselt kernel");
+    h->total_launches += 2;
+    CK(h, cudaMemcpyAsync(out, h->dnu, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream),
+       "copy nusselt");
+    CK(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    return DMRT_OK;
+}
+
+dmrt_status dmrt_nusselt_local(dmrt_t *h, int wall, float *local, int on_device)
+{
+    if (!h || !local) return DMRT_ERR_ARG;
+    if (wall != 0 && wall != 1) return fail(h, DMRT_ERR_ARG, "dmrt_nusselt_local: wall must be 0 or 1");
+    if (h->G.ny < 2) return fail(h, DMRT_ERR_ARG, "dmrt_nusselt_local: needs ny >= 2");
+    DeviceGuard dg(h->device);
+    const size_t n = static_cast<size_t>(h->G.nx) * h->G.nz;
+    float *dst = local;
+    if (!on_device) {
+        dmrt_status st = ensure_staging(h, n);
+        if (st != DMRT_OK) return st;
+        dst = h->staging;
+    }
+    CK(h,
+       lbm::launch_nusselt(h->wall, h->buf[h->cur], h->G, wall, dst, h->partials, h->dnu,
+                            h->stream),
+       "nusselt kernel");
+    h->total_launches += 2;
+    if (!on_device)
+        CK(h, cudaMemcpyAsync(local, dst, n * sizeof(float), cudaMemcpyDeviceToHost, h->stream),
+           "copy local nusselt");
+    CK(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    return DMRT_OK;
+}
+
+dmrt_status dmrt_residual(dmrt_t *h, double *r)
+{
+    if (!h || !r) return DMRT_ERR_ARG;
+    DeviceGuard dg(h->device);
+    if (h->snaps < 2) {
+        *r = INFINITY;
+        return DMRT_OK;
+    }
+    double res[8];
+    CK(h, cudaMemcpyAsync(res, h->dres, sizeof res, cudaMemcpyDeviceToHost, h->stream),
+       "copy residual");
+    CK(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    *r = res[4];
+    if (res[5] != 0.0 || !std::isfinite(res[4]))
+        return fail(h, DMRT_ERR_DIVERGED, "non-finite fields at step %ld", h->steps);
+    return DMRT_OK;
+}
+
+dmrt_status dmrt_run_to_steady(dmrt_t *h, double tol, long max_steps, long *steps_taken,
+                               double *r)
+{
+    if (!h || !(tol > 0.0) || max_steps < 0) return DMRT_ERR_ARG;
+    DeviceGuard dg(h->device);
+    long taken = 0;
+    double res = INFINITY;
+    dmrt_status st = DMRT_OK;
+    while (true) {
+        if (h->snaps >= 2) {
+            st = dmrt_residual(h, &res);
+            if (st != DMRT_OK) break;
+            if (res < tol) break;
+        }
+        if (taken >= max_steps) {
+            st = fail(h, DMRT_ERR_TIMEOUT, "no convergence to %g within %ld steps (r = %g)", tol,
+                      max_steps, res);
+            break;
+        }
+        long chunk = h->K - (h->steps % h->K);
+        if (chunk > max_steps - taken) chunk = max_steps - taken;
+        st = run_steps(h, chunk);
+        if (st != DMRT_OK) break;
+        taken += chunk;
+    }
+    if (steps_taken) *steps_taken = taken;
+    if (r) *r = res;
+    return st;
+}
+
+dmrt_status dmrt_set_populations(dmrt_t *h, const float *f, const float *g, int on_device)
+{
+    if (!h || !f || !g) return DMRT_ERR_ARG;
+    DeviceGuard dg(h->device);
+    const size_t cells = static_cast<size_t>(cell_count(h->G));
+    const float *df = f, *dg_ = g;
+    if (!on_device) {
+        dmrt_status st = ensure_staging(h, 26 * cells);
+        if (st != DMRT_OK) return st;
+        CK(h, cudaMemcpyAsync(h->staging, f, 19 * cells * sizeof(float), cudaMemcpyHostToDevice, h->stream),
+           "copy f");
+        CK(h, cudaMemcpyAsync(h->staging + 19 * cells, g, 7 * cells * sizeof(float),
+                              cudaMemcpyHostToDevice, h->stream),
+           "copy g");
+        df = h->staging;
+        dg_ = h->staging + 19 * cells;
+    }
+    CK(h, lbm::launch_set_populations(df, dg_, h->buf[h->cur], h->G, h->stream), "set kernel");
+    h->total_launches++;
+    h->snaps = 0;
+    CK(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    return DMRT_OK;
+}
+
+dmrt_status dmrt_get_populations(dmrt_t *h, float *f, float *g, int on_device)
+{
+    if (!h) return DMRT_ERR_ARG;
+    if (!f && !g) return DMRT_OK;
+    DeviceGuard dg(h->device);
+    const size_t cells = static_cast<size_t>(cell_count(h->G));
+    float *df = f, *dg_ = g;
+    if (!on_device) {
+        dmrt_status st = ensure_staging(h, 26 * cells);
+        if (st != DMRT_OK) return st;
+        df = f ? h->staging : nullptr;
+        dg_ = g ? h->staging + 19 * cells : nullptr;
+    }
+    CK(h, lbm::launch_get_populations(h->buf[h->cur], df, dg_, h->G, h->stream), "get kernel");
+    h->total_launches++;
+    if (!on_device) {
+        if (f)
+            CK(h, cudaMemcpyAsync(f, df, 19 * cells * sizeof(float), cudaMemcpyDeviceToHost, h->stream),
+               "copy f");
+        if (g)
+            CK(h, cudaMemcpyAsync(g, dg_, 7 * cells * sizeof(float), cudaMemcpyDeviceToHost, h->stream),
+               "copy g");
+    }
+    CK(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    return DMRT_OK;
+}
+
+dmrt_status dmrt_init_fields(dmrt_t *h, const float *rho, const float *u, const float *theta,
+                             int on_device)
+{
+    if (!h || !rho || !u || !theta) return DMRT_ERR_ARG;
+    DeviceGuard dg(h->device);
+    const size_t cells = static_cast<size_t>(cell_count(h->G));
+    const float *dr = rho, *du = u, *dt = theta;
+    if (!on_device) {
+        dmrt_status st = ensure_staging(h, 5 * cells);
+        if (st != DMRT_OK) return st;
+        CK(h, cudaMemcpyAsync(h->staging, rho, cells * sizeof(float), cudaMemcpyHostToDevice, h->stream),
+           "copy rho");
+        CK(h, cudaMemcpyAsync(h->staging + cells, u, 3 * cells * sizeof(float), cudaMemcpyHostToDevice,
+                              h->stream),
+           "copy u");
+        CK(h, cudaMemcpyAsync(h->staging + 4 * cells, theta, cells * sizeof(float),
+                              cudaMemcpyHostToDevice, h->stream),
+           "copy theta");
+        dr = h->staging;
+        du = h->staging + cells;
+        dt = h->staging + 4 * cells;
+    }
+    CK(h, lbm::launch_init_fields(dr, du, dt, h->buf[h->cur], h->G, h->stream), "init kernel");
+    h->total_launches++;
+    h->snaps = 0;
+    if (!on_device) CK(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    return DMRT_OK;
+}
+
+dmrt_status dmrt_get_params(const dmrt_t *h, dmrt_params *out)
+{
+    if (!h || !out) return DMRT_ERR_ARG;
+    out->nx = h->G.nx;
+    out->ny = h->G.ny;
+    out->nz = h->G.nz;
+    out->wall_type = h->wall;
+    out->storage = h->storage;
+    out->residual_interval = h->K;
+    out->nu = h->nu;
+    out->alpha = h->alpha;
+    out->gbeta = h->gbeta;
+    out->tau_nu = 3.0 * h->nu + 0.5;
+    out->tau_alpha = 0.5 + 4.0 * h->alpha;
+    out->steps = h->steps;
+    return DMRT_OK;
+}
+
+dmrt_status dmrt_set_timing(dmrt_t *h, int enabled)
+{
+    if (!h) return DMRT_ERR_ARG;
+    h->timing = enabled != 0;
+    return DMRT_OK;
+}
+
+dmrt_status dmrt_get_stats(dmrt_t *h, dmrt_stats *out, int reset)
+{
+    if (!h || !out) return DMRT_ERR_ARG;
+    DeviceGuard dg(h->device);
+    dmrt_status st = collect_timing(h);
+    if (st != DMRT_OK) return st;
+    out->step_launches = h->step_launches;
+    out->total_launches = h->total_launches;
+    out->step_ms = h->step_ms;
+    out->timed_steps = h->timed_steps;
+    out->bytes_per_cell = 2.0 * lbm::kPlanes * sizeof(float);
+    if (reset) {
+        h->step_launches = h->total_launches = h->timed_steps = 0;
+        h->step_ms = 0.0;
+    }
+    return DMRT_OK;
+}
+
+const char *dmrt_last_error(const dmrt_t *h)
+{
+    if (!h) return "null handle";
+    return h->err.c_str();
+}
+
+const char *dmrt_status_string(int status)
+{
+    if (status < 0 || status > DMRT_ERR_TIMEOUT) return "DMRT_UNKNOWN";
+    return kStatusNames[status];
+}
+
+const char *dmrt_version(void) { return "dmrt-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

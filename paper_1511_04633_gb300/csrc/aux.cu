@@ -1,0 +1,376 @@
+// aux.cu -- the non-step kernels: fields of the pulled populations
+// (Eqs. (20), (30)), the convergence residual, the Nusselt numbers
+// (Eqs. (39)-(41)) and population / field import-export.
+//
+// Reductions are deterministic: each block reduces its cells in a fixed
+// warp-shuffle tree into an FP64 partial, and one finishing block sums the
+// partials in index order.  No floating-point atomics are used.
+#include <cmath>
+
+#include "internal.h"
+
+namespace lbm {
+
+namespace {
+
+constexpr int kRedThreads = 256;  // threads of the per-cell reduction blocks
+constexpr int kFinThreads = 512;  // threads of the finishing blocks
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double warp_max(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Block-wide sum of N values per thread (fixed order).  Every thread of the
+// block (THREADS of them, 1-D or 2-D, a multiple of 32) must call it; the
+// thread with linear index 0 receives the totals.
+template <int N, int THREADS>
+__device__ __forceinline__ void block_sum(double (&v)[N])
+{
+    __shared__ double sh[THREADS / 32][N];
+    const int t = threadIdx.y * blockDim.x + threadIdx.x;
+    const int lane = t & 31, warp = t >> 5;
+#pragma unroll
+    for (int k = 0; k < N; ++k) v[k] = warp_sum(v[k]);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < N; ++k) sh[warp][k] = v[k];
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            double w = (lane < THREADS / 32) ? sh[lane][k] : 0.0;
+            v[k] = warp_sum(w);
+        }
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------- fields
+
+template <int WALL>
+__global__ void fields_kernel(const float *__restrict__ src, const Geometry G, float *rho,
+                              float *u, float *theta)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= G.nx || y >= G.ny) return;
+    float d[19], g[7];
+    pull_f<WALL>(src, G, x, y, z, d);
+    pull_g<WALL>(src, G, x, y, z, g);
+    const Macro m = macro_of(d, g);
+    const float r = 1.0f + m.drho;
+    const long long c = (static_cast<long long>(z) * G.ny + y) * G.nx + x;
+    const long long cells = static_cast<long long>(G.nx) * G.ny * G.nz;
+    if (rho) rho[c] = r;
+    if (u) {
+        u[c] = m.jx / r;
+        u[cells + c] = m.jy / r;
+        u[2 * cells + c] = m.jz / r;
+    }
+    if (theta) theta[c] = m.T;
+}
+
+// ---------------------------------------------------------------- residual
+
+// Per block: sums of |dtheta|^2, |theta|^2, |du|^2, |u|^2 against the
+// snapshot, which is then overwritten with the current fields.
+template <int WALL>
+__global__ void __launch_bounds__(kRedThreads) residual_kernel(
+    const float *__restrict__ src, const Geometry G, float *__restrict__ snap, int have_prev,
+    double *__restrict__ partials)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    if (x < G.nx && y < G.ny) {
+        float d[19], g[7];
+        pull_f<WALL>(src, G, x, y, z, d);
+        pull_g<WALL>(src, G, x, y, z, g);
+        const Macro m = macro_of(d, g);
+        const float r = 1.0f + m.drho;
+        const float now[4] = {m.T, m.jx / r, m.jy / r, m.jz / r};
+        const long long c = (static_cast<long long>(z) * G.ny + y) * G.nx + x;
+        const long long cells = static_cast<long long>(G.nx) * G.ny * G.nz;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float prev = snap[k * cells + c];
+            const double dk = have_prev ? static_cast<double>(now[k]) - prev : 0.0;
+            const int slot = (k == 0) ? 0 : 2;
+            v[slot] += dk * dk;
+            v[slot + 1] += static_cast<double>(now[k]) * now[k];
+            snap[k * cells + c] = now[k];
+        }
+    }
+    block_sum<4, kRedThreads>(v);
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        const long long b = (static_cast<long long>(blockIdx.z) * gridDim.y + blockIdx.y) *
+                                gridDim.x + blockIdx.x;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) partials[b * 4 + k] = v[k];
+    }
+}
+
+__device__ double rel_change(double num2, double den2)
+{
+    if (den2 == 0.0) return num2 == 0.0 ? 0.0 : INFINITY;
+    return sqrt(num2) / sqrt(den2);
+}
+
+__global__ void __launch_bounds__(kFinThreads) residual_finish(const double *__restrict__ partials,
+                                                                 long long nparts, int have_prev,
+                                                                 int K, double *result)
+{
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    for (long long p = threadIdx.x; p < nparts; p += kFinThreads)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[k] += partials[p * 4 + k];
+    block_sum<4, kFinThreads>(v);
+    if (threadIdx.x == 0) {
+        bool finite = true;
+        for (int k = 0; k < 4; ++k) {
+            result[k] = v[k];
+            finite = finite && isfinite(v[k]);
+        }
+        double r = have_prev ? fmax(rel_change(v[0], v[1]), rel_change(v[2], v[3])) / K : INFINITY;
+        result[4] = finite ? r : NAN;
+        result[5] = finite ? 0.0 : 1.0;
+    }
+}
+
+// ---------------------------------------------------------------- Nusselt
+
+// One block per z row: the local Nu of every wall cell of that row, from the
+// pulled temperatures 1/2 and 3/2 cells off the wall (Eq. (39)).
+template <int WALL>
+__global__ void __launch_bounds__(kRedThreads) nusselt_kernel(const float *__restrict__ src,
+                                                               const Geometry G, int wall,
+                                                               float *local,
+                                                               double *__restrict__ partials)
+{
+    const int z = blockIdx.x;
+    const int y1 = wall == 0 ? 0 : G.ny - 1;
+    const int y2 = wall == 0 ? 1 : G.ny - 2;
+    const double th_w = wall == 0 ? 0.5 : -0.5;
+    const double H = static_cast<double>(G.ny);
+    const int c_lo = (G.nx % 2 == 0) ? G.nx / 2 - 1 : (G.nx - 1) / 2;
+    const int c_hi = (G.nx % 2 == 0) ? G.nx / 2 : (G.nx - 1) / 2;
+    double v[2] = {0.0, 0.0};
+    double mx = -INFINITY;
+    for (int x = threadIdx.x; x < G.nx; x += blockDim.x) {
+        float g[7];
+        pull_g<WALL>(src, G, x, y1, z, g);
+        float t1 = 0.f;
+#pragma unroll
+        for (int i = 0; i < 7; ++i) t1 += g[i];
+        pull_g<WALL>(src, G, x, y2, z, g);
+        float t2 = 0.f;
+#pragma unroll
+        for (int i = 0; i < 7; ++i) t2 += g[i];
+        const double dth_ds = (-8.0 * th_w + 9.0 * t1 - static_cast<double>(t2)) / 3.0;
+        const double nu = wall == 0 ? -H * dth_ds : H * dth_ds;
+        if (local) local[static_cast<long long>(z) * G.nx + x] = static_cast<float>(nu);
+        v[0] += nu;
+        if (x == c_lo || x == c_hi) v[1] += nu;
+        mx = fmax(mx, nu);
+    }
+    __shared__ double shm[kRedThreads / 32];
+    mx = warp_max(mx);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) shm[warp] = mx;
+    block_sum<2, kRedThreads>(v);
+    if (threadIdx.x == 0) {
+        double m = shm[0];
+        for (int w = 1; w < kRedThreads / 32; ++w) m = fmax(m, shm[w]);
+        partials[z * 3 + 0] = v[0];
+        partials[z * 3 + 1] = v[1];
+        partials[z * 3 + 2] = m;
+    }
+}
+
+__global__ void nusselt_finish(const double *__restrict__ partials, const Geometry G,
+                               double *out3)
+{
+    if (threadIdx.x != 0) return;
+    double s = 0.0, mid = 0.0, mx = -INFINITY;
+    for (int z = 0; z < G.nz; ++z) {
+        s += partials[z * 3 + 0];
+        mid += partials[z * 3 + 1];
+        mx = fmax(mx, partials[z * 3 + 2]);
+    }
+    const int ncol = (G.nx % 2 == 0) ? 2 : 1;
+    out3[0] = s / (static_cast<double>(G.nx) * G.nz);
+    out3[1] = mid / (static_cast<double>(G.nz) * ncol);
+    out3[2] = mx;
+}
+
+// ---------------------------------------------------------------- import / export
+
+__global__ void set_populations_kernel(const float *__restrict__ f, const float *__restrict__ g,
+                                       float *__restrict__ dst, const Geometry G)
+{
+    const long long cells = static_cast<long long>(G.nx) * G.ny * G.nz;
+    for (long long c = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; c < cells;
+         c += static_cast<long long>(gridDim.x) * blockDim.x) {
+        static_for<0, 19>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            dst[i * G.plane + c] = f[i * cells + c] - q19_w(i);
+        });
+        for (int i = 0; i < 7; ++i) dst[(19 + i) * G.plane + c] = g[i * cells + c];
+    }
+}
+
+__global__ void get_populations_kernel(const float *__restrict__ src, float *f, float *g,
+                                       const Geometry G)
+{
+    const long long cells = static_cast<long long>(G.nx) * G.ny * G.nz;
+    for (long long c = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; c < cells;
+         c += static_cast<long long>(gridDim.x) * blockDim.x) {
+        if (f)
+            static_for<0, 19>([&](auto I) {
+                constexpr int i = decltype(I)::value;
+                f[i * cells + c] = src[i * G.plane + c] + q19_w(i);
+            });
+        if (g)
+            for (int i = 0; i < 7; ++i) g[i * cells + c] = src[(19 + i) * G.plane + c];
+    }
+}
+
+// Equilibrium of given fields: d_i = f_eq,i(rho, u) - w_i (Eq. (17)) and
+// g_i = w_T,i theta (1 + 4 e_i.u), the velocity form of n_eq (Eq. (33)).
+__global__ void init_fields_kernel(const float *__restrict__ rho, const float *__restrict__ u,
+                                   const float *__restrict__ theta, float *__restrict__ dst,
+                                   const Geometry G)
+{
+    const long long cells = static_cast<long long>(G.nx) * G.ny * G.nz;
+    for (long long c = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; c < cells;
+         c += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const float r = rho[c];
+        const float dr = r - 1.0f;
+        const float vx = u[c], vy = u[cells + c], vz = u[2 * cells + c];
+        const float th = theta[c];
+        const float vv = vx * vx + vy * vy + vz * vz;
+        static_for<0, 19>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            constexpr float ex = q19_ex(i), ey = q19_ey(i), ez = q19_ez(i);
+            const float ev = ex * vx + ey * vy + ez * vz;
+            dst[i * G.plane + c] = q19_w(i) * (dr + r * (3.0f * ev + 4.5f * ev * ev - 1.5f * vv));
+        });
+        static_for<0, 7>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            constexpr float ex = q7_ex(i), ey = q7_ey(i), ez = q7_ez(i);
+            dst[(19 + i) * G.plane + c] = q7_w(i) * th * (1.0f + 4.0f * (ex * vx + ey * vy + ez * vz));
+        });
+    }
+}
+
+dim3 cell_grid(const Geometry &G, dim3 block)
+{
+    return dim3((G.nx + block.x - 1) / block.x, (G.ny + block.y - 1) / block.y, G.nz);
+}
+
+dim3 flat_grid(const Geometry &G)
+{
+    const long long cells = static_cast<long long>(G.nx) * G.ny * G.nz;
+    long long blocks = (cells + 255) / 256;
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    if (blocks < 1) blocks = 1;
+    return dim3(static_cast<unsigned>(blocks));
+}
+
+const dim3 kRedBlock(32, kRedThreads / 32, 1);
+
+}  // namespace
+
+// ---------------------------------------------------------------- launchers
+
+cudaError_t launch_fields(int wall, const float *src, const Geometry &G, float *rho, float *u,
+                          float *theta, cudaStream_t s)
+{
+    dim3 block(32, 4, 1);
+    dim3 grid = cell_grid(G, block);
+    switch (wall) {
+    case 0: fields_kernel<0><<<grid, block, 0, s>>>(src, G, rho, u, theta); break;
+    case 1: fields_kernel<1><<<grid, block, 0, s>>>(src, G, rho, u, theta); break;
+    case 2: fields_kernel<2><<<grid, block, 0, s>>>(src, G, rho, u, theta); break;
+    case 3: fields_kernel<3><<<grid, block, 0, s>>>(src, G, rho, u, theta); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+size_t residual_partials(const Geometry &G)
+{
+    dim3 grid = cell_grid(G, kRedBlock);
+    return static_cast<size_t>(grid.x) * grid.y * grid.z;
+}
+
+cudaError_t launch_residual(int wall, const float *src, const Geometry &G, float *snap,
+                            int have_prev, int K, double *partials, double *result,
+                            cudaStream_t s)
+{
+    dim3 grid = cell_grid(G, kRedBlock);
+    switch (wall) {
+    case 0: residual_kernel<0><<<grid, kRedBlock, 0, s>>>(src, G, snap, have_prev, partials); break;
+    case 1: residual_kernel<1><<<grid, kRedBlock, 0, s>>>(src, G, snap, have_prev, partials); break;
+    case 2: residual_kernel<2><<<grid, kRedBlock, 0, s>>>(src, G, snap, have_prev, partials); break;
+    case 3: residual_kernel<3><<<grid, kRedBlock, 0, s>>>(src, G, snap, have_prev, partials); break;
+    default: return cudaErrorInvalidValue;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const long long nparts = static_cast<long long>(grid.x) * grid.y * grid.z;
+    residual_finish<<<1, kFinThreads, 0, s>>>(partials, nparts, have_prev, K, result);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_nusselt(int wall_type, const float *src, const Geometry &G, int wall,
+                           float *local, double *partials, double *out3, cudaStream_t s)
+{
+    dim3 grid(G.nz), block(kRedThreads);
+    switch (wall_type) {
+    case 0: nusselt_kernel<0><<<grid, block, 0, s>>>(src, G, wall, local, partials); break;
+    case 1: nusselt_kernel<1><<<grid, block, 0, s>>>(src, G, wall, local, partials); break;
+    case 2: nusselt_kernel<2><<<grid, block, 0, s>>>(src, G, wall, local, partials); break;
+    case 3: nusselt_kernel<3><<<grid, block, 0, s>>>(src, G, wall, local, partials); break;
+    default: return cudaErrorInvalidValue;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    nusselt_finish<<<1, 32, 0, s>>>(partials, G, out3);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_populations(const float *f, const float *g, float *dst, const Geometry &G,
+                                   cudaStream_t s)
+{
+    set_populations_kernel<<<flat_grid(G), 256, 0, s>>>(f, g, dst, G);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_get_populations(const float *src, float *f, float *g, const Geometry &G,
+                                   cudaStream_t s)
+{
+    get_populations_kernel<<<flat_grid(G), 256, 0, s>>>(src, f, g, G);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_fields(const float *rho, const float *u, const float *theta, float *dst,
+                               const Geometry &G, cudaStream_t s)
+{
+    init_fields_kernel<<<flat_grid(G), 256, 0, s>>>(rho, u, theta, dst, G);
+    return cudaGetLastError();
+}
+
+}  // namespace lbm

@@ -1,0 +1,59 @@
+"""The C-ABI library loads and exports every function declared in
+include/dmrt.h; argument validation needs no GPU."""
+
+import ctypes
+
+import pytest
+
+from paper_1511_04633_gb300 import build, dmrt
+
+
+def test_library_builds_and_loads():
+    path = build.build()
+    assert path.endswith("libdmrt.so")
+    lib = dmrt.load()
+    assert lib is not None
+
+
+def test_every_declared_function_is_exported():
+    names = dmrt.declared_functions()
+    assert len(names) >= 20
+    raw = ctypes.CDLL(dmrt.library_path())
+    missing = [n for n in names if not hasattr(raw, n)]
+    assert not missing, missing
+
+
+def test_status_strings_and_version():
+    assert dmrt.dmrt_status_string(0) == "DMRT_OK"
+    assert dmrt.dmrt_status_string(4) == "DMRT_ERR_DIVERGED"
+    assert dmrt.dmrt_status_string(99) == "DMRT_UNKNOWN"
+    assert "sm_103a" in dmrt.dmrt_version()
+
+
+@pytest.mark.parametrize("grid,Ra,Pr,Ma,wall", [
+    ((1, 8, 8), 1e4, 0.71, 0.1, 1),     # wall box thinner than 2 cells
+    ((8, 8, 8), -1.0, 0.71, 0.1, 1),    # Ra <= 0
+    ((8, 8, 8), 1e4, 0.0, 0.1, 1),      # Pr <= 0
+    ((8, 8, 8), 1e4, 0.71, 0.35, 1),    # Ma >= 0.3
+    ((8, 8, 8), 1e4, 0.71, 0.1, 7),     # unknown wall type
+    ((2000, 2000, 2000), 1e4, 0.71, 0.1, 1),  # more than 2^31 cells
+])
+def test_create_rejects_bad_arguments_without_touching_the_gpu(grid, Ra, Pr, Ma, wall):
+    with pytest.raises(dmrt.DmrtError) as ei:
+        dmrt.dmrt_create(grid, Ra, Pr, Ma, wall)
+    assert ei.value.status == dmrt.ERR_ARG
+
+
+def test_create_lattice_rejects_nonpositive_transport():
+    for nu, alpha in ((0.0, 0.1), (0.1, -1.0), (float("nan"), 0.1)):
+        with pytest.raises(dmrt.DmrtError) as ei:
+            dmrt.dmrt_create_lattice((8, 8, 8), nu, alpha, 0.0, 1)
+        assert ei.value.status == dmrt.ERR_ARG
+
+
+def test_null_handle_calls_are_rejected():
+    lib = dmrt.load()
+    assert lib.dmrt_step(None, 1) == dmrt.ERR_ARG
+    assert lib.dmrt_sync(None) == dmrt.ERR_ARG
+    assert lib.dmrt_last_error(None) == b"null handle"
+    lib.dmrt_destroy(None)

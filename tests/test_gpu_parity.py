@@ -1,0 +1,270 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances: the FP32 fields must match the oracle to max |d| <= 1e-5 (rho,
+lattice-unit velocity, theta) and the Nusselt numbers to 1e-4 relative after
+a fixed step count.  One step from the same populations must agree to 1e-6
+(the rounding of one FP32 collision).
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1511_04633_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+FIELD_TOL = 1e-5
+NU_RTOL = 1e-4
+STEP_TOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def dm():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1511_04633_gb300 import dmrt
+    dmrt.load()
+    return dmrt
+
+
+def _pair(dm, grid, wall, *, Ra=None, lattice=None, residual_interval=0):
+    if lattice is not None:
+        gpu = dm.Cavity(grid, wall_type=wall, lattice=lattice, residual_interval=residual_interval)
+        orc = oracle.Oracle(grid, wall, *lattice)
+    else:
+        gpu = dm.Cavity(grid, Ra, wall_type=wall, residual_interval=residual_interval)
+        orc = oracle.Oracle.physical(grid, wall, Ra)
+    return gpu, orc
+
+
+def _compare_fields(gpu, orc, tol=FIELD_TOL):
+    rg, ug, tg = gpu.fields()
+    ro, uo, to = orc.fields()
+    err = {"rho": np.abs(rg - ro).max(), "u": np.abs(ug - uo).max(), "theta": np.abs(tg - to).max()}
+    assert max(err.values()) <= tol, err
+    return err
+
+
+def _compare_nusselt(gpu, orc, walls=(0, 1)):
+    for w in walls:
+        ng = gpu.nusselt(w)
+        (no, loc_o) = orc.nusselt(w)
+        for a, b in zip(ng, no):
+            assert abs(a - b) <= NU_RTOL * abs(b), (w, ng, no)
+        loc_g = gpu.nusselt_local(w)
+        assert np.abs(loc_g - loc_o).max() <= NU_RTOL * max(1.0, np.abs(loc_o).max())
+
+
+# ------------------------------------------------------------------ one step, random states
+
+@pytest.mark.parametrize("wall", [0, 1, 2, 3])
+@pytest.mark.parametrize("grid", [(16, 16, 16), (37, 20, 13), (2, 3, 2)])
+def test_one_step_from_random_populations(dm, wall, grid):
+    gpu, orc = _pair(dm, grid, wall, lattice=(0.03, 0.05, 2e-3))
+    f = inputs.random_populations(grid, 19, seed=100 + wall)
+    g = inputs.random_thermal_populations(grid, seed=200 + wall)
+    gpu.set_populations(f, g)
+    orc.set_populations(f.astype(np.float64), g.astype(np.float64))
+    # fields of the pulled state before any collision (wall rules only)
+    _compare_fields(gpu, orc, tol=STEP_TOL)
+    gpu.step(1)
+    orc.step(1)
+    fg, gg = gpu.populations()
+    fo, go = orc.populations()
+    assert np.abs(fg - fo).max() <= STEP_TOL
+    assert np.abs(gg - go).max() <= STEP_TOL
+    _compare_fields(gpu, orc, tol=STEP_TOL)
+
+
+@pytest.mark.parametrize("wall", [1, 2, 3])
+def test_wall_rules_with_a_single_perturbed_cell(dm, wall):
+    """A lone population spike next to an edge and a corner exercises every
+    bounce-back and anti-bounce-back branch on its own."""
+    grid = (6, 5, 7)
+    gpu, orc = _pair(dm, grid, wall, lattice=(0.04, 0.06, 1e-3))
+    nx, ny, nz = grid
+    f = np.zeros((19, nz, ny, nx), np.float32)
+    w = oracle.weights19().astype(np.float32)
+    f += w[:, None, None, None]
+    g = np.zeros((7, nz, ny, nx), np.float32)
+    for (x, y, z) in [(0, 0, 0), (nx - 1, ny - 1, nz - 1), (0, ny - 1, 3), (nx - 1, 2, 0)]:
+        f[:, z, y, x] *= 1.05
+        g[:, z, y, x] = 0.1 * np.arange(1, 8, dtype=np.float32)
+    gpu.set_populations(f, g)
+    orc.set_populations(f.astype(np.float64), g.astype(np.float64))
+    for _ in range(3):
+        gpu.step(1)
+        orc.step(1)
+        fg, gg = gpu.populations()
+        fo, go = orc.populations()
+        assert np.abs(fg - fo).max() <= STEP_TOL
+        assert np.abs(gg - go).max() <= STEP_TOL
+
+
+# ------------------------------------------------------------------ trajectories
+
+def test_config1_type1_32cube_ra1e3_2000_steps(dm):
+    """32^3, Type 1, Ra = 1e3, Pr = 0.71, Ma = 0.1, from rest, 2000 steps."""
+    grid = (32, 32, 32)
+    gpu, orc = _pair(dm, grid, 1, Ra=1e3)
+    gpu.step(2000)
+    orc.step(2000)
+    _compare_fields(gpu, orc)
+    _compare_nusselt(gpu, orc)
+
+
+@pytest.mark.parametrize("wall,Ra", [(2, 1e5), (3, 1e4), (1, 1e5)])
+def test_16cube_types(dm, wall, Ra):
+    grid = (16, 16, 16)
+    gpu, orc = _pair(dm, grid, wall, Ra=Ra)
+    gpu.step(800)
+    orc.step(800)
+    _compare_fields(gpu, orc)
+    _compare_nusselt(gpu, orc)
+
+
+def test_ragged_grid_spans_several_tiles(dm):
+    grid = (37, 20, 13)
+    gpu, orc = _pair(dm, grid, 2, Ra=3e4)
+    gpu.step(400)
+    orc.step(400)
+    _compare_fields(gpu, orc)
+    _compare_nusselt(gpu, orc)
+
+
+def test_periodic_random_state(dm):
+    grid = (12, 10, 9)
+    gpu, orc = _pair(dm, grid, 0, lattice=(0.05, 0.04, 1e-3))
+    rho, u, th = inputs.random_fields(grid, seed=7)
+    gpu.init_fields(rho, u, th)
+    orc.init_fields(rho.astype(np.float64), u.astype(np.float64), th.astype(np.float64))
+    _compare_fields(gpu, orc, tol=STEP_TOL)
+    gpu.step(300)
+    orc.step(300)
+    _compare_fields(gpu, orc)
+
+
+def test_periodic_conservation_on_gpu(dm):
+    grid = (16, 16, 16)
+    gpu = dm.Cavity(grid, wall_type=0, lattice=(0.05, 0.04, 0.0))
+    rho, u, th = inputs.random_fields(grid, seed=8)
+    gpu.init_fields(rho, u, th)
+    r0, _, t0 = gpu.fields()
+    gpu.step(1000)
+    r1, _, t1 = gpu.fields()
+    assert abs(r1.astype(np.float64).sum() - r0.astype(np.float64).sum()) < 1e-6 * r0.size
+    assert abs(t1.astype(np.float64).sum() - t0.astype(np.float64).sum()) < 1e-5
+
+
+@pytest.mark.parametrize("wall", [1, 2, 3])
+def test_rest_state_stays_exactly_at_rest(dm, wall):
+    grid = (8, 9, 10)
+    gpu = dm.Cavity(grid, wall_type=wall, lattice=(0.05, 0.08, 0.0))
+    gpu.step(500)
+    rho, u, th = gpu.fields()
+    assert np.all(u == 0.0)
+    assert np.all(rho == 1.0)
+    assert np.abs(th).max() > 0.1
+
+
+def test_smallest_wall_box(dm):
+    grid = (2, 2, 2)
+    gpu, orc = _pair(dm, grid, 2, lattice=(0.1, 0.1, 1e-3))
+    gpu.step(50)
+    orc.step(50)
+    _compare_fields(gpu, orc)
+
+
+def test_zero_steps_and_empty_calls(dm):
+    gpu = dm.Cavity((8, 8, 8), 1e4, wall_type=1)
+    gpu.step(0)
+    assert gpu.params["steps"] == 0
+    assert math.isinf(gpu.residual())
+    dm.dmrt_get_populations(gpu.h, None, None)
+
+
+# ------------------------------------------------------------------ residual, divergence
+
+def test_residual_matches_the_oracle_definition(dm):
+    grid = (16, 16, 16)
+    K = 50
+    gpu, orc = _pair(dm, grid, 1, Ra=1e4, residual_interval=K)
+    gpu.step(3 * K)
+    orc.step(2 * K)
+    _, u_prev, t_prev = orc.fields()
+    orc.step(K)
+    _, u_now, t_now = orc.fields()
+    r_o = oracle.residual(t_now, u_now, t_prev, u_prev, K)
+    r_g = gpu.residual()
+    assert abs(r_g - r_o) <= 1e-3 * r_o
+
+
+def test_nan_populations_report_divergence(dm):
+    grid = (8, 8, 8)
+    gpu = dm.Cavity(grid, 1e4, wall_type=1, residual_interval=10)
+    f = inputs.random_populations(grid, 19, seed=9)
+    g = inputs.random_thermal_populations(grid, seed=10)
+    f[3, 4, 4, 4] = np.nan
+    gpu.set_populations(f, g)
+    gpu.step(20)
+    with pytest.raises(dm.DmrtError) as ei:
+        gpu.residual()
+    assert ei.value.status == dm.ERR_DIVERGED
+
+
+def test_run_to_steady_stops_on_budget(dm):
+    gpu = dm.Cavity((8, 8, 8), 1e4, wall_type=1, residual_interval=10)
+    ok, n, r = gpu.run_to_steady(1e-30, 40)
+    assert not ok and n == 40
+
+
+def test_bitwise_deterministic(dm):
+    grid = (20, 20, 20)
+    a = dm.Cavity(grid, 1e5, wall_type=3)
+    b = dm.Cavity(grid, 1e5, wall_type=3)
+    a.step(200)
+    b.step(200)
+    fa, ga = a.populations()
+    fb, gb = b.populations()
+    assert np.array_equal(fa, fb) and np.array_equal(ga, gb)
+    assert a.nusselt(0) == b.nusselt(0)
+
+
+# ------------------------------------------------------------------ full size (128^3)
+
+def test_full_size_128cube_type2_one_step_and_nusselt(dm):
+    """The benchmark workload (128^3, Type 2, Ra = 1e5) in the launch shape the
+    benchmark times: after 300 GPU steps from rest, one more GPU step must
+    match the oracle's step from the same state everywhere."""
+    grid = (128, 128, 128)
+    gpu = dm.Cavity(grid, 1e5, wall_type=2)
+    gpu.step(300)
+    f, g = gpu.populations()
+    orc = oracle.Oracle.physical(grid, 2, 1e5)
+    orc.set_populations(f.astype(np.float64), g.astype(np.float64))
+    # Nusselt numbers of this state
+    for w in (0, 1):
+        ng = gpu.nusselt(w)
+        no, _ = orc.nusselt(w)
+        for a, b in zip(ng, no):
+            assert abs(a - b) <= NU_RTOL * abs(b)
+    _compare_fields(gpu, orc, tol=STEP_TOL)
+    del f, g
+    gpu.step(1)
+    orc.step(1)
+    fg, gg = gpu.populations()
+    fo, go = orc.populations()
+    assert np.abs(fg - fo).max() <= STEP_TOL
+    assert np.abs(gg - go).max() <= STEP_TOL
+
+
+def test_full_size_128cube_trajectory(dm):
+    grid = (128, 128, 128)
+    gpu, orc = _pair(dm, grid, 2, Ra=1e5)
+    gpu.step(40)
+    orc.step(40)
+    _compare_fields(gpu, orc)
