@@ -140,6 +140,32 @@ dmrt_status dmrt_nusselt(dmrt_t *h, int wall, double out[3]);
 /* The local Nusselt number of wall 0 or 1 as a float32 [z][x] map. */
 dmrt_status dmrt_nusselt_local(dmrt_t *h, int wall, float *local, int on_device);
 
+/* Nusselt numbers of a caller's temperature field without allocating any
+ * device memory.  The paper has no counterpart: this serves callers that may
+ * not allocate device memory once running (a host application whose memory
+ * pool owns the device memory, or a time-critical loop where cudaMalloc /
+ * cudaFree would stall the device).
+ *
+ * theta: device pointer, float32 [z][y][x] (nx*ny*nz), e.g. filled by
+ * dmrt_fields(..., on_device = 1).  wall 0 = hot wall y = 0, 1 = cold wall
+ * y = H.  The result out[3] (host memory) is (Nu_3D, Nu_2D, Nu_max), with the
+ * discretisation of dmrt_nusselt.  stream: a cudaStream_t (NULL = the legacy
+ * default stream); the call synchronises it.
+ *
+ * Scratch: a fixed array of 3 * 8192 + 4 doubles (about 192 KB) in the
+ * library's own device memory, placed when the library is loaded on a GPU and
+ * held by every GPU that loads it until the process exits.  nz may be at most
+ * 8192; larger nz, nx*ny*nz >= 2^31, ny < 2, a NULL pointer or a wall other
+ * than 0 / 1 return DMRT_ERR_ARG before any GPU work.  The call never calls
+ * cudaMalloc or cudaFree.  Its first call on a device, with that device
+ * current, looks up the array's device address (cudaGetSymbolAddress); make
+ * that first call before any stream capture.  Every call shares the one
+ * array: each call writes every slot it reads, so nothing carries over, but
+ * calls that overlap on the GPU (other streams, other host threads) race and
+ * must be serialised by the caller.  DMRT_ERR_CUDA if a CUDA call fails. */
+dmrt_status dmrt_nusselt_noalloc(const float *theta, int nx, int ny, int nz, int wall,
+                                 void *stream, double out[3]);
+
 /* The convergence residual from the last two residual points (K steps
  * apart): r = max(|theta^n - theta^{n-K}|_2 / |theta^n|_2,
  * |u^n - u^{n-K}|_2 / |u^n|_2) / K, in FP64.  +inf until two points exist.

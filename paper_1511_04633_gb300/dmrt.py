@@ -86,6 +86,7 @@ def load(build_if_missing: bool = True):
             "dmrt_fields": ([vp, vp, vp, vp, i], i),
             "dmrt_nusselt": ([vp, i, P(d)], i),
             "dmrt_nusselt_local": ([vp, i, vp, i], i),
+            "dmrt_nusselt_noalloc": ([vp, i, i, i, i, vp, P(d)], i),
             "dmrt_residual": ([vp, P(d)], i),
             "dmrt_run_to_steady": ([vp, d, l_, P(l_), P(d)], i),
             "dmrt_set_populations": ([vp, vp, vp, i], i),
@@ -200,6 +201,19 @@ def dmrt_nusselt(h, wall: int = 0):
 def dmrt_nusselt_local(h, wall, local):
     p, side = _ptr(local)
     check(h, load().dmrt_nusselt_local(h, wall, p, side), "dmrt_nusselt_local")
+
+
+def dmrt_nusselt_noalloc(theta, wall: int = 0, stream=None):
+    """Nusselt numbers of a CUDA float32 tensor theta[z][y][x], computed
+    without any device allocation (see include/dmrt.h)."""
+    p, side = _ptr(theta)
+    if side != 1:
+        raise TypeError("theta must be a CUDA tensor")
+    nz, ny, nx = theta.shape
+    raw = getattr(stream, "cuda_stream", stream)
+    out = (ctypes.c_double * 3)()
+    check(None, load().dmrt_nusselt_noalloc(p, nx, ny, nz, wall, raw, out), "dmrt_nusselt_noalloc")
+    return tuple(out)
 
 
 def dmrt_residual(h) -> float:
