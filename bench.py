@@ -234,7 +234,10 @@ def run_dmrt(args, rank, local, world):
     torch.cuda.set_device(local)
     dist = init_dist(world, "nccl")
     device = torch.device("cuda", local)
-    stream = torch.cuda.current_stream(device)
+    # a dedicated stream: the library launches on it and the events below are
+    # recorded on it (torch's default stream is the legacy NULL stream)
+    stream = torch.cuda.Stream(device)
+    torch.cuda.set_stream(stream)
     dmrt.load()
 
     cells = GRID[0] * GRID[1] * GRID[2]

@@ -91,7 +91,8 @@ typedef struct dmrt_stats {
  * The fluid starts at rest: rho = 1, u = 0, theta = 0 (populations at the
  * equilibrium of Eq. (17), energy populations zero).  Runs on the current
  * CUDA device.  Every grid dimension must be >= 2 (>= 1 for PERIODIC) and
- * nx*ny*nz < 2^31.  On error *out is NULL. */
+ * at most 65535, and nx*ny*nz <= 165,191,040 (the 26 population planes are
+ * addressed with 32-bit indices; e.g. up to 548^3).  On error *out is NULL. */
 dmrt_status dmrt_create(dmrt_t **out, const int grid[3], double Ra, double Pr, double Ma,
                         int wall_type);
 

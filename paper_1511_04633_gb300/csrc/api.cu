@@ -26,6 +26,7 @@ struct dmrt {
     int K = 100;
     double nu = 0, alpha = 0, gbeta = 0;
     Geometry G{};
+    lbm::StepGeometry S{};
     CollideParams C{};
     lbm::BlockShape block{32, 4};
 
@@ -45,6 +46,12 @@ struct dmrt {
     long steps = 0;
     int snaps = 0;  // residual points taken since the last reset (capped at 2)
 
+    // CUDA graphs of one full residual interval (K steps), one per starting
+    // buffer; captured on first use, replayed afterwards.
+    bool use_graphs = true;
+    bool use_pdl = true;
+    cudaGraphExec_t interval_graph[2] = {nullptr, nullptr};
+
     bool timing = false;
     std::vector<cudaEvent_t> ev_pool;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
@@ -56,6 +63,9 @@ struct dmrt {
 };
 
 namespace {
+
+// Longest residual interval that is replayed as one captured graph.
+constexpr long kMaxGraphSteps = 1000;
 
 const char *kStatusNames[] = {"DMRT_OK", "DMRT_ERR_ARG", "DMRT_ERR_CUDA", "DMRT_ERR_OOM",
                               "DMRT_ERR_DIVERGED", "DMRT_ERR_TIMEOUT"};
@@ -179,7 +189,39 @@ dmrt_status run_residual(dmrt_t *h)
     return DMRT_OK;
 }
 
-// Launch n fused steps, taking a residual point after every K-th step.
+// Capture K consecutive step launches starting from buffer `start` into an
+// executable graph.  Returns false (and leaves graphs off) if the stream
+// cannot be captured, e.g. the legacy default stream.
+bool capture_interval(dmrt_t *h, int start)
+{
+    if (h->stream == nullptr) return false;
+    if (cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    int cur = start;
+    bool ok = true;
+    for (long s = 0; s < h->K && ok; ++s) {
+        ok = lbm::launch_step(h->wall, h->buf[cur], h->buf[cur ^ 1], h->S, h->G, h->C, h->block,
+                              h->stream, h->use_pdl) == cudaSuccess;
+        cur ^= 1;
+    }
+    cudaGraph_t graph = nullptr;
+    ok = (cudaStreamEndCapture(h->stream, &graph) == cudaSuccess) && ok && graph;
+    cudaGraphExec_t exec = nullptr;
+    if (ok) ok = cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+    if (graph) cudaGraphDestroy(graph);
+    if (!ok) {
+        cudaGetLastError();
+        if (exec) cudaGraphExecDestroy(exec);
+        return false;
+    }
+    h->interval_graph[start] = exec;
+    return true;
+}
+
+// Launch n fused steps, taking a residual point after every K-th step.  A
+// whole interval of K steps replays a captured graph.
 dmrt_status run_steps(dmrt_t *h, long n)
 {
     long done = 0;
@@ -193,10 +235,24 @@ dmrt_status run_steps(dmrt_t *h, long n)
             if (!e0 || !e1) return fail(h, DMRT_ERR_CUDA, "cudaEventCreate failed");
             CK(h, cudaEventRecord(e0, h->stream), "cudaEventRecord");
         }
-        for (long s = 0; s < chunk; ++s) {
+        bool graphed = false;
+        if (chunk == h->K && h->K <= kMaxGraphSteps && h->use_graphs) {
+            if (!h->interval_graph[h->cur] && !capture_interval(h, h->cur)) h->use_graphs = false;
+            if (h->interval_graph[h->cur]) {
+                CK(h, cudaGraphLaunch(h->interval_graph[h->cur], h->stream), "cudaGraphLaunch");
+                if (h->K & 1) h->cur ^= 1;
+                h->steps += chunk;
+                h->step_launches += chunk;
+                h->total_launches += chunk;
+                graphed = true;
+            }
+        }
+        for (long s = 0; s < chunk && !graphed; ++s) {
             float *src = h->buf[h->cur];
             float *dst = h->buf[h->cur ^ 1];
-            CK(h, lbm::launch_step(h->wall, src, dst, h->G, h->C, h->block, h->stream),
+            CK(h,
+               lbm::launch_step(h->wall, src, dst, h->S, h->G, h->C, h->block, h->stream,
+                                h->use_pdl),
                "step kernel");
             h->cur ^= 1;
             h->steps++;
@@ -228,7 +284,8 @@ dmrt_status create_common(dmrt_t **out, const int grid[3], double nu, double alp
     for (int a = 0; a < 3; ++a)
         if (grid[a] < minext || grid[a] > 65535) return DMRT_ERR_ARG;
     const long long cells = static_cast<long long>(grid[0]) * grid[1] * grid[2];
-    if (cells >= (1LL << 31)) return DMRT_ERR_ARG;
+    // the step kernel addresses all 26 planes with 32-bit indices
+    if ((cells + 63) / 64 * 64 * lbm::kPlanes >= (1LL << 32)) return DMRT_ERR_ARG;
     if (!(nu > 0.0) || !(alpha > 0.0) || !std::isfinite(nu) || !std::isfinite(alpha) ||
         !std::isfinite(gbeta))
         return DMRT_ERR_ARG;
@@ -260,10 +317,15 @@ dmrt_status create_common(dmrt_t **out, const int grid[3], double nu, double alp
     // alignment of every plane start)
     h->G.plane = (cells + 63) / 64 * 64;
     h->G.inv_ny = 1.0f / static_cast<float>(grid[1]);
+    lbm::fill_step_geometry(h->G, h->S);
     fill_rates(h);
+#ifdef DMRT_BLOCK_X
+    h->block = {DMRT_BLOCK_X, DMRT_BLOCK_Y};
+#else
     if (grid[0] >= 128) h->block = {128, 1};
     else if (grid[0] >= 64) h->block = {64, 2};
     else h->block = {32, 4};
+#endif
 
     auto bail = [&](dmrt_status st) {
         dmrt_destroy(h);
@@ -287,6 +349,12 @@ dmrt_status create_common(dmrt_t **out, const int grid[3], double nu, double alp
     e = cudaStreamCreateWithFlags(&h->own, cudaStreamNonBlocking);
     if (e != cudaSuccess) return bail(DMRT_ERR_CUDA);
     h->stream = h->own;
+#ifdef DMRT_NO_GRAPHS
+    h->use_graphs = false;
+#endif
+#ifdef DMRT_NO_PDL
+    h->use_pdl = false;
+#endif
     // start from rest: f = w (zero deviations), g = 0 (theta = 0)
     e = cudaMemsetAsync(h->buf[0], 0, buf_bytes, h->stream);
     if (e != cudaSuccess) return bail(DMRT_ERR_CUDA);
@@ -342,6 +410,8 @@ void dmrt_destroy(dmrt_t *h)
         cudaEventDestroy(p.second);
     }
     for (auto e : h->ev_pool) cudaEventDestroy(e);
+    for (auto &g : h->interval_graph)
+        if (g) cudaGraphExecDestroy(g);
     for (int b = 0; b < 2; ++b)
         if (h->buf[b]) cudaFree(h->buf[b]);
     if (h->snap) cudaFree(h->snap);

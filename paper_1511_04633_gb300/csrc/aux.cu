@@ -199,20 +199,31 @@ __global__ void __launch_bounds__(kRedThreads) nusselt_kernel(const float *__res
     }
 }
 
-__global__ void nusselt_finish(const double *__restrict__ partials, const Geometry G,
-                               double *out3)
+// Sums the per-row partials in a fixed order: each thread takes rows
+// t, t + 256, ...; then one fixed shuffle tree.
+__global__ void __launch_bounds__(kRedThreads) nusselt_finish(const double *__restrict__ partials,
+                                                               const Geometry G, double *out3)
 {
-    if (threadIdx.x != 0) return;
-    double s = 0.0, mid = 0.0, mx = -INFINITY;
-    for (int z = 0; z < G.nz; ++z) {
-        s += partials[z * 3 + 0];
-        mid += partials[z * 3 + 1];
+    double v[2] = {0.0, 0.0};
+    double mx = -INFINITY;
+    for (int z = threadIdx.x; z < G.nz; z += kRedThreads) {
+        v[0] += partials[z * 3 + 0];
+        v[1] += partials[z * 3 + 1];
         mx = fmax(mx, partials[z * 3 + 2]);
     }
-    const int ncol = (G.nx % 2 == 0) ? 2 : 1;
-    out3[0] = s / (static_cast<double>(G.nx) * G.nz);
-    out3[1] = mid / (static_cast<double>(G.nz) * ncol);
-    out3[2] = mx;
+    __shared__ double shm[kRedThreads / 32];
+    mx = warp_max(mx);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) shm[warp] = mx;
+    block_sum<2, kRedThreads>(v);
+    if (threadIdx.x == 0) {
+        double m = shm[0];
+        for (int w = 1; w < kRedThreads / 32; ++w) m = fmax(m, shm[w]);
+        const int ncol = (G.nx % 2 == 0) ? 2 : 1;
+        out3[0] = v[0] / (static_cast<double>(G.nx) * G.nz);
+        out3[1] = v[1] / (static_cast<double>(G.nz) * ncol);
+        out3[2] = m;
+    }
 }
 
 // ---------------------------------------------------------------- import / export
@@ -348,7 +359,7 @@ cudaError_t launch_nusselt(int wall_type, const float *src, const Geometry &G, i
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    nusselt_finish<<<1, 32, 0, s>>>(partials, G, out3);
+    nusselt_finish<<<1, kRedThreads, 0, s>>>(partials, G, out3);
     return cudaGetLastError();
 }
 

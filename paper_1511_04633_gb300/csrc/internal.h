@@ -16,9 +16,15 @@ struct BlockShape {
     int bx, by;
 };
 
+// Offset tables of the step kernel for a geometry (see StepGeometry).
+void fill_step_geometry(const Geometry &G, StepGeometry &S);
+
 // One fused time step: pull from `src`, collide, force, store into `dst`.
-cudaError_t launch_step(int wall, const float *src, float *dst, const Geometry &G,
-                        const CollideParams &C, BlockShape b, cudaStream_t s);
+// pdl: launch with programmatic stream serialisation (the kernel waits for
+// the previous grid itself).
+cudaError_t launch_step(int wall, const float *src, float *dst, const StepGeometry &S,
+                        const Geometry &G, const CollideParams &C, BlockShape b, cudaStream_t s,
+                        bool pdl);
 
 // Fields of the pulled populations (any output may be null).
 cudaError_t launch_fields(int wall, const float *src, const Geometry &G, float *rho, float *u,

@@ -146,6 +146,18 @@ struct Geometry {
     float inv_ny;     // 1/ny for the linear wall profile
 };
 
+// Launch-parameter tables of the step kernel for walled boxes: the source of
+// plane q for a cell with flat index c is c + nb[q] (the neighbour at
+// c - e_q), or c + bb[q] when that link leaves the box (the opposite plane
+// of the cell itself).  32-bit indices: 26 * plane < 2^32.
+struct StepGeometry {
+    int nx, ny, nz;
+    unsigned plane;
+    int nb[26];
+    int bb[26];
+    float inv_ny;
+};
+
 // ---------------------------------------------------------------- pull with walls
 
 // Wall rule of a D3Q7 link that leaves the box through a face on `axis`
@@ -246,7 +258,7 @@ __device__ __forceinline__ void pull_g(const float *__restrict__ src, const Geom
     });
 }
 
-// ---------------------------------------------------------------- collision
+// ---------------------------------------------------------------- moments
 
 // Macroscopic moments of pulled populations (Eqs. (20), (30)).
 struct Macro {
@@ -268,115 +280,6 @@ __device__ __forceinline__ Macro macro_of(const float d[19], const float g[7])
     });
     static_for<0, 7>([&](auto I) { m.T += g[decltype(I)::value]; });
     return m;
-}
-
-// m_k = sum_i M_ki d_i for one moment k (zero coefficients dropped).
-template <int K>
-__device__ __forceinline__ float moment19(const float d[19])
-{
-    float acc = 0.f;
-    static_for<0, 19>([&](auto I) {
-        constexpr int i = decltype(I)::value;
-        constexpr int c = m19(K, i);
-        if constexpr (c == 1) acc += d[i];
-        else if constexpr (c == -1) acc -= d[i];
-        else if constexpr (c != 0) acc = fmaf(static_cast<float>(c), d[i], acc);
-    });
-    return acc;
-}
-
-template <int K>
-__device__ __forceinline__ float moment7(const float g[7])
-{
-    float acc = 0.f;
-    static_for<0, 7>([&](auto I) {
-        constexpr int i = decltype(I)::value;
-        constexpr int c = m7(K, i);
-        if constexpr (c == 1) acc += g[i];
-        else if constexpr (c == -1) acc -= g[i];
-        else if constexpr (c != 0) acc = fmaf(static_cast<float>(c), g[i], acc);
-    });
-    return acc;
-}
-
-// In-place collision of one cell: MRT relaxation of both lattices
-// (Eqs. (19), (24), (29), (33)) and the buoyancy force (Eqs. (15)-(17)).
-// d holds f - w, g the energy populations; on return both are post-collision.
-__device__ __forceinline__ void collide_cell(const CollideParams &C, float d[19], float g[7])
-{
-    const Macro mc = macro_of(d, g);
-    const float rho = 1.0f + mc.drho;
-    const float jx = mc.jx, jy = mc.jy, jz = mc.jz;
-    const float jxx = jx * jx, jyy = jy * jy, jzz = jz * jz;
-    const float jj = jxx + jyy + jzz;
-
-    // non-equilibrium part of each relaxed moment, scaled by s_k/|M_k|^2.
-    // Equilibria of Eq. (24) with rho0 = 1, minus the rest moments.
-    float a[19];
-    a[1] = C.rs[1] * (moment19<1>(d) - (-11.0f * mc.drho + 19.0f * jj));
-    a[2] = C.rs[2] * (moment19<2>(d) - (3.0f * mc.drho - 5.5f * jj));
-    a[4] = C.rs[4] * (moment19<4>(d) + (2.0f / 3.0f) * jx);
-    a[6] = C.rs[6] * (moment19<6>(d) + (2.0f / 3.0f) * jy);
-    a[8] = C.rs[8] * (moment19<8>(d) + (2.0f / 3.0f) * jz);
-    const float pxx = 2.0f * jxx - (jyy + jzz);
-    const float pww = jyy - jzz;
-    a[9] = C.rs[9] * (moment19<9>(d) - pxx);
-    a[10] = C.rs[10] * (moment19<10>(d) + 0.5f * pxx);
-    a[11] = C.rs[11] * (moment19<11>(d) - pww);
-    a[12] = C.rs[12] * (moment19<12>(d) + 0.5f * pww);
-    a[13] = C.rs[13] * (moment19<13>(d) - jx * jy);
-    a[14] = C.rs[14] * (moment19<14>(d) - jy * jz);
-    a[15] = C.rs[15] * (moment19<15>(d) - jx * jz);
-    a[16] = C.rs[16] * moment19<16>(d);
-    a[17] = C.rs[17] * moment19<17>(d);
-    a[18] = C.rs[18] * moment19<18>(d);
-
-    // buoyancy G = (0, 0, g beta (theta - theta_ref)) (Eq. (16), gravity -z)
-    const float inv_rho = 1.0f / rho;
-    const float vx = jx * inv_rho, vy = jy * inv_rho, vz = jz * inv_rho;
-    const float vv = vx * vx + vy * vy + vz * vz;
-    const float Gz3 = 3.0f * C.gbeta * (mc.T - C.theta_ref);  // G_z / c_s^2
-
-    // back-transform of the collision increment plus the force
-    static_for<0, 19>([&](auto I) {
-        constexpr int i = decltype(I)::value;
-        float dc = 0.f;
-        static_for<1, 19>([&](auto K) {
-            constexpr int k = decltype(K)::value;
-            if constexpr (k != 3 && k != 5 && k != 7) {
-                constexpr int c = m19(k, i);
-                if constexpr (c == 1) dc += a[k];
-                else if constexpr (c == -1) dc -= a[k];
-                else if constexpr (c != 0) dc = fmaf(static_cast<float>(c), a[k], dc);
-            }
-        });
-        constexpr float ex = q19_ex(i), ey = q19_ey(i), ez = q19_ez(i);
-        const float ev = ex * vx + ey * vy + ez * vz;
-        const float feq = rho * q19_w(i) * (1.0f + 3.0f * ev + 4.5f * ev * ev - 1.5f * vv);
-        const float F = Gz3 * (ez - vz) * feq;  // Eq. (15)
-        d[i] = d[i] - dc + F;
-    });
-
-    // energy: n - n_eq with n_eq = (T, V T, 3/4 T, 0, 0) (Eqs. (33),(34))
-    float b[7];
-    b[1] = C.rq[1] * (moment7<1>(g) - vx * mc.T);
-    b[2] = C.rq[2] * (moment7<2>(g) - vy * mc.T);
-    b[3] = C.rq[3] * (moment7<3>(g) - vz * mc.T);
-    b[4] = C.rq[4] * (moment7<4>(g) - 0.75f * mc.T);
-    b[5] = C.rq[5] * moment7<5>(g);
-    b[6] = C.rq[6] * moment7<6>(g);
-    static_for<0, 7>([&](auto I) {
-        constexpr int i = decltype(I)::value;
-        float dc = 0.f;
-        static_for<1, 7>([&](auto K) {
-            constexpr int k = decltype(K)::value;
-            constexpr int c = m7(k, i);
-            if constexpr (c == 1) dc += b[k];
-            else if constexpr (c == -1) dc -= b[k];
-            else if constexpr (c != 0) dc = fmaf(static_cast<float>(c), b[k], dc);
-        });
-        g[i] -= dc;
-    });
 }
 
 }  // namespace lbm

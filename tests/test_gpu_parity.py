@@ -136,6 +136,20 @@ def test_ragged_grid_spans_several_tiles(dm):
     _compare_nusselt(gpu, orc)
 
 
+@pytest.mark.parametrize("K", [7, 10])
+def test_graph_replayed_intervals_match_the_oracle(dm, K):
+    """Whole residual intervals replay a captured graph; an odd K swaps the
+    ping-pong buffers between replays."""
+    grid = (20, 18, 16)
+    gpu, orc = _pair(dm, grid, 3, Ra=5e4, residual_interval=K)
+    gpu.step(3)        # leaves the next interval misaligned: plain launches first
+    gpu.step(10 * K)   # then graph replays
+    orc.step(3 + 10 * K)
+    _compare_fields(gpu, orc)
+    st = dm.dmrt_get_stats(gpu.h)
+    assert st["step_launches"] == 3 + 10 * K
+
+
 def test_periodic_random_state(dm):
     grid = (12, 10, 9)
     gpu, orc = _pair(dm, grid, 0, lattice=(0.05, 0.04, 1e-3))
