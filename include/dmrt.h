@@ -55,10 +55,16 @@ typedef enum {
     DMRT_WALL_TYPE3 = 3,
 } dmrt_wall;
 
-/* Population storage format in HBM.  F32 stores f_i - w_i and g_i in float32
- * (208 bytes moved per cell update). */
+/* Population storage format in HBM.  Every format stores the deviations
+ * f_i - w_i from the rest equilibrium (rho = 1, u = 0) and the g_i; the
+ * collision always runs in FP32.
+ *  F32 : float32, 208 bytes moved per cell update.
+ *  BF16: bfloat16 rounded to nearest, 104 bytes per cell update.
+ *  F16 : IEEE half of the values times 2^10, rounded to nearest, 104 bytes. */
 typedef enum {
     DMRT_STORE_F32 = 0,
+    DMRT_STORE_BF16 = 1,
+    DMRT_STORE_F16 = 2,
 } dmrt_storage;
 
 /* Optional creation settings; pass NULL for the defaults. */

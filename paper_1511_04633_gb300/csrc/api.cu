@@ -30,7 +30,7 @@ struct dmrt {
     CollideParams C{};
     lbm::BlockShape block{32, 4};
 
-    float *buf[2] = {nullptr, nullptr};  // ping-pong population buffers
+    void *buf[2] = {nullptr, nullptr};   // ping-pong population buffers (storage type)
     int cur = 0;                          // buffer holding the current state
     float *snap = nullptr;                // residual snapshot: theta, u (4 planes)
     double *partials = nullptr;           // reduction scratch
@@ -181,8 +181,8 @@ dmrt_status collect_timing(dmrt_t *h)
 dmrt_status run_residual(dmrt_t *h)
 {
     CK(h,
-       lbm::launch_residual(h->wall, h->buf[h->cur], h->G, h->snap, h->snaps > 0 ? 1 : 0, h->K,
-                             h->partials, h->dres, h->stream),
+       lbm::launch_residual(h->wall, h->storage, h->buf[h->cur], h->G, h->snap,
+                            h->snaps > 0 ? 1 : 0, h->K, h->partials, h->dres, h->stream),
        "residual kernel");
     h->total_launches += 2;
     if (h->snaps < 2) h->snaps++;
@@ -202,8 +202,8 @@ bool capture_interval(dmrt_t *h, int start)
     int cur = start;
     bool ok = true;
     for (long s = 0; s < h->K && ok; ++s) {
-        ok = lbm::launch_step(h->wall, h->buf[cur], h->buf[cur ^ 1], h->S, h->G, h->C, h->block,
-                              h->stream, h->use_pdl) == cudaSuccess;
+        ok = lbm::launch_step(h->wall, h->storage, h->buf[cur], h->buf[cur ^ 1], h->S, h->G, h->C,
+                              h->block, h->stream, h->use_pdl) == cudaSuccess;
         cur ^= 1;
     }
     cudaGraph_t graph = nullptr;
@@ -248,11 +248,9 @@ dmrt_status run_steps(dmrt_t *h, long n)
             }
         }
         for (long s = 0; s < chunk && !graphed; ++s) {
-            float *src = h->buf[h->cur];
-            float *dst = h->buf[h->cur ^ 1];
             CK(h,
-               lbm::launch_step(h->wall, src, dst, h->S, h->G, h->C, h->block, h->stream,
-                                h->use_pdl),
+               lbm::launch_step(h->wall, h->storage, h->buf[h->cur], h->buf[h->cur ^ 1], h->S,
+                                h->G, h->C, h->block, h->stream, h->use_pdl),
                "step kernel");
             h->cur ^= 1;
             h->steps++;
@@ -295,7 +293,8 @@ dmrt_status create_common(dmrt_t **out, const int grid[3], double nu, double alp
         if (opts->residual_interval > 0) K = opts->residual_interval;
         if (opts->residual_interval < 0) return DMRT_ERR_ARG;
     }
-    if (storage != DMRT_STORE_F32) return DMRT_ERR_ARG;
+    if (storage != DMRT_STORE_F32 && storage != DMRT_STORE_BF16 && storage != DMRT_STORE_F16)
+        return DMRT_ERR_ARG;
 
     dmrt_t *h = new (std::nothrow) dmrt();
     if (!h) return DMRT_ERR_OOM;
@@ -332,7 +331,8 @@ dmrt_status create_common(dmrt_t **out, const int grid[3], double nu, double alp
         return st;
     };
     cudaError_t e;
-    const size_t buf_bytes = static_cast<size_t>(h->G.plane) * lbm::kPlanes * sizeof(float);
+    const size_t buf_bytes =
+        static_cast<size_t>(h->G.plane) * lbm::kPlanes * lbm::storage_bytes(h->storage);
     for (int b = 0; b < 2; ++b) {
         e = cudaMalloc(&h->buf[b], buf_bytes);
         if (e != cudaSuccess) return bail(e == cudaErrorMemoryAllocation ? DMRT_ERR_OOM : DMRT_ERR_CUDA);
@@ -461,7 +461,7 @@ dmrt_status dmrt_fields(dmrt_t *h, float *rho, float *u, float *theta, int on_de
         du = u ? h->staging + cells : nullptr;
         dth = theta ? h->staging + 4 * cells : nullptr;
     }
-    CK(h, lbm::launch_fields(h->wall, h->buf[h->cur], h->G, drho, du, dth, h->stream),
+    CK(h, lbm::launch_fields(h->wall, h->storage, h->buf[h->cur], h->G, drho, du, dth, h->stream),
        "fields kernel");
     h->total_launches++;
     if (!on_device) {
@@ -486,8 +486,8 @@ dmrt_status dmrt_nusselt(dmrt_t *h, int wall, double out[3])
     if (h->G.ny < 2) return fail(h, DMRT_ERR_ARG, "dmrt_nusselt: needs ny >= 2");
     DeviceGuard dg(h->device);
     CK(h,
-       lbm::launch_nusselt(h->wall, h->buf[h->cur], h->G, wall, nullptr, h->partials, h->dnu,
-                            h->stream),
+       lbm::launch_nusselt(h->wall, h->storage, h->buf[h->cur], h->G, wall, nullptr, h->partials,
+                           h->dnu, h->stream),
        "nusselt kernel");
     h->total_launches += 2;
     CK(h, cudaMemcpyAsync(out, h->dnu, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream),
@@ -510,8 +510,8 @@ dmrt_status dmrt_nusselt_local(dmrt_t *h, int wall, float *local, int on_device)
         dst = h->staging;
     }
     CK(h,
-       lbm::launch_nusselt(h->wall, h->buf[h->cur], h->G, wall, dst, h->partials, h->dnu,
-                            h->stream),
+       lbm::launch_nusselt(h->wall, h->storage, h->buf[h->cur], h->G, wall, dst, h->partials,
+                           h->dnu, h->stream),
        "nusselt kernel");
     h->total_launches += 2;
     if (!on_device)
@@ -586,7 +586,8 @@ dmrt_status dmrt_set_populations(dmrt_t *h, const float *f, const float *g, int 
         df = h->staging;
         dg_ = h->staging + 19 * cells;
     }
-    CK(h, lbm::launch_set_populations(df, dg_, h->buf[h->cur], h->G, h->stream), "set kernel");
+    CK(h, lbm::launch_set_populations(h->storage, df, dg_, h->buf[h->cur], h->G, h->stream),
+       "set kernel");
     h->total_launches++;
     h->snaps = 0;
     CK(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
@@ -606,7 +607,8 @@ dmrt_status dmrt_get_populations(dmrt_t *h, float *f, float *g, int on_device)
         df = f ? h->staging : nullptr;
         dg_ = g ? h->staging + 19 * cells : nullptr;
     }
-    CK(h, lbm::launch_get_populations(h->buf[h->cur], df, dg_, h->G, h->stream), "get kernel");
+    CK(h, lbm::launch_get_populations(h->storage, h->buf[h->cur], df, dg_, h->G, h->stream),
+       "get kernel");
     h->total_launches++;
     if (!on_device) {
         if (f)
@@ -642,7 +644,8 @@ dmrt_status dmrt_init_fields(dmrt_t *h, const float *rho, const float *u, const 
         du = h->staging + cells;
         dt = h->staging + 4 * cells;
     }
-    CK(h, lbm::launch_init_fields(dr, du, dt, h->buf[h->cur], h->G, h->stream), "init kernel");
+    CK(h, lbm::launch_init_fields(h->storage, dr, du, dt, h->buf[h->cur], h->G, h->stream),
+       "init kernel");
     h->total_launches++;
     h->snaps = 0;
     if (!on_device) CK(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
@@ -684,7 +687,7 @@ dmrt_status dmrt_get_stats(dmrt_t *h, dmrt_stats *out, int reset)
     out->total_launches = h->total_launches;
     out->step_ms = h->step_ms;
     out->timed_steps = h->timed_steps;
-    out->bytes_per_cell = 2.0 * lbm::kPlanes * sizeof(float);
+    out->bytes_per_cell = 2.0 * lbm::kPlanes * lbm::storage_bytes(h->storage);
     if (reset) {
         h->step_launches = h->total_launches = h->timed_steps = 0;
         h->step_ms = 0.0;

@@ -57,17 +57,17 @@ __device__ __forceinline__ void block_sum(double (&v)[N])
 
 // ---------------------------------------------------------------- fields
 
-template <int WALL>
-__global__ void fields_kernel(const float *__restrict__ src, const Geometry G, float *rho,
-                              float *u, float *theta)
+template <int WALL, typename T>
+__global__ void fields_kernel(const T *__restrict__ src, const Geometry G, float *rho, float *u,
+                              float *theta)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
     if (x >= G.nx || y >= G.ny) return;
     float d[19], g[7];
-    pull_f<WALL>(src, G, x, y, z, d);
-    pull_g<WALL>(src, G, x, y, z, g);
+    pull_f<WALL, T>(src, G, x, y, z, d);
+    pull_g<WALL, T>(src, G, x, y, z, g);
     const Macro m = macro_of(d, g);
     const float r = 1.0f + m.drho;
     const long long c = (static_cast<long long>(z) * G.ny + y) * G.nx + x;
@@ -85,9 +85,9 @@ __global__ void fields_kernel(const float *__restrict__ src, const Geometry G, f
 
 // Per block: sums of |dtheta|^2, |theta|^2, |du|^2, |u|^2 against the
 // snapshot, which is then overwritten with the current fields.
-template <int WALL>
+template <int WALL, typename T>
 __global__ void __launch_bounds__(kRedThreads) residual_kernel(
-    const float *__restrict__ src, const Geometry G, float *__restrict__ snap, int have_prev,
+    const T *__restrict__ src, const Geometry G, float *__restrict__ snap, int have_prev,
     double *__restrict__ partials)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -96,8 +96,8 @@ __global__ void __launch_bounds__(kRedThreads) residual_kernel(
     double v[4] = {0.0, 0.0, 0.0, 0.0};
     if (x < G.nx && y < G.ny) {
         float d[19], g[7];
-        pull_f<WALL>(src, G, x, y, z, d);
-        pull_g<WALL>(src, G, x, y, z, g);
+        pull_f<WALL, T>(src, G, x, y, z, d);
+        pull_g<WALL, T>(src, G, x, y, z, g);
         const Macro m = macro_of(d, g);
         const float r = 1.0f + m.drho;
         const float now[4] = {m.T, m.jx / r, m.jy / r, m.jz / r};
@@ -153,8 +153,8 @@ __global__ void __launch_bounds__(kFinThreads) residual_finish(const double *__r
 
 // One block per z row: the local Nu of every wall cell of that row, from the
 // pulled temperatures 1/2 and 3/2 cells off the wall (Eq. (39)).
-template <int WALL>
-__global__ void __launch_bounds__(kRedThreads) nusselt_kernel(const float *__restrict__ src,
+template <int WALL, typename T>
+__global__ void __launch_bounds__(kRedThreads) nusselt_kernel(const T *__restrict__ src,
                                                                const Geometry G, int wall,
                                                                float *local,
                                                                double *__restrict__ partials)
@@ -170,11 +170,11 @@ __global__ void __launch_bounds__(kRedThreads) nusselt_kernel(const float *__res
     double mx = -INFINITY;
     for (int x = threadIdx.x; x < G.nx; x += blockDim.x) {
         float g[7];
-        pull_g<WALL>(src, G, x, y1, z, g);
+        pull_g<WALL, T>(src, G, x, y1, z, g);
         float t1 = 0.f;
 #pragma unroll
         for (int i = 0; i < 7; ++i) t1 += g[i];
-        pull_g<WALL>(src, G, x, y2, z, g);
+        pull_g<WALL, T>(src, G, x, y2, z, g);
         float t2 = 0.f;
 #pragma unroll
         for (int i = 0; i < 7; ++i) t2 += g[i];
@@ -228,21 +228,23 @@ __global__ void __launch_bounds__(kRedThreads) nusselt_finish(const double *__re
 
 // ---------------------------------------------------------------- import / export
 
+template <typename T>
 __global__ void set_populations_kernel(const float *__restrict__ f, const float *__restrict__ g,
-                                       float *__restrict__ dst, const Geometry G)
+                                       T *__restrict__ dst, const Geometry G)
 {
     const long long cells = static_cast<long long>(G.nx) * G.ny * G.nz;
     for (long long c = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; c < cells;
          c += static_cast<long long>(gridDim.x) * blockDim.x) {
         static_for<0, 19>([&](auto I) {
             constexpr int i = decltype(I)::value;
-            dst[i * G.plane + c] = f[i * cells + c] - q19_w(i);
+            Store<T>::st(dst + i * G.plane + c, f[i * cells + c] - q19_w(i));
         });
-        for (int i = 0; i < 7; ++i) dst[(19 + i) * G.plane + c] = g[i * cells + c];
+        for (int i = 0; i < 7; ++i) Store<T>::st(dst + (19 + i) * G.plane + c, g[i * cells + c]);
     }
 }
 
-__global__ void get_populations_kernel(const float *__restrict__ src, float *f, float *g,
+template <typename T>
+__global__ void get_populations_kernel(const T *__restrict__ src, float *f, float *g,
                                        const Geometry G)
 {
     const long long cells = static_cast<long long>(G.nx) * G.ny * G.nz;
@@ -251,17 +253,18 @@ __global__ void get_populations_kernel(const float *__restrict__ src, float *f, 
         if (f)
             static_for<0, 19>([&](auto I) {
                 constexpr int i = decltype(I)::value;
-                f[i * cells + c] = src[i * G.plane + c] + q19_w(i);
+                f[i * cells + c] = Store<T>::ld(src + i * G.plane + c) + q19_w(i);
             });
         if (g)
-            for (int i = 0; i < 7; ++i) g[i * cells + c] = src[(19 + i) * G.plane + c];
+            for (int i = 0; i < 7; ++i) g[i * cells + c] = Store<T>::ld(src + (19 + i) * G.plane + c);
     }
 }
 
 // Equilibrium of given fields: d_i = f_eq,i(rho, u) - w_i (Eq. (17)) and
 // g_i = w_T,i theta (1 + 4 e_i.u), the velocity form of n_eq (Eq. (33)).
+template <typename T>
 __global__ void init_fields_kernel(const float *__restrict__ rho, const float *__restrict__ u,
-                                   const float *__restrict__ theta, float *__restrict__ dst,
+                                   const float *__restrict__ theta, T *__restrict__ dst,
                                    const Geometry G)
 {
     const long long cells = static_cast<long long>(G.nx) * G.ny * G.nz;
@@ -276,12 +279,14 @@ __global__ void init_fields_kernel(const float *__restrict__ rho, const float *_
             constexpr int i = decltype(I)::value;
             constexpr float ex = q19_ex(i), ey = q19_ey(i), ez = q19_ez(i);
             const float ev = ex * vx + ey * vy + ez * vz;
-            dst[i * G.plane + c] = q19_w(i) * (dr + r * (3.0f * ev + 4.5f * ev * ev - 1.5f * vv));
+            Store<T>::st(dst + i * G.plane + c,
+                         q19_w(i) * (dr + r * (3.0f * ev + 4.5f * ev * ev - 1.5f * vv)));
         });
         static_for<0, 7>([&](auto I) {
             constexpr int i = decltype(I)::value;
             constexpr float ex = q7_ex(i), ey = q7_ey(i), ez = q7_ez(i);
-            dst[(19 + i) * G.plane + c] = q7_w(i) * th * (1.0f + 4.0f * (ex * vx + ey * vy + ez * vz));
+            Store<T>::st(dst + (19 + i) * G.plane + c,
+                         q7_w(i) * th * (1.0f + 4.0f * (ex * vx + ey * vy + ez * vz)));
         });
     }
 }
@@ -306,18 +311,18 @@ const dim3 kRedBlock(32, kRedThreads / 32, 1);
 
 // ---------------------------------------------------------------- launchers
 
-cudaError_t launch_fields(int wall, const float *src, const Geometry &G, float *rho, float *u,
-                          float *theta, cudaStream_t s)
+cudaError_t launch_fields(int wall, int storage, const void *src, const Geometry &G, float *rho,
+                          float *u, float *theta, cudaStream_t s)
 {
-    dim3 block(32, 4, 1);
-    dim3 grid = cell_grid(G, block);
-    switch (wall) {
-    case 0: fields_kernel<0><<<grid, block, 0, s>>>(src, G, rho, u, theta); break;
-    case 1: fields_kernel<1><<<grid, block, 0, s>>>(src, G, rho, u, theta); break;
-    case 2: fields_kernel<2><<<grid, block, 0, s>>>(src, G, rho, u, theta); break;
-    case 3: fields_kernel<3><<<grid, block, 0, s>>>(src, G, rho, u, theta); break;
-    default: return cudaErrorInvalidValue;
-    }
+    const dim3 block(32, 4, 1);
+    const dim3 grid = cell_grid(G, block);
+    cudaError_t e = dispatch(wall, storage, [&](auto W, auto *tp) {
+        using T = std::remove_pointer_t<decltype(tp)>;
+        fields_kernel<decltype(W)::value, T>
+            <<<grid, block, 0, s>>>(static_cast<const T *>(src), G, rho, u, theta);
+        return cudaSuccess;
+    });
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
@@ -327,60 +332,75 @@ size_t residual_partials(const Geometry &G)
     return static_cast<size_t>(grid.x) * grid.y * grid.z;
 }
 
-cudaError_t launch_residual(int wall, const float *src, const Geometry &G, float *snap,
-                            int have_prev, int K, double *partials, double *result,
+cudaError_t launch_residual(int wall, int storage, const void *src, const Geometry &G,
+                            float *snap, int have_prev, int K, double *partials, double *result,
                             cudaStream_t s)
 {
-    dim3 grid = cell_grid(G, kRedBlock);
-    switch (wall) {
-    case 0: residual_kernel<0><<<grid, kRedBlock, 0, s>>>(src, G, snap, have_prev, partials); break;
-    case 1: residual_kernel<1><<<grid, kRedBlock, 0, s>>>(src, G, snap, have_prev, partials); break;
-    case 2: residual_kernel<2><<<grid, kRedBlock, 0, s>>>(src, G, snap, have_prev, partials); break;
-    case 3: residual_kernel<3><<<grid, kRedBlock, 0, s>>>(src, G, snap, have_prev, partials); break;
-    default: return cudaErrorInvalidValue;
-    }
-    cudaError_t e = cudaGetLastError();
+    const dim3 grid = cell_grid(G, kRedBlock);
+    cudaError_t e = dispatch(wall, storage, [&](auto W, auto *tp) {
+        using T = std::remove_pointer_t<decltype(tp)>;
+        residual_kernel<decltype(W)::value, T>
+            <<<grid, kRedBlock, 0, s>>>(static_cast<const T *>(src), G, snap, have_prev, partials);
+        return cudaSuccess;
+    });
+    if (e != cudaSuccess) return e;
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const long long nparts = static_cast<long long>(grid.x) * grid.y * grid.z;
     residual_finish<<<1, kFinThreads, 0, s>>>(partials, nparts, have_prev, K, result);
     return cudaGetLastError();
 }
 
-cudaError_t launch_nusselt(int wall_type, const float *src, const Geometry &G, int wall,
-                           float *local, double *partials, double *out3, cudaStream_t s)
+cudaError_t launch_nusselt(int wall_type, int storage, const void *src, const Geometry &G,
+                           int wall, float *local, double *partials, double *out3,
+                           cudaStream_t s)
 {
-    dim3 grid(G.nz), block(kRedThreads);
-    switch (wall_type) {
-    case 0: nusselt_kernel<0><<<grid, block, 0, s>>>(src, G, wall, local, partials); break;
-    case 1: nusselt_kernel<1><<<grid, block, 0, s>>>(src, G, wall, local, partials); break;
-    case 2: nusselt_kernel<2><<<grid, block, 0, s>>>(src, G, wall, local, partials); break;
-    case 3: nusselt_kernel<3><<<grid, block, 0, s>>>(src, G, wall, local, partials); break;
-    default: return cudaErrorInvalidValue;
-    }
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = dispatch(wall_type, storage, [&](auto W, auto *tp) {
+        using T = std::remove_pointer_t<decltype(tp)>;
+        nusselt_kernel<decltype(W)::value, T>
+            <<<G.nz, kRedThreads, 0, s>>>(static_cast<const T *>(src), G, wall, local, partials);
+        return cudaSuccess;
+    });
+    if (e != cudaSuccess) return e;
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     nusselt_finish<<<1, kRedThreads, 0, s>>>(partials, G, out3);
     return cudaGetLastError();
 }
 
-cudaError_t launch_set_populations(const float *f, const float *g, float *dst, const Geometry &G,
-                                   cudaStream_t s)
+cudaError_t launch_set_populations(int storage, const float *f, const float *g, void *dst,
+                                   const Geometry &G, cudaStream_t s)
 {
-    set_populations_kernel<<<flat_grid(G), 256, 0, s>>>(f, g, dst, G);
+    cudaError_t e = dispatch(0, storage, [&](auto, auto *tp) {
+        using T = std::remove_pointer_t<decltype(tp)>;
+        set_populations_kernel<T><<<flat_grid(G), 256, 0, s>>>(f, g, static_cast<T *>(dst), G);
+        return cudaSuccess;
+    });
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
-cudaError_t launch_get_populations(const float *src, float *f, float *g, const Geometry &G,
-                                   cudaStream_t s)
+cudaError_t launch_get_populations(int storage, const void *src, float *f, float *g,
+                                   const Geometry &G, cudaStream_t s)
 {
-    get_populations_kernel<<<flat_grid(G), 256, 0, s>>>(src, f, g, G);
+    cudaError_t e = dispatch(0, storage, [&](auto, auto *tp) {
+        using T = std::remove_pointer_t<decltype(tp)>;
+        get_populations_kernel<T><<<flat_grid(G), 256, 0, s>>>(static_cast<const T *>(src), f, g, G);
+        return cudaSuccess;
+    });
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
-cudaError_t launch_init_fields(const float *rho, const float *u, const float *theta, float *dst,
-                               const Geometry &G, cudaStream_t s)
+cudaError_t launch_init_fields(int storage, const float *rho, const float *u, const float *theta,
+                               void *dst, const Geometry &G, cudaStream_t s)
 {
-    init_fields_kernel<<<flat_grid(G), 256, 0, s>>>(rho, u, theta, dst, G);
+    cudaError_t e = dispatch(0, storage, [&](auto, auto *tp) {
+        using T = std::remove_pointer_t<decltype(tp)>;
+        init_fields_kernel<T><<<flat_grid(G), 256, 0, s>>>(rho, u, theta, static_cast<T *>(dst), G);
+        return cudaSuccess;
+    });
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

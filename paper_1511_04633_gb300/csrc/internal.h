@@ -8,6 +8,8 @@
 
 namespace lbm {
 
+// Storage codes follow dmrt_storage: 0 = float, 1 = bf16, 2 = f16.
+
 // Planes in one population buffer: 19 D3Q19 deviations, then 7 D3Q7.
 constexpr int kPlanes = 26;
 
@@ -22,33 +24,34 @@ void fill_step_geometry(const Geometry &G, StepGeometry &S);
 // One fused time step: pull from `src`, collide, force, store into `dst`.
 // pdl: launch with programmatic stream serialisation (the kernel waits for
 // the previous grid itself).
-cudaError_t launch_step(int wall, const float *src, float *dst, const StepGeometry &S,
-                        const Geometry &G, const CollideParams &C, BlockShape b, cudaStream_t s,
-                        bool pdl);
+cudaError_t launch_step(int wall, int storage, const void *src, void *dst,
+                        const StepGeometry &S, const Geometry &G, const CollideParams &C,
+                        BlockShape b, cudaStream_t s, bool pdl);
 
 // Fields of the pulled populations (any output may be null).
-cudaError_t launch_fields(int wall, const float *src, const Geometry &G, float *rho, float *u,
-                          float *theta, cudaStream_t s);
+cudaError_t launch_fields(int wall, int storage, const void *src, const Geometry &G, float *rho,
+                          float *u, float *theta, cudaStream_t s);
 
 // Residual: compare (theta, u) with `snap`, refresh `snap`, reduce in FP64.
 // `partials` needs residual_partials(G) * 4 doubles; `result` 8 doubles:
 // [0..3] = sums |dtheta|^2, |theta|^2, |du|^2, |u|^2; [4] = r; [5] = nonfinite.
 size_t residual_partials(const Geometry &G);
-cudaError_t launch_residual(int wall, const float *src, const Geometry &G, float *snap,
-                            int have_prev, int K, double *partials, double *result,
+cudaError_t launch_residual(int wall, int storage, const void *src, const Geometry &G,
+                            float *snap, int have_prev, int K, double *partials, double *result,
                             cudaStream_t s);
 
 // Nusselt numbers of wall 0 (hot) / 1 (cold): `partials` needs 3 * nz doubles,
 // `out3` 3 doubles; `local` (nullable) receives the [z][x] map.
-cudaError_t launch_nusselt(int wall_type, const float *src, const Geometry &G, int wall,
-                           float *local, double *partials, double *out3, cudaStream_t s);
+cudaError_t launch_nusselt(int wall_type, int storage, const void *src, const Geometry &G,
+                           int wall, float *local, double *partials, double *out3,
+                           cudaStream_t s);
 
 // Population and field import / export (dense [q][cells] arrays).
-cudaError_t launch_set_populations(const float *f, const float *g, float *dst, const Geometry &G,
-                                   cudaStream_t s);
-cudaError_t launch_get_populations(const float *src, float *f, float *g, const Geometry &G,
-                                   cudaStream_t s);
-cudaError_t launch_init_fields(const float *rho, const float *u, const float *theta, float *dst,
-                               const Geometry &G, cudaStream_t s);
+cudaError_t launch_set_populations(int storage, const float *f, const float *g, void *dst,
+                                   const Geometry &G, cudaStream_t s);
+cudaError_t launch_get_populations(int storage, const void *src, float *f, float *g,
+                                   const Geometry &G, cudaStream_t s);
+cudaError_t launch_init_fields(int storage, const float *rho, const float *u, const float *theta,
+                               void *dst, const Geometry &G, cudaStream_t s);
 
 }  // namespace lbm

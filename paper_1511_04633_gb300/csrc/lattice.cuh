@@ -14,10 +14,52 @@
 // only keeps FP32 rounding relative to the small deviations.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include <cstdint>
 #include <type_traits>
 
 namespace lbm {
+
+// ---------------------------------------------------------------- storage formats
+
+// Population storage in HBM.  Every format holds the deviations f_i - w_i and
+// the energy populations g_i; the collision always runs in FP32.
+//  float         : as is (104 bytes per cell and buffer).
+//  __nv_bfloat16 : rounded to nearest (52 bytes per cell and buffer).
+//  __half        : stored times 2^10, rounded to nearest.  The deviations and
+//                  g_i stay below ~0.2 in magnitude, so the scale keeps values
+//                  down to ~6e-8 out of the FP16 subnormal range while the
+//                  largest stay far below the FP16 maximum.  The scale is a
+//                  power of two, so it adds no rounding of its own.
+template <typename T>
+struct Store;
+
+template <>
+struct Store<float> {
+    static __device__ __forceinline__ float ld(const float *p) { return *p; }
+    static __device__ __forceinline__ void st(float *p, float v) { *p = v; }
+};
+
+template <>
+struct Store<__nv_bfloat16> {
+    static __device__ __forceinline__ float ld(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
+    static __device__ __forceinline__ void st(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+};
+
+template <>
+struct Store<__half> {
+    static constexpr float kScale = 1024.0f;
+    static __device__ __forceinline__ float ld(const __half *p)
+    {
+        return __half2float(*p) * (1.0f / kScale);
+    }
+    static __device__ __forceinline__ void st(__half *p, float v) { *p = __float2half_rn(v * kScale); }
+};
+
+// Storage code of the C ABI (0 = F32, 1 = BF16, 2 = F16) -> element size.
+inline int storage_bytes(int storage) { return storage == 0 ? 4 : 2; }
 
 // ---------------------------------------------------------------- compile-time loops
 
@@ -171,8 +213,8 @@ __device__ constexpr bool dirichlet_axis(int axis)
 // Pull the 19 D3Q19 deviations that arrive at cell (x,y,z) from the stored
 // post-collision state `src` (planes 0..18).  A link that leaves the box is
 // replaced by half-way bounce-back from the resting wall: f_i(x) = f*_opp(x).
-template <int WALL>
-__device__ __forceinline__ void pull_f(const float *__restrict__ src, const Geometry &G,
+template <int WALL, typename T>
+__device__ __forceinline__ void pull_f(const T *__restrict__ src, const Geometry &G,
                                        int x, int y, int z, float d[19])
 {
     const int nx = G.nx, ny = G.ny, nz = G.nz;
@@ -186,13 +228,13 @@ __device__ __forceinline__ void pull_f(const float *__restrict__ src, const Geom
         constexpr int ex = q19_ex(i), ey = q19_ey(i), ez = q19_ez(i);
         constexpr int opp = q19_opp(i);
         if constexpr (i == 0) {
-            d[0] = src[self];
+            d[0] = Store<T>::ld(src + self);
         } else if constexpr (WALL == 0) {
             int sx = x - ex, sy = y - ey, sz = z - ez;
             sx = sx < 0 ? nx - 1 : (sx >= nx ? 0 : sx);
             sy = sy < 0 ? ny - 1 : (sy >= ny ? 0 : sy);
             sz = sz < 0 ? nz - 1 : (sz >= nz ? 0 : sz);
-            d[i] = src[i * P + (sz * ny + sy) * nx + sx];
+            d[i] = Store<T>::ld(src + i * P + (sz * ny + sy) * nx + sx);
         } else {
             bool out = false;
             if constexpr (ex == 1) out = out || xlo;
@@ -203,7 +245,7 @@ __device__ __forceinline__ void pull_f(const float *__restrict__ src, const Geom
             if constexpr (ez == -1) out = out || zhi;
             const int off = ex + ey * nx + ez * nx * ny;
             const long long a = out ? (opp * P + self) : (i * P + (self - off));
-            d[i] = src[a];
+            d[i] = Store<T>::ld(src + a);
         }
     });
 }
@@ -214,27 +256,27 @@ __device__ __forceinline__ void pull_f(const float *__restrict__ src, const Geom
 // an adiabatic wall bounce-back g_i(x) = g*_opp(x).  theta_w is +1/2 on the
 // hot wall y = 0, -1/2 on the cold wall y = H and 1/2 - (y + 1/2)/ny on the
 // linear x / z walls of Types 2 and 3 (Eqs. (6),(7),(9),(10)).
-template <int WALL>
-__device__ __forceinline__ void pull_g(const float *__restrict__ src, const Geometry &G,
+template <int WALL, typename T>
+__device__ __forceinline__ void pull_g(const T *__restrict__ src, const Geometry &G,
                                        int x, int y, int z, float g[7])
 {
     const int nx = G.nx, ny = G.ny, nz = G.nz;
     const long long P = G.plane;
     const int self = (z * ny + y) * nx + x;
-    const float *gs = src + 19 * P;
+    const T *gs = src + 19 * P;
     const float th_lin = 0.5f - (static_cast<float>(y) + 0.5f) * G.inv_ny;
     static_for<0, 7>([&](auto I) {
         constexpr int i = decltype(I)::value;
         constexpr int ex = q7_ex(i), ey = q7_ey(i), ez = q7_ez(i);
         constexpr int opp = q7_opp(i);
         if constexpr (i == 0) {
-            g[0] = gs[self];
+            g[0] = Store<T>::ld(gs + self);
         } else if constexpr (WALL == 0) {
             int sx = x - ex, sy = y - ey, sz = z - ez;
             sx = sx < 0 ? nx - 1 : (sx >= nx ? 0 : sx);
             sy = sy < 0 ? ny - 1 : (sy >= ny ? 0 : sy);
             sz = sz < 0 ? nz - 1 : (sz >= nz ? 0 : sz);
-            g[i] = gs[i * P + (sz * ny + sy) * nx + sx];
+            g[i] = Store<T>::ld(gs + i * P + (sz * ny + sy) * nx + sx);
         } else {
             constexpr int axis = ex != 0 ? 0 : (ey != 0 ? 1 : 2);
             bool out;
@@ -246,7 +288,7 @@ __device__ __forceinline__ void pull_g(const float *__restrict__ src, const Geom
             else out = (z == nz - 1);
             const int off = ex + ey * nx + ez * nx * ny;
             const long long a = out ? (opp * P + self) : (i * P + (self - off));
-            float v = gs[a];
+            float v = Store<T>::ld(gs + a);
             if constexpr (dirichlet_axis<WALL>(axis)) {
                 float tw;
                 if constexpr (axis == 1) tw = (ey == 1) ? 0.5f : -0.5f;
@@ -280,6 +322,35 @@ __device__ __forceinline__ Macro macro_of(const float d[19], const float g[7])
     });
     static_for<0, 7>([&](auto I) { m.T += g[decltype(I)::value]; });
     return m;
+}
+
+// ---------------------------------------------------------------- host dispatch
+
+// Calls f(std::integral_constant<int, WALL>{}, (T *)nullptr) for the runtime
+// wall type (0..3) and storage code (0 = float, 1 = bf16, 2 = f16); the null
+// pointer only carries the storage type.
+template <typename T, typename F>
+inline cudaError_t dispatch_wall(int wall, F &&f)
+{
+    T *tp = nullptr;
+    switch (wall) {
+    case 0: return f(std::integral_constant<int, 0>{}, tp);
+    case 1: return f(std::integral_constant<int, 1>{}, tp);
+    case 2: return f(std::integral_constant<int, 2>{}, tp);
+    case 3: return f(std::integral_constant<int, 3>{}, tp);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename F>
+inline cudaError_t dispatch(int wall, int storage, F &&f)
+{
+    switch (storage) {
+    case 0: return dispatch_wall<float>(wall, f);
+    case 1: return dispatch_wall<__nv_bfloat16>(wall, f);
+    case 2: return dispatch_wall<__half>(wall, f);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace lbm

@@ -192,15 +192,15 @@ __device__ __forceinline__ void collide_pairs(const CollideParams &C, float d[19
 // Pull of walled boxes (Types 1-3) through the precomputed offset tables:
 // plane q of the neighbour at self + nb[q], or the bounce-back source at
 // self + bb[q] when the link leaves the box (Sec. 3.1 and 3.2 wall rules).
-template <int WALL>
-__device__ __forceinline__ void pull_tables(const float *__restrict__ src, const StepGeometry &S,
+template <int WALL, typename T>
+__device__ __forceinline__ void pull_tables(const T *__restrict__ src, const StepGeometry &S,
                                             unsigned self, int x, int y, int z, float d[19],
                                             float g[7])
 {
     const bool xlo = (x == 0), xhi = (x == S.nx - 1);
     const bool ylo = (y == 0), yhi = (y == S.ny - 1);
     const bool zlo = (z == 0), zhi = (z == S.nz - 1);
-    d[0] = src[self];
+    d[0] = Store<T>::ld(src + self);
     static_for<1, 19>([&](auto I) {
         constexpr int i = decltype(I)::value;
         constexpr int ex = q19_ex(i), ey = q19_ey(i), ez = q19_ez(i);
@@ -211,9 +211,9 @@ __device__ __forceinline__ void pull_tables(const float *__restrict__ src, const
         if constexpr (ey == -1) out = out || yhi;
         if constexpr (ez == 1) out = out || zlo;
         if constexpr (ez == -1) out = out || zhi;
-        d[i] = src[self + static_cast<unsigned>(out ? S.bb[i] : S.nb[i])];
+        d[i] = Store<T>::ld(src + (self + static_cast<unsigned>(out ? S.bb[i] : S.nb[i])));
     });
-    g[0] = src[self + static_cast<unsigned>(S.nb[19])];
+    g[0] = Store<T>::ld(src + (self + static_cast<unsigned>(S.nb[19])));
     const float th_lin = 0.5f - (static_cast<float>(y) + 0.5f) * S.inv_ny;
     static_for<1, 7>([&](auto I) {
         constexpr int i = decltype(I)::value;
@@ -226,7 +226,7 @@ __device__ __forceinline__ void pull_tables(const float *__restrict__ src, const
         else if constexpr (i == 4) out = yhi;
         else if constexpr (i == 5) out = zlo;
         else out = zhi;
-        float v = src[self + static_cast<unsigned>(out ? S.bb[19 + i] : S.nb[19 + i])];
+        float v = Store<T>::ld(src + (self + static_cast<unsigned>(out ? S.bb[19 + i] : S.nb[19 + i])));
         if constexpr (dirichlet_axis<WALL>(axis)) {
             float tw;
             if constexpr (axis == 1) tw = (ey == 1) ? 0.5f : -0.5f;
@@ -246,10 +246,10 @@ __device__ __forceinline__ void pull_tables(const float *__restrict__ src, const
 #define DMRT_STEP_MIN_BLOCKS 4
 #endif
 
-template <int WALL>
-__global__ void __launch_bounds__(256, DMRT_STEP_MIN_BLOCKS) step_kernel(const float *__restrict__ src,
-                                                   float *__restrict__ dst, const StepGeometry S,
-                                                   const Geometry G, const CollideParams C)
+template <int WALL, typename T>
+__global__ void __launch_bounds__(256, DMRT_STEP_MIN_BLOCKS)
+    step_kernel(const T *__restrict__ src, T *__restrict__ dst, const StepGeometry S,
+                const Geometry G, const CollideParams C)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -265,19 +265,19 @@ __global__ void __launch_bounds__(256, DMRT_STEP_MIN_BLOCKS) step_kernel(const f
     const unsigned self = (static_cast<unsigned>(z) * S.ny + y) * S.nx + x;
     float d[19], g[7];
     if constexpr (WALL == 0) {
-        pull_f<0>(src, G, x, y, z, d);
-        pull_g<0>(src, G, x, y, z, g);
+        pull_f<0, T>(src, G, x, y, z, d);
+        pull_g<0, T>(src, G, x, y, z, g);
     } else {
-        pull_tables<WALL>(src, S, self, x, y, z, d, g);
+        pull_tables<WALL, T>(src, S, self, x, y, z, d, g);
     }
     collide_pairs(C, d, g);
     static_for<0, 19>([&](auto I) {
         constexpr int i = decltype(I)::value;
-        dst[self + i * S.plane] = d[i];
+        Store<T>::st(dst + (self + i * S.plane), d[i]);
     });
     static_for<0, 7>([&](auto I) {
         constexpr int i = decltype(I)::value;
-        dst[self + (19 + i) * S.plane] = g[i];
+        Store<T>::st(dst + (self + (19 + i) * S.plane), g[i]);
     });
 }
 
@@ -303,11 +303,9 @@ void fill_step_geometry(const Geometry &G, StepGeometry &S)
     }
 }
 
-namespace {
-
-template <int WALL>
-cudaError_t launch_step_t(const float *src, float *dst, const StepGeometry &S, const Geometry &G,
-                          const CollideParams &C, BlockShape b, cudaStream_t s, bool pdl)
+cudaError_t launch_step(int wall, int storage, const void *src, void *dst,
+                        const StepGeometry &S, const Geometry &G, const CollideParams &C,
+                        BlockShape b, cudaStream_t s, bool pdl)
 {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((G.nx + b.bx - 1) / b.bx, (G.ny + b.by - 1) / b.by, G.nz);
@@ -319,23 +317,11 @@ cudaError_t launch_step_t(const float *src, float *dst, const StepGeometry &S, c
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = pdl ? 1 : 0;
-    return cudaLaunchKernelEx(&cfg, step_kernel<WALL>, src, dst, S, G, C);
-}
-
-}  // namespace
-
-cudaError_t launch_step(int wall, const float *src, float *dst, const StepGeometry &S,
-                        const Geometry &G, const CollideParams &C, BlockShape b, cudaStream_t s,
-                        bool pdl)
-{
-    cudaError_t e;
-    switch (wall) {
-    case 0: e = launch_step_t<0>(src, dst, S, G, C, b, s, pdl); break;
-    case 1: e = launch_step_t<1>(src, dst, S, G, C, b, s, pdl); break;
-    case 2: e = launch_step_t<2>(src, dst, S, G, C, b, s, pdl); break;
-    case 3: e = launch_step_t<3>(src, dst, S, G, C, b, s, pdl); break;
-    default: return cudaErrorInvalidValue;
-    }
+    cudaError_t e = dispatch(wall, storage, [&](auto W, auto *tp) {
+        using T = std::remove_pointer_t<decltype(tp)>;
+        return cudaLaunchKernelEx(&cfg, step_kernel<decltype(W)::value, T>,
+                                  static_cast<const T *>(src), static_cast<T *>(dst), S, G, C);
+    });
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }

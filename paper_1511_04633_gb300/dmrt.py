@@ -22,7 +22,7 @@ from . import build as _build
 
 OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_DIVERGED, ERR_TIMEOUT = range(6)
 WALL_PERIODIC, WALL_TYPE1, WALL_TYPE2, WALL_TYPE3 = 0, 1, 2, 3
-STORE_F32 = 0
+STORE_F32, STORE_BF16, STORE_F16 = 0, 1, 2
 
 HEADER = os.path.join(_build.INCLUDE, "dmrt.h")
 
