@@ -7,6 +7,11 @@ Nusselt numbers, i.e. one pass of the whole hot path.  Throughput is MLUPS
 (million coupled D3Q19 + D3Q7 cell updates per second).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl dmrt|reference]
+                    [--storage f32|bf16|f16] [--grid N --wall T --ra RA]
+
+The defaults measure the 128^3 Type 2 cavity in FP32 storage; --grid 256
+--wall 3 --ra 1e6 --storage bf16 (or f16) measures the 256^3 Type 3 cavity with
+16-bit population storage.
 
 With N > 1 (launched by torchrun) every rank runs an independent replica of
 the same cavity ("replicas only": a single cavity is not sharded); the
@@ -34,10 +39,17 @@ GRID = (128, 128, 128)
 WALL = 2
 RA, PR, MA = 1e5, 0.71, 0.1
 LBM_STEPS_PER_STEP = 100
-BYTES_PER_CELL = 208  # 26 float32 populations read + written per cell update
+STORAGES = {"f32": 0, "bf16": 1, "f16": 2}
 METRIC = "MLUPS and % HBM roofline per coupled step"
-WORKLOAD = ("128^3 cavity, Type 2 (linear side walls), Ra=1e5, Pr=0.71, Ma=0.1, from rest; "
-            "one step = 100 fused LBM steps + residual + hot-wall Nu")
+WALL_NAMES = {1: "Type 1 (adiabatic side walls)", 2: "Type 2 (linear side walls)",
+              3: "Type 3 (linear x walls, adiabatic z walls)"}
+
+
+def workload(args) -> str:
+    n = args.grid
+    return (f"{n}^3 cavity, {WALL_NAMES[args.wall]}, Ra={args.ra:g}, Pr={PR}, Ma={MA}, from rest, "
+            f"{args.storage} population storage; one step = {args.inner} fused LBM steps + "
+            f"residual + hot-wall Nu")
 STEP_KERNEL_SOURCES = ["paper_1511_04633_gb300/csrc/step.cu",
                        "paper_1511_04633_gb300/csrc/lattice.cuh"]
 
@@ -156,29 +168,32 @@ def step_kernel_digest() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
+def profiled_traffic(storage: str = "f32", wall: int = 2):
     """DRAM bytes per step-kernel launch from the committed ncu summary, only
-    if it was taken on the current kernel sources."""
+    if it was taken on the current kernel sources for this storage and wall."""
     path = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
     try:
         with open(path) as fh:
             t = json.load(fh)
     except (OSError, ValueError):
         return None
-    if t.get("source_digest") != step_kernel_digest():
-        return None
-    return t.get("dram_bytes_per_launch")
+    recs = t if isinstance(t, list) else [t]
+    for rec in recs:
+        if (rec.get("source_digest") == step_kernel_digest()
+                and rec.get("storage", "f32") == storage and rec.get("wall", 2) == wall):
+            return rec.get("dram_bytes_per_launch")
+    return None
 
 
 # ---------------------------------------------------------------- CPU oracle legs
 
-def oracle_sample(seconds: float = 12.0, max_steps: int = 400):
+def oracle_sample(grid, wall, ra, seconds: float = 12.0, max_steps: int = 400):
     """Time the FP64 oracle on the benchmark cavity: steps from rest until
     `seconds` of CPU work (at least 2).  Returns (MLUPS, cores, steps)."""
     import oracle
-    o = oracle.Oracle.physical(GRID, WALL, RA, PR, MA)
+    o = oracle.Oracle.physical(grid, wall, ra, PR, MA)
     o.step(1)  # first touch of the buffers
-    cells = GRID[0] * GRID[1] * GRID[2]
+    cells = grid[0] * grid[1] * grid[2]
     n = 0
     t0 = time.perf_counter()
     while n < 2 or (time.perf_counter() - t0 < seconds and n < max_steps):
@@ -196,8 +211,9 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     import oracle
-    o = oracle.Oracle.physical(GRID, WALL, RA, PR, MA)
-    cells = GRID[0] * GRID[1] * GRID[2]
+    grid = (args.grid,) * 3
+    o = oracle.Oracle.physical(grid, args.wall, args.ra, PR, MA)
+    cells = grid[0] * grid[1] * grid[2]
     per_step = args.ref_lbm_steps
     for _ in range(args.warmup):
         o.step(per_step)
@@ -208,14 +224,14 @@ def run_reference(args, rank, world):
     o.close()
     value = cells * per_step * args.steps / dt / 1e6
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    sample = f"{per_step} oracle LBM steps of the 128^3 Type 2 cavity per benchmark step"
+    sample = f"{per_step} FP64 oracle LBM step(s) of the {args.grid}^3 Type {args.wall} cavity per benchmark step"
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "grid": list(GRID), "wall_type": WALL, "Ra": RA,
-                   "parallelism": "replicas"},
+        "config": {"workload": workload(args), "grid": list(grid), "wall_type": args.wall,
+                   "Ra": args.ra, "parallelism": "replicas"},
         "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -240,8 +256,10 @@ def run_dmrt(args, rank, local, world):
     torch.cuda.set_stream(stream)
     dmrt.load()
 
-    cells = GRID[0] * GRID[1] * GRID[2]
-    cav = dmrt.Cavity(GRID, RA, PR, MA, WALL)
+    grid = (args.grid,) * 3
+    cells = grid[0] * grid[1] * grid[2]
+    storage = STORAGES[args.storage]
+    cav = dmrt.Cavity(grid, args.ra, PR, MA, args.wall, storage=storage)
     dmrt.dmrt_set_stream(cav.h, stream)
     inner = args.inner
 
@@ -276,15 +294,16 @@ def run_dmrt(args, rank, local, world):
 
     # roofline of the dominant kernel (the fused step), from its own events
     launch_s = stats["step_ms"] / 1e3 / max(stats["timed_steps"], 1)
-    achieved = BYTES_PER_CELL * cells / launch_s / 1e9
+    bytes_per_cell = stats["bytes_per_cell"]
+    achieved = bytes_per_cell * cells / launch_s / 1e9
     peak, peak_src = measured_peaks()
-    traffic = profiled_traffic()
+    traffic = profiled_traffic(args.storage, args.wall)
 
     # end to end through the C ABI with host buffers: upload the start fields
     # from pinned memory, step, read the fields and Nu back
-    rho_h = torch.ones(GRID[::-1], dtype=torch.float32).pin_memory()
-    u_h = torch.zeros((3,) + GRID[::-1], dtype=torch.float32).pin_memory()
-    th_h = torch.zeros(GRID[::-1], dtype=torch.float32).pin_memory()
+    rho_h = torch.ones(grid[::-1], dtype=torch.float32).pin_memory()
+    u_h = torch.zeros((3,) + grid[::-1], dtype=torch.float32).pin_memory()
+    th_h = torch.zeros(grid[::-1], dtype=torch.float32).pin_memory()
     rho_o = torch.empty_like(rho_h).pin_memory()
     u_o = torch.empty_like(u_h).pin_memory()
     th_o = torch.empty_like(th_h).pin_memory()
@@ -317,23 +336,28 @@ def run_dmrt(args, rank, local, world):
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        mlups, cores, n = oracle_sample(args.cpu_seconds)
+        mlups, cores, n = oracle_sample(grid, args.wall, args.ra, args.cpu_seconds)
         cpu = {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle",
-               "sample": f"{n} FP64 oracle LBM steps of the 128^3 Type 2 cavity from rest"}
+               "sample": f"{n} FP64 oracle LBM steps of the {args.grid}^3 Type {args.wall} "
+                         f"cavity from rest"}
 
     line = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "grid": list(GRID), "wall_type": WALL, "Ra": RA, "Pr": PR,
-                   "Ma": MA, "lbm_steps_per_step": inner, "storage": "f32 deviations",
-                   "l2": "inputs larger than L2 (two 218 MB population buffers)",
+        "config": {"workload": workload(args), "grid": list(grid), "wall_type": args.wall,
+                   "Ra": args.ra, "Pr": PR, "Ma": MA, "lbm_steps_per_step": inner,
+                   "storage": f"{args.storage} deviations from rest equilibrium"
+                              + ("" if storage == 0 else ", stochastic rounding"),
+                   "l2": f"inputs larger than L2 (two {bytes_per_cell / 2 * cells / 1e6:.0f} MB "
+                         f"population buffers)" if bytes_per_cell / 2 * cells > 129e6
+                         else "inputs fit in L2: not a DRAM measurement",
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
-                     "kernel": "step_kernel<2>", "bytes_per_cell": BYTES_PER_CELL,
-                     "launch_us": launch_s * 1e6},
+                     "kernel": f"step_kernel<{args.wall}, {args.storage}>",
+                     "bytes_per_cell": bytes_per_cell, "launch_us": launch_s * 1e6},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
@@ -356,6 +380,10 @@ def main(argv=None):
     ap.add_argument("--ref-lbm-steps", type=int, default=1,
                     help="oracle LBM steps per reference benchmark step")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--storage", choices=sorted(STORAGES), default="f32")
+    ap.add_argument("--grid", type=int, default=GRID[0], help="cubic cavity edge")
+    ap.add_argument("--wall", type=int, choices=[1, 2, 3], default=WALL)
+    ap.add_argument("--ra", type=float, default=RA)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args(argv)
     if args.warmup < 3:

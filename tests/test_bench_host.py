@@ -69,9 +69,11 @@ def test_traffic_is_dropped_when_the_kernel_changed(tmp_path, monkeypatch):
         p.parent.mkdir(parents=True, exist_ok=True)
         p.write_text("kernel v1")
     (tmp_path / "profiles").mkdir()
-    rec = {"source_digest": bench.step_kernel_digest(), "dram_bytes_per_launch": 123}
+    rec = {"source_digest": bench.step_kernel_digest(), "dram_bytes_per_launch": 123,
+           "storage": "f32", "wall": 2}
     (tmp_path / "profiles" / "step_kernel_traffic.json").write_text(json.dumps(rec))
     assert bench.profiled_traffic() == 123
+    assert bench.profiled_traffic("bf16", 2) is None
     (tmp_path / bench.STEP_KERNEL_SOURCES[0]).write_text("kernel v2")
     assert bench.profiled_traffic() is None
 
