@@ -67,15 +67,28 @@ typedef enum {
     DMRT_STORE_F16 = 2,
 } dmrt_storage;
 
-/* Optional creation settings; pass NULL for the defaults. */
+/* Rounding of the 16-bit stores (no effect on F32).  A 16-bit store drops
+ * any per-step change below half an ulp, so with round-to-nearest a slowly
+ * evolving solution stagnates; stochastic rounding keeps the expected stored
+ * value equal to the FP32 value (random bits: a PCG hash of the cell index and
+ * the step number).  AUTO = STOCHASTIC for BF16 and F16. */
+typedef enum {
+    DMRT_ROUND_AUTO = 0,
+    DMRT_ROUND_NEAREST = 1,
+    DMRT_ROUND_STOCHASTIC = 2,
+} dmrt_rounding;
+
+/* Optional creation settings; pass NULL for the defaults (zero-initialised
+ * fields select the defaults). */
 typedef struct dmrt_opts {
     int storage;           /* dmrt_storage; default DMRT_STORE_F32 */
-    int residual_interval; /* K of the convergence residual; default 100 */
+    int residual_interval; /* K of the convergence residual; 0 = 100 */
+    int rounding;          /* dmrt_rounding; default DMRT_ROUND_AUTO */
 } dmrt_opts;
 
 /* Derived lattice parameters of a handle (read-only view). */
 typedef struct dmrt_params {
-    int nx, ny, nz, wall_type, storage, residual_interval;
+    int nx, ny, nz, wall_type, storage, residual_interval, rounding;
     double nu, alpha, gbeta;   /* lattice viscosity, diffusivity, g*beta*dT */
     double tau_nu, tau_alpha;  /* 3 nu + 1/2 (Eq. (26)); 1/2 + 4 alpha (Eq. (36)) */
     long steps;                /* time steps taken since creation / last reset */

@@ -23,6 +23,7 @@ struct dmrt {
     int device = 0;
     int wall = 1;
     int storage = DMRT_STORE_F32;
+    bool stochastic = false;  // 16-bit stores round stochastically
     int K = 100;
     double nu = 0, alpha = 0, gbeta = 0;
     Geometry G{};
@@ -202,8 +203,8 @@ bool capture_interval(dmrt_t *h, int start)
     int cur = start;
     bool ok = true;
     for (long s = 0; s < h->K && ok; ++s) {
-        ok = lbm::launch_step(h->wall, h->storage, h->buf[cur], h->buf[cur ^ 1], h->S, h->G, h->C,
-                              h->block, h->stream, h->use_pdl) == cudaSuccess;
+        ok = lbm::launch_step(h->wall, h->storage, h->stochastic, h->buf[cur], h->buf[cur ^ 1],
+                              h->S, h->G, h->C, h->block, h->stream, h->use_pdl) == cudaSuccess;
         cur ^= 1;
     }
     cudaGraph_t graph = nullptr;
@@ -249,8 +250,9 @@ dmrt_status run_steps(dmrt_t *h, long n)
         }
         for (long s = 0; s < chunk && !graphed; ++s) {
             CK(h,
-               lbm::launch_step(h->wall, h->storage, h->buf[h->cur], h->buf[h->cur ^ 1], h->S,
-                                h->G, h->C, h->block, h->stream, h->use_pdl),
+               lbm::launch_step(h->wall, h->storage, h->stochastic, h->buf[h->cur],
+                                h->buf[h->cur ^ 1], h->S, h->G, h->C, h->block, h->stream,
+                                h->use_pdl),
                "step kernel");
             h->cur ^= 1;
             h->steps++;
@@ -287,12 +289,14 @@ dmrt_status create_common(dmrt_t **out, const int grid[3], double nu, double alp
     if (!(nu > 0.0) || !(alpha > 0.0) || !std::isfinite(nu) || !std::isfinite(alpha) ||
         !std::isfinite(gbeta))
         return DMRT_ERR_ARG;
-    int storage = DMRT_STORE_F32, K = 100;
+    int storage = DMRT_STORE_F32, K = 100, rounding = DMRT_ROUND_AUTO;
     if (opts) {
         storage = opts->storage;
+        rounding = opts->rounding;
         if (opts->residual_interval > 0) K = opts->residual_interval;
         if (opts->residual_interval < 0) return DMRT_ERR_ARG;
     }
+    if (rounding < DMRT_ROUND_AUTO || rounding > DMRT_ROUND_STOCHASTIC) return DMRT_ERR_ARG;
     if (storage != DMRT_STORE_F32 && storage != DMRT_STORE_BF16 && storage != DMRT_STORE_F16)
         return DMRT_ERR_ARG;
 
@@ -304,6 +308,7 @@ dmrt_status create_common(dmrt_t **out, const int grid[3], double nu, double alp
     }
     h->wall = wall_type;
     h->storage = storage;
+    h->stochastic = storage != DMRT_STORE_F32 && rounding != DMRT_ROUND_NEAREST;
     h->K = K;
     h->nu = nu;
     h->alpha = alpha;
@@ -331,8 +336,9 @@ dmrt_status create_common(dmrt_t **out, const int grid[3], double nu, double alp
         return st;
     };
     cudaError_t e;
+    // populations, then a 256-byte tail holding the step counter
     const size_t buf_bytes =
-        static_cast<size_t>(h->G.plane) * lbm::kPlanes * lbm::storage_bytes(h->storage);
+        static_cast<size_t>(h->G.plane) * lbm::kPlanes * lbm::storage_bytes(h->storage) + 256;
     for (int b = 0; b < 2; ++b) {
         e = cudaMalloc(&h->buf[b], buf_bytes);
         if (e != cudaSuccess) return bail(e == cudaErrorMemoryAllocation ? DMRT_ERR_OOM : DMRT_ERR_CUDA);
@@ -660,6 +666,8 @@ dmrt_status dmrt_get_params(const dmrt_t *h, dmrt_params *out)
     out->nz = h->G.nz;
     out->wall_type = h->wall;
     out->storage = h->storage;
+    out->rounding = h->storage == DMRT_STORE_F32 ? DMRT_ROUND_NEAREST
+                    : (h->stochastic ? DMRT_ROUND_STOCHASTIC : DMRT_ROUND_NEAREST);
     out->residual_interval = h->K;
     out->nu = h->nu;
     out->alpha = h->alpha;

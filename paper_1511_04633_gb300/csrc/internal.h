@@ -22,9 +22,11 @@ struct BlockShape {
 void fill_step_geometry(const Geometry &G, StepGeometry &S);
 
 // One fused time step: pull from `src`, collide, force, store into `dst`.
+// stochastic: 16-bit stores round stochastically (ignored for FP32).
 // pdl: launch with programmatic stream serialisation (the kernel waits for
-// the previous grid itself).
-cudaError_t launch_step(int wall, int storage, const void *src, void *dst,
+// the previous grid itself).  Each buffer holds kPlanes * plane elements and
+// then one 32-bit step counter (used by stochastic rounding).
+cudaError_t launch_step(int wall, int storage, bool stochastic, const void *src, void *dst,
                         const StepGeometry &S, const Geometry &G, const CollideParams &C,
                         BlockShape b, cudaStream_t s, bool pdl);
 

@@ -61,6 +61,58 @@ struct Store<__half> {
 // Storage code of the C ABI (0 = F32, 1 = BF16, 2 = F16) -> element size.
 inline int storage_bytes(int storage) { return storage == 0 ? 4 : 2; }
 
+// ---------------------------------------------------------------- stochastic rounding
+
+// A 16-bit store rounds away every per-step change smaller than half an ulp,
+// so a slowly evolving population stops evolving (the solution stagnates).
+// Stochastic rounding keeps the expected stored value equal to the FP32 value:
+// it rounds up with probability (v - lower) / ulp.  The random bits come from
+// the PCG hash (one step of the 32-bit LCG with multiplier 747796405 and
+// increment 2891336453, then the RXS-M-XS output permutation; O'Neill 2014, in
+// the single-call form of Jarzynski and Olano, JCGT 9(3), 2020) of the cell
+// index and the step number, spread over the 26 planes of a cell by a Weyl
+// sequence with the golden-ratio increment.
+__host__ __device__ __forceinline__ unsigned pcg_hash(unsigned v)
+{
+    const unsigned state = v * 747796405u + 2891336453u;
+    const unsigned word = ((state >> ((state >> 28u) + 4u)) ^ state) * 277803737u;
+    return (word >> 22u) ^ word;
+}
+
+constexpr unsigned kWeyl = 0x9E3779B9u;  // 2^32 / golden ratio
+
+template <typename T>
+struct StoreSR;
+
+// bfloat16 keeps the high 16 bits of the FP32 pattern: adding 16 random bits
+// below them and truncating rounds the magnitude up with the right
+// probability (a carry into the exponent is the correct next value).
+template <>
+struct StoreSR<__nv_bfloat16> {
+    static __device__ __forceinline__ void st(__nv_bfloat16 *p, float v, unsigned r)
+    {
+        const unsigned bits = __float_as_uint(v) + (r >> 16);
+        *reinterpret_cast<unsigned short *>(p) = static_cast<unsigned short>(bits >> 16);
+    }
+};
+
+// half: add uniform noise in [-ulp/2, ulp/2) of the half value, then round to
+// nearest, which rounds up with probability (v - lower) / ulp.  The ulp of a
+// half with the FP32 exponent e is 2^(e - 127 - 10), and 2^-24 in the half
+// subnormal range.
+template <>
+struct StoreSR<__half> {
+    static __device__ __forceinline__ void st(__half *p, float v, unsigned r)
+    {
+        const float s = v * Store<__half>::kScale;
+        const int e = static_cast<int>((__float_as_uint(s) >> 23) & 0xFFu);
+        const int ue = e - 10 > 103 ? e - 10 : 103;
+        const float ulp = __uint_as_float(static_cast<unsigned>(ue) << 23);
+        const float u = static_cast<float>(r >> 8) * (1.0f / 16777216.0f) - 0.5f;
+        *p = __float2half_rn(fmaf(u, ulp, s));
+    }
+};
+
 // ---------------------------------------------------------------- compile-time loops
 
 template <int B, int E, typename F>

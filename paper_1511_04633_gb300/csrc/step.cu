@@ -246,7 +246,12 @@ __device__ __forceinline__ void pull_tables(const T *__restrict__ src, const Ste
 #define DMRT_STEP_MIN_BLOCKS 4
 #endif
 
-template <int WALL, typename T>
+// SR = true: 16-bit stores round stochastically.  The step number that seeds
+// the random bits lives in a word after the populations of each buffer
+// (`counter_at` elements in): every step reads it from its source buffer and
+// one thread writes it, plus one, to the destination, so a replayed graph
+// still draws fresh bits each step and runs stay bitwise reproducible.
+template <int WALL, typename T, bool SR>
 __global__ void __launch_bounds__(256, DMRT_STEP_MIN_BLOCKS)
     step_kernel(const T *__restrict__ src, T *__restrict__ dst, const StepGeometry S,
                 const Geometry G, const CollideParams C)
@@ -271,14 +276,29 @@ __global__ void __launch_bounds__(256, DMRT_STEP_MIN_BLOCKS)
         pull_tables<WALL, T>(src, S, self, x, y, z, d, g);
     }
     collide_pairs(C, d, g);
-    static_for<0, 19>([&](auto I) {
-        constexpr int i = decltype(I)::value;
-        Store<T>::st(dst + (self + i * S.plane), d[i]);
-    });
-    static_for<0, 7>([&](auto I) {
-        constexpr int i = decltype(I)::value;
-        Store<T>::st(dst + (self + (19 + i) * S.plane), g[i]);
-    });
+    if constexpr (SR) {
+        const size_t counter_at = static_cast<size_t>(kPlanes) * S.plane;
+        const unsigned step = *reinterpret_cast<const unsigned *>(src + counter_at);
+        if (self == 0) *reinterpret_cast<unsigned *>(dst + counter_at) = step + 1u;
+        const unsigned base = pcg_hash(self ^ pcg_hash(step));
+        static_for<0, 19>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            StoreSR<T>::st(dst + (self + i * S.plane), d[i], base + i * kWeyl);
+        });
+        static_for<0, 7>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            StoreSR<T>::st(dst + (self + (19 + i) * S.plane), g[i], base + (19 + i) * kWeyl);
+        });
+    } else {
+        static_for<0, 19>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            Store<T>::st(dst + (self + i * S.plane), d[i]);
+        });
+        static_for<0, 7>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            Store<T>::st(dst + (self + (19 + i) * S.plane), g[i]);
+        });
+    }
 }
 
 }  // namespace
@@ -303,7 +323,7 @@ void fill_step_geometry(const Geometry &G, StepGeometry &S)
     }
 }
 
-cudaError_t launch_step(int wall, int storage, const void *src, void *dst,
+cudaError_t launch_step(int wall, int storage, bool stochastic, const void *src, void *dst,
                         const StepGeometry &S, const Geometry &G, const CollideParams &C,
                         BlockShape b, cudaStream_t s, bool pdl)
 {
@@ -319,8 +339,15 @@ cudaError_t launch_step(int wall, int storage, const void *src, void *dst,
     cfg.numAttrs = pdl ? 1 : 0;
     cudaError_t e = dispatch(wall, storage, [&](auto W, auto *tp) {
         using T = std::remove_pointer_t<decltype(tp)>;
-        return cudaLaunchKernelEx(&cfg, step_kernel<decltype(W)::value, T>,
-                                  static_cast<const T *>(src), static_cast<T *>(dst), S, G, C);
+        constexpr int WL = decltype(W)::value;
+        if constexpr (!std::is_same_v<T, float>) {
+            if (stochastic)
+                return cudaLaunchKernelEx(&cfg, step_kernel<WL, T, true>,
+                                          static_cast<const T *>(src), static_cast<T *>(dst), S,
+                                          G, C);
+        }
+        return cudaLaunchKernelEx(&cfg, step_kernel<WL, T, false>, static_cast<const T *>(src),
+                                  static_cast<T *>(dst), S, G, C);
     });
     if (e != cudaSuccess) return e;
     return cudaGetLastError();

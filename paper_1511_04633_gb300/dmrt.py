@@ -23,6 +23,7 @@ from . import build as _build
 OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_DIVERGED, ERR_TIMEOUT = range(6)
 WALL_PERIODIC, WALL_TYPE1, WALL_TYPE2, WALL_TYPE3 = 0, 1, 2, 3
 STORE_F32, STORE_BF16, STORE_F16 = 0, 1, 2
+ROUND_AUTO, ROUND_NEAREST, ROUND_STOCHASTIC = 0, 1, 2
 
 HEADER = os.path.join(_build.INCLUDE, "dmrt.h")
 
@@ -34,13 +35,14 @@ class DmrtError(RuntimeError):
 
 
 class dmrt_opts(ctypes.Structure):
-    _fields_ = [("storage", ctypes.c_int), ("residual_interval", ctypes.c_int)]
+    _fields_ = [("storage", ctypes.c_int), ("residual_interval", ctypes.c_int),
+                ("rounding", ctypes.c_int)]
 
 
 class dmrt_params(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
                 ("wall_type", ctypes.c_int), ("storage", ctypes.c_int),
-                ("residual_interval", ctypes.c_int),
+                ("residual_interval", ctypes.c_int), ("rounding", ctypes.c_int),
                 ("nu", ctypes.c_double), ("alpha", ctypes.c_double), ("gbeta", ctypes.c_double),
                 ("tau_nu", ctypes.c_double), ("tau_alpha", ctypes.c_double),
                 ("steps", ctypes.c_long)]
@@ -148,22 +150,23 @@ def check(h, status: int, what: str):
 # ---------------------------------------------------------------- C-named functions
 
 def dmrt_create(grid, Ra: float, Pr: float = 0.71, Ma: float = 0.1, wall_type: int = 1,
-                storage: int = STORE_F32, residual_interval: int = 0):
+                storage: int = STORE_F32, residual_interval: int = 0, rounding: int = ROUND_AUTO):
     L = load()
     h = ctypes.c_void_p()
     g = (ctypes.c_int * 3)(*grid)
-    opts = dmrt_opts(storage, residual_interval)
+    opts = dmrt_opts(storage, residual_interval, rounding)
     check(None, L.dmrt_create_ex(ctypes.byref(h), g, Ra, Pr, Ma, wall_type, ctypes.byref(opts)),
           "dmrt_create")
     return h
 
 
 def dmrt_create_lattice(grid, nu: float, alpha: float, gbeta: float, wall_type: int = 1,
-                        storage: int = STORE_F32, residual_interval: int = 0):
+                        storage: int = STORE_F32, residual_interval: int = 0,
+                        rounding: int = ROUND_AUTO):
     L = load()
     h = ctypes.c_void_p()
     g = (ctypes.c_int * 3)(*grid)
-    opts = dmrt_opts(storage, residual_interval)
+    opts = dmrt_opts(storage, residual_interval, rounding)
     check(None, L.dmrt_create_lattice(ctypes.byref(h), g, nu, alpha, gbeta, wall_type,
                                       ctypes.byref(opts)), "dmrt_create_lattice")
     return h
@@ -282,7 +285,7 @@ class Cavity:
     arrays shaped [z][y][x] (velocity [3][z][y][x])."""
 
     def __init__(self, grid, Ra=None, Pr=0.71, Ma=0.1, wall_type=1, *, lattice=None,
-                 storage=STORE_F32, residual_interval=0):
+                 storage=STORE_F32, residual_interval=0, rounding=ROUND_AUTO):
         self.grid = tuple(int(v) for v in grid)
         nx, ny, nz = self.grid
         self.shape = (nz, ny, nx)
@@ -290,9 +293,10 @@ class Cavity:
         if lattice is not None:
             nu, alpha, gbeta = lattice
             self.h = dmrt_create_lattice(self.grid, nu, alpha, gbeta, wall_type, storage,
-                                         residual_interval)
+                                         residual_interval, rounding)
         else:
-            self.h = dmrt_create(self.grid, Ra, Pr, Ma, wall_type, storage, residual_interval)
+            self.h = dmrt_create(self.grid, Ra, Pr, Ma, wall_type, storage, residual_interval,
+                                 rounding)
 
     def close(self):
         if getattr(self, "h", None):
