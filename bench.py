@@ -51,6 +51,7 @@ def workload(args) -> str:
             f"{args.storage} population storage; one step = {args.inner} fused LBM steps + "
             f"residual + hot-wall Nu")
 STEP_KERNEL_SOURCES = ["paper_1511_04633_gb300/csrc/step.cu",
+                       "paper_1511_04633_gb300/csrc/step_body.cuh",
                        "paper_1511_04633_gb300/csrc/lattice.cuh"]
 
 
@@ -369,6 +370,100 @@ def run_dmrt(args, rank, local, world):
         dist.destroy_process_group()
 
 
+def run_ensemble(args, rank, local, world):
+    """The batched ensemble of seeded cavities: one launch per time step over
+    all of them, against the same cavities as separate handles run one after
+    another."""
+    import torch
+    from paper_1511_04633_gb300 import dmrt, inputs
+
+    torch.cuda.set_device(local)
+    dist = init_dist(world, "nccl")
+    device = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device)
+    torch.cuda.set_stream(stream)
+    draws = inputs.ensemble_draws(args.members, seed=args.seed)
+    cav = [{"grid": (d["n"],) * 3, "Ra": d["Ra"], "wall": d["wall"]} for d in draws]
+    storage = STORAGES[args.storage]
+    ens = dmrt.Ensemble(cav, storage=storage)
+    dmrt.dmrt_ensemble_set_stream(ens.e, stream)
+    report = ens.autotune(trials=3)
+    cells = ens.cells
+    inner = args.inner
+
+    def one_step():
+        ens.step(inner)
+        return ens.nusselt(0)
+
+    for _ in range(args.warmup):
+        one_step()
+    dmrt.dmrt_ensemble_get_stats(ens.e, reset=True)
+    dmrt.dmrt_ensemble_set_timing(ens.e, True)
+    barrier(dist)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            one_step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier(dist)
+    secs = reduce_max(dist, ev0.elapsed_time(ev1) / 1e3, device)
+    stats = dmrt.dmrt_ensemble_get_stats(ens.e, reset=True)
+    value = aggregate(cells * inner * args.steps, world, secs)
+    launch_s = stats["step_ms"] / 1e3 / max(stats["timed_steps"], 1)
+    achieved = stats["bytes_per_cell"] * cells / launch_s / 1e9
+    peak, peak_src = measured_peaks()
+    taus = [ens.params(k)["tau_nu"] for k in range(len(cav))]
+    ens.close()
+
+    # the same cavities as 64 separate handles, stepped one after another
+    singles = [dmrt.Cavity(c["grid"], c["Ra"], wall_type=c["wall"], storage=storage) for c in cav]
+    for s in singles:
+        dmrt.dmrt_set_stream(s.h, stream)
+        s.step(inner)
+        s.nusselt(0)
+    sep_steps = max(2, args.steps // 4)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(sep_steps):
+        for s in singles:
+            s.step(inner)
+            s.nusselt(0)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    sep_secs = reduce_max(dist, ev0.elapsed_time(ev1) / 1e3, device)
+    separate = aggregate(cells * inner * sep_steps, world, sep_secs)
+    for s in singles:
+        s.close()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"ensemble of {len(cav)} seeded cavities (edge in 32/48/64/96, "
+                                   f"log10 Ra in [3, 6], types 1-3, seed {args.seed}), "
+                                   f"{args.storage} storage; one step = {inner} LBM steps of all "
+                                   f"members + residuals + hot-wall Nu of all",
+                       "cells": cells, "min_tau_nu": min(taus), "autotune": report,
+                       "parallelism": f"replicas x{world}"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
+                         "kernel": "ensemble_step_kernel", "bytes_per_cell": stats["bytes_per_cell"],
+                         "launch_us": launch_s * 1e6},
+            "separate_runs": {"value": separate, "unit": "MLUPS",
+                              "what": f"the same {len(cav)} cavities as separate handles, "
+                                      f"stepped one after another"},
+            "gpu_launches": stats["total_launches"], "clocks": clocks.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -384,6 +479,10 @@ def main(argv=None):
     ap.add_argument("--grid", type=int, default=GRID[0], help="cubic cavity edge")
     ap.add_argument("--wall", type=int, choices=[1, 2, 3], default=WALL)
     ap.add_argument("--ra", type=float, default=RA)
+    ap.add_argument("--ensemble", action="store_true",
+                    help="measure the batched ensemble of seeded cavities instead")
+    ap.add_argument("--members", type=int, default=64)
+    ap.add_argument("--seed", type=int, default=1234)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args(argv)
     if args.warmup < 3:
@@ -391,6 +490,9 @@ def main(argv=None):
     rank, local, world = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.ensemble:
+        run_ensemble(args, rank, local, world)
         return
     run_dmrt(args, rank, local, world)
 

@@ -222,6 +222,80 @@ dmrt_status dmrt_set_timing(dmrt_t *h, int enabled);
  * is on).  reset = 1 zeroes them afterwards. */
 dmrt_status dmrt_get_stats(dmrt_t *h, dmrt_stats *out, int reset);
 
+/* ------------------------------------------------------------------------
+ * Ensembles: many independent cavities advanced together.  Every time step
+ * is ONE kernel launch over all cavities (a table maps each thread block to
+ * its cavity, tile and parameters); a whole residual interval of K steps
+ * replays one captured CUDA graph.  Cavities may differ in size, Ra, Pr, Ma
+ * and wall type; they share the storage format and K.  Members are numbered
+ * 0..count-1 in the order given.  The method per cavity is exactly that of a
+ * single handle (same kernels' arithmetic, bitwise identical results).
+ * ---------------------------------------------------------------------- */
+typedef struct dmrt_ensemble dmrt_ensemble_t;
+
+/* One member: grid, physical numbers (as dmrt_create) and wall type. */
+typedef struct dmrt_cavity_desc {
+    int grid[3];
+    double Ra, Pr, Ma;
+    int wall_type;
+} dmrt_cavity_desc;
+
+/* Create an ensemble of `count` >= 1 cavities (each validated as by
+ * dmrt_create, walled types 1-3 only; the first invalid one fails the call
+ * with DMRT_ERR_ARG).  All
+ * start from rest.  opts as for dmrt_create_ex (NULL = defaults).  The total
+ * population storage must fit the 32-bit cell indexing of each member and the
+ * device memory. */
+dmrt_status dmrt_ensemble_create(dmrt_ensemble_t **out, int count, const dmrt_cavity_desc *cavities,
+                                 const dmrt_opts *opts);
+
+void dmrt_ensemble_destroy(dmrt_ensemble_t *e);
+
+/* As dmrt_set_stream / dmrt_sync / dmrt_set_timing / dmrt_get_stats. */
+dmrt_status dmrt_ensemble_set_stream(dmrt_ensemble_t *e, void *stream);
+dmrt_status dmrt_ensemble_sync(dmrt_ensemble_t *e);
+dmrt_status dmrt_ensemble_set_timing(dmrt_ensemble_t *e, int enabled);
+dmrt_status dmrt_ensemble_get_stats(dmrt_ensemble_t *e, dmrt_stats *out, int reset);
+
+/* Pick the thread-block size (128 or 256 threads) and, per distinct cavity
+ * width, the tile width along x (32, 64 or 128 cells) by timing `trials`
+ * launches of each candidate on the live buffers (the state is not
+ * advanced).  `report` (may be NULL) receives a one-line summary of the
+ * choices and times.  Without a call the defaults are 128 threads and the
+ * widest tile not wider than the cavity (rounded up to 32). */
+dmrt_status dmrt_ensemble_autotune(dmrt_ensemble_t *e, int trials, char *report, int report_len);
+
+/* Advance every member n >= 0 steps (residual every K steps, per member). */
+dmrt_status dmrt_ensemble_step(dmrt_ensemble_t *e, long n);
+
+/* Per-member residuals r[count] (as dmrt_residual; +inf before two residual
+ * points).  DMRT_ERR_DIVERGED if any member holds a NaN/Inf; the r of that
+ * member is NaN.  Synchronises. */
+dmrt_status dmrt_ensemble_residual(dmrt_ensemble_t *e, double *r);
+
+/* Step until every member's residual is below tol or max_steps more steps
+ * are taken (DMRT_ERR_TIMEOUT).  Members that diverge end the run with
+ * DMRT_ERR_DIVERGED.  *steps_taken and *converged (either may be NULL)
+ * receive the steps run and how many members are below tol. */
+dmrt_status dmrt_ensemble_run_to_steady(dmrt_ensemble_t *e, double tol, long max_steps,
+                                        long *steps_taken, int *converged);
+
+/* Nusselt numbers of wall 0 or 1 for every member: out[3*i + 0..2] =
+ * (Nu_3D, Nu_2D, Nu_max) of member i (as dmrt_nusselt).  Synchronises. */
+dmrt_status dmrt_ensemble_nusselt(dmrt_ensemble_t *e, int wall, double *out);
+
+/* Per-member access, with the layouts of the single-handle calls. */
+dmrt_status dmrt_ensemble_fields(dmrt_ensemble_t *e, int member, float *rho, float *u,
+                                 float *theta, int on_device);
+dmrt_status dmrt_ensemble_init_fields(dmrt_ensemble_t *e, int member, const float *rho,
+                                      const float *u, const float *theta, int on_device);
+dmrt_status dmrt_ensemble_get_populations(dmrt_ensemble_t *e, int member, float *f, float *g,
+                                          int on_device);
+dmrt_status dmrt_ensemble_member_params(const dmrt_ensemble_t *e, int member, dmrt_params *out);
+
+/* Text of the last error on this ensemble ("" if none). */
+const char *dmrt_ensemble_last_error(const dmrt_ensemble_t *e);
+
 /* Text of the last error on this handle ("" if none; static if h is NULL). */
 const char *dmrt_last_error(const dmrt_t *h);
 

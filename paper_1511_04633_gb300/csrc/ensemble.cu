@@ -1,0 +1,1103 @@
+// ensemble.cu -- many independent cavities advanced together: one kernel
+// launch per time step covers every cavity of the ensemble, and a residual
+// interval of K steps replays one captured CUDA graph.
+//
+// Each cavity keeps its own 26-plane population slab inside two shared
+// ping-pong buffers (A-B scheme, as for a single cavity).  A table of cavity
+// descriptors (sizes, strides, tile shape, relaxation rates, wall type) lives
+// in device memory, and a block map gives every thread block of the launch
+// its cavity; the block's position inside that cavity follows from the
+// cavity's first block index.  The per-cell arithmetic is the single-cavity
+// body (step_body.cuh), and stochastic rounding draws the same bits from the
+// cell index and step number, so a member evolves bitwise like a single
+// handle of the same cavity.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <map>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "dmrt.h"
+#include "reduce.cuh"
+#include "step_body.cuh"
+
+namespace lbm {
+
+struct __align__(8) CavityDesc {
+    int nx, ny, nz, wall;
+    unsigned plane, nxy;
+    float inv_ny;
+    int bx, by;              // step tile shape, bx * by = threads per block
+    int tiles_x, tiles_y;    // step tiles along x and y
+    long long block_start;   // first step block of this cavity in the launch
+    long long offset;        // element offset of the cavity's slab in each buffer
+    long long snap_offset;   // float offset of its 4 snapshot planes
+    long long red_start;     // first residual block (32 x 8 tiles)
+    int red_tiles_x, red_tiles_y;
+    CollideParams C;
+};
+
+namespace {
+
+constexpr int kEnsRedThreads = 256;
+constexpr int kMinBlocksEns = 4;
+
+// ---------------------------------------------------------------- step
+
+// One cell of a walled cavity (Types 1-3; the wall type is a per-cavity
+// runtime value, which only changes the thermal rule on the x and z walls).
+template <typename T, bool SR>
+__device__ __forceinline__ void ensemble_cell(const T *__restrict__ src, T *__restrict__ dst,
+                                              const CavityDesc &D, int x, int y, int z,
+                                              unsigned salt)
+{
+    const int nx = D.nx, ny = D.ny, nz = D.nz;
+    const unsigned plane = D.plane;
+    const unsigned self = (static_cast<unsigned>(z) * ny + y) * nx + x;
+    float d[19], g[7];
+    const bool dir_x = D.wall != 1;  // Types 2 and 3: linear x walls
+    const bool dir_z = D.wall == 2;  // Type 2: linear z walls
+    pull_offsets<kRuntimeWall, T>(src, ComputedOffsets{plane, static_cast<unsigned>(nx), D.nxy}, nx,
+                                  ny, nz, D.inv_ny, self, x, y, z, d, g, dir_x, dir_z);
+    collide_pairs(D.C, d, g);
+    // same random word as a single cavity (step.cu) at the same step
+    store_cell<T, SR>(dst, self, plane, d, g, SR ? pcg_hash(self ^ salt) : 0u);
+}
+
+template <typename T, bool SR>
+__global__ void __launch_bounds__(256, kMinBlocksEns)
+    ensemble_step_kernel(const T *__restrict__ srcb, T *__restrict__ dstb,
+                         const CavityDesc *__restrict__ descs, const int *__restrict__ blockmap,
+                         long long counter_at)
+{
+    // programmatic dependent launch (see step.cu)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;");
+    unsigned salt = 0;
+    if constexpr (SR) {
+        const unsigned step = *reinterpret_cast<const unsigned *>(srcb + counter_at);
+        if (blockIdx.x == 0 && threadIdx.x == 0)
+            *reinterpret_cast<unsigned *>(dstb + counter_at) = step + 1u;
+        salt = pcg_hash(step);
+    }
+    // the block's cavity descriptor, staged in shared memory: its fields are
+    // then re-read cheaply instead of occupying registers through the step
+    __shared__ CavityDesc D;
+    {
+        const int c = blockmap[blockIdx.x];
+        const unsigned *g = reinterpret_cast<const unsigned *>(descs + c);
+        unsigned *sdst = reinterpret_cast<unsigned *>(&D);
+        for (int w = threadIdx.x; w < static_cast<int>(sizeof(CavityDesc) / 4); w += blockDim.x)
+            sdst[w] = g[w];
+    }
+    __syncthreads();
+    const int bx = D.bx;
+    const long long b = static_cast<long long>(blockIdx.x) - D.block_start;
+    const int tx = static_cast<int>(threadIdx.x) % bx, ty = static_cast<int>(threadIdx.x) / bx;
+    const int tix = static_cast<int>(b % D.tiles_x);
+    const long long r = b / D.tiles_x;
+    const int tiy = static_cast<int>(r % D.tiles_y);
+    const int z = static_cast<int>(r / D.tiles_y);
+    const int x = tix * bx + tx, y = tiy * D.by + ty;
+    if (x >= D.nx || y >= D.ny) return;
+    ensemble_cell<T, SR>(srcb + D.offset, dstb + D.offset, D, x, y, z, salt);
+}
+
+// ---------------------------------------------------------------- residual
+
+__device__ __forceinline__ Geometry geometry_of(const CavityDesc &D)
+{
+    Geometry G;
+    G.nx = D.nx;
+    G.ny = D.ny;
+    G.nz = D.nz;
+    G.pad = 0;
+    G.plane = D.plane;
+    G.inv_ny = D.inv_ny;
+    return G;
+}
+
+template <int WALL, typename T>
+__device__ __forceinline__ Macro pulled_macro(const T *src, const Geometry &G, int x, int y, int z)
+{
+    float d[19], g[7];
+    pull_f<WALL, T>(src, G, x, y, z, d);
+    pull_g<WALL, T>(src, G, x, y, z, g);
+    return macro_of(d, g);
+}
+
+// Per residual block (32 x 8 cells of one cavity): the sums of the A11
+// residual against the cavity's snapshot, which is then refreshed.
+template <typename T>
+__global__ void __launch_bounds__(kEnsRedThreads)
+    ensemble_residual_kernel(const T *__restrict__ srcb, const CavityDesc *__restrict__ descs,
+                             const int *__restrict__ redmap, float *__restrict__ snapb,
+                             int have_prev, double *__restrict__ partials)
+{
+    const int c = redmap[blockIdx.x];
+    const CavityDesc &D = descs[c];
+    const long long b = static_cast<long long>(blockIdx.x) - D.red_start;
+    const int x = static_cast<int>(b % D.red_tiles_x) * 32 + threadIdx.x;
+    const long long r = b / D.red_tiles_x;
+    const int y = static_cast<int>(r % D.red_tiles_y) * 8 + threadIdx.y;
+    const int z = static_cast<int>(r / D.red_tiles_y);
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    if (x < D.nx && y < D.ny) {
+        const Geometry G = geometry_of(D);
+        const T *src = srcb + D.offset;
+        Macro m;
+        switch (D.wall) {
+        case 0: m = pulled_macro<0, T>(src, G, x, y, z); break;
+        case 1: m = pulled_macro<1, T>(src, G, x, y, z); break;
+        case 2: m = pulled_macro<2, T>(src, G, x, y, z); break;
+        default: m = pulled_macro<3, T>(src, G, x, y, z); break;
+        }
+        const float rr = 1.0f + m.drho;
+        const float now[4] = {m.T, m.jx / rr, m.jy / rr, m.jz / rr};
+        const long long cells = static_cast<long long>(D.nx) * D.ny * D.nz;
+        const long long cell = (static_cast<long long>(z) * D.ny + y) * D.nx + x;
+        float *snap = snapb + D.snap_offset;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float prev = snap[k * cells + cell];
+            const double dk = have_prev ? static_cast<double>(now[k]) - prev : 0.0;
+            const int slot = (k == 0) ? 0 : 2;
+            v[slot] += dk * dk;
+            v[slot + 1] += static_cast<double>(now[k]) * now[k];
+            snap[k * cells + cell] = now[k];
+        }
+    }
+    block_sum<4, kEnsRedThreads>(v);
+    if (threadIdx.x == 0 && threadIdx.y == 0)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) partials[static_cast<long long>(blockIdx.x) * 4 + k] = v[k];
+}
+
+__device__ double ens_rel_change(double num2, double den2)
+{
+    if (den2 == 0.0) return num2 == 0.0 ? 0.0 : INFINITY;
+    return sqrt(num2) / sqrt(den2);
+}
+
+// One block per cavity: its residual blocks summed in index order.
+__global__ void __launch_bounds__(kEnsRedThreads)
+    ensemble_residual_finish(const CavityDesc *__restrict__ descs, const double *__restrict__ partials,
+                             int have_prev, int K, double *result)
+{
+    const int c = blockIdx.x;
+    const CavityDesc &D = descs[c];
+    const long long nb = static_cast<long long>(D.red_tiles_x) * D.red_tiles_y * D.nz;
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    for (long long p = threadIdx.x; p < nb; p += kEnsRedThreads)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[k] += partials[(D.red_start + p) * 4 + k];
+    block_sum<4, kEnsRedThreads>(v);
+    if (threadIdx.x == 0) {
+        bool finite = true;
+        for (int k = 0; k < 4; ++k) finite = finite && isfinite(v[k]);
+        const double rr =
+            have_prev ? fmax(ens_rel_change(v[0], v[1]), ens_rel_change(v[2], v[3])) / K : INFINITY;
+        result[c * 2 + 0] = finite ? rr : NAN;
+        result[c * 2 + 1] = finite ? 0.0 : 1.0;
+    }
+}
+
+// ---------------------------------------------------------------- Nusselt
+
+template <int WALL, typename T>
+__device__ __forceinline__ float pulled_T(const T *src, const Geometry &G, int x, int y, int z)
+{
+    float g[7];
+    pull_g<WALL, T>(src, G, x, y, z, g);
+    float t = 0.f;
+#pragma unroll
+    for (int i = 0; i < 7; ++i) t += g[i];
+    return t;
+}
+
+// Block (z, cavity): local Nu of one row of the wall (as nusselt_kernel).
+template <typename T>
+__global__ void __launch_bounds__(kEnsRedThreads)
+    ensemble_nusselt_kernel(const T *__restrict__ srcb, const CavityDesc *__restrict__ descs,
+                            int wall, int max_nz, double *__restrict__ partials)
+{
+    const int c = blockIdx.y, z = blockIdx.x;
+    const CavityDesc &D = descs[c];
+    if (z >= D.nz) return;  // uniform per block
+    const Geometry G = geometry_of(D);
+    const T *src = srcb + D.offset;
+    const int y1 = wall == 0 ? 0 : D.ny - 1;
+    const int y2 = wall == 0 ? 1 : D.ny - 2;
+    const double th_w = wall == 0 ? 0.5 : -0.5;
+    const double H = static_cast<double>(D.ny);
+    const int c_lo = (D.nx % 2 == 0) ? D.nx / 2 - 1 : (D.nx - 1) / 2;
+    const int c_hi = (D.nx % 2 == 0) ? D.nx / 2 : (D.nx - 1) / 2;
+    double v[2] = {0.0, 0.0};
+    double mx = -INFINITY;
+    for (int x = threadIdx.x; x < D.nx; x += kEnsRedThreads) {
+        float t1, t2;
+        switch (D.wall) {
+        case 0: t1 = pulled_T<0, T>(src, G, x, y1, z); t2 = pulled_T<0, T>(src, G, x, y2, z); break;
+        case 1: t1 = pulled_T<1, T>(src, G, x, y1, z); t2 = pulled_T<1, T>(src, G, x, y2, z); break;
+        case 2: t1 = pulled_T<2, T>(src, G, x, y1, z); t2 = pulled_T<2, T>(src, G, x, y2, z); break;
+        default: t1 = pulled_T<3, T>(src, G, x, y1, z); t2 = pulled_T<3, T>(src, G, x, y2, z); break;
+        }
+        const double dth_ds = (-8.0 * th_w + 9.0 * t1 - static_cast<double>(t2)) / 3.0;
+        const double nu = wall == 0 ? -H * dth_ds : H * dth_ds;
+        v[0] += nu;
+        if (x == c_lo || x == c_hi) v[1] += nu;
+        mx = fmax(mx, nu);
+    }
+    __shared__ double shm[kEnsRedThreads / 32];
+    mx = warp_max(mx);
+    if ((threadIdx.x & 31) == 0) shm[threadIdx.x >> 5] = mx;
+    block_sum<2, kEnsRedThreads>(v);
+    if (threadIdx.x == 0) {
+        double m = shm[0];
+        for (int w = 1; w < kEnsRedThreads / 32; ++w) m = fmax(m, shm[w]);
+        double *p = partials + (static_cast<long long>(c) * max_nz + z) * 3;
+        p[0] = v[0];
+        p[1] = v[1];
+        p[2] = m;
+    }
+}
+
+__global__ void __launch_bounds__(kEnsRedThreads)
+    ensemble_nusselt_finish(const CavityDesc *__restrict__ descs, const double *__restrict__ partials,
+                            int max_nz, double *out)
+{
+    const int c = blockIdx.x;
+    const CavityDesc &D = descs[c];
+    double v[2] = {0.0, 0.0};
+    double mx = -INFINITY;
+    for (int z = threadIdx.x; z < D.nz; z += kEnsRedThreads) {
+        const double *p = partials + (static_cast<long long>(c) * max_nz + z) * 3;
+        v[0] += p[0];
+        v[1] += p[1];
+        mx = fmax(mx, p[2]);
+    }
+    __shared__ double shm[kEnsRedThreads / 32];
+    mx = warp_max(mx);
+    if ((threadIdx.x & 31) == 0) shm[threadIdx.x >> 5] = mx;
+    block_sum<2, kEnsRedThreads>(v);
+    if (threadIdx.x == 0) {
+        double m = shm[0];
+        for (int w = 1; w < kEnsRedThreads / 32; ++w) m = fmax(m, shm[w]);
+        const int ncol = (D.nx % 2 == 0) ? 2 : 1;
+        out[c * 3 + 0] = v[0] / (static_cast<double>(D.nx) * D.nz);
+        out[c * 3 + 1] = v[1] / (static_cast<double>(D.nz) * ncol);
+        out[c * 3 + 2] = m;
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- launchers
+
+cudaError_t launch_ensemble_step(int storage, bool stochastic, const void *src, void *dst,
+                                 const CavityDesc *descs, const int *blockmap, long long blocks,
+                                 int threads, long long counter_at, cudaStream_t s, bool pdl)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(static_cast<unsigned>(blocks));
+    cfg.blockDim = dim3(threads);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    cudaError_t e = dispatch(1, storage, [&](auto, auto *tp) {
+        using T = std::remove_pointer_t<decltype(tp)>;
+        if constexpr (!std::is_same_v<T, float>) {
+            if (stochastic)
+                return cudaLaunchKernelEx(&cfg, ensemble_step_kernel<T, true>,
+                                          static_cast<const T *>(src), static_cast<T *>(dst), descs,
+                                          blockmap, counter_at);
+        }
+        return cudaLaunchKernelEx(&cfg, ensemble_step_kernel<T, false>, static_cast<const T *>(src),
+                                  static_cast<T *>(dst), descs, blockmap, counter_at);
+    });
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ensemble_residual(int storage, const void *src, const CavityDesc *descs,
+                                     const int *redmap, long long red_blocks, int count,
+                                     float *snap, int have_prev, int K, double *partials,
+                                     double *result, cudaStream_t s)
+{
+    cudaError_t e = dispatch(1, storage, [&](auto, auto *tp) {
+        using T = std::remove_pointer_t<decltype(tp)>;
+        ensemble_residual_kernel<T><<<static_cast<unsigned>(red_blocks), dim3(32, 8), 0, s>>>(
+            static_cast<const T *>(src), descs, redmap, snap, have_prev, partials);
+        return cudaSuccess;
+    });
+    if (e != cudaSuccess) return e;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    ensemble_residual_finish<<<count, kEnsRedThreads, 0, s>>>(descs, partials, have_prev, K, result);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ensemble_nusselt(int storage, const void *src, const CavityDesc *descs,
+                                    int count, int max_nz, int wall, double *partials,
+                                    double *out, cudaStream_t s)
+{
+    cudaError_t e = dispatch(1, storage, [&](auto, auto *tp) {
+        using T = std::remove_pointer_t<decltype(tp)>;
+        ensemble_nusselt_kernel<T><<<dim3(max_nz, count), kEnsRedThreads, 0, s>>>(
+            static_cast<const T *>(src), descs, wall, max_nz, partials);
+        return cudaSuccess;
+    });
+    if (e != cudaSuccess) return e;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    ensemble_nusselt_finish<<<count, kEnsRedThreads, 0, s>>>(descs, partials, max_nz, out);
+    return cudaGetLastError();
+}
+
+}  // namespace lbm
+
+// ====================================================================== host
+
+struct dmrt_ensemble {
+    int device = 0;
+    int count = 0;
+    int storage = DMRT_STORE_F32;
+    bool stochastic = false;
+    int K = 100;
+    std::vector<dmrt_cavity_desc> in;
+    std::vector<double> nu, alpha, gbeta;
+    std::vector<lbm::CavityDesc> desc;
+    lbm::CavityDesc *d_desc = nullptr;
+    int *d_blockmap = nullptr;
+    long long step_blocks = 0;
+    size_t blockmap_cap = 0;
+    int *d_redmap = nullptr;
+    long long red_blocks = 0;
+    int threads = 128;
+    int max_nz = 0;
+    long long total_elems = 0;  // population elements per buffer (all cavities)
+    long long total_cells = 0;
+    void *buf[2] = {nullptr, nullptr};
+    int cur = 0;
+    float *snap = nullptr;
+    double *partials = nullptr;
+    size_t npartials = 0;
+    double *dres = nullptr;  // 2 doubles per member
+    double *dnu = nullptr;   // 3 doubles per member
+    float *staging = nullptr;
+    size_t staging_floats = 0;
+    cudaStream_t own = nullptr, stream = nullptr;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    bool use_graphs = true;
+    bool use_pdl = true;
+    long steps = 0;
+    int snaps = 0;
+    bool timing = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
+    std::vector<long> ev_counts;
+    long step_launches = 0, total_launches = 0, timed_steps = 0;
+    double step_ms = 0.0;
+    std::string err;
+};
+
+namespace {
+
+constexpr long kEnsMaxGraphSteps = 1000;
+
+dmrt_status efail(dmrt_ensemble_t *e, dmrt_status st, const char *fmt, ...)
+    __attribute__((format(printf, 3, 4)));
+
+dmrt_status efail(dmrt_ensemble_t *e, dmrt_status st, const char *fmt, ...)
+{
+    if (e) {
+        char b[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(b, sizeof b, fmt, ap);
+        va_end(ap);
+        e->err = b;
+    }
+    return st;
+}
+
+dmrt_status ecuda(dmrt_ensemble_t *e, cudaError_t c, const char *what)
+{
+    return efail(e, c == cudaErrorMemoryAllocation ? DMRT_ERR_OOM : DMRT_ERR_CUDA, "%s: %s (%s)",
+                 what, cudaGetErrorName(c), cudaGetErrorString(c));
+}
+
+#define ECK(e, call, what)                                   \
+    do {                                                     \
+        cudaError_t c_ = (call);                             \
+        if (c_ != cudaSuccess) return ecuda(e, c_, what);    \
+    } while (0)
+
+struct EDeviceGuard {
+    int prev = -1;
+    explicit EDeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~EDeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+void fill_rates_desc(lbm::CavityDesc &D, double nu, double alpha, double gbeta)
+{
+    const double s_nu = 1.0 / (3.0 * nu + 0.5);  // Eq. (26)
+    double s[19];
+    for (int k = 0; k < 19; ++k) s[k] = 1.0;
+    s[1] = 1.19;
+    s[2] = s[10] = s[12] = 1.4;
+    s[4] = s[6] = s[8] = 1.2;
+    s[16] = s[17] = s[18] = 1.98;
+    s[9] = s[11] = s[13] = s[14] = s[15] = s_nu;
+    for (int k = 0; k < 19; ++k) D.C.rs[k] = static_cast<float>(s[k] / lbm::m19_norm2(k));
+    const double tau_a = 0.5 + 4.0 * alpha;  // Eq. (36), eps = 1/4
+    const double q[7] = {1.0, 1.0 / tau_a, 1.0 / tau_a, 1.0 / tau_a, 1.0, 1.0, 1.0};
+    for (int k = 0; k < 7; ++k) D.C.rq[k] = static_cast<float>(q[k] / lbm::m7_norm2(k));
+    D.C.gbeta = static_cast<float>(gbeta);
+    D.C.theta_ref = 0.0f;
+}
+
+// Default tile width: the widest of 128 / 64 / 32 not wider than the cavity
+// (rounded up to 32), limited by the block size.
+int default_bx(int nx, int threads)
+{
+    const int w = (nx + 31) / 32 * 32;
+    int bx = 32;
+    for (int cand : {64, 128})
+        if (cand <= w && cand <= threads) bx = cand;
+    return bx;
+}
+
+// Lay out step tiles (and block starts) for the members in `which` with the
+// current bx of each; returns the block map.
+std::vector<int> layout_step(dmrt_ensemble_t *e, const std::vector<int> &which)
+{
+    std::vector<int> map;
+    long long start = 0;
+    for (int c : which) {
+        lbm::CavityDesc &D = e->desc[c];
+        D.by = e->threads / D.bx;
+        D.tiles_x = (D.nx + D.bx - 1) / D.bx;
+        D.tiles_y = (D.ny + D.by - 1) / D.by;
+        D.block_start = start;
+        const long long nb = static_cast<long long>(D.tiles_x) * D.tiles_y * D.nz;
+        map.insert(map.end(), static_cast<size_t>(nb), c);
+        start += nb;
+    }
+    return map;
+}
+
+dmrt_status upload_layout(dmrt_ensemble_t *e, const std::vector<int> &map)
+{
+    if (map.size() > e->blockmap_cap) {
+        if (e->d_blockmap) cudaFree(e->d_blockmap);
+        e->d_blockmap = nullptr;
+        e->blockmap_cap = 0;
+        ECK(e, cudaMalloc(&e->d_blockmap, map.size() * sizeof(int)), "cudaMalloc(blockmap)");
+        e->blockmap_cap = map.size();
+    }
+    ECK(e, cudaMemcpyAsync(e->d_blockmap, map.data(), map.size() * sizeof(int),
+                           cudaMemcpyHostToDevice, e->stream),
+        "copy blockmap");
+    ECK(e, cudaMemcpyAsync(e->d_desc, e->desc.data(), e->desc.size() * sizeof(lbm::CavityDesc),
+                           cudaMemcpyHostToDevice, e->stream),
+        "copy descriptors");
+    ECK(e, cudaStreamSynchronize(e->stream), "cudaStreamSynchronize");
+    e->step_blocks = static_cast<long long>(map.size());
+    return DMRT_OK;
+}
+
+void drop_graphs(dmrt_ensemble_t *e)
+{
+    for (auto &g : e->graph)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+}
+
+cudaError_t launch_one_step(dmrt_ensemble_t *e, int from)
+{
+    return lbm::launch_ensemble_step(e->storage, e->stochastic, e->buf[from], e->buf[from ^ 1],
+                                     e->d_desc, e->d_blockmap, e->step_blocks, e->threads,
+                                     e->total_elems, e->stream, e->use_pdl);
+}
+
+bool capture_interval(dmrt_ensemble_t *e, int start)
+{
+    if (e->stream == nullptr) return false;
+    if (cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    int cur = start;
+    bool ok = true;
+    for (long s = 0; s < e->K && ok; ++s) {
+        ok = launch_one_step(e, cur) == cudaSuccess;
+        cur ^= 1;
+    }
+    cudaGraph_t graph = nullptr;
+    ok = (cudaStreamEndCapture(e->stream, &graph) == cudaSuccess) && ok && graph;
+    cudaGraphExec_t exec = nullptr;
+    if (ok) ok = cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+    if (graph) cudaGraphDestroy(graph);
+    if (!ok) {
+        cudaGetLastError();
+        if (exec) cudaGraphExecDestroy(exec);
+        return false;
+    }
+    e->graph[start] = exec;
+    return true;
+}
+
+dmrt_status run_residual(dmrt_ensemble_t *e)
+{
+    ECK(e,
+        lbm::launch_ensemble_residual(e->storage, e->buf[e->cur], e->d_desc, e->d_redmap,
+                                      e->red_blocks, e->count, e->snap, e->snaps > 0 ? 1 : 0, e->K,
+                                      e->partials, e->dres, e->stream),
+        "ensemble residual");
+    e->total_launches += 2;
+    if (e->snaps < 2) e->snaps++;
+    return DMRT_OK;
+}
+
+dmrt_status run_steps(dmrt_ensemble_t *e, long n)
+{
+    long done = 0;
+    while (done < n) {
+        const long chunk = std::min(n - done, e->K - (e->steps % e->K));
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (e->timing) {
+            ECK(e, cudaEventCreate(&e0), "cudaEventCreate");
+            ECK(e, cudaEventCreate(&e1), "cudaEventCreate");
+            ECK(e, cudaEventRecord(e0, e->stream), "cudaEventRecord");
+        }
+        bool graphed = false;
+        if (chunk == e->K && e->K <= kEnsMaxGraphSteps && e->use_graphs) {
+            if (!e->graph[e->cur] && !capture_interval(e, e->cur)) e->use_graphs = false;
+            if (e->graph[e->cur]) {
+                ECK(e, cudaGraphLaunch(e->graph[e->cur], e->stream), "cudaGraphLaunch");
+                if (e->K & 1) e->cur ^= 1;
+                graphed = true;
+            }
+        }
+        for (long s = 0; s < chunk && !graphed; ++s) {
+            ECK(e, launch_one_step(e, e->cur), "ensemble step");
+            e->cur ^= 1;
+        }
+        e->steps += chunk;
+        e->step_launches += chunk;
+        e->total_launches += chunk;
+        if (e->timing) {
+            ECK(e, cudaEventRecord(e1, e->stream), "cudaEventRecord");
+            e->ev_pending.emplace_back(e0, e1);
+            e->ev_counts.push_back(chunk);
+        }
+        done += chunk;
+        if (e->steps % e->K == 0) {
+            dmrt_status st = run_residual(e);
+            if (st != DMRT_OK) return st;
+        }
+    }
+    return DMRT_OK;
+}
+
+dmrt_status ensure_staging(dmrt_ensemble_t *e, size_t floats)
+{
+    if (e->staging_floats >= floats) return DMRT_OK;
+    if (e->staging) cudaFree(e->staging);
+    e->staging = nullptr;
+    e->staging_floats = 0;
+    ECK(e, cudaMalloc(&e->staging, floats * sizeof(float)), "cudaMalloc(staging)");
+    e->staging_floats = floats;
+    return DMRT_OK;
+}
+
+lbm::Geometry member_geometry(const lbm::CavityDesc &D)
+{
+    lbm::Geometry G{};
+    G.nx = D.nx;
+    G.ny = D.ny;
+    G.nz = D.nz;
+    G.plane = D.plane;
+    G.inv_ny = D.inv_ny;
+    return G;
+}
+
+void *member_ptr(dmrt_ensemble_t *e, int member, int which)
+{
+    return static_cast<char *>(e->buf[which]) +
+           static_cast<size_t>(e->desc[member].offset) * lbm::storage_bytes(e->storage);
+}
+
+}  // namespace
+
+extern "C" {
+
+dmrt_status dmrt_ensemble_create(dmrt_ensemble_t **out, int count, const dmrt_cavity_desc *cav,
+                                 const dmrt_opts *opts)
+{
+    if (!out) return DMRT_ERR_ARG;
+    *out = nullptr;
+    if (count < 1 || !cav) return DMRT_ERR_ARG;
+    int storage = DMRT_STORE_F32, K = 100, rounding = DMRT_ROUND_AUTO;
+    if (opts) {
+        storage = opts->storage;
+        rounding = opts->rounding;
+        if (opts->residual_interval > 0) K = opts->residual_interval;
+        if (opts->residual_interval < 0) return DMRT_ERR_ARG;
+    }
+    if (storage < DMRT_STORE_F32 || storage > DMRT_STORE_F16) return DMRT_ERR_ARG;
+    if (rounding < DMRT_ROUND_AUTO || rounding > DMRT_ROUND_STOCHASTIC) return DMRT_ERR_ARG;
+
+    dmrt_ensemble_t *e = new (std::nothrow) dmrt_ensemble();
+    if (!e) return DMRT_ERR_OOM;
+    auto bail = [&](dmrt_status st) {
+        dmrt_ensemble_destroy(e);
+        return st;
+    };
+    if (cudaGetDevice(&e->device) != cudaSuccess) return bail(DMRT_ERR_CUDA);
+    e->count = count;
+    e->storage = storage;
+    e->stochastic = storage != DMRT_STORE_F32 && rounding != DMRT_ROUND_NEAREST;
+    e->K = K;
+    e->in.assign(cav, cav + count);
+    e->desc.resize(count);
+    long long offset = 0, snap_off = 0, red_start = 0;
+    std::vector<int> redmap;
+    for (int c = 0; c < count; ++c) {
+        const dmrt_cavity_desc &d = cav[c];
+        const int nx = d.grid[0], ny = d.grid[1], nz = d.grid[2];
+        const int minext = 2;
+        if (d.wall_type < 1 || d.wall_type > 3 || nx < minext || ny < 2 || nz < minext ||
+            nx > 65535 || ny > 65535 || nz > 65535 || !(d.Ra > 0.0) || !(d.Pr > 0.0) ||
+            !(d.Ma > 0.0) || !(d.Ma < 0.3) || !std::isfinite(d.Ra) || !std::isfinite(d.Pr))
+            return bail(DMRT_ERR_ARG);
+        const long long cells = static_cast<long long>(nx) * ny * nz;
+        const long long plane = (cells + 63) / 64 * 64;
+        if (plane * lbm::kPlanes >= (1LL << 32)) return bail(DMRT_ERR_ARG);
+        // Eq. (38), H = ny, dT = 1 (as dmrt_create)
+        const double H = ny, uc = d.Ma / std::sqrt(3.0);
+        const double gb = uc * uc / H, nu = uc * H * std::sqrt(d.Pr / d.Ra), al = nu / d.Pr;
+        e->nu.push_back(nu);
+        e->alpha.push_back(al);
+        e->gbeta.push_back(gb);
+        lbm::CavityDesc &D = e->desc[c];
+        D = lbm::CavityDesc{};
+        D.nx = nx;
+        D.ny = ny;
+        D.nz = nz;
+        D.wall = d.wall_type;
+        D.plane = static_cast<unsigned>(plane);
+        D.nxy = static_cast<unsigned>(nx) * ny;
+        D.inv_ny = 1.0f / static_cast<float>(ny);
+        D.bx = default_bx(nx, e->threads);
+        D.offset = offset;
+        D.snap_offset = snap_off;
+        D.red_tiles_x = (nx + 31) / 32;
+        D.red_tiles_y = (ny + 7) / 8;
+        D.red_start = red_start;
+        const long long nred = static_cast<long long>(D.red_tiles_x) * D.red_tiles_y * nz;
+        redmap.insert(redmap.end(), static_cast<size_t>(nred), c);
+        red_start += nred;
+        fill_rates_desc(D, nu, al, gb);
+        offset += plane * lbm::kPlanes;
+        snap_off += 4 * cells;
+        e->total_cells += cells;
+        e->max_nz = std::max(e->max_nz, nz);
+    }
+    e->total_elems = offset;
+    e->red_blocks = red_start;
+    std::vector<int> all(count);
+    for (int c = 0; c < count; ++c) all[c] = c;
+    const std::vector<int> map = layout_step(e, all);
+
+    cudaError_t c;
+    const size_t buf_bytes = static_cast<size_t>(offset) * lbm::storage_bytes(storage) + 256;
+    for (int b = 0; b < 2; ++b) {
+        c = cudaMalloc(&e->buf[b], buf_bytes);
+        if (c != cudaSuccess) return bail(c == cudaErrorMemoryAllocation ? DMRT_ERR_OOM : DMRT_ERR_CUDA);
+    }
+    if (cudaMalloc(&e->snap, static_cast<size_t>(snap_off) * sizeof(float)) != cudaSuccess)
+        return bail(DMRT_ERR_OOM);
+    e->npartials = std::max<size_t>(static_cast<size_t>(red_start) * 4,
+                                    static_cast<size_t>(count) * e->max_nz * 3);
+    if (cudaMalloc(&e->partials, e->npartials * sizeof(double)) != cudaSuccess) return bail(DMRT_ERR_OOM);
+    if (cudaMalloc(&e->dres, static_cast<size_t>(count) * 5 * sizeof(double)) != cudaSuccess)
+        return bail(DMRT_ERR_OOM);
+    e->dnu = e->dres + 2 * count;
+    if (cudaMalloc(&e->d_desc, static_cast<size_t>(count) * sizeof(lbm::CavityDesc)) != cudaSuccess)
+        return bail(DMRT_ERR_OOM);
+    if (cudaMalloc(&e->d_redmap, redmap.size() * sizeof(int)) != cudaSuccess) return bail(DMRT_ERR_OOM);
+    if (cudaStreamCreateWithFlags(&e->own, cudaStreamNonBlocking) != cudaSuccess)
+        return bail(DMRT_ERR_CUDA);
+    e->stream = e->own;
+    if (cudaMemcpyAsync(e->d_redmap, redmap.data(), redmap.size() * sizeof(int),
+                        cudaMemcpyHostToDevice, e->stream) != cudaSuccess)
+        return bail(DMRT_ERR_CUDA);
+    if (upload_layout(e, map) != DMRT_OK) return bail(DMRT_ERR_CUDA);
+    for (int b = 0; b < 2; ++b)
+        if (cudaMemsetAsync(e->buf[b], 0, buf_bytes, e->stream) != cudaSuccess) return bail(DMRT_ERR_CUDA);
+    if (cudaStreamSynchronize(e->stream) != cudaSuccess) return bail(DMRT_ERR_CUDA);
+    *out = e;
+    return DMRT_OK;
+}
+
+void dmrt_ensemble_destroy(dmrt_ensemble_t *e)
+{
+    if (!e) return;
+    EDeviceGuard dg(e->device);
+    if (e->stream) cudaStreamSynchronize(e->stream);
+    for (auto &p : e->ev_pending) {
+        cudaEventDestroy(p.first);
+        cudaEventDestroy(p.second);
+    }
+    drop_graphs(e);
+    for (int b = 0; b < 2; ++b)
+        if (e->buf[b]) cudaFree(e->buf[b]);
+    if (e->snap) cudaFree(e->snap);
+    if (e->partials) cudaFree(e->partials);
+    if (e->dres) cudaFree(e->dres);
+    if (e->d_desc) cudaFree(e->d_desc);
+    if (e->d_blockmap) cudaFree(e->d_blockmap);
+    if (e->d_redmap) cudaFree(e->d_redmap);
+    if (e->staging) cudaFree(e->staging);
+    if (e->own) cudaStreamDestroy(e->own);
+    delete e;
+}
+
+dmrt_status dmrt_ensemble_set_stream(dmrt_ensemble_t *e, void *stream)
+{
+    if (!e) return DMRT_ERR_ARG;
+    EDeviceGuard dg(e->device);
+    ECK(e, cudaStreamSynchronize(e->stream), "cudaStreamSynchronize");
+    e->stream = stream ? static_cast<cudaStream_t>(stream) : e->own;
+    return DMRT_OK;
+}
+
+dmrt_status dmrt_ensemble_sync(dmrt_ensemble_t *e)
+{
+    if (!e) return DMRT_ERR_ARG;
+    EDeviceGuard dg(e->device);
+    ECK(e, cudaStreamSynchronize(e->stream), "cudaStreamSynchronize");
+    return DMRT_OK;
+}
+
+dmrt_status dmrt_ensemble_set_timing(dmrt_ensemble_t *e, int enabled)
+{
+    if (!e) return DMRT_ERR_ARG;
+    e->timing = enabled != 0;
+    return DMRT_OK;
+}
+
+dmrt_status dmrt_ensemble_get_stats(dmrt_ensemble_t *e, dmrt_stats *out, int reset)
+{
+    if (!e || !out) return DMRT_ERR_ARG;
+    EDeviceGuard dg(e->device);
+    for (size_t k = 0; k < e->ev_pending.size(); ++k) {
+        auto &p = e->ev_pending[k];
+        ECK(e, cudaEventSynchronize(p.second), "cudaEventSynchronize");
+        float ms = 0.f;
+        ECK(e, cudaEventElapsedTime(&ms, p.first, p.second), "cudaEventElapsedTime");
+        e->step_ms += ms;
+        e->timed_steps += e->ev_counts[k];
+        cudaEventDestroy(p.first);
+        cudaEventDestroy(p.second);
+    }
+    e->ev_pending.clear();
+    e->ev_counts.clear();
+    out->step_launches = e->step_launches;
+    out->total_launches = e->total_launches;
+    out->step_ms = e->step_ms;
+    out->timed_steps = e->timed_steps;
+    out->bytes_per_cell = 2.0 * lbm::kPlanes * lbm::storage_bytes(e->storage);
+    if (reset) {
+        e->step_launches = e->total_launches = e->timed_steps = 0;
+        e->step_ms = 0.0;
+    }
+    return DMRT_OK;
+}
+
+dmrt_status dmrt_ensemble_autotune(dmrt_ensemble_t *e, int trials, char *report, int report_len)
+{
+    if (!e || trials < 1) return DMRT_ERR_ARG;
+    EDeviceGuard dg(e->device);
+    ECK(e, cudaStreamSynchronize(e->stream), "cudaStreamSynchronize");
+    drop_graphs(e);
+    cudaEvent_t t0, t1;
+    ECK(e, cudaEventCreate(&t0), "cudaEventCreate");
+    ECK(e, cudaEventCreate(&t1), "cudaEventCreate");
+    // time `trials` launches of the current layout of `which` (state kept:
+    // every launch recomputes the same next state from buf[cur])
+    auto time_layout = [&](const std::vector<int> &which, float *ms) -> dmrt_status {
+        dmrt_status st = upload_layout(e, layout_step(e, which));
+        if (st != DMRT_OK) return st;
+        ECK(e, launch_one_step(e, e->cur), "autotune warm-up");
+        ECK(e, cudaEventRecord(t0, e->stream), "cudaEventRecord");
+        for (int t = 0; t < trials; ++t) ECK(e, launch_one_step(e, e->cur), "autotune launch");
+        ECK(e, cudaEventRecord(t1, e->stream), "cudaEventRecord");
+        ECK(e, cudaEventSynchronize(t1), "cudaEventSynchronize");
+        ECK(e, cudaEventElapsedTime(ms, t0, t1), "cudaEventElapsedTime");
+        *ms /= trials;
+        return DMRT_OK;
+    };
+    std::map<int, std::vector<int>> groups;  // nx -> members
+    for (int c = 0; c < e->count; ++c) groups[e->desc[c].nx].push_back(c);
+    std::vector<int> all(e->count);
+    for (int c = 0; c < e->count; ++c) all[c] = c;
+    int best_threads = e->threads;
+    float best_total = INFINITY;
+    std::vector<int> best_bx(e->count);
+    std::string rep;
+    for (int threads : {128, 256}) {
+        e->threads = threads;
+        for (auto &g : groups) {
+            int best = -1;
+            float best_ms = INFINITY;
+            for (int bx : {32, 64, 128}) {
+                if (bx > threads || bx > (g.first + 31) / 32 * 32 + 32) continue;
+                for (int c : g.second) e->desc[c].bx = bx;
+                float ms = 0.f;
+                dmrt_status st = time_layout(g.second, &ms);
+                if (st != DMRT_OK) return st;
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best = bx;
+                }
+            }
+            for (int c : g.second) e->desc[c].bx = best;
+        }
+        float total = 0.f;
+        dmrt_status st = time_layout(all, &total);
+        if (st != DMRT_OK) return st;
+        char line[160];
+        snprintf(line, sizeof line, "threads=%d:%.1fus[", threads, total * 1e3f);
+        rep += line;
+        for (auto &g : groups) {
+            snprintf(line, sizeof line, " nx%d:bx%d", g.first, e->desc[g.second[0]].bx);
+            rep += line;
+        }
+        rep += " ] ";
+        if (total < best_total) {
+            best_total = total;
+            best_threads = threads;
+            for (int c = 0; c < e->count; ++c) best_bx[c] = e->desc[c].bx;
+        }
+    }
+    e->threads = best_threads;
+    for (int c = 0; c < e->count; ++c) e->desc[c].bx = best_bx[c];
+    dmrt_status st = upload_layout(e, layout_step(e, all));
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    if (st != DMRT_OK) return st;
+    char line[64];
+    snprintf(line, sizeof line, "chosen threads=%d", best_threads);
+    rep += line;
+    if (report && report_len > 0) snprintf(report, static_cast<size_t>(report_len), "%s", rep.c_str());
+    return DMRT_OK;
+}
+
+dmrt_status dmrt_ensemble_step(dmrt_ensemble_t *e, long n)
+{
+    if (!e) return DMRT_ERR_ARG;
+    if (n < 0) return efail(e, DMRT_ERR_ARG, "dmrt_ensemble_step: n = %ld < 0", n);
+    EDeviceGuard dg(e->device);
+    return run_steps(e, n);
+}
+
+dmrt_status dmrt_ensemble_residual(dmrt_ensemble_t *e, double *r)
+{
+    if (!e || !r) return DMRT_ERR_ARG;
+    EDeviceGuard dg(e->device);
+    if (e->snaps < 2) {
+        for (int c = 0; c < e->count; ++c) r[c] = INFINITY;
+        return DMRT_OK;
+    }
+    std::vector<double> res(static_cast<size_t>(e->count) * 2);
+    ECK(e, cudaMemcpyAsync(res.data(), e->dres, res.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                           e->stream),
+        "copy residuals");
+    ECK(e, cudaStreamSynchronize(e->stream), "cudaStreamSynchronize");
+    dmrt_status st = DMRT_OK;
+    for (int c = 0; c < e->count; ++c) {
+        r[c] = res[2 * c];
+        if (res[2 * c + 1] != 0.0 && st == DMRT_OK)
+            st = efail(e, DMRT_ERR_DIVERGED, "member %d holds non-finite fields at step %ld", c,
+                       e->steps);
+    }
+    return st;
+}
+
+dmrt_status dmrt_ensemble_run_to_steady(dmrt_ensemble_t *e, double tol, long max_steps,
+                                        long *steps_taken, int *converged)
+{
+    if (!e || !(tol > 0.0) || max_steps < 0) return DMRT_ERR_ARG;
+    EDeviceGuard dg(e->device);
+    std::vector<double> r(static_cast<size_t>(e->count), INFINITY);
+    long taken = 0;
+    int conv = 0;
+    dmrt_status st = DMRT_OK;
+    while (true) {
+        if (e->snaps >= 2) {
+            st = dmrt_ensemble_residual(e, r.data());
+            conv = 0;
+            for (double v : r) conv += (v < tol);
+            if (st != DMRT_OK || conv == e->count) break;
+        }
+        if (taken >= max_steps) {
+            st = efail(e, DMRT_ERR_TIMEOUT, "%d of %d members below %g after %ld steps", conv,
+                       e->count, tol, taken);
+            break;
+        }
+        long chunk = e->K - (e->steps % e->K);
+        if (chunk > max_steps - taken) chunk = max_steps - taken;
+        st = run_steps(e, chunk);
+        if (st != DMRT_OK) break;
+        taken += chunk;
+    }
+    if (steps_taken) *steps_taken = taken;
+    if (converged) *converged = conv;
+    return st;
+}
+
+dmrt_status dmrt_ensemble_nusselt(dmrt_ensemble_t *e, int wall, double *out)
+{
+    if (!e || !out || (wall != 0 && wall != 1)) return DMRT_ERR_ARG;
+    EDeviceGuard dg(e->device);
+    ECK(e,
+        lbm::launch_ensemble_nusselt(e->storage, e->buf[e->cur], e->d_desc, e->count, e->max_nz,
+                                     wall, e->partials, e->dnu, e->stream),
+        "ensemble nusselt");
+    e->total_launches += 2;
+    ECK(e, cudaMemcpyAsync(out, e->dnu, static_cast<size_t>(e->count) * 3 * sizeof(double),
+                           cudaMemcpyDeviceToHost, e->stream),
+        "copy nusselt");
+    ECK(e, cudaStreamSynchronize(e->stream), "cudaStreamSynchronize");
+    return DMRT_OK;
+}
+
+dmrt_status dmrt_ensemble_fields(dmrt_ensemble_t *e, int member, float *rho, float *u,
+                                 float *theta, int on_device)
+{
+    if (!e || member < 0 || member >= e->count) return DMRT_ERR_ARG;
+    EDeviceGuard dg(e->device);
+    const lbm::CavityDesc &D = e->desc[member];
+    const lbm::Geometry G = member_geometry(D);
+    const size_t cells = static_cast<size_t>(D.nx) * D.ny * D.nz;
+    float *dr = rho, *du = u, *dt = theta;
+    if (!on_device) {
+        dmrt_status st = ensure_staging(e, 5 * cells);
+        if (st != DMRT_OK) return st;
+        dr = rho ? e->staging : nullptr;
+        du = u ? e->staging + cells : nullptr;
+        dt = theta ? e->staging + 4 * cells : nullptr;
+    }
+    ECK(e, lbm::launch_fields(D.wall, e->storage, member_ptr(e, member, e->cur), G, dr, du, dt, e->stream),
+        "fields kernel");
+    e->total_launches++;
+    if (!on_device) {
+        if (rho) ECK(e, cudaMemcpyAsync(rho, dr, cells * 4, cudaMemcpyDeviceToHost, e->stream), "copy rho");
+        if (u) ECK(e, cudaMemcpyAsync(u, du, 3 * cells * 4, cudaMemcpyDeviceToHost, e->stream), "copy u");
+        if (theta)
+            ECK(e, cudaMemcpyAsync(theta, dt, cells * 4, cudaMemcpyDeviceToHost, e->stream), "copy theta");
+    }
+    ECK(e, cudaStreamSynchronize(e->stream), "cudaStreamSynchronize");
+    return DMRT_OK;
+}
+
+dmrt_status dmrt_ensemble_init_fields(dmrt_ensemble_t *e, int member, const float *rho,
+                                      const float *u, const float *theta, int on_device)
+{
+    if (!e || member < 0 || member >= e->count || !rho || !u || !theta) return DMRT_ERR_ARG;
+    EDeviceGuard dg(e->device);
+    const lbm::CavityDesc &D = e->desc[member];
+    const lbm::Geometry G = member_geometry(D);
+    const size_t cells = static_cast<size_t>(D.nx) * D.ny * D.nz;
+    const float *dr = rho, *du = u, *dt = theta;
+    if (!on_device) {
+        dmrt_status st = ensure_staging(e, 5 * cells);
+        if (st != DMRT_OK) return st;
+        ECK(e, cudaMemcpyAsync(e->staging, rho, cells * 4, cudaMemcpyHostToDevice, e->stream), "copy rho");
+        ECK(e, cudaMemcpyAsync(e->staging + cells, u, 3 * cells * 4, cudaMemcpyHostToDevice, e->stream),
+            "copy u");
+        ECK(e, cudaMemcpyAsync(e->staging + 4 * cells, theta, cells * 4, cudaMemcpyHostToDevice, e->stream),
+            "copy theta");
+        dr = e->staging;
+        du = e->staging + cells;
+        dt = e->staging + 4 * cells;
+    }
+    ECK(e, lbm::launch_init_fields(e->storage, dr, du, dt, member_ptr(e, member, e->cur), G, e->stream),
+        "init kernel");
+    e->total_launches++;
+    e->snaps = 0;
+    ECK(e, cudaStreamSynchronize(e->stream), "cudaStreamSynchronize");
+    return DMRT_OK;
+}
+
+dmrt_status dmrt_ensemble_get_populations(dmrt_ensemble_t *e, int member, float *f, float *g,
+                                          int on_device)
+{
+    if (!e || member < 0 || member >= e->count) return DMRT_ERR_ARG;
+    if (!f && !g) return DMRT_OK;
+    EDeviceGuard dg(e->device);
+    const lbm::CavityDesc &D = e->desc[member];
+    const lbm::Geometry G = member_geometry(D);
+    const size_t cells = static_cast<size_t>(D.nx) * D.ny * D.nz;
+    float *df = f, *dgp = g;
+    if (!on_device) {
+        dmrt_status st = ensure_staging(e, 26 * cells);
+        if (st != DMRT_OK) return st;
+        df = f ? e->staging : nullptr;
+        dgp = g ? e->staging + 19 * cells : nullptr;
+    }
+    ECK(e, lbm::launch_get_populations(e->storage, member_ptr(e, member, e->cur), df, dgp, G, e->stream),
+        "get kernel");
+    e->total_launches++;
+    if (!on_device) {
+        if (f) ECK(e, cudaMemcpyAsync(f, df, 19 * cells * 4, cudaMemcpyDeviceToHost, e->stream), "copy f");
+        if (g) ECK(e, cudaMemcpyAsync(g, dgp, 7 * cells * 4, cudaMemcpyDeviceToHost, e->stream), "copy g");
+    }
+    ECK(e, cudaStreamSynchronize(e->stream), "cudaStreamSynchronize");
+    return DMRT_OK;
+}
+
+dmrt_status dmrt_ensemble_member_params(const dmrt_ensemble_t *e, int member, dmrt_params *out)
+{
+    if (!e || !out || member < 0 || member >= e->count) return DMRT_ERR_ARG;
+    const lbm::CavityDesc &D = e->desc[member];
+    out->nx = D.nx;
+    out->ny = D.ny;
+    out->nz = D.nz;
+    out->wall_type = D.wall;
+    out->storage = e->storage;
+    out->residual_interval = e->K;
+    out->rounding = e->stochastic ? DMRT_ROUND_STOCHASTIC : DMRT_ROUND_NEAREST;
+    out->nu = e->nu[member];
+    out->alpha = e->alpha[member];
+    out->gbeta = e->gbeta[member];
+    out->tau_nu = 3.0 * e->nu[member] + 0.5;
+    out->tau_alpha = 0.5 + 4.0 * e->alpha[member];
+    out->steps = e->steps;
+    return DMRT_OK;
+}
+
+const char *dmrt_ensemble_last_error(const dmrt_ensemble_t *e)
+{
+    if (!e) return "null ensemble";
+    return e->err.c_str();
+}
+
+}  // extern "C"

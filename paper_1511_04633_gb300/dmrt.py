@@ -54,6 +54,11 @@ class dmrt_stats(ctypes.Structure):
                 ("bytes_per_cell", ctypes.c_double)]
 
 
+class dmrt_cavity_desc(ctypes.Structure):
+    _fields_ = [("grid", ctypes.c_int * 3), ("Ra", ctypes.c_double), ("Pr", ctypes.c_double),
+                ("Ma", ctypes.c_double), ("wall_type", ctypes.c_int)]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -98,6 +103,22 @@ def load(build_if_missing: bool = True):
             "dmrt_set_timing": ([vp, i], i),
             "dmrt_get_stats": ([vp, P(dmrt_stats), i], i),
             "dmrt_last_error": ([vp], ctypes.c_char_p),
+            "dmrt_ensemble_create": ([P(vp), i, P(dmrt_cavity_desc), P(dmrt_opts)], i),
+            "dmrt_ensemble_destroy": ([vp], None),
+            "dmrt_ensemble_set_stream": ([vp, vp], i),
+            "dmrt_ensemble_sync": ([vp], i),
+            "dmrt_ensemble_set_timing": ([vp, i], i),
+            "dmrt_ensemble_get_stats": ([vp, P(dmrt_stats), i], i),
+            "dmrt_ensemble_autotune": ([vp, i, ctypes.c_char_p, i], i),
+            "dmrt_ensemble_step": ([vp, l_], i),
+            "dmrt_ensemble_residual": ([vp, P(d)], i),
+            "dmrt_ensemble_run_to_steady": ([vp, d, l_, P(l_), P(i)], i),
+            "dmrt_ensemble_nusselt": ([vp, i, P(d)], i),
+            "dmrt_ensemble_fields": ([vp, i, vp, vp, vp, i], i),
+            "dmrt_ensemble_init_fields": ([vp, i, vp, vp, vp, i], i),
+            "dmrt_ensemble_get_populations": ([vp, i, vp, vp, i], i),
+            "dmrt_ensemble_member_params": ([vp, i, P(dmrt_params)], i),
+            "dmrt_ensemble_last_error": ([vp], ctypes.c_char_p),
             "dmrt_status_string": ([i], ctypes.c_char_p),
             "dmrt_version": ([], ctypes.c_char_p),
         }
@@ -139,11 +160,14 @@ def _same_side(*arrs):
     return sides.pop() if sides else 0
 
 
-def check(h, status: int, what: str):
+def check(h, status: int, what: str, ensemble: bool = False):
     if status != OK:
         L = load()
         name = L.dmrt_status_string(status).decode()
-        msg = L.dmrt_last_error(h).decode() if h else ""
+        if h:
+            msg = (L.dmrt_ensemble_last_error(h) if ensemble else L.dmrt_last_error(h)).decode()
+        else:
+            msg = ""
         raise DmrtError(status, f"{what}: {name} {msg}".strip())
 
 
@@ -360,3 +384,178 @@ class Cavity:
         dmrt_init_fields(self.h, np.ascontiguousarray(rho, np.float32),
                          np.ascontiguousarray(u, np.float32),
                          np.ascontiguousarray(theta, np.float32))
+
+
+# ---------------------------------------------------------------- ensembles
+
+def _echeck(e, status, what):
+    check(e, status, what, ensemble=True)
+
+
+def dmrt_ensemble_create(cavities, storage: int = STORE_F32, residual_interval: int = 0,
+                         rounding: int = ROUND_AUTO):
+    """cavities: iterable of dicts {"grid": (nx, ny, nz), "Ra", "Pr", "Ma", "wall"}."""
+    L = load()
+    cav = list(cavities)
+    arr = (dmrt_cavity_desc * len(cav))()
+    for k, c in enumerate(cav):
+        arr[k].grid[:] = list(c["grid"])
+        arr[k].Ra = c["Ra"]
+        arr[k].Pr = c.get("Pr", 0.71)
+        arr[k].Ma = c.get("Ma", 0.1)
+        arr[k].wall_type = c["wall"]
+    e = ctypes.c_void_p()
+    opts = dmrt_opts(storage, residual_interval, rounding)
+    _echeck(None, L.dmrt_ensemble_create(ctypes.byref(e), len(cav), arr, ctypes.byref(opts)),
+            "dmrt_ensemble_create")
+    return e
+
+
+def dmrt_ensemble_destroy(e):
+    load().dmrt_ensemble_destroy(e)
+
+
+def dmrt_ensemble_set_stream(e, stream):
+    raw = getattr(stream, "cuda_stream", stream)
+    _echeck(e, load().dmrt_ensemble_set_stream(e, raw), "dmrt_ensemble_set_stream")
+
+
+def dmrt_ensemble_sync(e):
+    _echeck(e, load().dmrt_ensemble_sync(e), "dmrt_ensemble_sync")
+
+
+def dmrt_ensemble_set_timing(e, enabled: bool):
+    _echeck(e, load().dmrt_ensemble_set_timing(e, int(bool(enabled))), "dmrt_ensemble_set_timing")
+
+
+def dmrt_ensemble_get_stats(e, reset: bool = False) -> dict:
+    s = dmrt_stats()
+    _echeck(e, load().dmrt_ensemble_get_stats(e, ctypes.byref(s), int(bool(reset))),
+            "dmrt_ensemble_get_stats")
+    return {k: getattr(s, k) for k, _ in dmrt_stats._fields_}
+
+
+def dmrt_ensemble_autotune(e, trials: int = 5) -> str:
+    buf = ctypes.create_string_buffer(4096)
+    _echeck(e, load().dmrt_ensemble_autotune(e, trials, buf, len(buf)), "dmrt_ensemble_autotune")
+    return buf.value.decode()
+
+
+def dmrt_ensemble_step(e, n: int):
+    _echeck(e, load().dmrt_ensemble_step(e, int(n)), "dmrt_ensemble_step")
+
+
+def dmrt_ensemble_residual(e, count: int) -> np.ndarray:
+    r = np.zeros(count)
+    _echeck(e, load().dmrt_ensemble_residual(e, r.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+            "dmrt_ensemble_residual")
+    return r
+
+
+def dmrt_ensemble_run_to_steady(e, tol: float, max_steps: int):
+    n = ctypes.c_long()
+    conv = ctypes.c_int()
+    st = load().dmrt_ensemble_run_to_steady(e, tol, int(max_steps), ctypes.byref(n), ctypes.byref(conv))
+    if st not in (OK, ERR_TIMEOUT):
+        _echeck(e, st, "dmrt_ensemble_run_to_steady")
+    return st == OK, n.value, conv.value
+
+
+def dmrt_ensemble_nusselt(e, count: int, wall: int = 0) -> np.ndarray:
+    out = np.zeros((count, 3))
+    _echeck(e, load().dmrt_ensemble_nusselt(e, wall, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+            "dmrt_ensemble_nusselt")
+    return out
+
+
+def dmrt_ensemble_fields(e, member: int, rho=None, u=None, theta=None):
+    side = _same_side(rho, u, theta)
+    _echeck(e, load().dmrt_ensemble_fields(e, member, _ptr(rho)[0], _ptr(u)[0], _ptr(theta)[0], side),
+            "dmrt_ensemble_fields")
+
+
+def dmrt_ensemble_init_fields(e, member: int, rho, u, theta):
+    side = _same_side(rho, u, theta)
+    _echeck(e, load().dmrt_ensemble_init_fields(e, member, _ptr(rho)[0], _ptr(u)[0], _ptr(theta)[0],
+                                                side), "dmrt_ensemble_init_fields")
+
+
+def dmrt_ensemble_get_populations(e, member: int, f=None, g=None):
+    side = _same_side(f, g)
+    _echeck(e, load().dmrt_ensemble_get_populations(e, member, _ptr(f)[0], _ptr(g)[0], side),
+            "dmrt_ensemble_get_populations")
+
+
+def dmrt_ensemble_member_params(e, member: int) -> dict:
+    p = dmrt_params()
+    _echeck(e, load().dmrt_ensemble_member_params(e, member, ctypes.byref(p)),
+            "dmrt_ensemble_member_params")
+    return {k: getattr(p, k) for k, _ in dmrt_params._fields_}
+
+
+class Ensemble:
+    """Many cavities stepped by one launch per time step.  ``cavities`` is a
+    list of dicts {"grid": (nx, ny, nz), "Ra": .., "wall": 1..3, ["Pr", "Ma"]}."""
+
+    def __init__(self, cavities, storage=STORE_F32, residual_interval=0, rounding=ROUND_AUTO):
+        self.cavities = [dict(c) for c in cavities]
+        self.count = len(self.cavities)
+        self.e = dmrt_ensemble_create(self.cavities, storage, residual_interval, rounding)
+
+    def close(self):
+        if getattr(self, "e", None):
+            dmrt_ensemble_destroy(self.e)
+            self.e = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def cells(self) -> int:
+        return sum(int(np.prod(c["grid"])) for c in self.cavities)
+
+    def autotune(self, trials=5):
+        return dmrt_ensemble_autotune(self.e, trials)
+
+    def step(self, n=1):
+        dmrt_ensemble_step(self.e, n)
+
+    def sync(self):
+        dmrt_ensemble_sync(self.e)
+
+    def residual(self):
+        return dmrt_ensemble_residual(self.e, self.count)
+
+    def run_to_steady(self, tol, max_steps):
+        return dmrt_ensemble_run_to_steady(self.e, tol, max_steps)
+
+    def nusselt(self, wall=0):
+        return dmrt_ensemble_nusselt(self.e, self.count, wall)
+
+    def params(self, member):
+        return dmrt_ensemble_member_params(self.e, member)
+
+    def fields(self, member):
+        nx, ny, nz = self.cavities[member]["grid"]
+        shape = (nz, ny, nx)
+        rho = np.empty(shape, np.float32)
+        u = np.empty((3,) + shape, np.float32)
+        th = np.empty(shape, np.float32)
+        dmrt_ensemble_fields(self.e, member, rho, u, th)
+        return rho, u, th
+
+    def init_fields(self, member, rho, u, theta):
+        dmrt_ensemble_init_fields(self.e, member, np.ascontiguousarray(rho, np.float32),
+                                  np.ascontiguousarray(u, np.float32),
+                                  np.ascontiguousarray(theta, np.float32))
+
+    def populations(self, member):
+        nx, ny, nz = self.cavities[member]["grid"]
+        shape = (nz, ny, nx)
+        f = np.empty((19,) + shape, np.float32)
+        g = np.empty((7,) + shape, np.float32)
+        dmrt_ensemble_get_populations(self.e, member, f, g)
+        return f, g
