@@ -296,6 +296,95 @@ dmrt_status dmrt_ensemble_member_params(const dmrt_ensemble_t *e, int member, dm
 /* Text of the last error on this ensemble ("" if none). */
 const char *dmrt_ensemble_last_error(const dmrt_ensemble_t *e);
 
+/* ------------------------------------------------------------------------
+ * Warm-start surrogate: a 3-D convolutional U-Net mapping a cavity's
+ * parameters (Ra, wall type) to an approximate steady state on an n^3 grid:
+ * 5 channels (u_x, u_y, u_z)/u_c, theta and (rho - 1)/(3 u_c^2) (the density
+ * carries the hydrostatic balance of the buoyancy, so a warm start with it
+ * releases no pressure transient), trained on the GPU by this library's own forward
+ * and backward kernels (FP32 accumulation; weights and activations in FP32 or
+ * BF16).  Its prediction only initialises a cavity (dmrt_warm_start); the
+ * lattice Boltzmann solve then runs to its own convergence criterion.
+ * The paper has no such component: it serves the time-to-steady-state goal.
+ *
+ * Network with depth D and channels c_0..c_D (8 input features per voxel:
+ * (log10 Ra - 4.5)/1.5, one-hot wall type, x, y, z in [-1, 1], 1/2 - Y):
+ *   a_0 = act(conv3(x; 8 -> c_0)), s_0 = act(conv3(a_0; c_0 -> c_0));
+ *   a_l = act(conv3(avgpool2(s_{l-1}); c_{l-1} -> c_l)), s_l = act(conv3(a_l))
+ *   for l = 1..D; h_D = s_D; for l = D-1..0: d_l = act(conv3(h_{l+1};
+ *   c_{l+1} -> c_l)), m_l = up2(d_l) + s_l, h_l = act(conv3(m_l; c_l -> c_l));
+ *   out = conv1(h_0; c_0 -> 5).  act: leaky ReLU, slope 0.1.  Loss: mean
+ *   squared error.  Optimiser: Adam (0.9, 0.999, 1e-8) on FP32 master weights.
+ * Tensors are channels-last [batch][z][y][x][channel]; parameters are one
+ * flat FP32 vector, layer by layer in the order above (each conv's weights
+ * [tap][cout][cin], taps (dz, dy, dx) with dx fastest, then its biases).
+ * ---------------------------------------------------------------------- */
+typedef struct dmrt_surrogate dmrt_surrogate_t;
+
+typedef struct dmrt_surrogate_cfg {
+    int grid;        /* n: edge of the cubic grid; n / 2^depth a multiple of 8 */
+    int depth;       /* pooling levels D, 1..3 */
+    int channels[4]; /* c_0..c_D, each dividing 256 and <= 128 */
+    int storage;     /* DMRT_STORE_F32 or DMRT_STORE_BF16 */
+    int max_batch;   /* largest batch of one call */
+    unsigned seed;   /* initial weights: He-uniform from a PCG hash of the seed
+                        (the 1x1 output head and all biases start at zero) */
+} dmrt_surrogate_cfg;
+
+dmrt_status dmrt_surrogate_create(dmrt_surrogate_t **out, const dmrt_surrogate_cfg *cfg);
+void dmrt_surrogate_destroy(dmrt_surrogate_t *s);
+dmrt_status dmrt_surrogate_set_stream(dmrt_surrogate_t *s, void *stream);
+
+/* Number of parameters (-1 for NULL); get / set the FP32 master parameters
+ * (host arrays of that length; set also resets the Adam state). */
+long long dmrt_surrogate_param_count(const dmrt_surrogate_t *s);
+dmrt_status dmrt_surrogate_get_params(dmrt_surrogate_t *s, float *params, long long count);
+dmrt_status dmrt_surrogate_set_params(dmrt_surrogate_t *s, const float *params, long long count);
+
+/* Prediction for `batch` samples (host arrays Ra[batch] > 0, wall[batch] in
+ * 1..3): out[batch][n^3][5] FP32 (host or device per on_device). */
+dmrt_status dmrt_surrogate_predict(dmrt_surrogate_t *s, int batch, const double *ra, const int *wall,
+                                   float *out, int on_device);
+
+/* One Adam step on a batch; target is a DEVICE array [batch][n^3][5] FP32;
+ * *loss (may be NULL) receives the batch loss before the step. */
+dmrt_status dmrt_surrogate_train_step(dmrt_surrogate_t *s, int batch, const double *ra, const int *wall,
+                                      const float *target, float lr, double *loss);
+
+/* Loss and its gradient with respect to every parameter (host grad[count]),
+ * without updating; and the loss alone. */
+dmrt_status dmrt_surrogate_gradients(dmrt_surrogate_t *s, int batch, const double *ra, const int *wall,
+                                     const float *target, float *grad, double *loss);
+dmrt_status dmrt_surrogate_loss(dmrt_surrogate_t *s, int batch, const double *ra, const int *wall,
+                                const float *target, double *loss);
+
+/* Training target of one sample from the planar device fields of
+ * dmrt_fields (u [3][n^3], theta [n^3], rho [n^3] or NULL for rho = 1):
+ * target[n^3][5] (device), velocities divided by uc, density as
+ * (rho - 1)/(3 uc^2).  Queued on `stream` (NULL = legacy default stream). */
+dmrt_status dmrt_surrogate_target_from_fields(const float *u, const float *theta, const float *rho, int n,
+                                              double uc, float *target, void *stream);
+
+/* Initialise a cubic cavity from the surrogate's prediction for (Ra, wall):
+ * the n^3 prediction is resampled trilinearly to the cavity's grid, the
+ * velocity scaled by the cavity's u_c = sqrt(g beta H) and the density by
+ * 3 u_c^2, and the cavity set to the equilibrium of (rho, u, theta) as by
+ * dmrt_init_fields.  Allocates a
+ * temporary device buffer of 5 floats per cavity cell. */
+dmrt_status dmrt_warm_start(dmrt_t *h, dmrt_surrogate_t *s, double Ra, int wall);
+
+const char *dmrt_surrogate_last_error(const dmrt_surrogate_t *s);
+
+/* One convolution layer of the surrogate on device arrays (for testing and
+ * reuse): y = act(conv_k(x, w) + bias) with the layouts above; storage
+ * DMRT_STORE_BF16 reads x and w as bfloat16 (tensor cores when cin is a
+ * multiple of 8 and both pointers are 16-byte aligned) and writes y as
+ * bfloat16 (out_f32 = 0) or float (out_f32 = 1); DMRT_STORE_F32 is all float.
+ * k in {1, 3}; n a multiple of 8; act 0 = none, 1 = leaky ReLU (0.1); bias
+ * (float, may be NULL).  Queued on `stream`; synchronises it. */
+dmrt_status dmrt_nn_conv3d(const void *x, const void *w, const float *bias, void *y, int batch, int n,
+                           int cin, int cout, int k, int act, int storage, int out_f32, void *stream);
+
 /* Text of the last error on this handle ("" if none; static if h is NULL). */
 const char *dmrt_last_error(const dmrt_t *h);
 

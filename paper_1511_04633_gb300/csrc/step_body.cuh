@@ -199,12 +199,16 @@ struct ComputedOffsets {
     template <int Q>
     __device__ __forceinline__ unsigned nb() const
     {
+        // the neighbour offset e.(1, nx, nx*ny) is signed; the sum is taken
+        // modulo 2^32 and is non-negative, since plane exceeds any offset
         if constexpr (Q < 19) {
             constexpr int ex = q19_ex(Q), ey = q19_ey(Q), ez = q19_ez(Q);
-            return Q * plane - (ex + ey * nx + ez * nxy);
+            const int off = ex + ey * static_cast<int>(nx) + ez * static_cast<int>(nxy);
+            return Q * plane - static_cast<unsigned>(off);
         } else {
             constexpr int ex = q7_ex(Q - 19), ey = q7_ey(Q - 19), ez = q7_ez(Q - 19);
-            return Q * plane - (ex + ey * nx + ez * nxy);
+            const int off = ex + ey * static_cast<int>(nx) + ez * static_cast<int>(nxy);
+            return Q * plane - static_cast<unsigned>(off);
         }
     }
     template <int Q>

@@ -59,6 +59,11 @@ class dmrt_cavity_desc(ctypes.Structure):
                 ("Ma", ctypes.c_double), ("wall_type", ctypes.c_int)]
 
 
+class dmrt_surrogate_cfg(ctypes.Structure):
+    _fields_ = [("grid", ctypes.c_int), ("depth", ctypes.c_int), ("channels", ctypes.c_int * 4),
+                ("storage", ctypes.c_int), ("max_batch", ctypes.c_int), ("seed", ctypes.c_uint)]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -119,6 +124,20 @@ def load(build_if_missing: bool = True):
             "dmrt_ensemble_get_populations": ([vp, i, vp, vp, i], i),
             "dmrt_ensemble_member_params": ([vp, i, P(dmrt_params)], i),
             "dmrt_ensemble_last_error": ([vp], ctypes.c_char_p),
+            "dmrt_surrogate_create": ([P(vp), P(dmrt_surrogate_cfg)], i),
+            "dmrt_surrogate_destroy": ([vp], None),
+            "dmrt_surrogate_set_stream": ([vp, vp], i),
+            "dmrt_surrogate_param_count": ([vp], ctypes.c_longlong),
+            "dmrt_surrogate_get_params": ([vp, P(ctypes.c_float), ctypes.c_longlong], i),
+            "dmrt_surrogate_set_params": ([vp, P(ctypes.c_float), ctypes.c_longlong], i),
+            "dmrt_surrogate_predict": ([vp, i, P(d), P(i), vp, i], i),
+            "dmrt_surrogate_train_step": ([vp, i, P(d), P(i), vp, ctypes.c_float, P(d)], i),
+            "dmrt_surrogate_gradients": ([vp, i, P(d), P(i), vp, P(ctypes.c_float), P(d)], i),
+            "dmrt_surrogate_loss": ([vp, i, P(d), P(i), vp, P(d)], i),
+            "dmrt_surrogate_target_from_fields": ([vp, vp, vp, i, d, vp, vp], i),
+            "dmrt_warm_start": ([vp, vp, d, i], i),
+            "dmrt_surrogate_last_error": ([vp], ctypes.c_char_p),
+            "dmrt_nn_conv3d": ([vp, vp, vp, vp, i, i, i, i, i, i, i, i, vp], i),
             "dmrt_status_string": ([i], ctypes.c_char_p),
             "dmrt_version": ([], ctypes.c_char_p),
         }
@@ -160,11 +179,13 @@ def _same_side(*arrs):
     return sides.pop() if sides else 0
 
 
-def check(h, status: int, what: str, ensemble: bool = False):
+def check(h, status: int, what: str, ensemble: bool = False, surrogate: bool = False):
     if status != OK:
         L = load()
         name = L.dmrt_status_string(status).decode()
-        if h:
+        if h and surrogate:
+            msg = L.dmrt_surrogate_last_error(h).decode()
+        elif h:
             msg = (L.dmrt_ensemble_last_error(h) if ensemble else L.dmrt_last_error(h)).decode()
         else:
             msg = ""
@@ -559,3 +580,167 @@ class Ensemble:
         g = np.empty((7,) + shape, np.float32)
         dmrt_ensemble_get_populations(self.e, member, f, g)
         return f, g
+
+
+# ---------------------------------------------------------------- warm-start surrogate
+
+def _scheck(s, status, what):
+    check(s, status, what, surrogate=True)
+
+
+def _samples(ra, wall):
+    ra = np.ascontiguousarray(np.atleast_1d(ra), dtype=np.float64)
+    wall = np.ascontiguousarray(np.atleast_1d(wall), dtype=np.int32)
+    if ra.shape != wall.shape:
+        raise ValueError("Ra and wall must have the same length")
+    return (len(ra), ra, ra.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), wall,
+            wall.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+
+
+def dmrt_surrogate_create(grid: int, depth: int, channels, storage: int = STORE_BF16,
+                          max_batch: int = 1, seed: int = 1):
+    cfg = dmrt_surrogate_cfg()
+    cfg.grid, cfg.depth, cfg.storage, cfg.max_batch, cfg.seed = grid, depth, storage, max_batch, seed
+    ch = list(channels) + [0] * (4 - len(channels))
+    cfg.channels[:] = ch[:4]
+    s = ctypes.c_void_p()
+    _scheck(None, load().dmrt_surrogate_create(ctypes.byref(s), ctypes.byref(cfg)), "dmrt_surrogate_create")
+    return s
+
+
+def dmrt_surrogate_destroy(s):
+    load().dmrt_surrogate_destroy(s)
+
+
+def dmrt_surrogate_set_stream(s, stream):
+    raw = getattr(stream, "cuda_stream", stream)
+    _scheck(s, load().dmrt_surrogate_set_stream(s, raw), "dmrt_surrogate_set_stream")
+
+
+def dmrt_surrogate_param_count(s) -> int:
+    return int(load().dmrt_surrogate_param_count(s))
+
+
+def dmrt_surrogate_get_params(s) -> np.ndarray:
+    n = dmrt_surrogate_param_count(s)
+    out = np.empty(n, np.float32)
+    _scheck(s, load().dmrt_surrogate_get_params(s, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), n),
+            "dmrt_surrogate_get_params")
+    return out
+
+
+def dmrt_surrogate_set_params(s, params):
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    _scheck(s, load().dmrt_surrogate_set_params(s, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), p.size),
+            "dmrt_surrogate_set_params")
+
+
+def dmrt_surrogate_predict(s, ra, wall, out):
+    """out: float32 array / tensor [batch][n^3][5] (host or CUDA)."""
+    b, _, rp, _, wp = _samples(ra, wall)
+    ptr, side = _ptr(out)
+    _scheck(s, load().dmrt_surrogate_predict(s, b, rp, wp, ptr, side), "dmrt_surrogate_predict")
+
+
+def dmrt_surrogate_train_step(s, ra, wall, target, lr: float) -> float:
+    """target: CUDA float32 tensor [batch][n^3][5]; returns the batch loss."""
+    b, _, rp, _, wp = _samples(ra, wall)
+    ptr, side = _ptr(target)
+    if side != 1:
+        raise TypeError("target must be a CUDA tensor")
+    loss = ctypes.c_double()
+    _scheck(s, load().dmrt_surrogate_train_step(s, b, rp, wp, ptr, lr, ctypes.byref(loss)),
+            "dmrt_surrogate_train_step")
+    return loss.value
+
+
+def dmrt_surrogate_gradients(s, ra, wall, target):
+    b, _, rp, _, wp = _samples(ra, wall)
+    ptr, side = _ptr(target)
+    if side != 1:
+        raise TypeError("target must be a CUDA tensor")
+    g = np.empty(dmrt_surrogate_param_count(s), np.float32)
+    loss = ctypes.c_double()
+    _scheck(s, load().dmrt_surrogate_gradients(s, b, rp, wp, ptr, g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                               ctypes.byref(loss)), "dmrt_surrogate_gradients")
+    return g, loss.value
+
+
+def dmrt_surrogate_loss(s, ra, wall, target) -> float:
+    b, _, rp, _, wp = _samples(ra, wall)
+    ptr, side = _ptr(target)
+    if side != 1:
+        raise TypeError("target must be a CUDA tensor")
+    loss = ctypes.c_double()
+    _scheck(s, load().dmrt_surrogate_loss(s, b, rp, wp, ptr, ctypes.byref(loss)), "dmrt_surrogate_loss")
+    return loss.value
+
+
+def dmrt_surrogate_target_from_fields(u, theta, rho, n: int, uc: float, target, stream=None):
+    raw = getattr(stream, "cuda_stream", stream)
+    st = load().dmrt_surrogate_target_from_fields(_ptr(u)[0], _ptr(theta)[0], _ptr(rho)[0], n, uc,
+                                                  _ptr(target)[0], raw)
+    check(None, st, "dmrt_surrogate_target_from_fields")
+
+
+def dmrt_warm_start(h, s, Ra: float, wall: int):
+    _scheck(s, load().dmrt_warm_start(h, s, Ra, wall), "dmrt_warm_start")
+
+
+class Surrogate:
+    """The warm-start network (see include/dmrt.h)."""
+
+    def __init__(self, grid=64, depth=3, channels=(16, 32, 64, 128), storage=STORE_BF16, max_batch=1,
+                 seed=1):
+        self.grid, self.depth, self.channels = grid, depth, tuple(channels)
+        self.max_batch = max_batch
+        self.s = dmrt_surrogate_create(grid, depth, channels, storage, max_batch, seed)
+
+    def close(self):
+        if getattr(self, "s", None):
+            dmrt_surrogate_destroy(self.s)
+            self.s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def param_count(self):
+        return dmrt_surrogate_param_count(self.s)
+
+    def params(self):
+        return dmrt_surrogate_get_params(self.s)
+
+    def set_params(self, p):
+        dmrt_surrogate_set_params(self.s, p)
+
+    def predict(self, ra, wall):
+        b = len(np.atleast_1d(ra))
+        out = np.empty((b, self.grid ** 3, 5), np.float32)
+        dmrt_surrogate_predict(self.s, ra, wall, out)
+        return out
+
+    def train_step(self, ra, wall, target, lr):
+        return dmrt_surrogate_train_step(self.s, ra, wall, target, lr)
+
+    def gradients(self, ra, wall, target):
+        return dmrt_surrogate_gradients(self.s, ra, wall, target)
+
+    def loss(self, ra, wall, target):
+        return dmrt_surrogate_loss(self.s, ra, wall, target)
+
+    def warm_start(self, cavity, Ra, wall):
+        h = cavity.h if hasattr(cavity, "h") else cavity
+        dmrt_warm_start(h, self.s, Ra, wall)
+
+
+def dmrt_nn_conv3d(x, w, bias, y, batch, n, cin, cout, k, act=0, storage=STORE_BF16, stream=None):
+    """One surrogate convolution on CUDA tensors (see include/dmrt.h)."""
+    raw = getattr(stream, "cuda_stream", stream)
+    out_f32 = 1 if str(y.dtype) == "torch.float32" else 0
+    bp = None if bias is None else bias.data_ptr()
+    check(None, load().dmrt_nn_conv3d(x.data_ptr(), w.data_ptr(), bp, y.data_ptr(), batch, n, cin, cout,
+                                      k, act, storage, out_f32, raw), "dmrt_nn_conv3d")

@@ -57,6 +57,18 @@ def ensemble_draws(n: int = 64, seed: int = 1234, edges=(32, 48, 64, 96),
     return out
 
 
+def random_weights(count: int, seed: int, scale: float = 0.3):
+    """`count` float32 values uniform in +-scale (network parameters)."""
+    rng = np.random.default_rng(seed)
+    return rng.uniform(-scale, scale, size=count).astype(np.float32)
+
+
+def random_targets(shape, seed: int, scale: float = 1.0):
+    """float32 normal values of the given shape (training targets)."""
+    rng = np.random.default_rng(seed)
+    return (scale * rng.standard_normal(size=shape)).astype(np.float32)
+
+
 def sample_cells(grid, count: int, seed: int):
     """`count` distinct flat cell indices (x fastest), always including the
     eight corners, for sampled comparisons on large grids."""
@@ -69,4 +81,4 @@ def sample_cells(grid, count: int, seed: int):
 
 
 __all__ = ["random_populations", "random_thermal_populations", "random_fields",
-           "ensemble_draws", "sample_cells"]
+           "ensemble_draws", "random_weights", "random_targets", "sample_cells"]

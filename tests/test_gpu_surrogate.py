@@ -1,0 +1,140 @@
+"""The warm-start surrogate's CUDA forward and backward passes against the
+FP64 numpy oracle of the same network, its training, and its warm start."""
+
+import numpy as np
+import pytest
+
+from oracle import surrogate as S
+from paper_1511_04633_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+CFG = dict(grid=16, depth=1, channels=(8, 16))
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1511_04633_gb300 import dmrt
+    dmrt.load()
+    return torch, dmrt
+
+
+def _setup(dm, storage, seed=5):
+    sur = dm.Surrogate(CFG["grid"], CFG["depth"], CFG["channels"], storage=storage, max_batch=2)
+    net = S.UNet(CFG["grid"], CFG["depth"], CFG["channels"])
+    assert sur.param_count == net.count
+    p = inputs.random_weights(net.count, seed=seed, scale=0.3)
+    sur.set_params(p)
+    return sur, net, p
+
+
+def test_forward_matches_the_oracle_fp32(env):
+    torch, dm = env
+    sur, net, p = _setup(dm, dm.STORE_F32)
+    ra, wall = [2e3, 3e5], [1, 3]
+    got = sur.predict(ra, wall)
+    ref, _ = net.forward(p.astype(np.float64), S.features(ra, wall, CFG["grid"]))
+    ref = ref.reshape(2, -1, 5)
+    assert np.abs(got - ref).max() <= 1e-4 * max(1.0, np.abs(ref).max())
+
+
+def test_gradients_match_the_oracle_fp32(env):
+    torch, dm = env
+    sur, net, p = _setup(dm, dm.STORE_F32)
+    ra, wall = [5e3, 8e4], [2, 1]
+    n = CFG["grid"]
+    t = inputs.random_targets((2, n, n, n, 5), seed=9)
+    g_gpu, loss_gpu = sur.gradients(ra, wall, torch.from_numpy(t.reshape(2, -1, 5)).cuda())
+    loss_ref, g_ref = net.loss_and_grad(p.astype(np.float64), S.features(ra, wall, n), t.astype(np.float64))
+    assert abs(loss_gpu - loss_ref) <= 1e-5 * loss_ref
+    rel = np.linalg.norm(g_gpu - g_ref) / np.linalg.norm(g_ref)
+    assert rel <= 1e-4, rel
+    # every layer, not just the largest
+    for (wo, bo), (cin, cout, k, _) in zip(net.offsets, net.layers):
+        seg = slice(wo, bo + cout)
+        r = np.linalg.norm(g_gpu[seg] - g_ref[seg]) / max(np.linalg.norm(g_ref[seg]), 1e-30)
+        assert r <= 1e-3, (cin, cout, k, r)
+
+
+def test_bf16_storage_tracks_the_oracle(env):
+    torch, dm = env
+    sur, net, p = _setup(dm, dm.STORE_BF16)
+    ra, wall = [5e3, 8e4], [2, 1]
+    n = CFG["grid"]
+    got = sur.predict(ra, wall)
+    pb = torch.from_numpy(p).to(torch.bfloat16).float().numpy().astype(np.float64)
+    ref, _ = net.forward(pb, S.features(ra, wall, n))
+    ref = ref.reshape(2, -1, 5)
+    assert np.abs(got - ref).max() <= 5e-2 * np.abs(ref).max()
+    t = inputs.random_targets((2, n, n, n, 5), seed=9)
+    g_gpu, _ = sur.gradients(ra, wall, torch.from_numpy(t.reshape(2, -1, 5)).cuda())
+    _, g_ref = net.loss_and_grad(pb, S.features(ra, wall, n), t.astype(np.float64))
+    cos = float(np.dot(g_gpu, g_ref) / (np.linalg.norm(g_gpu) * np.linalg.norm(g_ref)))
+    assert cos >= 0.99, cos
+
+
+@pytest.mark.parametrize("k,cin,cout", [(3, 16, 32), (3, 8, 16), (3, 32, 5), (1, 16, 5), (3, 128, 64)])
+@pytest.mark.parametrize("out_f32", [False, True])
+def test_tensor_core_convolution_matches_the_definition(env, k, cin, cout, out_f32):
+    """The bf16 tensor-core convolution on values exactly representable in
+    bf16 against the oracle's FP64 convolution: only the FP32 accumulation
+    and (for bf16 output) the final rounding differ."""
+    torch, dm = env
+    n, batch = 16, 2
+    x = torch.from_numpy(inputs.random_targets((batch, n, n, n, cin), seed=21)).to(torch.bfloat16)
+    w = torch.from_numpy(inputs.random_weights(k ** 3 * cout * cin, seed=22, scale=0.2)).to(torch.bfloat16)
+    b = torch.from_numpy(inputs.random_weights(cout, seed=23, scale=0.5))
+    y = torch.empty((batch, n, n, n, cout), dtype=torch.float32 if out_f32 else torch.bfloat16, device="cuda")
+    dm.dmrt_nn_conv3d(x.cuda(), w.cuda(), b.cuda(), y, batch, n, cin, cout, k, act=1)
+    ref = S.leaky(S.conv3d(x.double().numpy(), w.double().numpy().reshape(k ** 3, cout, cin), b.double().numpy(), k))
+    got = y.double().cpu().numpy()
+    scale = np.abs(ref).max()
+    tol = 2e-5 if out_f32 else 8e-3
+    assert np.abs(got - ref).max() <= tol * scale
+
+
+def test_training_overfits_a_batch_and_is_repeatable(env):
+    torch, dm = env
+    n = CFG["grid"]
+    t = torch.from_numpy(inputs.random_targets((2, n ** 3, 5), seed=11, scale=0.5)).cuda()
+    ra, wall = [3e3, 2e5], [2, 3]
+    runs = []
+    for _ in range(2):
+        sur = dm.Surrogate(CFG["grid"], CFG["depth"], CFG["channels"], storage=dm.STORE_BF16,
+                           max_batch=2, seed=3)
+        losses = [sur.train_step(ra, wall, t, 2e-3) for _ in range(60)]
+        runs.append((losses, sur.params()))
+    assert runs[0][0][-1] < 0.5 * runs[0][0][0]
+    assert runs[0][0] == runs[1][0]
+    assert np.array_equal(runs[0][1], runs[1][1])
+
+
+def test_warm_start_resamples_and_scales_the_prediction(env):
+    """A network whose output is the constant (0, 0, 0, 0.2, 0.5) warm-starts a
+    cavity to u = 0, theta = 0.2 away from the Dirichlet walls and rho =
+    1 + 0.5 * 3 u_c^2."""
+    torch, dm = env
+    sur = dm.Surrogate(CFG["grid"], CFG["depth"], CFG["channels"], storage=dm.STORE_F32)
+    net = S.UNet(CFG["grid"], CFG["depth"], CFG["channels"])
+    p = np.zeros(net.count, np.float32)
+    wo, bo = net.offsets[-1]
+    p[bo + 3] = 0.2  # head bias of theta
+    p[bo + 4] = 0.5  # head bias of (rho - 1) / (3 u_c^2)
+    sur.set_params(p)
+    cav = dm.Cavity((24, 24, 24), 1e4, wall_type=1)
+    sur.warm_start(cav, 1e4, 1)
+    rho, u, th = cav.fields()
+    uc = np.sqrt(cav.params["gbeta"] * 24)
+    assert np.abs(u).max() == 0.0
+    assert np.abs(rho - (1 + 0.5 * 3 * uc * uc)).max() < 1e-6
+    assert np.abs(th[:, 1:-1, :] - 0.2).max() < 1e-6
+
+
+def test_surrogate_rejects_bad_configurations(env):
+    torch, dm = env
+    for grid, depth, ch in ((20, 1, (8, 16)), (16, 2, (8, 16, 32)), (16, 1, (12, 16))):
+        with pytest.raises(dm.DmrtError):
+            dm.Surrogate(grid, depth, ch)
