@@ -157,6 +157,14 @@ dmrt_status dmrt_fields(dmrt_t *h, float *rho, float *u, float *theta, int on_de
  * Requires ny >= 2.  Synchronises. */
 dmrt_status dmrt_nusselt(dmrt_t *h, int wall, double out[3]);
 
+/* Conservative cross-check of dmrt_nusselt (same three outputs): the heat
+ * carried across the wall links in the coming step by the stored
+ * populations of the first fluid layer, q = 2 w_T theta_w - 2 g*_(-y) on the
+ * hot wall and 2 g*_(+y) - 2 w_T theta_w on the cold wall (anti-bounce-back
+ * returns -g* + 2 w_T theta_w), Nu = H q / alpha.  Exact for the conduction
+ * state; equal on both walls at a steady state.  Walled cavities only. */
+dmrt_status dmrt_nusselt_flux(dmrt_t *h, int wall, double out[3]);
+
 /* The local Nusselt number of wall 0 or 1 as a float32 [z][x] map. */
 dmrt_status dmrt_nusselt_local(dmrt_t *h, int wall, float *local, int on_device);
 
@@ -211,6 +219,26 @@ dmrt_status dmrt_get_populations(dmrt_t *h, float *f, float *g, int on_device);
  * Resets the residual history (used for warm starts). */
 dmrt_status dmrt_init_fields(dmrt_t *h, const float *rho, const float *u, const float *theta,
                              int on_device);
+
+/* Checkpoint / resume.  A checkpoint is a self-describing host byte blob:
+ * the handle's grid, wall type, storage, lattice parameters and step count,
+ * its stored populations (with the stochastic-rounding step counter) and its
+ * residual history.  Loading it into a handle created with the same grid,
+ * wall type, storage, residual interval and lattice parameters restores the
+ * state exactly: the continued run is bitwise identical to an uninterrupted
+ * one.  dmrt_checkpoint_size gives the blob size; save writes it to `dst`
+ * (host, `size` bytes at least); load reads it (DMRT_ERR_ARG if the blob does
+ * not match the handle).  Both synchronise. */
+long long dmrt_checkpoint_size(const dmrt_t *h);
+dmrt_status dmrt_checkpoint_save(dmrt_t *h, void *dst, long long size);
+dmrt_status dmrt_checkpoint_load(dmrt_t *h, const void *src, long long size);
+
+/* Anisotropic diffusion (Eqs. (35)-(37)): replace the isotropic thermal
+ * relaxation by the full tensor D (row-major 3x3, lattice units, symmetric
+ * positive definite): tau_bar_ij = delta_ij / 2 + 4 D_ij, and the flux
+ * moments relax with the inverse of that block.  dmrt_nusselt_flux then uses
+ * D_yy.  DMRT_ERR_ARG if D is not symmetric positive definite. */
+dmrt_status dmrt_set_diffusion(dmrt_t *h, const double D[9]);
 
 /* Read the derived lattice parameters. */
 dmrt_status dmrt_get_params(const dmrt_t *h, dmrt_params *out);

@@ -63,6 +63,8 @@ def lib():
             L.orc_set_options.argtypes = [vp, ctypes.c_double, ctypes.c_int]
             L.orc_set_rates.argtypes = [vp, P, P]
             L.orc_get_rates.argtypes = [vp, P, P]
+            L.orc_set_diffusion.restype = ctypes.c_int
+            L.orc_set_diffusion.argtypes = [vp, P]
             L.orc_steps.restype = ctypes.c_long
             L.orc_steps.argtypes = [vp]
             L.orc_set_populations.argtypes = [vp, P, P]
@@ -73,6 +75,8 @@ def lib():
             L.orc_fields.argtypes = [vp, P, P, P]
             L.orc_nusselt.restype = ctypes.c_int
             L.orc_nusselt.argtypes = [vp, ctypes.c_int, P, P]
+            L.orc_nusselt_flux.restype = ctypes.c_int
+            L.orc_nusselt_flux.argtypes = [vp, ctypes.c_int, P, P]
             L.orc_nusselt_from_theta.restype = ctypes.c_int
             L.orc_nusselt_from_theta.argtypes = [P] + [ctypes.c_int] * 4 + [P, P]
             L.orc_residual.restype = ctypes.c_double
@@ -248,6 +252,12 @@ class Oracle:
         q = np.ascontiguousarray(q, dtype=np.float64)
         lib().orc_set_rates(self._h, _d(s), _d(q))
 
+    def set_diffusion(self, D):
+        """Eqs. (35)-(37) with a general (anisotropic) diffusion tensor D."""
+        D = np.ascontiguousarray(D, dtype=np.float64).reshape(9)
+        if lib().orc_set_diffusion(self._h, _d(D)) != 0:
+            raise np.linalg.LinAlgError("singular relaxation matrix")
+
     @property
     def steps(self) -> int:
         return int(lib().orc_steps(self._h))
@@ -287,6 +297,15 @@ class Oracle:
         T = np.zeros(self.shape)
         lib().orc_fields(self._h, _d(rho), _d(u), _d(T))
         return rho, u, T
+
+    def nusselt_flux(self, wall: int = 0):
+        """Link-flux Nusselt numbers ((Nu_3D, Nu_2D, Nu_max), local[z][x])."""
+        out = np.zeros(3)
+        local = np.zeros((self.shape[0], self.shape[2]))
+        rc = lib().orc_nusselt_flux(self._h, wall, _d(out), _d(local))
+        if rc != 0:
+            raise ValueError("nusselt_flux needs walls")
+        return tuple(float(v) for v in out), local
 
     def nusselt(self, wall: int = 0):
         """((Nu_3D, Nu_2D, Nu_max), local[z][x])."""

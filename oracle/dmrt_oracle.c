@@ -151,6 +151,9 @@ typedef struct orc {
     double theta_ref; /* A6 */
     int rho0_local;   /* A4 test switch */
     double s[Q19], q[Q7];
+    /* Eq. (35): the full relaxation matrix Q (inverse of the printed Q^-1);
+     * diagonal (q) unless a diffusion tensor was set */
+    double Qm[Q7][Q7];
     double M[Q19][Q19], Minv[Q19][Q19];
     double N[Q7][Q7], Ninv[Q7][Q7];
     int opp19[Q19], opp7[Q7];
@@ -319,6 +322,12 @@ static long cell_index(const orc_t *o, int x, int y, int z)
     return ((long)z * o->ny + y) * o->nx + x;
 }
 
+static void q_from_rates(orc_t *o)
+{
+    for (int r = 0; r < Q7; ++r)
+        for (int c = 0; c < Q7; ++c) o->Qm[r][c] = (r == c) ? o->q[r] : 0.0;
+}
+
 static void set_default_rates(orc_t *o)
 {
     double s_nu = 1.0 / (3.0 * o->nu + 0.5); /* Eq. (26) */
@@ -327,6 +336,7 @@ static void set_default_rates(orc_t *o)
     o->q[0] = 1.0;
     o->q[1] = o->q[2] = o->q[3] = 1.0 / tau_a;
     o->q[4] = o->q[5] = o->q[6] = 1.0;
+    q_from_rates(o);
 }
 
 orc_t *orc_create(int nx, int ny, int nz, int wall, double nu, double alpha, double gbeta)
@@ -388,6 +398,22 @@ void orc_set_rates(orc_t *o, const double *s, const double *q)
 {
     memcpy(o->s, s, sizeof(o->s));
     memcpy(o->q, q, sizeof(o->q));
+    q_from_rates(o);
+}
+
+/* Eqs. (35)-(37) with a general diffusion tensor D (row-major 3x3, lattice
+ * units, dt = dx = 1): Q^-1 = diag(tau_1, [tau_bar_ij], tau_5, tau_6, tau_7)
+ * with tau_bar_ij = delta_ij / 2 + D_ij / eps, eps = 1/4, and
+ * tau_1 = tau_5 = tau_6 = tau_7 = 1; Q is its inverse.  Returns 0, or -1 if
+ * the matrix is singular. */
+int orc_set_diffusion(orc_t *o, const double *D)
+{
+    double Qi[Q7][Q7];
+    for (int r = 0; r < Q7; ++r)
+        for (int c = 0; c < Q7; ++c) Qi[r][c] = (r == c) ? 1.0 : 0.0;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) Qi[1 + i][1 + j] = (i == j ? 0.5 : 0.0) + D[3 * i + j] / EPS_EQ36;
+    return orc_invert(&Qi[0][0], Q7, &o->Qm[0][0]);
 }
 
 void orc_get_rates(const orc_t *o, double *s, double *q)
@@ -460,7 +486,12 @@ static void collide(const orc_t *o, const double *fin, const double *gin,
     double n[Q7], neq[Q7], ns[Q7];
     matvec(&o->N[0][0], gin, n, Q7);
     orc_neq(T, V, neq);
-    for (int k = 0; k < Q7; ++k) ns[k] = n[k] - o->q[k] * (n[k] - neq[k]);
+    /* Eq. (29): n* = n - Q (n - n_eq), Q the full matrix of Eq. (35) */
+    for (int k = 0; k < Q7; ++k) {
+        double acc = 0.0;
+        for (int l = 0; l < Q7; ++l) acc += o->Qm[k][l] * (n[l] - neq[l]);
+        ns[k] = n[k] - acc;
+    }
     matvec(&o->Ninv[0][0], ns, gout, Q7);
 }
 
@@ -620,6 +651,40 @@ int orc_nusselt(const orc_t *o, int wall, double out[3], double *local)
     int rc = orc_nusselt_from_theta(T, o->nx, o->ny, o->nz, wall, out, local);
     free(T);
     return rc;
+}
+
+/* Conservative cross-check of Eq. (39): the heat carried across the wall
+ * links in one step, from the stored populations.  At the hot wall the
+ * population g*_(-y) of a first-layer cell leaves through the wall and the
+ * anti-bounce-back population -g*_(-y) + 2 w_T theta_w enters, so the net
+ * flux in +y per unit area is 2 w_T theta_w - 2 g*_(-y); at the cold wall
+ * it is 2 g*_(+y) - 2 w_T theta_w.  Nu = H q / (alpha dT), dT = 1.
+ * Same averages as orc_nusselt_from_theta. */
+int orc_nusselt_flux(const orc_t *o, int wall, double out[3], double *local)
+{
+    if (o->wall == 0 || o->ny < 1) return -1;
+    const int ym = (wall == 0) ? 4 : 3; /* D3Q7 index of -y / +y */
+    const int y = (wall == 0) ? 0 : o->ny - 1;
+    const double th_w = (wall == 0) ? 0.5 : -0.5;
+    const double H = (double)o->ny;
+    const int nx = o->nx, nz = o->nz;
+    double sum = 0.0, mid = 0.0, mx = -INFINITY;
+    int c_lo = (nx % 2 == 0) ? nx / 2 - 1 : (nx - 1) / 2;
+    int c_hi = (nx % 2 == 0) ? nx / 2 : (nx - 1) / 2;
+    for (int z = 0; z < nz; ++z)
+        for (int x = 0; x < nx; ++x) {
+            double gl = o->g[ym * o->cells + cell_index(o, x, y, z)];
+            double q = (wall == 0) ? 2.0 * W7[3] * th_w - 2.0 * gl : 2.0 * gl - 2.0 * W7[4] * th_w;
+            double nu_loc = H * q / o->alpha;
+            if (local) local[(long)z * nx + x] = nu_loc;
+            sum += nu_loc;
+            if (nu_loc > mx) mx = nu_loc;
+            if (x == c_lo || x == c_hi) mid += nu_loc;
+        }
+    out[0] = sum / ((double)nx * nz);
+    out[1] = mid / ((double)nz * (c_lo == c_hi ? 1 : 2));
+    out[2] = mx;
+    return 0;
 }
 
 /* Reading A11, from two snapshots taken K steps apart.  u is [3][cells]. */

@@ -502,6 +502,22 @@ dmrt_status dmrt_nusselt(dmrt_t *h, int wall, double out[3])
     return DMRT_OK;
 }
 
+dmrt_status dmrt_nusselt_flux(dmrt_t *h, int wall, double out[3])
+{
+    if (!h || !out) return DMRT_ERR_ARG;
+    if (wall != 0 && wall != 1) return fail(h, DMRT_ERR_ARG, "dmrt_nusselt_flux: wall must be 0 or 1");
+    if (h->wall == DMRT_WALL_PERIODIC) return fail(h, DMRT_ERR_ARG, "dmrt_nusselt_flux: needs walls");
+    DeviceGuard dg(h->device);
+    CK(h,
+       lbm::launch_nusselt_flux(h->storage, h->buf[h->cur], h->G, wall, h->alpha, nullptr, h->partials, h->dnu,
+                                h->stream),
+       "nusselt flux kernel");
+    h->total_launches += 2;
+    CK(h, cudaMemcpyAsync(out, h->dnu, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "copy nusselt");
+    CK(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    return DMRT_OK;
+}
+
 dmrt_status dmrt_nusselt_local(dmrt_t *h, int wall, float *local, int on_device)
 {
     if (!h || !local) return DMRT_ERR_ARG;
@@ -658,6 +674,90 @@ dmrt_status dmrt_init_fields(dmrt_t *h, const float *rho, const float *u, const 
     return DMRT_OK;
 }
 
+namespace {
+
+struct CheckpointHeader {
+    char magic[8];
+    int version, nx, ny, nz, wall, storage, stochastic, K, snaps;
+    double nu, alpha, gbeta;
+    long long steps, pop_bytes, snap_bytes;
+};
+
+constexpr char kMagic[8] = {'D', 'M', 'R', 'T', 'C', 'K', 'P', '1'};
+
+long long pop_bytes(const dmrt_t *h)
+{
+    return static_cast<long long>(h->G.plane) * lbm::kPlanes * lbm::storage_bytes(h->storage) + 256;
+}
+
+long long snap_bytes(const dmrt_t *h) { return cell_count(h->G) * 4 * static_cast<long long>(sizeof(float)); }
+
+}  // namespace
+
+long long dmrt_checkpoint_size(const dmrt_t *h)
+{
+    if (!h) return -1;
+    return static_cast<long long>(sizeof(CheckpointHeader)) + pop_bytes(h) + snap_bytes(h) + 8 * sizeof(double);
+}
+
+dmrt_status dmrt_checkpoint_save(dmrt_t *h, void *dst, long long size)
+{
+    if (!h || !dst || size < dmrt_checkpoint_size(h)) return DMRT_ERR_ARG;
+    DeviceGuard dg(h->device);
+    CheckpointHeader hd{};
+    memcpy(hd.magic, kMagic, 8);
+    hd.version = 1;
+    hd.nx = h->G.nx;
+    hd.ny = h->G.ny;
+    hd.nz = h->G.nz;
+    hd.wall = h->wall;
+    hd.storage = h->storage;
+    hd.stochastic = h->stochastic ? 1 : 0;
+    hd.K = h->K;
+    hd.snaps = h->snaps;
+    hd.nu = h->nu;
+    hd.alpha = h->alpha;
+    hd.gbeta = h->gbeta;
+    hd.steps = h->steps;
+    hd.pop_bytes = pop_bytes(h);
+    hd.snap_bytes = snap_bytes(h);
+    char *p = static_cast<char *>(dst);
+    memcpy(p, &hd, sizeof hd);
+    p += sizeof hd;
+    CK(h, cudaMemcpyAsync(p, h->buf[h->cur], hd.pop_bytes, cudaMemcpyDeviceToHost, h->stream), "copy populations");
+    p += hd.pop_bytes;
+    CK(h, cudaMemcpyAsync(p, h->snap, hd.snap_bytes, cudaMemcpyDeviceToHost, h->stream), "copy snapshot");
+    p += hd.snap_bytes;
+    CK(h, cudaMemcpyAsync(p, h->dres, 8 * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "copy residual");
+    CK(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    return DMRT_OK;
+}
+
+dmrt_status dmrt_checkpoint_load(dmrt_t *h, const void *src, long long size)
+{
+    if (!h || !src || size < static_cast<long long>(sizeof(CheckpointHeader))) return DMRT_ERR_ARG;
+    CheckpointHeader hd;
+    memcpy(&hd, src, sizeof hd);
+    if (memcmp(hd.magic, kMagic, 8) != 0 || hd.version != 1)
+        return fail(h, DMRT_ERR_ARG, "not a dmrt checkpoint");
+    if (hd.nx != h->G.nx || hd.ny != h->G.ny || hd.nz != h->G.nz || hd.wall != h->wall ||
+        hd.storage != h->storage || hd.stochastic != (h->stochastic ? 1 : 0) || hd.K != h->K ||
+        hd.nu != h->nu || hd.alpha != h->alpha || hd.gbeta != h->gbeta || hd.pop_bytes != pop_bytes(h) ||
+        hd.snap_bytes != snap_bytes(h) || size < dmrt_checkpoint_size(h))
+        return fail(h, DMRT_ERR_ARG, "checkpoint of a different cavity (grid, walls, storage or parameters)");
+    DeviceGuard dg(h->device);
+    const char *p = static_cast<const char *>(src) + sizeof hd;
+    CK(h, cudaMemcpyAsync(h->buf[h->cur], p, hd.pop_bytes, cudaMemcpyHostToDevice, h->stream), "copy populations");
+    p += hd.pop_bytes;
+    CK(h, cudaMemcpyAsync(h->snap, p, hd.snap_bytes, cudaMemcpyHostToDevice, h->stream), "copy snapshot");
+    p += hd.snap_bytes;
+    CK(h, cudaMemcpyAsync(h->dres, p, 8 * sizeof(double), cudaMemcpyHostToDevice, h->stream), "copy residual");
+    CK(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    h->steps = hd.steps;
+    h->snaps = hd.snaps;
+    return DMRT_OK;
+}
+
 dmrt_status dmrt_get_params(const dmrt_t *h, dmrt_params *out)
 {
     if (!h || !out) return DMRT_ERR_ARG;
@@ -675,6 +775,44 @@ dmrt_status dmrt_get_params(const dmrt_t *h, dmrt_params *out)
     out->tau_nu = 3.0 * h->nu + 0.5;
     out->tau_alpha = 0.5 + 4.0 * h->alpha;
     out->steps = h->steps;
+    return DMRT_OK;
+}
+
+dmrt_status dmrt_set_diffusion(dmrt_t *h, const double D[9])
+{
+    if (!h || !D) return DMRT_ERR_ARG;
+    // symmetric positive definite (leading minors), finite
+    for (int k = 0; k < 9; ++k)
+        if (!std::isfinite(D[k])) return fail(h, DMRT_ERR_ARG, "dmrt_set_diffusion: non-finite entry");
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            if (D[3 * i + j] != D[3 * j + i]) return fail(h, DMRT_ERR_ARG, "dmrt_set_diffusion: D not symmetric");
+    const double m1 = D[0], m2 = D[0] * D[4] - D[1] * D[3];
+    const double m3 = D[0] * (D[4] * D[8] - D[5] * D[7]) - D[1] * (D[3] * D[8] - D[5] * D[6]) +
+                      D[2] * (D[3] * D[7] - D[4] * D[6]);
+    if (!(m1 > 0.0 && m2 > 0.0 && m3 > 0.0))
+        return fail(h, DMRT_ERR_ARG, "dmrt_set_diffusion: D not positive definite");
+    // Eq. (36): tau_bar = I/2 + D / eps, eps = 1/4; the flux block of Q is its inverse
+    double t[9];
+    for (int k = 0; k < 9; ++k) t[k] = 4.0 * D[k] + ((k % 4 == 0) ? 0.5 : 0.0);
+    const double det = t[0] * (t[4] * t[8] - t[5] * t[7]) - t[1] * (t[3] * t[8] - t[5] * t[6]) +
+                       t[2] * (t[3] * t[7] - t[4] * t[6]);
+    const double inv[9] = {(t[4] * t[8] - t[5] * t[7]) / det, (t[2] * t[7] - t[1] * t[8]) / det,
+                           (t[1] * t[5] - t[2] * t[4]) / det, (t[5] * t[6] - t[3] * t[8]) / det,
+                           (t[0] * t[8] - t[2] * t[6]) / det, (t[2] * t[3] - t[0] * t[5]) / det,
+                           (t[3] * t[7] - t[4] * t[6]) / det, (t[1] * t[6] - t[0] * t[7]) / det,
+                           (t[0] * t[4] - t[1] * t[3]) / det};
+    for (int k = 0; k < 9; ++k) h->C.qa[k] = static_cast<float>(inv[k] / 2.0);  // |N_1|^2 = 2
+    h->C.aniso = 1;
+    h->alpha = D[4];  // the wall-normal diffusivity, used by dmrt_nusselt_flux
+    // captured graphs hold the old parameters
+    DeviceGuard dg(h->device);
+    CK(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    for (auto &gx : h->interval_graph)
+        if (gx) {
+            cudaGraphExecDestroy(gx);
+            gx = nullptr;
+        }
     return DMRT_OK;
 }
 

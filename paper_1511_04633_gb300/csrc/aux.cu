@@ -188,6 +188,49 @@ __global__ void __launch_bounds__(kRedThreads) nusselt_finish(const double *__re
     }
 }
 
+// Link-flux Nusselt number of one z row: the heat carried across the wall
+// links in one step by the stored populations of the first fluid layer,
+// q = 2 w_T theta_w - 2 g*_(-y) (hot wall) or 2 g*_(+y) - 2 w_T theta_w
+// (cold wall), Nu = H q / alpha.  Same per-row partials as nusselt_kernel.
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads) nusselt_flux_kernel(const T *__restrict__ src,
+                                                                    const Geometry G, int wall,
+                                                                    double inv_alpha, float *local,
+                                                                    double *__restrict__ partials)
+{
+    const int z = blockIdx.x;
+    const int y = wall == 0 ? 0 : G.ny - 1;
+    const int plane = wall == 0 ? 19 + 4 : 19 + 3;  // D3Q7 -y / +y
+    const double th_w = wall == 0 ? 0.5 : -0.5;
+    const double H = static_cast<double>(G.ny);
+    const int c_lo = (G.nx % 2 == 0) ? G.nx / 2 - 1 : (G.nx - 1) / 2;
+    const int c_hi = (G.nx % 2 == 0) ? G.nx / 2 : (G.nx - 1) / 2;
+    double v[2] = {0.0, 0.0};
+    double mx = -INFINITY;
+    for (int x = threadIdx.x; x < G.nx; x += blockDim.x) {
+        const long long c = (static_cast<long long>(z) * G.ny + y) * G.nx + x;
+        const double gl = Store<T>::ld(src + plane * G.plane + c);
+        const double q = wall == 0 ? 0.25 * th_w - 2.0 * gl : 2.0 * gl - 0.25 * th_w;
+        const double nu = H * q * inv_alpha;
+        if (local) local[static_cast<long long>(z) * G.nx + x] = static_cast<float>(nu);
+        v[0] += nu;
+        if (x == c_lo || x == c_hi) v[1] += nu;
+        mx = fmax(mx, nu);
+    }
+    __shared__ double shm[kRedThreads / 32];
+    mx = warp_max(mx);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) shm[warp] = mx;
+    block_sum<2, kRedThreads>(v);
+    if (threadIdx.x == 0) {
+        double m = shm[0];
+        for (int w = 1; w < kRedThreads / 32; ++w) m = fmax(m, shm[w]);
+        partials[z * 3 + 0] = v[0];
+        partials[z * 3 + 1] = v[1];
+        partials[z * 3 + 2] = m;
+    }
+}
+
 // ---------------------------------------------------------------- import / export
 
 template <typename T>
@@ -321,6 +364,22 @@ cudaError_t launch_nusselt(int wall_type, int storage, const void *src, const Ge
         using T = std::remove_pointer_t<decltype(tp)>;
         nusselt_kernel<decltype(W)::value, T>
             <<<G.nz, kRedThreads, 0, s>>>(static_cast<const T *>(src), G, wall, local, partials);
+        return cudaSuccess;
+    });
+    if (e != cudaSuccess) return e;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    nusselt_finish<<<1, kRedThreads, 0, s>>>(partials, G, out3);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_nusselt_flux(int storage, const void *src, const Geometry &G, int wall, double alpha,
+                                float *local, double *partials, double *out3, cudaStream_t s)
+{
+    cudaError_t e = dispatch(1, storage, [&](auto, auto *tp) {
+        using T = std::remove_pointer_t<decltype(tp)>;
+        nusselt_flux_kernel<T><<<G.nz, kRedThreads, 0, s>>>(static_cast<const T *>(src), G, wall, 1.0 / alpha,
+                                                            local, partials);
         return cudaSuccess;
     });
     if (e != cudaSuccess) return e;

@@ -48,6 +48,10 @@ cudaError_t launch_nusselt(int wall_type, int storage, const void *src, const Ge
                            int wall, float *local, double *partials, double *out3,
                            cudaStream_t s);
 
+// Link-flux Nusselt numbers of wall 0 / 1 from the stored populations.
+cudaError_t launch_nusselt_flux(int storage, const void *src, const Geometry &G, int wall, double alpha,
+                                float *local, double *partials, double *out3, cudaStream_t s);
+
 // Population and field import / export (dense [q][cells] arrays).
 cudaError_t launch_set_populations(int storage, const float *f, const float *g, void *dst,
                                    const Geometry &G, cudaStream_t s);

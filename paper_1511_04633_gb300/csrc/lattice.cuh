@@ -231,6 +231,11 @@ struct CollideParams {
     float rq[7];      // q_k / |N_k|^2 (Eqs. (35),(36)); entry 0 unused
     float gbeta;      // g beta dT (lattice units)
     float theta_ref;  // reference temperature of Eq. (16)
+    // anisotropic diffusion (Eqs. (35)-(37) with off-diagonal tau_bar): the
+    // 3x3 block of Q acting on the flux moments, divided by |N_k|^2 = 2;
+    // used instead of rq[1..3] when aniso != 0
+    float qa[9];
+    int aniso;
 };
 
 struct Geometry {

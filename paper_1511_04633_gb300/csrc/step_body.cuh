@@ -165,9 +165,17 @@ __device__ __forceinline__ void collide_pairs(const CollideParams &C, float d[19
     d[17] -= E16 - O16;
 
     // ---- energy: n - n^eq with n^eq = (T, V T, 3/4 T, 0, 0) (Eqs. (33),(34))
-    const float c1 = C.rq[1] * (tax - vx * T);
-    const float c2 = C.rq[2] * (tay - vy * T);
-    const float c3 = C.rq[3] * (taz - vz * T);
+    const float e1 = tax - vx * T, e2 = tay - vy * T, e3 = taz - vz * T;
+    float c1, c2, c3;
+    if (C.aniso) {  // uniform: the full flux block of Q (Eq. (35))
+        c1 = fmaf(C.qa[0], e1, fmaf(C.qa[1], e2, C.qa[2] * e3));
+        c2 = fmaf(C.qa[3], e1, fmaf(C.qa[4], e2, C.qa[5] * e3));
+        c3 = fmaf(C.qa[6], e1, fmaf(C.qa[7], e2, C.qa[8] * e3));
+    } else {
+        c1 = C.rq[1] * e1;
+        c2 = C.rq[2] * e2;
+        c3 = C.rq[3] * e3;
+    }
     const float c4 = C.rq[4] * (6.0f * g[0] - tsm - 0.75f * T);
     const float c5 = C.rq[5] * (2.0f * tsx - (tsy + tsz));
     const float c6 = C.rq[6] * (tsy - tsz);

@@ -98,6 +98,7 @@ def load(build_if_missing: bool = True):
             "dmrt_fields": ([vp, vp, vp, vp, i], i),
             "dmrt_nusselt": ([vp, i, P(d)], i),
             "dmrt_nusselt_local": ([vp, i, vp, i], i),
+            "dmrt_nusselt_flux": ([vp, i, P(d)], i),
             "dmrt_nusselt_noalloc": ([vp, i, i, i, i, vp, P(d)], i),
             "dmrt_residual": ([vp, P(d)], i),
             "dmrt_run_to_steady": ([vp, d, l_, P(l_), P(d)], i),
@@ -105,6 +106,10 @@ def load(build_if_missing: bool = True):
             "dmrt_get_populations": ([vp, vp, vp, i], i),
             "dmrt_init_fields": ([vp, vp, vp, vp, i], i),
             "dmrt_get_params": ([vp, P(dmrt_params)], i),
+            "dmrt_set_diffusion": ([vp, P(d)], i),
+            "dmrt_checkpoint_size": ([vp], ctypes.c_longlong),
+            "dmrt_checkpoint_save": ([vp, vp, ctypes.c_longlong], i),
+            "dmrt_checkpoint_load": ([vp, vp, ctypes.c_longlong], i),
             "dmrt_set_timing": ([vp, i], i),
             "dmrt_get_stats": ([vp, P(dmrt_stats), i], i),
             "dmrt_last_error": ([vp], ctypes.c_char_p),
@@ -246,6 +251,12 @@ def dmrt_nusselt(h, wall: int = 0):
     return tuple(out)
 
 
+def dmrt_nusselt_flux(h, wall: int = 0):
+    out = (ctypes.c_double * 3)()
+    check(h, load().dmrt_nusselt_flux(h, wall, out), "dmrt_nusselt_flux")
+    return tuple(out)
+
+
 def dmrt_nusselt_local(h, wall, local):
     p, side = _ptr(local)
     check(h, load().dmrt_nusselt_local(h, wall, p, side), "dmrt_nusselt_local")
@@ -299,6 +310,27 @@ def dmrt_get_params(h) -> dict:
     p = dmrt_params()
     check(h, load().dmrt_get_params(h, ctypes.byref(p)), "dmrt_get_params")
     return {k: getattr(p, k) for k, _ in dmrt_params._fields_}
+
+
+def dmrt_set_diffusion(h, D):
+    arr = (ctypes.c_double * 9)(*np.asarray(D, dtype=np.float64).reshape(9).tolist())
+    check(h, load().dmrt_set_diffusion(h, arr), "dmrt_set_diffusion")
+
+
+def dmrt_checkpoint_size(h) -> int:
+    return int(load().dmrt_checkpoint_size(h))
+
+
+def dmrt_checkpoint_save(h) -> bytes:
+    n = dmrt_checkpoint_size(h)
+    buf = ctypes.create_string_buffer(n)
+    check(h, load().dmrt_checkpoint_save(h, buf, n), "dmrt_checkpoint_save")
+    return buf.raw
+
+
+def dmrt_checkpoint_load(h, blob: bytes):
+    buf = ctypes.create_string_buffer(bytes(blob), len(blob))
+    check(h, load().dmrt_checkpoint_load(h, buf, len(blob)), "dmrt_checkpoint_load")
 
 
 def dmrt_set_timing(h, enabled: bool):
@@ -380,6 +412,9 @@ class Cavity:
     def nusselt(self, wall=0):
         return dmrt_nusselt(self.h, wall)
 
+    def nusselt_flux(self, wall=0):
+        return dmrt_nusselt_flux(self.h, wall)
+
     def nusselt_local(self, wall=0):
         out = np.empty((self.grid[2], self.grid[0]), np.float32)
         dmrt_nusselt_local(self.h, wall, out)
@@ -394,6 +429,15 @@ class Cavity:
     def set_populations(self, f, g):
         dmrt_set_populations(self.h, np.ascontiguousarray(f, np.float32),
                              np.ascontiguousarray(g, np.float32))
+
+    def set_diffusion(self, D):
+        dmrt_set_diffusion(self.h, D)
+
+    def save(self) -> bytes:
+        return dmrt_checkpoint_save(self.h)
+
+    def load(self, blob: bytes):
+        dmrt_checkpoint_load(self.h, blob)
 
     def populations(self):
         f = np.empty((19,) + self.shape, np.float32)

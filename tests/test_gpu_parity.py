@@ -55,6 +55,10 @@ def _compare_nusselt(gpu, orc, walls=(0, 1)):
         (no, loc_o) = orc.nusselt(w)
         for a, b in zip(ng, no):
             assert abs(a - b) <= NU_RTOL * abs(b), (w, ng, no)
+        fg = gpu.nusselt_flux(w)
+        (fo, _) = orc.nusselt_flux(w)
+        for a, b in zip(fg, fo):
+            assert abs(a - b) <= NU_RTOL * max(abs(b), 1.0), (w, fg, fo)
         loc_g = gpu.nusselt_local(w)
         assert np.abs(loc_g - loc_o).max() <= NU_RTOL * max(1.0, np.abs(loc_o).max())
 
@@ -160,6 +164,39 @@ def test_periodic_random_state(dm):
     gpu.step(300)
     orc.step(300)
     _compare_fields(gpu, orc)
+
+
+def _tensor():
+    a, b = 0.6, 0.9
+    Rz = np.array([[np.cos(a), -np.sin(a), 0], [np.sin(a), np.cos(a), 0], [0, 0, 1]])
+    Rx = np.array([[1, 0, 0], [0, np.cos(b), -np.sin(b)], [0, np.sin(b), np.cos(b)]])
+    R = Rz @ Rx
+    D = R @ np.diag([0.02, 0.05, 0.08]) @ R.T
+    return (D + D.T) / 2
+
+
+@pytest.mark.parametrize("wall,grid", [(0, (12, 10, 9)), (2, (16, 14, 12)), (3, (16, 16, 16))])
+def test_anisotropic_diffusion_matches_the_oracle(dm, wall, grid):
+    D = _tensor()
+    lattice = (0.05, 0.05, 1e-3)
+    gpu, orc = _pair(dm, grid, wall, lattice=lattice, residual_interval=10)
+    gpu.set_diffusion(D)
+    orc.set_diffusion(D)
+    if wall == 0:
+        rho, u, th = inputs.random_fields(grid, seed=17)
+        gpu.init_fields(rho, u, th)
+        orc.init_fields(rho.astype(np.float64), u.astype(np.float64), th.astype(np.float64))
+    gpu.step(300)   # graph replays (K = 10) after the tensor was set
+    orc.step(300)
+    _compare_fields(gpu, orc)
+
+
+def test_set_diffusion_rejects_bad_tensors(dm):
+    gpu = dm.Cavity((8, 8, 8), 1e4, wall_type=1)
+    for D in (np.diag([0.1, -0.1, 0.1]), np.array([[0.1, 0.2, 0], [0, 0.1, 0], [0, 0, 0.1]])):
+        with pytest.raises(dm.DmrtError) as ei:
+            gpu.set_diffusion(D)
+        assert ei.value.status == dm.ERR_ARG
 
 
 def test_periodic_conservation_on_gpu(dm):

@@ -97,17 +97,20 @@ def test_tensor_core_convolution_matches_the_definition(env, k, cin, cout, out_f
 
 
 def test_training_overfits_a_batch_and_is_repeatable(env):
+    """The student (zero output head) learns the outputs of a teacher network
+    with random weights; two runs from the same seed are bitwise equal."""
     torch, dm = env
-    n = CFG["grid"]
-    t = torch.from_numpy(inputs.random_targets((2, n ** 3, 5), seed=11, scale=0.5)).cuda()
     ra, wall = [3e3, 2e5], [2, 3]
+    teacher = dm.Surrogate(CFG["grid"], CFG["depth"], CFG["channels"], storage=dm.STORE_F32, max_batch=2)
+    teacher.set_params(inputs.random_weights(teacher.param_count, seed=12, scale=0.2))
+    t = torch.from_numpy(teacher.predict(ra, wall)).cuda()
     runs = []
     for _ in range(2):
         sur = dm.Surrogate(CFG["grid"], CFG["depth"], CFG["channels"], storage=dm.STORE_BF16,
                            max_batch=2, seed=3)
-        losses = [sur.train_step(ra, wall, t, 2e-3) for _ in range(60)]
+        losses = [sur.train_step(ra, wall, t, 2e-3) for _ in range(120)]
         runs.append((losses, sur.params()))
-    assert runs[0][0][-1] < 0.5 * runs[0][0][0]
+    assert runs[0][0][-1] < 0.3 * runs[0][0][0]
     assert runs[0][0] == runs[1][0]
     assert np.array_equal(runs[0][1], runs[1][1])
 

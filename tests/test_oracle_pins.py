@@ -327,6 +327,9 @@ def test_conduction_limit_is_linear_with_unit_nusselt(orc, wall):
         (n3, n2, nmax), local = o.nusselt(w)
         assert abs(n3 - 1) < 1e-8 and abs(n2 - 1) < 1e-8 and abs(nmax - 1) < 1e-8
         assert np.abs(local - 1).max() < 1e-8
+        # the heat carried across the wall links is the conductive flux alpha / H
+        (f3, f2, fmax), flocal = o.nusselt_flux(w)
+        assert np.abs(flocal - 1).max() < 1e-8
 
 
 def _decay_rate(series, n_steps):
@@ -370,6 +373,48 @@ def test_thermal_wave_decays_at_the_eq36_diffusivity(orc):
         o.step(1000)
     rate = _decay_rate(amps, 1000)
     assert abs(rate / (alpha * k * k) - 1) < 5e-3
+
+
+def _rotated_tensor(d, angles):
+    a, b = angles
+    Rz = np.array([[np.cos(a), -np.sin(a), 0], [np.sin(a), np.cos(a), 0], [0, 0, 1]])
+    Rx = np.array([[1, 0, 0], [0, np.cos(b), -np.sin(b)], [0, np.sin(b), np.cos(b)]])
+    R = Rz @ Rx
+    return R @ np.diag(d) @ R.T
+
+
+@pytest.mark.parametrize("kvec", [(1, 1, 0), (1, 0, 1), (0, 1, -1), (1, 1, 1)])
+def test_anisotropic_diffusion_decays_at_k_D_k(orc, kvec):
+    """Eqs. (35)-(37) with off-diagonal tau_bar: a theta mode exp(i k.x) in a
+    periodic box decays at the textbook rate k.D.k of the full tensor."""
+    n = 32
+    grid = (n, n, n)
+    D = _rotated_tensor([0.02, 0.05, 0.08], (0.6, 0.9))
+    o = orc.Oracle(grid, 0, 0.05, 0.05, 0.0)
+    o.set_diffusion(D)
+    k = 2 * math.pi / n * np.array(kvec, dtype=float)
+    z, y, x = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    phase = k[0] * x + k[1] * y + k[2] * z
+    o.init_fields(np.ones(o.shape), np.zeros((3,) + o.shape), 0.1 * np.cos(phase))
+    o.step(20)
+    amps = []
+    for _ in range(2):
+        _, _, T = o.fields()
+        amps.append(2 * np.mean(T * np.cos(phase)))
+        o.step(300)
+    rate = _decay_rate(amps, 300)
+    assert abs(rate / (k @ D @ k) - 1) < 1e-2
+
+
+def test_isotropic_tensor_reproduces_the_default_rates(orc):
+    grid = (6, 7, 5)
+    a = orc.Oracle.physical(grid, 2, 3e4)
+    b = orc.Oracle.physical(grid, 2, 3e4)
+    _, alpha, _ = orc.lattice_from_physics(7, 3e4, 0.71, 0.1)
+    b.set_diffusion(alpha * np.eye(3))
+    a.step(50)
+    b.step(50)
+    np.testing.assert_allclose(a.populations()[1], b.populations()[1], atol=1e-15)
 
 
 def test_temperature_is_advected_by_the_flow_velocity(orc):
@@ -433,6 +478,20 @@ def test_nusselt_is_exact_for_quadratic_profiles(orc):
     # odd nx: the single centre column
     (o3, o2, _), loc = orc.nusselt_from_theta(theta[..., :5], wall=0)
     assert abs(o2 - a[:, 2].mean()) < 1e-12
+
+
+def test_flux_nusselt_balances_at_steady_convection(orc):
+    """At a convecting steady state every heat unit entering through the hot
+    wall leaves through the cold wall: the link fluxes of the two walls are
+    equal (conservation), and the gradient formula agrees with them to its
+    discretisation error."""
+    o = orc.Oracle.physical((10, 10, 10), 2, 1e4)
+    o.step(6000)
+    (h3, _, _), _ = o.nusselt_flux(0)
+    (c3, _, _), _ = o.nusselt_flux(1)
+    assert abs(h3 - c3) < 1e-6 * h3
+    (g3, _, _), _ = o.nusselt(0)
+    assert abs(g3 - h3) < 0.05 * h3
 
 
 def test_residual_definition(orc):
