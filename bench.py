@@ -45,14 +45,23 @@ WALL_NAMES = {1: "Type 1 (adiabatic side walls)", 2: "Type 2 (linear side walls)
               3: "Type 3 (linear x walls, adiabatic z walls)"}
 
 
+STREAMINGS = {"ab": 0, "inplace": 1}
+
+
 def workload(args) -> str:
     n = args.grid
+    scheme = "" if args.streaming == "ab" else ", in-place streaming (one population buffer)"
     return (f"{n}^3 cavity, {WALL_NAMES[args.wall]}, Ra={args.ra:g}, Pr={PR}, Ma={MA}, from rest, "
-            f"{args.storage} population storage; one step = {args.inner} fused LBM steps + "
+            f"{args.storage} population storage{scheme}; one step = {args.inner} fused LBM steps + "
             f"residual + hot-wall Nu")
+
+
 STEP_KERNEL_SOURCES = ["paper_1511_04633_gb300/csrc/step.cu",
                        "paper_1511_04633_gb300/csrc/step_body.cuh",
                        "paper_1511_04633_gb300/csrc/lattice.cuh"]
+INPLACE_KERNEL_SOURCES = ["paper_1511_04633_gb300/csrc/step_inplace.cu",
+                          "paper_1511_04633_gb300/csrc/step_body.cuh",
+                          "paper_1511_04633_gb300/csrc/lattice.cuh"]
 
 
 # ---------------------------------------------------------------- distributed plumbing
@@ -161,17 +170,18 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def step_kernel_digest() -> str:
+def step_kernel_digest(streaming: str = "ab") -> str:
     h = hashlib.sha256()
-    for rel in STEP_KERNEL_SOURCES:
+    for rel in (STEP_KERNEL_SOURCES if streaming == "ab" else INPLACE_KERNEL_SOURCES):
         with open(os.path.join(ROOT, rel), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(storage: str = "f32", wall: int = 2):
+def profiled_traffic(storage: str = "f32", wall: int = 2, streaming: str = "ab"):
     """DRAM bytes per step-kernel launch from the committed ncu summary, only
-    if it was taken on the current kernel sources for this storage and wall."""
+    if it was taken on the current kernel sources for this storage, wall and
+    streaming scheme."""
     path = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
     try:
         with open(path) as fh:
@@ -180,8 +190,9 @@ def profiled_traffic(storage: str = "f32", wall: int = 2):
         return None
     recs = t if isinstance(t, list) else [t]
     for rec in recs:
-        if (rec.get("source_digest") == step_kernel_digest()
-                and rec.get("storage", "f32") == storage and rec.get("wall", 2) == wall):
+        if (rec.get("source_digest") == step_kernel_digest(streaming)
+                and rec.get("storage", "f32") == storage and rec.get("wall", 2) == wall
+                and rec.get("streaming", "ab") == streaming):
             return rec.get("dram_bytes_per_launch")
     return None
 
@@ -260,7 +271,8 @@ def run_dmrt(args, rank, local, world):
     grid = (args.grid,) * 3
     cells = grid[0] * grid[1] * grid[2]
     storage = STORAGES[args.storage]
-    cav = dmrt.Cavity(grid, args.ra, PR, MA, args.wall, storage=storage)
+    cav = dmrt.Cavity(grid, args.ra, PR, MA, args.wall, storage=storage,
+                      streaming=STREAMINGS[args.streaming])
     dmrt.dmrt_set_stream(cav.h, stream)
     inner = args.inner
 
@@ -298,7 +310,7 @@ def run_dmrt(args, rank, local, world):
     bytes_per_cell = stats["bytes_per_cell"]
     achieved = bytes_per_cell * cells / launch_s / 1e9
     peak, peak_src = measured_peaks()
-    traffic = profiled_traffic(args.storage, args.wall)
+    traffic = profiled_traffic(args.storage, args.wall, args.streaming)
 
     # end to end through the C ABI with host buffers: upload the start fields
     # from pinned memory, step, read the fields and Nu back
@@ -335,6 +347,7 @@ def run_dmrt(args, rank, local, world):
             dist.destroy_process_group()
         return
 
+    nbuf = 2 if args.streaming == "ab" else 1
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         mlups, cores, n = oracle_sample(grid, args.wall, args.ra, args.cpu_seconds)
@@ -351,13 +364,16 @@ def run_dmrt(args, rank, local, world):
                    "Ra": args.ra, "Pr": PR, "Ma": MA, "lbm_steps_per_step": inner,
                    "storage": f"{args.storage} deviations from rest equilibrium"
                               + ("" if storage == 0 else ", stochastic rounding"),
-                   "l2": f"inputs larger than L2 (two {bytes_per_cell / 2 * cells / 1e6:.0f} MB "
-                         f"population buffers)" if bytes_per_cell / 2 * cells > 129e6
+                   "streaming": "two population buffers (A-B)" if args.streaming == "ab"
+                                else "in place: one population buffer, two alternating kernels",
+                   "l2": f"inputs larger than L2 ({nbuf} x {bytes_per_cell / 2 * cells / 1e6:.0f} MB "
+                         f"population buffer)" if bytes_per_cell / 2 * cells > 129e6
                          else "inputs fit in L2: not a DRAM measurement",
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
-                     "kernel": f"step_kernel<{args.wall}, {args.storage}>",
+                     "kernel": (f"step_kernel<{args.wall}, {args.storage}>" if args.streaming == "ab"
+                                else f"step_inplace_kernel<{args.wall}, {args.storage}> (both phases)"),
                      "bytes_per_cell": bytes_per_cell, "launch_us": launch_s * 1e6},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": h2d,
@@ -476,6 +492,8 @@ def main(argv=None):
                     help="oracle LBM steps per reference benchmark step")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--storage", choices=sorted(STORAGES), default="f32")
+    ap.add_argument("--streaming", choices=sorted(STREAMINGS), default="ab",
+                    help="two population buffers, or one updated in place")
     ap.add_argument("--grid", type=int, default=GRID[0], help="cubic cavity edge")
     ap.add_argument("--wall", type=int, choices=[1, 2, 3], default=WALL)
     ap.add_argument("--ra", type=float, default=RA)

@@ -78,12 +78,26 @@ typedef enum {
     DMRT_ROUND_STOCHASTIC = 2,
 } dmrt_rounding;
 
+/* How the populations stream (the method is the same; only the memory
+ * scheme differs).
+ *  AB     : two population buffers; each step pulls from one and writes the
+ *           other (2 x 26 values per cell held on the device).
+ *  INPLACE: one buffer updated in place by two alternating kernels (the AA
+ *           access pattern): half the population memory, the same HBM
+ *           traffic per step, and bitwise the same results as AB in every
+ *           call of this API.  Not available for ensembles. */
+typedef enum {
+    DMRT_STREAM_AB = 0,
+    DMRT_STREAM_INPLACE = 1,
+} dmrt_streaming;
+
 /* Optional creation settings; pass NULL for the defaults (zero-initialised
  * fields select the defaults). */
 typedef struct dmrt_opts {
     int storage;           /* dmrt_storage; default DMRT_STORE_F32 */
     int residual_interval; /* K of the convergence residual; 0 = 100 */
     int rounding;          /* dmrt_rounding; default DMRT_ROUND_AUTO */
+    int streaming;         /* dmrt_streaming; default DMRT_STREAM_AB */
 } dmrt_opts;
 
 /* Derived lattice parameters of a handle (read-only view). */
@@ -92,6 +106,8 @@ typedef struct dmrt_params {
     double nu, alpha, gbeta;   /* lattice viscosity, diffusivity, g*beta*dT */
     double tau_nu, tau_alpha;  /* 3 nu + 1/2 (Eq. (26)); 1/2 + 4 alpha (Eq. (36)) */
     long steps;                /* time steps taken since creation / last reset */
+    int streaming;             /* dmrt_streaming */
+    long long device_bytes;    /* device memory the handle holds now */
 } dmrt_params;
 
 /* Counters for profiling and for the benchmark's launch count. */
@@ -221,11 +237,12 @@ dmrt_status dmrt_init_fields(dmrt_t *h, const float *rho, const float *u, const 
                              int on_device);
 
 /* Checkpoint / resume.  A checkpoint is a self-describing host byte blob:
- * the handle's grid, wall type, storage, lattice parameters and step count,
- * its stored populations (with the stochastic-rounding step counter) and its
+ * the handle's grid, wall type, storage, streaming scheme, lattice
+ * parameters and step count, its stored populations (with the
+ * stochastic-rounding step counters, in the buffer's own layout) and its
  * residual history.  Loading it into a handle created with the same grid,
- * wall type, storage, residual interval and lattice parameters restores the
- * state exactly: the continued run is bitwise identical to an uninterrupted
+ * wall type, storage, streaming scheme, residual interval and lattice
+ * parameters restores the state exactly: the continued run is bitwise identical to an uninterrupted
  * one.  dmrt_checkpoint_size gives the blob size; save writes it to `dst`
  * (host, `size` bytes at least); load reads it (DMRT_ERR_ARG if the blob does
  * not match the handle).  Both synchronise. */
@@ -412,6 +429,17 @@ const char *dmrt_surrogate_last_error(const dmrt_surrogate_t *s);
  * (float, may be NULL).  Queued on `stream`; synchronises it. */
 dmrt_status dmrt_nn_conv3d(const void *x, const void *w, const float *bias, void *y, int batch, int n,
                            int cin, int cout, int k, int act, int storage, int out_f32, void *stream);
+
+/* Round n float32 values to a population storage format and back, exactly
+ * as the step kernel stores populations: in and out are device arrays of n
+ * floats (may alias); storage is a dmrt_storage, rounding a dmrt_rounding
+ * (AUTO = stochastic for 16-bit).  Stochastic rounding draws its bits from
+ * the PCG hash of (i XOR hash(seed)) for element i, so a call is
+ * deterministic.  F16 values are stored times 2^10, as in the cavity
+ * buffers.  Queued on `stream` (NULL = the legacy default stream); does not
+ * synchronise.  DMRT_ERR_ARG for a bad storage, rounding or n < 0. */
+dmrt_status dmrt_round_to_storage(int storage, int rounding, const float *in, float *out, long long n,
+                                  unsigned seed, void *stream);
 
 /* Text of the last error on this handle ("" if none; static if h is NULL). */
 const char *dmrt_last_error(const dmrt_t *h);

@@ -1,7 +1,8 @@
 // api.cu -- host implementation of the C ABI declared in include/dmrt.h.
 //
-// The handle owns two population buffers (A-B ping-pong, 26 planes each), the
-// residual snapshot and the reduction scratch.  Every entry point validates
+// The handle owns its population buffers (two for the A-B ping-pong scheme,
+// one for in-place streaming; 26 planes each), the residual snapshot and the
+// reduction scratch.  Every entry point validates
 // its arguments, queues work on the handle's stream and converts CUDA errors
 // into a dmrt_status plus a message; nothing throws across the ABI.
 #include <algorithm>
@@ -33,6 +34,10 @@ struct dmrt {
 
     void *buf[2] = {nullptr, nullptr};   // ping-pong population buffers (storage type)
     int cur = 0;                          // buffer holding the current state
+    bool inplace = false;                 // one buffer, in-place streaming (buf[0])
+    int parity = 0;                       // in-place: layout of the state (steps mod 2)
+    lbm::InplaceGeometry SI{};
+    long long device_bytes = 0;           // device memory held by the handle
     float *snap = nullptr;                // residual snapshot: theta, u (4 planes)
     double *partials = nullptr;           // reduction scratch
     size_t npartials = 0;
@@ -48,7 +53,8 @@ struct dmrt {
     int snaps = 0;  // residual points taken since the last reset (capped at 2)
 
     // CUDA graphs of one full residual interval (K steps), one per starting
-    // buffer; captured on first use, replayed afterwards.
+    // buffer (A-B) or layout (in-place); captured on first use, replayed
+    // afterwards.
     bool use_graphs = true;
     bool use_pdl = true;
     cudaGraphExec_t interval_graph[2] = {nullptr, nullptr};
@@ -119,6 +125,31 @@ long long cell_count(const Geometry &G)
     return static_cast<long long>(G.nx) * G.ny * G.nz;
 }
 
+// Geometry of the current state, with the layout the aux kernels must read.
+Geometry state_geometry(const dmrt_t *h)
+{
+    Geometry G = h->G;
+    G.layout = !h->inplace ? lbm::kLayoutAB
+                           : (h->parity ? lbm::kLayoutStreamed : lbm::kLayoutSwapped);
+    return G;
+}
+
+// Which of the two alternating states the handle is in: the current buffer
+// (A-B) or the layout parity (in-place).  Toggles with every step.
+int &phase(dmrt_t *h) { return h->inplace ? h->parity : h->cur; }
+
+// One fused step from state `ph`.
+cudaError_t launch_one_step(dmrt_t *h, int ph)
+{
+    if (h->inplace)
+        return lbm::launch_step_inplace(h->wall, h->storage, h->stochastic, h->buf[0], ph, h->SI,
+                                        h->G, h->C, h->block, h->stream, h->use_pdl);
+    return lbm::launch_step(h->wall, h->storage, h->stochastic, h->buf[ph], h->buf[ph ^ 1], h->S,
+                            h->G, h->C, h->block, h->stream, h->use_pdl);
+}
+
+bool periodic(const dmrt_t *h) { return h->wall == DMRT_WALL_PERIODIC; }
+
 // Relaxation rates of Eq. (26) (flow) and Eqs. (35),(36) (energy), folded with
 // the squared norms of the moment basis.
 void fill_rates(dmrt_t *h)
@@ -143,10 +174,12 @@ dmrt_status ensure_staging(dmrt_t *h, size_t floats)
 {
     if (h->staging_floats >= floats) return DMRT_OK;
     if (h->staging) cudaFree(h->staging);
+    h->device_bytes -= static_cast<long long>(h->staging_floats * sizeof(float));
     h->staging = nullptr;
     h->staging_floats = 0;
     CK(h, cudaMalloc(&h->staging, floats * sizeof(float)), "cudaMalloc(staging)");
     h->staging_floats = floats;
+    h->device_bytes += static_cast<long long>(floats * sizeof(float));
     return DMRT_OK;
 }
 
@@ -182,7 +215,7 @@ dmrt_status collect_timing(dmrt_t *h)
 dmrt_status run_residual(dmrt_t *h)
 {
     CK(h,
-       lbm::launch_residual(h->wall, h->storage, h->buf[h->cur], h->G, h->snap,
+       lbm::launch_residual(h->wall, h->storage, h->buf[h->cur], state_geometry(h), h->snap,
                             h->snaps > 0 ? 1 : 0, h->K, h->partials, h->dres, h->stream),
        "residual kernel");
     h->total_launches += 2;
@@ -190,7 +223,7 @@ dmrt_status run_residual(dmrt_t *h)
     return DMRT_OK;
 }
 
-// Capture K consecutive step launches starting from buffer `start` into an
+// Capture K consecutive step launches starting from state `start` into an
 // executable graph.  Returns false (and leaves graphs off) if the stream
 // cannot be captured, e.g. the legacy default stream.
 bool capture_interval(dmrt_t *h, int start)
@@ -200,12 +233,11 @@ bool capture_interval(dmrt_t *h, int start)
         cudaGetLastError();
         return false;
     }
-    int cur = start;
+    int ph = start;
     bool ok = true;
     for (long s = 0; s < h->K && ok; ++s) {
-        ok = lbm::launch_step(h->wall, h->storage, h->stochastic, h->buf[cur], h->buf[cur ^ 1],
-                              h->S, h->G, h->C, h->block, h->stream, h->use_pdl) == cudaSuccess;
-        cur ^= 1;
+        ok = launch_one_step(h, ph) == cudaSuccess;
+        ph ^= 1;
     }
     cudaGraph_t graph = nullptr;
     ok = (cudaStreamEndCapture(h->stream, &graph) == cudaSuccess) && ok && graph;
@@ -237,11 +269,12 @@ dmrt_status run_steps(dmrt_t *h, long n)
             CK(h, cudaEventRecord(e0, h->stream), "cudaEventRecord");
         }
         bool graphed = false;
+        int &ph = phase(h);
         if (chunk == h->K && h->K <= kMaxGraphSteps && h->use_graphs) {
-            if (!h->interval_graph[h->cur] && !capture_interval(h, h->cur)) h->use_graphs = false;
-            if (h->interval_graph[h->cur]) {
-                CK(h, cudaGraphLaunch(h->interval_graph[h->cur], h->stream), "cudaGraphLaunch");
-                if (h->K & 1) h->cur ^= 1;
+            if (!h->interval_graph[ph] && !capture_interval(h, ph)) h->use_graphs = false;
+            if (h->interval_graph[ph]) {
+                CK(h, cudaGraphLaunch(h->interval_graph[ph], h->stream), "cudaGraphLaunch");
+                if (h->K & 1) ph ^= 1;
                 h->steps += chunk;
                 h->step_launches += chunk;
                 h->total_launches += chunk;
@@ -249,12 +282,8 @@ dmrt_status run_steps(dmrt_t *h, long n)
             }
         }
         for (long s = 0; s < chunk && !graphed; ++s) {
-            CK(h,
-               lbm::launch_step(h->wall, h->storage, h->stochastic, h->buf[h->cur],
-                                h->buf[h->cur ^ 1], h->S, h->G, h->C, h->block, h->stream,
-                                h->use_pdl),
-               "step kernel");
-            h->cur ^= 1;
+            CK(h, launch_one_step(h, ph), "step kernel");
+            ph ^= 1;
             h->steps++;
             h->step_launches++;
             h->total_launches++;
@@ -270,6 +299,21 @@ dmrt_status run_steps(dmrt_t *h, long n)
             if (st != DMRT_OK) return st;
         }
     }
+    return DMRT_OK;
+}
+
+// In-place handles: before a whole new state is written, return to the
+// swapped layout, carrying the step counter over to the word the next
+// phase-0 step reads.
+dmrt_status reset_layout(dmrt_t *h)
+{
+    if (!h->inplace || h->parity == 0) return DMRT_OK;
+    unsigned *ctr = reinterpret_cast<unsigned *>(
+        static_cast<char *>(h->buf[0]) +
+        static_cast<size_t>(h->G.plane) * lbm::kPlanes * lbm::storage_bytes(h->storage));
+    CK(h, cudaMemcpyAsync(ctr, ctr + 1, sizeof(unsigned), cudaMemcpyDeviceToDevice, h->stream),
+       "copy step counter");
+    h->parity = 0;
     return DMRT_OK;
 }
 
@@ -289,14 +333,16 @@ dmrt_status create_common(dmrt_t **out, const int grid[3], double nu, double alp
     if (!(nu > 0.0) || !(alpha > 0.0) || !std::isfinite(nu) || !std::isfinite(alpha) ||
         !std::isfinite(gbeta))
         return DMRT_ERR_ARG;
-    int storage = DMRT_STORE_F32, K = 100, rounding = DMRT_ROUND_AUTO;
+    int storage = DMRT_STORE_F32, K = 100, rounding = DMRT_ROUND_AUTO, streaming = DMRT_STREAM_AB;
     if (opts) {
         storage = opts->storage;
         rounding = opts->rounding;
+        streaming = opts->streaming;
         if (opts->residual_interval > 0) K = opts->residual_interval;
         if (opts->residual_interval < 0) return DMRT_ERR_ARG;
     }
     if (rounding < DMRT_ROUND_AUTO || rounding > DMRT_ROUND_STOCHASTIC) return DMRT_ERR_ARG;
+    if (streaming != DMRT_STREAM_AB && streaming != DMRT_STREAM_INPLACE) return DMRT_ERR_ARG;
     if (storage != DMRT_STORE_F32 && storage != DMRT_STORE_BF16 && storage != DMRT_STORE_F16)
         return DMRT_ERR_ARG;
 
@@ -309,6 +355,7 @@ dmrt_status create_common(dmrt_t **out, const int grid[3], double nu, double alp
     h->wall = wall_type;
     h->storage = storage;
     h->stochastic = storage != DMRT_STORE_F32 && rounding != DMRT_ROUND_NEAREST;
+    h->inplace = streaming == DMRT_STREAM_INPLACE;
     h->K = K;
     h->nu = nu;
     h->alpha = alpha;
@@ -316,12 +363,13 @@ dmrt_status create_common(dmrt_t **out, const int grid[3], double nu, double alp
     h->G.nx = grid[0];
     h->G.ny = grid[1];
     h->G.nz = grid[2];
-    h->G.pad = 0;
+    h->G.layout = lbm::kLayoutAB;
     // pad each plane to a whole number of 128-byte lines (and 256-byte
     // alignment of every plane start)
     h->G.plane = (cells + 63) / 64 * 64;
     h->G.inv_ny = 1.0f / static_cast<float>(grid[1]);
     lbm::fill_step_geometry(h->G, h->S);
+    lbm::fill_inplace_geometry(h->G, h->SI);
     fill_rates(h);
 #ifdef DMRT_BLOCK_X
     h->block = {DMRT_BLOCK_X, DMRT_BLOCK_Y};
@@ -336,21 +384,26 @@ dmrt_status create_common(dmrt_t **out, const int grid[3], double nu, double alp
         return st;
     };
     cudaError_t e;
-    // populations, then a 256-byte tail holding the step counter
+    // populations, then a 256-byte tail holding the step counter(s)
     const size_t buf_bytes =
         static_cast<size_t>(h->G.plane) * lbm::kPlanes * lbm::storage_bytes(h->storage) + 256;
-    for (int b = 0; b < 2; ++b) {
+    const int nbuf = h->inplace ? 1 : 2;
+    for (int b = 0; b < nbuf; ++b) {
         e = cudaMalloc(&h->buf[b], buf_bytes);
         if (e != cudaSuccess) return bail(e == cudaErrorMemoryAllocation ? DMRT_ERR_OOM : DMRT_ERR_CUDA);
+        h->device_bytes += static_cast<long long>(buf_bytes);
     }
     e = cudaMalloc(&h->snap, static_cast<size_t>(cells) * 4 * sizeof(float));
     if (e != cudaSuccess) return bail(DMRT_ERR_OOM);
+    h->device_bytes += cells * 4 * static_cast<long long>(sizeof(float));
     h->npartials = lbm::residual_partials(h->G) * 4;
     if (h->npartials < 3 * static_cast<size_t>(grid[2])) h->npartials = 3 * grid[2];
     e = cudaMalloc(&h->partials, h->npartials * sizeof(double));
     if (e != cudaSuccess) return bail(DMRT_ERR_OOM);
+    h->device_bytes += static_cast<long long>(h->npartials * sizeof(double));
     e = cudaMalloc(&h->dres, 16 * sizeof(double));
     if (e != cudaSuccess) return bail(DMRT_ERR_OOM);
+    h->device_bytes += 16 * static_cast<long long>(sizeof(double));
     h->dnu = h->dres + 8;
     e = cudaStreamCreateWithFlags(&h->own, cudaStreamNonBlocking);
     if (e != cudaSuccess) return bail(DMRT_ERR_CUDA);
@@ -361,11 +414,12 @@ dmrt_status create_common(dmrt_t **out, const int grid[3], double nu, double alp
 #ifdef DMRT_NO_PDL
     h->use_pdl = false;
 #endif
-    // start from rest: f = w (zero deviations), g = 0 (theta = 0)
-    e = cudaMemsetAsync(h->buf[0], 0, buf_bytes, h->stream);
-    if (e != cudaSuccess) return bail(DMRT_ERR_CUDA);
-    e = cudaMemsetAsync(h->buf[1], 0, buf_bytes, h->stream);
-    if (e != cudaSuccess) return bail(DMRT_ERR_CUDA);
+    // start from rest: f = w (zero deviations), g = 0 (theta = 0); the zero
+    // state and counters are the same in every layout
+    for (int b = 0; b < nbuf; ++b) {
+        e = cudaMemsetAsync(h->buf[b], 0, buf_bytes, h->stream);
+        if (e != cudaSuccess) return bail(DMRT_ERR_CUDA);
+    }
     e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return bail(DMRT_ERR_CUDA);
     *out = h;
@@ -467,7 +521,7 @@ dmrt_status dmrt_fields(dmrt_t *h, float *rho, float *u, float *theta, int on_de
         du = u ? h->staging + cells : nullptr;
         dth = theta ? h->staging + 4 * cells : nullptr;
     }
-    CK(h, lbm::launch_fields(h->wall, h->storage, h->buf[h->cur], h->G, drho, du, dth, h->stream),
+    CK(h, lbm::launch_fields(h->wall, h->storage, h->buf[h->cur], state_geometry(h), drho, du, dth, h->stream),
        "fields kernel");
     h->total_launches++;
     if (!on_device) {
@@ -492,7 +546,7 @@ dmrt_status dmrt_nusselt(dmrt_t *h, int wall, double out[3])
     if (h->G.ny < 2) return fail(h, DMRT_ERR_ARG, "dmrt_nusselt: needs ny >= 2");
     DeviceGuard dg(h->device);
     CK(h,
-       lbm::launch_nusselt(h->wall, h->storage, h->buf[h->cur], h->G, wall, nullptr, h->partials,
+       lbm::launch_nusselt(h->wall, h->storage, h->buf[h->cur], state_geometry(h), wall, nullptr, h->partials,
                            h->dnu, h->stream),
        "nusselt kernel");
     h->total_launches += 2;
@@ -509,7 +563,7 @@ dmrt_status dmrt_nusselt_flux(dmrt_t *h, int wall, double out[3])
     if (h->wall == DMRT_WALL_PERIODIC) return fail(h, DMRT_ERR_ARG, "dmrt_nusselt_flux: needs walls");
     DeviceGuard dg(h->device);
     CK(h,
-       lbm::launch_nusselt_flux(h->storage, h->buf[h->cur], h->G, wall, h->alpha, nullptr, h->partials, h->dnu,
+       lbm::launch_nusselt_flux(h->storage, h->buf[h->cur], state_geometry(h), wall, h->alpha, nullptr, h->partials, h->dnu,
                                 h->stream),
        "nusselt flux kernel");
     h->total_launches += 2;
@@ -532,7 +586,7 @@ dmrt_status dmrt_nusselt_local(dmrt_t *h, int wall, float *local, int on_device)
         dst = h->staging;
     }
     CK(h,
-       lbm::launch_nusselt(h->wall, h->storage, h->buf[h->cur], h->G, wall, dst, h->partials,
+       lbm::launch_nusselt(h->wall, h->storage, h->buf[h->cur], state_geometry(h), wall, dst, h->partials,
                            h->dnu, h->stream),
        "nusselt kernel");
     h->total_launches += 2;
@@ -608,7 +662,12 @@ dmrt_status dmrt_set_populations(dmrt_t *h, const float *f, const float *g, int 
         df = h->staging;
         dg_ = h->staging + 19 * cells;
     }
-    CK(h, lbm::launch_set_populations(h->storage, df, dg_, h->buf[h->cur], h->G, h->stream),
+    {
+        dmrt_status st = reset_layout(h);
+        if (st != DMRT_OK) return st;
+    }
+    CK(h, lbm::launch_set_populations(h->storage, df, dg_, h->buf[h->cur], state_geometry(h), periodic(h),
+                                      h->stream),
        "set kernel");
     h->total_launches++;
     h->snaps = 0;
@@ -629,7 +688,8 @@ dmrt_status dmrt_get_populations(dmrt_t *h, float *f, float *g, int on_device)
         df = f ? h->staging : nullptr;
         dg_ = g ? h->staging + 19 * cells : nullptr;
     }
-    CK(h, lbm::launch_get_populations(h->storage, h->buf[h->cur], df, dg_, h->G, h->stream),
+    CK(h, lbm::launch_get_populations(h->storage, h->buf[h->cur], df, dg_, state_geometry(h), periodic(h),
+                                      h->stream),
        "get kernel");
     h->total_launches++;
     if (!on_device) {
@@ -666,7 +726,12 @@ dmrt_status dmrt_init_fields(dmrt_t *h, const float *rho, const float *u, const 
         du = h->staging + cells;
         dt = h->staging + 4 * cells;
     }
-    CK(h, lbm::launch_init_fields(h->storage, dr, du, dt, h->buf[h->cur], h->G, h->stream),
+    {
+        dmrt_status st = reset_layout(h);
+        if (st != DMRT_OK) return st;
+    }
+    CK(h, lbm::launch_init_fields(h->storage, dr, du, dt, h->buf[h->cur], state_geometry(h), periodic(h),
+                                  h->stream),
        "init kernel");
     h->total_launches++;
     h->snaps = 0;
@@ -679,11 +744,13 @@ namespace {
 struct CheckpointHeader {
     char magic[8];
     int version, nx, ny, nz, wall, storage, stochastic, K, snaps;
+    int streaming, parity;  // in-place streaming and the layout of the saved buffer
     double nu, alpha, gbeta;
     long long steps, pop_bytes, snap_bytes;
 };
 
 constexpr char kMagic[8] = {'D', 'M', 'R', 'T', 'C', 'K', 'P', '1'};
+constexpr int kCheckpointVersion = 2;
 
 long long pop_bytes(const dmrt_t *h)
 {
@@ -706,7 +773,9 @@ dmrt_status dmrt_checkpoint_save(dmrt_t *h, void *dst, long long size)
     DeviceGuard dg(h->device);
     CheckpointHeader hd{};
     memcpy(hd.magic, kMagic, 8);
-    hd.version = 1;
+    hd.version = kCheckpointVersion;
+    hd.streaming = h->inplace ? DMRT_STREAM_INPLACE : DMRT_STREAM_AB;
+    hd.parity = h->parity;
     hd.nx = h->G.nx;
     hd.ny = h->G.ny;
     hd.nz = h->G.nz;
@@ -738,13 +807,15 @@ dmrt_status dmrt_checkpoint_load(dmrt_t *h, const void *src, long long size)
     if (!h || !src || size < static_cast<long long>(sizeof(CheckpointHeader))) return DMRT_ERR_ARG;
     CheckpointHeader hd;
     memcpy(&hd, src, sizeof hd);
-    if (memcmp(hd.magic, kMagic, 8) != 0 || hd.version != 1)
+    if (memcmp(hd.magic, kMagic, 8) != 0 || hd.version != kCheckpointVersion)
         return fail(h, DMRT_ERR_ARG, "not a dmrt checkpoint");
     if (hd.nx != h->G.nx || hd.ny != h->G.ny || hd.nz != h->G.nz || hd.wall != h->wall ||
         hd.storage != h->storage || hd.stochastic != (h->stochastic ? 1 : 0) || hd.K != h->K ||
+        hd.streaming != (h->inplace ? DMRT_STREAM_INPLACE : DMRT_STREAM_AB) || hd.parity < 0 || hd.parity > 1 ||
         hd.nu != h->nu || hd.alpha != h->alpha || hd.gbeta != h->gbeta || hd.pop_bytes != pop_bytes(h) ||
         hd.snap_bytes != snap_bytes(h) || size < dmrt_checkpoint_size(h))
-        return fail(h, DMRT_ERR_ARG, "checkpoint of a different cavity (grid, walls, storage or parameters)");
+        return fail(h, DMRT_ERR_ARG,
+                    "checkpoint of a different cavity (grid, walls, storage, streaming or parameters)");
     DeviceGuard dg(h->device);
     const char *p = static_cast<const char *>(src) + sizeof hd;
     CK(h, cudaMemcpyAsync(h->buf[h->cur], p, hd.pop_bytes, cudaMemcpyHostToDevice, h->stream), "copy populations");
@@ -755,6 +826,7 @@ dmrt_status dmrt_checkpoint_load(dmrt_t *h, const void *src, long long size)
     CK(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
     h->steps = hd.steps;
     h->snaps = hd.snaps;
+    h->parity = hd.parity;
     return DMRT_OK;
 }
 
@@ -775,6 +847,8 @@ dmrt_status dmrt_get_params(const dmrt_t *h, dmrt_params *out)
     out->tau_nu = 3.0 * h->nu + 0.5;
     out->tau_alpha = 0.5 + 4.0 * h->alpha;
     out->steps = h->steps;
+    out->streaming = h->inplace ? DMRT_STREAM_INPLACE : DMRT_STREAM_AB;
+    out->device_bytes = h->device_bytes;
     return DMRT_OK;
 }
 
@@ -838,6 +912,21 @@ dmrt_status dmrt_get_stats(dmrt_t *h, dmrt_stats *out, int reset)
         h->step_launches = h->total_launches = h->timed_steps = 0;
         h->step_ms = 0.0;
     }
+    return DMRT_OK;
+}
+
+dmrt_status dmrt_round_to_storage(int storage, int rounding, const float *in, float *out, long long n,
+                                  unsigned seed, void *stream)
+{
+    if (storage != DMRT_STORE_F32 && storage != DMRT_STORE_BF16 && storage != DMRT_STORE_F16)
+        return DMRT_ERR_ARG;
+    if (rounding < DMRT_ROUND_AUTO || rounding > DMRT_ROUND_STOCHASTIC || n < 0) return DMRT_ERR_ARG;
+    if (n == 0) return DMRT_OK;
+    if (!in || !out) return DMRT_ERR_ARG;
+    const bool stochastic = storage != DMRT_STORE_F32 && rounding != DMRT_ROUND_NEAREST;
+    if (lbm::launch_round(storage, stochastic, in, out, n, seed, static_cast<cudaStream_t>(stream)) !=
+        cudaSuccess)
+        return DMRT_ERR_CUDA;
     return DMRT_OK;
 }
 

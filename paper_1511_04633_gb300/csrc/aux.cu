@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(kRedThreads) nusselt_flux_kernel(const T *__re
     double mx = -INFINITY;
     for (int x = threadIdx.x; x < G.nx; x += blockDim.x) {
         const long long c = (static_cast<long long>(z) * G.ny + y) * G.nx + x;
-        const double gl = Store<T>::ld(src + plane * G.plane + c);
+        const double gl = Store<T>::ld(src + state_index(G, false, plane, c, x, y, z));
         const double q = wall == 0 ? 0.25 * th_w - 2.0 * gl : 2.0 * gl - 0.25 * th_w;
         const double nu = H * q * inv_alpha;
         if (local) local[static_cast<long long>(z) * G.nx + x] = static_cast<float>(nu);
@@ -233,35 +233,52 @@ __global__ void __launch_bounds__(kRedThreads) nusselt_flux_kernel(const T *__re
 
 // ---------------------------------------------------------------- import / export
 
+// Coordinates of the flat cell index c.
+__device__ __forceinline__ void cell_xyz(const Geometry &G, long long c, int &x, int &y, int &z)
+{
+    x = static_cast<int>(c % G.nx);
+    const long long r = c / G.nx;
+    y = static_cast<int>(r % G.ny);
+    z = static_cast<int>(r / G.ny);
+}
+
+// The state slots are addressed through state_index, so import and export
+// see the same dense [q][cells] arrays whatever the buffer's layout.
 template <typename T>
 __global__ void set_populations_kernel(const float *__restrict__ f, const float *__restrict__ g,
-                                       T *__restrict__ dst, const Geometry G)
+                                       T *__restrict__ dst, const Geometry G, bool periodic)
 {
     const long long cells = static_cast<long long>(G.nx) * G.ny * G.nz;
     for (long long c = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; c < cells;
          c += static_cast<long long>(gridDim.x) * blockDim.x) {
+        int x, y, z;
+        cell_xyz(G, c, x, y, z);
         static_for<0, 19>([&](auto I) {
             constexpr int i = decltype(I)::value;
-            Store<T>::st(dst + i * G.plane + c, f[i * cells + c] - q19_w(i));
+            Store<T>::st(dst + state_index(G, periodic, i, c, x, y, z), f[i * cells + c] - q19_w(i));
         });
-        for (int i = 0; i < 7; ++i) Store<T>::st(dst + (19 + i) * G.plane + c, g[i * cells + c]);
+        for (int i = 0; i < 7; ++i)
+            Store<T>::st(dst + state_index(G, periodic, 19 + i, c, x, y, z), g[i * cells + c]);
     }
 }
 
 template <typename T>
 __global__ void get_populations_kernel(const T *__restrict__ src, float *f, float *g,
-                                       const Geometry G)
+                                       const Geometry G, bool periodic)
 {
     const long long cells = static_cast<long long>(G.nx) * G.ny * G.nz;
     for (long long c = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; c < cells;
          c += static_cast<long long>(gridDim.x) * blockDim.x) {
+        int x, y, z;
+        cell_xyz(G, c, x, y, z);
         if (f)
             static_for<0, 19>([&](auto I) {
                 constexpr int i = decltype(I)::value;
-                f[i * cells + c] = Store<T>::ld(src + i * G.plane + c) + q19_w(i);
+                f[i * cells + c] = Store<T>::ld(src + state_index(G, periodic, i, c, x, y, z)) + q19_w(i);
             });
         if (g)
-            for (int i = 0; i < 7; ++i) g[i * cells + c] = Store<T>::ld(src + (19 + i) * G.plane + c);
+            for (int i = 0; i < 7; ++i)
+                g[i * cells + c] = Store<T>::ld(src + state_index(G, periodic, 19 + i, c, x, y, z));
     }
 }
 
@@ -270,11 +287,13 @@ __global__ void get_populations_kernel(const T *__restrict__ src, float *f, floa
 template <typename T>
 __global__ void init_fields_kernel(const float *__restrict__ rho, const float *__restrict__ u,
                                    const float *__restrict__ theta, T *__restrict__ dst,
-                                   const Geometry G)
+                                   const Geometry G, bool periodic)
 {
     const long long cells = static_cast<long long>(G.nx) * G.ny * G.nz;
     for (long long c = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; c < cells;
          c += static_cast<long long>(gridDim.x) * blockDim.x) {
+        int x, y, z;
+        cell_xyz(G, c, x, y, z);
         const float r = rho[c];
         const float dr = r - 1.0f;
         const float vx = u[c], vy = u[cells + c], vz = u[2 * cells + c];
@@ -284,15 +303,29 @@ __global__ void init_fields_kernel(const float *__restrict__ rho, const float *_
             constexpr int i = decltype(I)::value;
             constexpr float ex = q19_ex(i), ey = q19_ey(i), ez = q19_ez(i);
             const float ev = ex * vx + ey * vy + ez * vz;
-            Store<T>::st(dst + i * G.plane + c,
+            Store<T>::st(dst + state_index(G, periodic, i, c, x, y, z),
                          q19_w(i) * (dr + r * (3.0f * ev + 4.5f * ev * ev - 1.5f * vv)));
         });
         static_for<0, 7>([&](auto I) {
             constexpr int i = decltype(I)::value;
             constexpr float ex = q7_ex(i), ey = q7_ey(i), ez = q7_ez(i);
-            Store<T>::st(dst + (19 + i) * G.plane + c,
+            Store<T>::st(dst + state_index(G, periodic, 19 + i, c, x, y, z),
                          q7_w(i) * th * (1.0f + 4.0f * (ex * vx + ey * vy + ez * vz)));
         });
+    }
+}
+
+// The storage rounding of the step kernel applied to a flat array.
+template <typename T, bool SR>
+__global__ void round_kernel(const float *in, float *out, long long n, unsigned seed)
+{
+    const unsigned hs = pcg_hash(seed);
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        T v;
+        if constexpr (SR) StoreSR<T>::st(&v, in[i], pcg_hash(static_cast<unsigned>(i) ^ hs));
+        else Store<T>::st(&v, in[i]);
+        out[i] = Store<T>::ld(&v);
     }
 }
 
@@ -390,11 +423,11 @@ cudaError_t launch_nusselt_flux(int storage, const void *src, const Geometry &G,
 }
 
 cudaError_t launch_set_populations(int storage, const float *f, const float *g, void *dst,
-                                   const Geometry &G, cudaStream_t s)
+                                   const Geometry &G, bool periodic, cudaStream_t s)
 {
     cudaError_t e = dispatch(0, storage, [&](auto, auto *tp) {
         using T = std::remove_pointer_t<decltype(tp)>;
-        set_populations_kernel<T><<<flat_grid(G), 256, 0, s>>>(f, g, static_cast<T *>(dst), G);
+        set_populations_kernel<T><<<flat_grid(G), 256, 0, s>>>(f, g, static_cast<T *>(dst), G, periodic);
         return cudaSuccess;
     });
     if (e != cudaSuccess) return e;
@@ -402,11 +435,32 @@ cudaError_t launch_set_populations(int storage, const float *f, const float *g, 
 }
 
 cudaError_t launch_get_populations(int storage, const void *src, float *f, float *g,
-                                   const Geometry &G, cudaStream_t s)
+                                   const Geometry &G, bool periodic, cudaStream_t s)
 {
     cudaError_t e = dispatch(0, storage, [&](auto, auto *tp) {
         using T = std::remove_pointer_t<decltype(tp)>;
-        get_populations_kernel<T><<<flat_grid(G), 256, 0, s>>>(static_cast<const T *>(src), f, g, G);
+        get_populations_kernel<T><<<flat_grid(G), 256, 0, s>>>(static_cast<const T *>(src), f, g, G, periodic);
+        return cudaSuccess;
+    });
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_round(int storage, bool stochastic, const float *in, float *out, long long n,
+                         unsigned seed, cudaStream_t s)
+{
+    long long blocks = (n + 255) / 256;
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    if (blocks < 1) blocks = 1;
+    cudaError_t e = dispatch(0, storage, [&](auto, auto *tp) {
+        using T = std::remove_pointer_t<decltype(tp)>;
+        if constexpr (!std::is_same_v<T, float>) {
+            if (stochastic) {
+                round_kernel<T, true><<<static_cast<unsigned>(blocks), 256, 0, s>>>(in, out, n, seed);
+                return cudaSuccess;
+            }
+        }
+        round_kernel<T, false><<<static_cast<unsigned>(blocks), 256, 0, s>>>(in, out, n, seed);
         return cudaSuccess;
     });
     if (e != cudaSuccess) return e;
@@ -414,11 +468,11 @@ cudaError_t launch_get_populations(int storage, const void *src, float *f, float
 }
 
 cudaError_t launch_init_fields(int storage, const float *rho, const float *u, const float *theta,
-                               void *dst, const Geometry &G, cudaStream_t s)
+                               void *dst, const Geometry &G, bool periodic, cudaStream_t s)
 {
     cudaError_t e = dispatch(0, storage, [&](auto, auto *tp) {
         using T = std::remove_pointer_t<decltype(tp)>;
-        init_fields_kernel<T><<<flat_grid(G), 256, 0, s>>>(rho, u, theta, static_cast<T *>(dst), G);
+        init_fields_kernel<T><<<flat_grid(G), 256, 0, s>>>(rho, u, theta, static_cast<T *>(dst), G, periodic);
         return cudaSuccess;
     });
     if (e != cudaSuccess) return e;

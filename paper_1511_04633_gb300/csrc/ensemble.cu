@@ -114,7 +114,7 @@ __device__ __forceinline__ Geometry geometry_of(const CavityDesc &D)
     G.nx = D.nx;
     G.ny = D.ny;
     G.nz = D.nz;
-    G.pad = 0;
+    G.layout = lbm::kLayoutAB;
     G.plane = D.plane;
     G.inv_ny = D.inv_ny;
     return G;
@@ -659,6 +659,7 @@ dmrt_status dmrt_ensemble_create(dmrt_ensemble_t **out, int count, const dmrt_ca
         rounding = opts->rounding;
         if (opts->residual_interval > 0) K = opts->residual_interval;
         if (opts->residual_interval < 0) return DMRT_ERR_ARG;
+        if (opts->streaming != DMRT_STREAM_AB) return DMRT_ERR_ARG;
     }
     if (storage < DMRT_STORE_F32 || storage > DMRT_STORE_F16) return DMRT_ERR_ARG;
     if (rounding < DMRT_ROUND_AUTO || rounding > DMRT_ROUND_STOCHASTIC) return DMRT_ERR_ARG;
@@ -1039,7 +1040,7 @@ dmrt_status dmrt_ensemble_init_fields(dmrt_ensemble_t *e, int member, const floa
         du = e->staging + cells;
         dt = e->staging + 4 * cells;
     }
-    ECK(e, lbm::launch_init_fields(e->storage, dr, du, dt, member_ptr(e, member, e->cur), G, e->stream),
+    ECK(e, lbm::launch_init_fields(e->storage, dr, du, dt, member_ptr(e, member, e->cur), G, false, e->stream),
         "init kernel");
     e->total_launches++;
     e->snaps = 0;
@@ -1063,7 +1064,7 @@ dmrt_status dmrt_ensemble_get_populations(dmrt_ensemble_t *e, int member, float 
         df = f ? e->staging : nullptr;
         dgp = g ? e->staging + 19 * cells : nullptr;
     }
-    ECK(e, lbm::launch_get_populations(e->storage, member_ptr(e, member, e->cur), df, dgp, G, e->stream),
+    ECK(e, lbm::launch_get_populations(e->storage, member_ptr(e, member, e->cur), df, dgp, G, false, e->stream),
         "get kernel");
     e->total_launches++;
     if (!on_device) {

@@ -30,6 +30,18 @@ cudaError_t launch_step(int wall, int storage, bool stochastic, const void *src,
                         const StepGeometry &S, const Geometry &G, const CollideParams &C,
                         BlockShape b, cudaStream_t s, bool pdl);
 
+// In-place streaming (one buffer).  The state alternates between two
+// layouts (see kLayoutSwapped / kLayoutStreamed): phase 0 reads the swapped
+// layout and leaves the streamed one, phase 1 the reverse.  Both phases do
+// the arithmetic of launch_step on the same populations, so the state after
+// any number of steps holds the same values as the two-buffer scheme's.  The
+// buffer's tail holds two 32-bit step counters: phase p reads word p and
+// writes word p ^ 1.
+void fill_inplace_geometry(const Geometry &G, InplaceGeometry &SI);
+cudaError_t launch_step_inplace(int wall, int storage, bool stochastic, void *buf, int phase,
+                                const InplaceGeometry &SI, const Geometry &G,
+                                const CollideParams &C, BlockShape b, cudaStream_t s, bool pdl);
+
 // Fields of the pulled populations (any output may be null).
 cudaError_t launch_fields(int wall, int storage, const void *src, const Geometry &G, float *rho,
                           float *u, float *theta, cudaStream_t s);
@@ -52,12 +64,18 @@ cudaError_t launch_nusselt(int wall_type, int storage, const void *src, const Ge
 cudaError_t launch_nusselt_flux(int storage, const void *src, const Geometry &G, int wall, double alpha,
                                 float *local, double *partials, double *out3, cudaStream_t s);
 
-// Population and field import / export (dense [q][cells] arrays).
+// Population and field import / export (dense [q][cells] arrays) in the
+// layout G.layout; `periodic`: the box has no walls.
 cudaError_t launch_set_populations(int storage, const float *f, const float *g, void *dst,
-                                   const Geometry &G, cudaStream_t s);
+                                   const Geometry &G, bool periodic, cudaStream_t s);
 cudaError_t launch_get_populations(int storage, const void *src, float *f, float *g,
-                                   const Geometry &G, cudaStream_t s);
+                                   const Geometry &G, bool periodic, cudaStream_t s);
 cudaError_t launch_init_fields(int storage, const float *rho, const float *u, const float *theta,
-                               void *dst, const Geometry &G, cudaStream_t s);
+                               void *dst, const Geometry &G, bool periodic, cudaStream_t s);
+
+// Round a flat float array to the storage format and back (the step
+// kernel's store rounding; stochastic bits from pcg_hash(i ^ pcg_hash(seed))).
+cudaError_t launch_round(int storage, bool stochastic, const float *in, float *out, long long n,
+                         unsigned seed, cudaStream_t s);
 
 }  // namespace lbm

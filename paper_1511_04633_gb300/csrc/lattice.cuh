@@ -84,6 +84,13 @@ constexpr unsigned kWeyl = 0x9E3779B9u;  // 2^32 / golden ratio
 template <typename T>
 struct StoreSR;
 
+// DMRT_SR_HW = 1: round with the hardware's stochastic-rounding conversion
+// (cvt.rs, PTX ISA 8.7, sm_100a and later) fed with the same random word;
+// 0: the integer formulations below.
+#ifndef DMRT_SR_HW
+#define DMRT_SR_HW 0
+#endif
+
 // bfloat16 keeps the high 16 bits of the FP32 pattern: adding 16 random bits
 // below them and truncating rounds the magnitude up with the right
 // probability (a carry into the exponent is the correct next value).
@@ -91,8 +98,14 @@ template <>
 struct StoreSR<__nv_bfloat16> {
     static __device__ __forceinline__ void st(__nv_bfloat16 *p, float v, unsigned r)
     {
+#if DMRT_SR_HW
+        unsigned pair;
+        asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(pair) : "f"(0.0f), "f"(v), "r"(r));
+        *reinterpret_cast<unsigned short *>(p) = static_cast<unsigned short>(pair);
+#else
         const unsigned bits = __float_as_uint(v) + (r >> 16);
         *reinterpret_cast<unsigned short *>(p) = static_cast<unsigned short>(bits >> 16);
+#endif
     }
 };
 
@@ -104,6 +117,14 @@ template <>
 struct StoreSR<__half> {
     static __device__ __forceinline__ void st(__half *p, float v, unsigned r)
     {
+#if DMRT_SR_HW
+        unsigned pair;
+        asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;"
+            : "=r"(pair)
+            : "f"(0.0f), "f"(v * Store<__half>::kScale), "r"(r));
+        *reinterpret_cast<unsigned short *>(p) = static_cast<unsigned short>(pair);
+        return;
+#endif
         const float s = v * Store<__half>::kScale;
         const int e = static_cast<int>((__float_as_uint(s) >> 23) & 0xFFu);
         const int ue = e - 10 > 103 ? e - 10 : 103;
@@ -238,9 +259,20 @@ struct CollideParams {
     int aniso;
 };
 
+// Where the stored state sits in a population buffer.  The state S is the
+// set of post-collision populations of the last step, S_i(x) for every cell x
+// and direction i (planes 0..18 D3Q19, 19..25 D3Q7).
+//  kLayoutAB      : two-buffer (A-B) scheme, S_i(x) in plane i at cell x.
+//  kLayoutSwapped : in-place scheme after an even number of steps, S_i(x) in
+//                   plane opp(i) at cell x.
+//  kLayoutStreamed: in-place scheme after an odd number of steps, S_i(x) in
+//                   plane i at cell x + e_i (already streamed), or in plane
+//                   opp(i) at cell x when x + e_i lies outside a walled box.
+constexpr int kLayoutAB = 0, kLayoutSwapped = 1, kLayoutStreamed = 2;
+
 struct Geometry {
     int nx, ny, nz;
-    int pad;
+    int layout;       // kLayout* of the buffer the aux kernels read or write
     long long plane;  // elements between consecutive population planes
     float inv_ny;     // 1/ny for the linear wall profile
 };
@@ -255,6 +287,16 @@ struct StepGeometry {
     int nb[26];
     int bb[26];
     float inv_ny;
+};
+
+// Tables of the in-place step's first phase (the kernel that reads the
+// swapped layout and writes the streamed one): loads use load.nb / load.bb
+// like StepGeometry; the value leaving cell c along q goes to c + sn[q], or
+// to c + sb[q] when that link leaves the box.
+struct InplaceGeometry {
+    StepGeometry load;
+    int sn[26];
+    int sb[26];
 };
 
 // ---------------------------------------------------------------- pull with walls
@@ -280,6 +322,9 @@ __device__ __forceinline__ void pull_f(const T *__restrict__ src, const Geometry
     const bool xlo = (x == 0), xhi = (x == nx - 1);
     const bool ylo = (y == 0), yhi = (y == ny - 1);
     const bool zlo = (z == 0), zhi = (z == nz - 1);
+    // plane and cell of S_i(x - e_i) (the population arriving at x) and of
+    // S_opp(x) (its bounce-back source) in the buffer's layout
+    const int L = G.layout;
     static_for<0, 19>([&](auto I) {
         constexpr int i = decltype(I)::value;
         constexpr int ex = q19_ex(i), ey = q19_ey(i), ez = q19_ez(i);
@@ -291,7 +336,9 @@ __device__ __forceinline__ void pull_f(const T *__restrict__ src, const Geometry
             sx = sx < 0 ? nx - 1 : (sx >= nx ? 0 : sx);
             sy = sy < 0 ? ny - 1 : (sy >= ny ? 0 : sy);
             sz = sz < 0 ? nz - 1 : (sz >= nz ? 0 : sz);
-            d[i] = Store<T>::ld(src + i * P + (sz * ny + sy) * nx + sx);
+            const int c = (L == kLayoutStreamed) ? self : (sz * ny + sy) * nx + sx;
+            const int p_in = (L == kLayoutSwapped) ? opp : i;
+            d[i] = Store<T>::ld(src + p_in * P + c);
         } else {
             bool out = false;
             if constexpr (ex == 1) out = out || xlo;
@@ -301,7 +348,10 @@ __device__ __forceinline__ void pull_f(const T *__restrict__ src, const Geometry
             if constexpr (ez == 1) out = out || zlo;
             if constexpr (ez == -1) out = out || zhi;
             const int off = ex + ey * nx + ez * nx * ny;
-            const long long a = out ? (opp * P + self) : (i * P + (self - off));
+            const int c_in = (L == kLayoutStreamed) ? self : self - off;
+            const int p_in = (L == kLayoutSwapped) ? opp : i;
+            const int p_out = (L == kLayoutAB) ? opp : i;
+            const long long a = out ? (p_out * P + self) : (p_in * P + c_in);
             d[i] = Store<T>::ld(src + a);
         }
     });
@@ -322,6 +372,7 @@ __device__ __forceinline__ void pull_g(const T *__restrict__ src, const Geometry
     const int self = (z * ny + y) * nx + x;
     const T *gs = src + 19 * P;
     const float th_lin = 0.5f - (static_cast<float>(y) + 0.5f) * G.inv_ny;
+    const int L = G.layout;
     static_for<0, 7>([&](auto I) {
         constexpr int i = decltype(I)::value;
         constexpr int ex = q7_ex(i), ey = q7_ey(i), ez = q7_ez(i);
@@ -333,7 +384,9 @@ __device__ __forceinline__ void pull_g(const T *__restrict__ src, const Geometry
             sx = sx < 0 ? nx - 1 : (sx >= nx ? 0 : sx);
             sy = sy < 0 ? ny - 1 : (sy >= ny ? 0 : sy);
             sz = sz < 0 ? nz - 1 : (sz >= nz ? 0 : sz);
-            g[i] = Store<T>::ld(gs + i * P + (sz * ny + sy) * nx + sx);
+            const int c = (L == kLayoutStreamed) ? self : (sz * ny + sy) * nx + sx;
+            const int p_in = (L == kLayoutSwapped) ? opp : i;
+            g[i] = Store<T>::ld(gs + p_in * P + c);
         } else {
             constexpr int axis = ex != 0 ? 0 : (ey != 0 ? 1 : 2);
             bool out;
@@ -344,7 +397,10 @@ __device__ __forceinline__ void pull_g(const T *__restrict__ src, const Geometry
             else if constexpr (ez == 1) out = (z == 0);
             else out = (z == nz - 1);
             const int off = ex + ey * nx + ez * nx * ny;
-            const long long a = out ? (opp * P + self) : (i * P + (self - off));
+            const int c_in = (L == kLayoutStreamed) ? self : self - off;
+            const int p_in = (L == kLayoutSwapped) ? opp : i;
+            const int p_out = (L == kLayoutAB) ? opp : i;
+            const long long a = out ? (p_out * P + self) : (p_in * P + c_in);
             float v = Store<T>::ld(gs + a);
             if constexpr (dirichlet_axis<WALL>(axis)) {
                 float tw;
@@ -355,6 +411,35 @@ __device__ __forceinline__ void pull_g(const T *__restrict__ src, const Geometry
             g[i] = v;
         }
     });
+}
+
+// Element index of S_q(x) (plane q = 0..25: D3Q19 direction q, or D3Q7
+// direction q - 19) of cell c = (z ny + y) nx + x in the buffer's layout.
+// `periodic`: the box wraps around (no walls).
+__device__ __forceinline__ long long state_index(const Geometry &G, bool periodic, int q, long long c,
+                                                 int x, int y, int z)
+{
+    int ex, ey, ez, opp;
+    if (q < 19) {
+        ex = q19_ex(q);
+        ey = q19_ey(q);
+        ez = q19_ez(q);
+        opp = q19_opp(q);
+    } else {
+        ex = q7_ex(q - 19);
+        ey = q7_ey(q - 19);
+        ez = q7_ez(q - 19);
+        opp = 19 + q7_opp(q - 19);
+    }
+    if (G.layout == kLayoutAB) return q * G.plane + c;
+    if (G.layout == kLayoutSwapped) return opp * G.plane + c;
+    int tx = x + ex, ty = y + ey, tz = z + ez;
+    const bool inside = tx >= 0 && tx < G.nx && ty >= 0 && ty < G.ny && tz >= 0 && tz < G.nz;
+    if (!inside && !periodic) return opp * G.plane + c;
+    tx = tx < 0 ? G.nx - 1 : (tx >= G.nx ? 0 : tx);
+    ty = ty < 0 ? G.ny - 1 : (ty >= G.ny ? 0 : ty);
+    tz = tz < 0 ? G.nz - 1 : (tz >= G.nz ? 0 : tz);
+    return q * G.plane + (static_cast<long long>(tz) * G.ny + ty) * G.nx + tx;
 }
 
 // ---------------------------------------------------------------- moments

@@ -1,0 +1,219 @@
+// step_inplace.cu -- the fused double-MRT time step (arXiv:1511.04633,
+// Eqs. (14), (19), (29)) on ONE population buffer: in-place streaming halves
+// the population memory of a cavity (26 values per cell instead of 52).
+//
+// Two kernels alternate (the AA access pattern of Bailey et al., "Accelerating
+// lattice Boltzmann fluid flow simulations using graphics processors", ICPP
+// 2009).  With S_i(x) the post-collision population of the previous step:
+//  - phase 0 starts from the swapped layout (S_i(x) in plane opp(i) at x).
+//    The cell pulls f_i(x) = S_i(x - e_i) from plane opp(i) at x - e_i, or,
+//    across a wall, the bounce-back source S_opp(x) from plane i at x; it
+//    collides and writes its S*_i(x) to plane i at x + e_i, or to plane
+//    opp(i) at x when x + e_i lies outside the box (the streamed layout).
+//  - phase 1 starts from the streamed layout, where every arriving
+//    population already sits in the cell's own slot of plane i; it collides
+//    and writes S*_i(x) to plane opp(i) at x, which is the swapped layout
+//    again.
+// In both phases each cell reads exactly the 26 slots it then writes, and no
+// two cells share a slot, so the update is race-free in place.  The wall
+// rules of Sec. 3 are applied where a population is read, as in the
+// two-buffer kernel, and the stochastic-rounding bits are keyed by the
+// producing cell and direction: the stored values are bitwise those of the
+// two-buffer scheme, only their addresses differ.
+#include "step_body.cuh"
+
+namespace lbm {
+
+namespace {
+
+// Minimum resident 256-thread blocks per SM of each phase (4 caps a kernel
+// at 64 registers, 3 at 80).  The phase-0 kernel needs its store offsets
+// beside the collision's values and spills ~50 bytes at 64 registers;
+// measured on GB300 (128^3, FP32), 80 registers for both phases give
+// 67.7 us per step against 75.2 us at 64.
+#ifndef DMRT_INPLACE_MIN_BLOCKS0
+#define DMRT_INPLACE_MIN_BLOCKS0 3
+#endif
+#ifndef DMRT_INPLACE_MIN_BLOCKS1
+#define DMRT_INPLACE_MIN_BLOCKS1 3
+#endif
+
+// Phase-1 loads: population q of a cell arrives in its own slot of plane q.
+struct LocalOffsets {
+    unsigned plane;
+    template <int Q>
+    __device__ __forceinline__ unsigned nb() const { return Q * plane; }
+    template <int Q>
+    __device__ __forceinline__ unsigned bb() const { return Q * plane; }
+};
+
+// Cell index of (x + dx, y + dy, z + dz) in a periodic box.
+__device__ __forceinline__ unsigned wrapped_cell(const StepGeometry &S, int x, int y, int z)
+{
+    x = x < 0 ? S.nx - 1 : (x >= S.nx ? 0 : x);
+    y = y < 0 ? S.ny - 1 : (y >= S.ny ? 0 : y);
+    z = z < 0 ? S.nz - 1 : (z >= S.nz ? 0 : z);
+    return (static_cast<unsigned>(z) * S.ny + y) * S.nx + x;
+}
+
+// Periodic boxes: the pull of either phase.
+template <typename T, int PHASE>
+__device__ __forceinline__ void load_periodic(const T *A, const StepGeometry &S, int x, int y, int z,
+                                              unsigned self, float d[19], float g[7])
+{
+    static_for<0, 26>([&](auto I) {
+        constexpr int q = decltype(I)::value;
+        constexpr int ex = q < 19 ? q19_ex(q) : q7_ex(q - 19);
+        constexpr int ey = q < 19 ? q19_ey(q) : q7_ey(q - 19);
+        constexpr int ez = q < 19 ? q19_ez(q) : q7_ez(q - 19);
+        constexpr int opp = q < 19 ? q19_opp(q) : 19 + q7_opp(q - 19);
+        unsigned a;
+        if constexpr (PHASE == 0) a = opp * S.plane + wrapped_cell(S, x - ex, y - ey, z - ez);
+        else a = q * S.plane + self;
+        const float v = Store<T>::ld(A + a);
+        if constexpr (q < 19) d[q] = v;
+        else g[q - 19] = v;
+    });
+}
+
+// Store the 26 post-collision values of one cell at addr(q) (plane and cell
+// of the slot), rounding stochastically with bits keyed by the direction q
+// as in the two-buffer store.
+template <typename T, bool SR, typename Addr>
+__device__ __forceinline__ void store_cell_to(T *A, const float d[19], const float g[7],
+                                              unsigned base, Addr &&addr)
+{
+    static_for<0, 26>([&](auto I) {
+        constexpr int q = decltype(I)::value;
+        float v;
+        if constexpr (q < 19) v = d[q];
+        else v = g[q - 19];
+        T *p = A + addr(I);
+        if constexpr (SR) StoreSR<T>::st(p, v, base + q * kWeyl);
+        else Store<T>::st(p, v);
+    });
+}
+
+template <int WALL, typename T, bool SR, int PHASE>
+__global__ void __launch_bounds__(256, PHASE == 0 ? DMRT_INPLACE_MIN_BLOCKS0 : DMRT_INPLACE_MIN_BLOCKS1)
+    step_inplace_kernel(T *__restrict__ A, const InplaceGeometry SI, const CollideParams C)
+{
+    const StepGeometry &S = SI.load;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    // programmatic dependent launch, as in the two-buffer kernel
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;");
+    if (x >= S.nx || y >= S.ny) return;
+    const unsigned self = (static_cast<unsigned>(z) * S.ny + y) * S.nx + x;
+    float d[19], g[7];
+    if constexpr (WALL == 0) {
+        load_periodic<T, PHASE>(A, S, x, y, z, self, d, g);
+    } else if constexpr (PHASE == 0) {
+        pull_offsets<WALL, T>(A, TableOffsets{S}, S.nx, S.ny, S.nz, S.inv_ny, self, x, y, z, d, g);
+    } else {
+        pull_offsets<WALL, T>(A, LocalOffsets{S.plane}, S.nx, S.ny, S.nz, S.inv_ny, self, x, y, z,
+                              d, g);
+    }
+    collide_pairs(C, d, g);
+    unsigned base = 0;
+    if constexpr (SR) {
+        unsigned *ctr = reinterpret_cast<unsigned *>(A + static_cast<size_t>(kPlanes) * S.plane);
+        const unsigned step = ctr[PHASE];
+        if (self == 0) ctr[PHASE ^ 1] = step + 1u;
+        base = pcg_hash(self ^ pcg_hash(step));
+    }
+    if constexpr (PHASE == 1) {
+        store_cell_to<T, SR>(A, d, g, base, [&](auto I) -> unsigned {
+            constexpr int q = decltype(I)::value;
+            constexpr int opp = q < 19 ? q19_opp(q) : 19 + q7_opp(q - 19);
+            return self + opp * S.plane;
+        });
+    } else if constexpr (WALL == 0) {
+        store_cell_to<T, SR>(A, d, g, base, [&](auto I) -> unsigned {
+            constexpr int q = decltype(I)::value;
+            constexpr int ex = q < 19 ? q19_ex(q) : q7_ex(q - 19);
+            constexpr int ey = q < 19 ? q19_ey(q) : q7_ey(q - 19);
+            constexpr int ez = q < 19 ? q19_ez(q) : q7_ez(q - 19);
+            return q * S.plane + wrapped_cell(S, x + ex, y + ey, z + ez);
+        });
+    } else {
+        // the box faces the cell touches, one bit each (kept in one register
+        // across the collision): x = 0, x = nx-1, y = 0, y = ny-1, z = 0, z = nz-1
+        const unsigned edge = (x == 0 ? 1u : 0u) | (x == S.nx - 1 ? 2u : 0u) |
+                              (y == 0 ? 4u : 0u) | (y == S.ny - 1 ? 8u : 0u) |
+                              (z == 0 ? 16u : 0u) | (z == S.nz - 1 ? 32u : 0u);
+        store_cell_to<T, SR>(A, d, g, base, [&](auto I) -> unsigned {
+            constexpr int q = decltype(I)::value;
+            constexpr int ex = q < 19 ? q19_ex(q) : q7_ex(q - 19);
+            constexpr int ey = q < 19 ? q19_ey(q) : q7_ey(q - 19);
+            constexpr int ez = q < 19 ? q19_ez(q) : q7_ez(q - 19);
+            // faces that x + e_q crosses
+            constexpr unsigned faces = (ex == 1 ? 2u : (ex == -1 ? 1u : 0u)) |
+                                       (ey == 1 ? 8u : (ey == -1 ? 4u : 0u)) |
+                                       (ez == 1 ? 32u : (ez == -1 ? 16u : 0u));
+            if constexpr (faces == 0) return self + static_cast<unsigned>(SI.sn[q]);
+            else return self + static_cast<unsigned>((edge & faces) ? SI.sb[q] : SI.sn[q]);
+        });
+    }
+}
+
+}  // namespace
+
+void fill_inplace_geometry(const Geometry &G, InplaceGeometry &SI)
+{
+    StepGeometry &S = SI.load;
+    S.nx = G.nx;
+    S.ny = G.ny;
+    S.nz = G.nz;
+    S.plane = static_cast<unsigned>(G.plane);
+    S.inv_ny = G.inv_ny;
+    const long long sy = G.nx, sz = static_cast<long long>(G.nx) * G.ny;
+    for (int q = 0; q < kPlanes; ++q) {
+        const int ex = q < 19 ? q19_ex(q) : q7_ex(q - 19);
+        const int ey = q < 19 ? q19_ey(q) : q7_ey(q - 19);
+        const int ez = q < 19 ? q19_ez(q) : q7_ez(q - 19);
+        const int opp = q < 19 ? q19_opp(q) : 19 + q7_opp(q - 19);
+        const long long off = ex + ey * sy + ez * sz;
+        // offsets are taken modulo 2^32 by the kernel (32-bit cell indices)
+        S.nb[q] = static_cast<int>(static_cast<unsigned>(opp * G.plane - off));
+        S.bb[q] = static_cast<int>(static_cast<unsigned>(q * G.plane));
+        SI.sn[q] = static_cast<int>(static_cast<unsigned>(q * G.plane + off));
+        SI.sb[q] = static_cast<int>(static_cast<unsigned>(opp * G.plane));
+    }
+}
+
+cudaError_t launch_step_inplace(int wall, int storage, bool stochastic, void *buf, int phase,
+                                const InplaceGeometry &SI, const Geometry &G,
+                                const CollideParams &C, BlockShape b, cudaStream_t s, bool pdl)
+{
+    if (phase != 0 && phase != 1) return cudaErrorInvalidValue;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((G.nx + b.bx - 1) / b.bx, (G.ny + b.by - 1) / b.by, G.nz);
+    cfg.blockDim = dim3(b.bx, b.by, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    cudaError_t e = dispatch(wall, storage, [&](auto W, auto *tp) {
+        using T = std::remove_pointer_t<decltype(tp)>;
+        constexpr int WL = decltype(W)::value;
+        T *A = static_cast<T *>(buf);
+        if constexpr (!std::is_same_v<T, float>) {
+            if (stochastic)
+                return phase == 0
+                           ? cudaLaunchKernelEx(&cfg, step_inplace_kernel<WL, T, true, 0>, A, SI, C)
+                           : cudaLaunchKernelEx(&cfg, step_inplace_kernel<WL, T, true, 1>, A, SI, C);
+        }
+        return phase == 0 ? cudaLaunchKernelEx(&cfg, step_inplace_kernel<WL, T, false, 0>, A, SI, C)
+                          : cudaLaunchKernelEx(&cfg, step_inplace_kernel<WL, T, false, 1>, A, SI, C);
+    });
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+}  // namespace lbm

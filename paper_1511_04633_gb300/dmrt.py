@@ -24,6 +24,7 @@ OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_DIVERGED, ERR_TIMEOUT = range(6)
 WALL_PERIODIC, WALL_TYPE1, WALL_TYPE2, WALL_TYPE3 = 0, 1, 2, 3
 STORE_F32, STORE_BF16, STORE_F16 = 0, 1, 2
 ROUND_AUTO, ROUND_NEAREST, ROUND_STOCHASTIC = 0, 1, 2
+STREAM_AB, STREAM_INPLACE = 0, 1
 
 HEADER = os.path.join(_build.INCLUDE, "dmrt.h")
 
@@ -36,7 +37,7 @@ class DmrtError(RuntimeError):
 
 class dmrt_opts(ctypes.Structure):
     _fields_ = [("storage", ctypes.c_int), ("residual_interval", ctypes.c_int),
-                ("rounding", ctypes.c_int)]
+                ("rounding", ctypes.c_int), ("streaming", ctypes.c_int)]
 
 
 class dmrt_params(ctypes.Structure):
@@ -45,7 +46,8 @@ class dmrt_params(ctypes.Structure):
                 ("residual_interval", ctypes.c_int), ("rounding", ctypes.c_int),
                 ("nu", ctypes.c_double), ("alpha", ctypes.c_double), ("gbeta", ctypes.c_double),
                 ("tau_nu", ctypes.c_double), ("tau_alpha", ctypes.c_double),
-                ("steps", ctypes.c_long)]
+                ("steps", ctypes.c_long), ("streaming", ctypes.c_int),
+                ("device_bytes", ctypes.c_longlong)]
 
 
 class dmrt_stats(ctypes.Structure):
@@ -100,6 +102,7 @@ def load(build_if_missing: bool = True):
             "dmrt_nusselt_local": ([vp, i, vp, i], i),
             "dmrt_nusselt_flux": ([vp, i, P(d)], i),
             "dmrt_nusselt_noalloc": ([vp, i, i, i, i, vp, P(d)], i),
+            "dmrt_round_to_storage": ([i, i, vp, vp, ctypes.c_longlong, ctypes.c_uint, vp], i),
             "dmrt_residual": ([vp, P(d)], i),
             "dmrt_run_to_steady": ([vp, d, l_, P(l_), P(d)], i),
             "dmrt_set_populations": ([vp, vp, vp, i], i),
@@ -200,11 +203,12 @@ def check(h, status: int, what: str, ensemble: bool = False, surrogate: bool = F
 # ---------------------------------------------------------------- C-named functions
 
 def dmrt_create(grid, Ra: float, Pr: float = 0.71, Ma: float = 0.1, wall_type: int = 1,
-                storage: int = STORE_F32, residual_interval: int = 0, rounding: int = ROUND_AUTO):
+                storage: int = STORE_F32, residual_interval: int = 0, rounding: int = ROUND_AUTO,
+                streaming: int = STREAM_AB):
     L = load()
     h = ctypes.c_void_p()
     g = (ctypes.c_int * 3)(*grid)
-    opts = dmrt_opts(storage, residual_interval, rounding)
+    opts = dmrt_opts(storage, residual_interval, rounding, streaming)
     check(None, L.dmrt_create_ex(ctypes.byref(h), g, Ra, Pr, Ma, wall_type, ctypes.byref(opts)),
           "dmrt_create")
     return h
@@ -212,11 +216,11 @@ def dmrt_create(grid, Ra: float, Pr: float = 0.71, Ma: float = 0.1, wall_type: i
 
 def dmrt_create_lattice(grid, nu: float, alpha: float, gbeta: float, wall_type: int = 1,
                         storage: int = STORE_F32, residual_interval: int = 0,
-                        rounding: int = ROUND_AUTO):
+                        rounding: int = ROUND_AUTO, streaming: int = STREAM_AB):
     L = load()
     h = ctypes.c_void_p()
     g = (ctypes.c_int * 3)(*grid)
-    opts = dmrt_opts(storage, residual_interval, rounding)
+    opts = dmrt_opts(storage, residual_interval, rounding, streaming)
     check(None, L.dmrt_create_lattice(ctypes.byref(h), g, nu, alpha, gbeta, wall_type,
                                       ctypes.byref(opts)), "dmrt_create_lattice")
     return h
@@ -273,6 +277,22 @@ def dmrt_nusselt_noalloc(theta, wall: int = 0, stream=None):
     out = (ctypes.c_double * 3)()
     check(None, load().dmrt_nusselt_noalloc(p, nx, ny, nz, wall, raw, out), "dmrt_nusselt_noalloc")
     return tuple(out)
+
+
+def dmrt_round_to_storage(x, storage: int, rounding: int = ROUND_AUTO, seed: int = 0, out=None,
+                          stream=None):
+    """Round a CUDA float32 tensor to a population storage format and back
+    with the step kernel's rounding; returns `out` (a new tensor if None)."""
+    p, side = _ptr(x)
+    if side != 1:
+        raise TypeError("x must be a CUDA tensor")
+    if out is None:
+        out = x.new_empty(x.shape)
+    q, _ = _ptr(out)
+    raw = getattr(stream, "cuda_stream", stream)
+    check(None, load().dmrt_round_to_storage(storage, rounding, p, q, x.numel(), seed, raw),
+          "dmrt_round_to_storage")
+    return out
 
 
 def dmrt_residual(h) -> float:
@@ -362,7 +382,8 @@ class Cavity:
     arrays shaped [z][y][x] (velocity [3][z][y][x])."""
 
     def __init__(self, grid, Ra=None, Pr=0.71, Ma=0.1, wall_type=1, *, lattice=None,
-                 storage=STORE_F32, residual_interval=0, rounding=ROUND_AUTO):
+                 storage=STORE_F32, residual_interval=0, rounding=ROUND_AUTO,
+                 streaming=STREAM_AB):
         self.grid = tuple(int(v) for v in grid)
         nx, ny, nz = self.grid
         self.shape = (nz, ny, nx)
@@ -370,10 +391,10 @@ class Cavity:
         if lattice is not None:
             nu, alpha, gbeta = lattice
             self.h = dmrt_create_lattice(self.grid, nu, alpha, gbeta, wall_type, storage,
-                                         residual_interval, rounding)
+                                         residual_interval, rounding, streaming)
         else:
             self.h = dmrt_create(self.grid, Ra, Pr, Ma, wall_type, storage, residual_interval,
-                                 rounding)
+                                 rounding, streaming)
 
     def close(self):
         if getattr(self, "h", None):

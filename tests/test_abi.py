@@ -57,3 +57,36 @@ def test_null_handle_calls_are_rejected():
     assert lib.dmrt_sync(None) == dmrt.ERR_ARG
     assert lib.dmrt_last_error(None) == b"null handle"
     lib.dmrt_destroy(None)
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """Every struct the binding passes across the ABI has the size and field
+    offsets that a C compiler gives the header's declaration."""
+    import os
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = [dmrt.dmrt_opts, dmrt.dmrt_params, dmrt.dmrt_stats, dmrt.dmrt_cavity_desc,
+               dmrt.dmrt_surrogate_cfg]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "dmrt.h"', "int main(void) {"]
+    for s in structs:
+        name = s.__name__
+        lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
+        for f, _ in s._fields_:
+            lines.append(f'printf("{name}.{f} %zu\\n", offsetof({name}, {f}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    include = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run([cc, "-I", include, str(src), "-o", str(exe)], check=True)
+    got = dict(l.rsplit(" ", 1) for l in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                          text=True).stdout.split("\n") if l)
+    for s in structs:
+        name = s.__name__
+        assert int(got[name]) == ctypes.sizeof(s), name
+        for f, _ in s._fields_:
+            assert int(got[f"{name}.{f}"]) == getattr(s, f).offset, (name, f)

@@ -122,3 +122,53 @@ def test_storage_reports_its_bytes(dm):
     for storage, bpc in ((0, 208), (1, 104), (2, 104)):
         c = dm.Cavity((8, 8, 8), 1e4, wall_type=1, storage=storage)
         assert dm.dmrt_get_stats(c.h)["bytes_per_cell"] == bpc
+
+
+def _neighbours(v, storage):
+    """The two storage values around v (as float64, lo < hi), F16 with its
+    2^10 scale."""
+    if storage == 1:
+        bits = np.array([v], np.float32).view(np.uint32)[0]
+        a = np.array([bits & 0xFFFF0000], np.uint32).view(np.float32)[0]
+        b = np.array([(bits & 0xFFFF0000) + 0x10000], np.uint32).view(np.float32)[0]
+        return tuple(sorted((float(a), float(b))))
+    s = np.float32(v) * np.float32(1024.0)
+    h = np.float16(s)
+    other = np.nextafter(h, np.float16(np.inf) if float(h) < float(s) else np.float16(-np.inf))
+    return tuple(sorted((float(h) / 1024.0, float(other) / 1024.0)))
+
+
+@pytest.mark.parametrize("storage", [1, 2], ids=["bf16", "f16"])
+@pytest.mark.parametrize("v", [0.3, -0.123456, 1.0e-3 + 1.7e-7, 0.0123, -4.321e-5, 3.1e-9])
+def test_stochastic_rounding_is_unbiased(dm, storage, v):
+    """Each rounded copy is one of the two neighbours of v, taken with
+    probability (v - lo)/(hi - lo): the store keeps the expected value."""
+    import torch
+    n = 1 << 20
+    v32 = float(np.float32(v))
+    x = torch.full((n,), v32, device="cuda", dtype=torch.float32)
+    y = dm.dmrt_round_to_storage(x, storage, dm.ROUND_STOCHASTIC, seed=12345).cpu().numpy().astype(np.float64)
+    lo, hi = _neighbours(v32, storage)
+    assert lo <= v32 <= hi
+    up = y == hi
+    assert np.all(up | (y == lo))
+    p = (v32 - lo) / (hi - lo)
+    # 6 sigma of the binomial count plus the 2^-12 resolution of the random bits
+    tol = 6.0 * math.sqrt(max(p * (1 - p), 1e-6) / n) + 2.0 ** -12
+    assert abs(up.mean() - p) <= tol, (up.mean(), p)
+    # a second seed draws different bits; the same seed the same ones
+    y2 = dm.dmrt_round_to_storage(x, storage, dm.ROUND_STOCHASTIC, seed=12345).cpu().numpy()
+    assert np.array_equal(y2.astype(np.float64), y)
+
+
+@pytest.mark.parametrize("storage", [1, 2], ids=["bf16", "f16"])
+def test_round_to_nearest_storage(dm, storage):
+    import torch
+    rng = np.random.default_rng(3)
+    v = (rng.standard_normal(4096) * 0.05).astype(np.float32)
+    y = dm.dmrt_round_to_storage(torch.from_numpy(v).cuda(), storage, dm.ROUND_NEAREST).cpu().numpy()
+    if storage == 1:
+        ref = torch.from_numpy(v).to(torch.bfloat16).float().numpy()
+    else:
+        ref = ((v * np.float32(1024.0)).astype(np.float16).astype(np.float32) / np.float32(1024.0))
+    assert np.array_equal(y, ref)
