@@ -401,7 +401,8 @@ def run_ensemble(args, rank, local, world):
     draws = inputs.ensemble_draws(args.members, seed=args.seed)
     cav = [{"grid": (d["n"],) * 3, "Ra": d["Ra"], "wall": d["wall"]} for d in draws]
     storage = STORAGES[args.storage]
-    ens = dmrt.Ensemble(cav, storage=storage)
+    streaming = STREAMINGS[args.streaming]
+    ens = dmrt.Ensemble(cav, storage=storage, streaming=streaming)
     dmrt.dmrt_ensemble_set_stream(ens.e, stream)
     report = ens.autotune(trials=3)
     cells = ens.cells
@@ -436,7 +437,8 @@ def run_ensemble(args, rank, local, world):
     ens.close()
 
     # the same cavities as 64 separate handles, stepped one after another
-    singles = [dmrt.Cavity(c["grid"], c["Ra"], wall_type=c["wall"], storage=storage) for c in cav]
+    singles = [dmrt.Cavity(c["grid"], c["Ra"], wall_type=c["wall"], storage=storage, streaming=streaming)
+               for c in cav]
     for s in singles:
         dmrt.dmrt_set_stream(s.h, stream)
         s.step(inner)
@@ -462,7 +464,9 @@ def run_ensemble(args, rank, local, world):
             "data": "synthetic",
             "config": {"workload": f"ensemble of {len(cav)} seeded cavities (edge in 32/48/64/96, "
                                    f"log10 Ra in [3, 6], types 1-3, seed {args.seed}), "
-                                   f"{args.storage} storage; one step = {inner} LBM steps of all "
+                                   f"{args.storage} storage"
+                                   + ("" if args.streaming == "ab" else ", in-place streaming")
+                                   + f"; one step = {inner} LBM steps of all "
                                    f"members + residuals + hot-wall Nu of all",
                        "cells": cells, "min_tau_nu": min(taus), "autotune": report,
                        "parallelism": f"replicas x{world}"},

@@ -85,7 +85,7 @@ typedef enum {
  *  INPLACE: one buffer updated in place by two alternating kernels (the AA
  *           access pattern): half the population memory, the same HBM
  *           traffic per step, and bitwise the same results as AB in every
- *           call of this API.  Not available for ensembles. */
+ *           call of this API (single cavities and ensembles). */
 typedef enum {
     DMRT_STREAM_AB = 0,
     DMRT_STREAM_INPLACE = 1,

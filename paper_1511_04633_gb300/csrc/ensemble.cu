@@ -3,7 +3,9 @@
 // interval of K steps replays one captured CUDA graph.
 //
 // Each cavity keeps its own 26-plane population slab inside two shared
-// ping-pong buffers (A-B scheme, as for a single cavity).  A table of cavity
+// ping-pong buffers (A-B scheme, as for a single cavity), or inside one
+// buffer updated in place by two alternating kernels (the in-place scheme of
+// step_inplace.cu, half the population memory).  A table of cavity
 // descriptors (sizes, strides, tile shape, relaxation rates, wall type) lives
 // in device memory, and a block map gives every thread block of the launch
 // its cavity; the block's position inside that cavity follows from the
@@ -44,8 +46,39 @@ namespace {
 
 constexpr int kEnsRedThreads = 256;
 constexpr int kMinBlocksEns = 4;
+// the in-place phases need their store offsets beside the collision's values
+// (as the single-cavity in-place kernels): 80 registers
+#ifndef DMRT_ENS_INPLACE_MIN_BLOCKS
+#define DMRT_ENS_INPLACE_MIN_BLOCKS 3
+#endif
+constexpr int kMinBlocksEnsInplace = DMRT_ENS_INPLACE_MIN_BLOCKS;
 
 // ---------------------------------------------------------------- step
+
+// Stage the descriptor of the block's cavity in shared memory and locate the
+// block's cell: false if the thread lies outside the cavity.
+__device__ __forceinline__ bool locate_cell(CavityDesc &D, const CavityDesc *__restrict__ descs,
+                                            const int *__restrict__ blockmap, int &x, int &y, int &z)
+{
+    {
+        const int c = blockmap[blockIdx.x];
+        const unsigned *g = reinterpret_cast<const unsigned *>(descs + c);
+        unsigned *sdst = reinterpret_cast<unsigned *>(&D);
+        for (int w = threadIdx.x; w < static_cast<int>(sizeof(CavityDesc) / 4); w += blockDim.x)
+            sdst[w] = g[w];
+    }
+    __syncthreads();
+    const int bx = D.bx;
+    const long long b = static_cast<long long>(blockIdx.x) - D.block_start;
+    const int tx = static_cast<int>(threadIdx.x) % bx, ty = static_cast<int>(threadIdx.x) / bx;
+    const int tix = static_cast<int>(b % D.tiles_x);
+    const long long r = b / D.tiles_x;
+    const int tiy = static_cast<int>(r % D.tiles_y);
+    z = static_cast<int>(r / D.tiles_y);
+    x = tix * bx + tx;
+    y = tiy * D.by + ty;
+    return x < D.nx && y < D.ny;
+}
 
 // One cell of a walled cavity (Types 1-3; the wall type is a per-cavity
 // runtime value, which only changes the thermal rule on the x and z walls).
@@ -63,8 +96,12 @@ __device__ __forceinline__ void ensemble_cell(const T *__restrict__ src, T *__re
     pull_offsets<kRuntimeWall, T>(src, ComputedOffsets{plane, static_cast<unsigned>(nx), D.nxy}, nx,
                                   ny, nz, D.inv_ny, self, x, y, z, d, g, dir_x, dir_z);
     collide_pairs(D.C, d, g);
+    // re-read the plane stride after a compiler barrier: otherwise the
+    // compiler keeps the load offsets live through the collision for the
+    // stores and spills (see ensemble_inplace_kernel)
+    asm volatile("" ::: "memory");
     // same random word as a single cavity (step.cu) at the same step
-    store_cell<T, SR>(dst, self, plane, d, g, SR ? pcg_hash(self ^ salt) : 0u);
+    store_cell<T, SR>(dst, self, D.plane, d, g, SR ? pcg_hash(self ^ salt) : 0u);
 }
 
 template <typename T, bool SR>
@@ -86,35 +123,77 @@ __global__ void __launch_bounds__(256, kMinBlocksEns)
     // the block's cavity descriptor, staged in shared memory: its fields are
     // then re-read cheaply instead of occupying registers through the step
     __shared__ CavityDesc D;
-    {
-        const int c = blockmap[blockIdx.x];
-        const unsigned *g = reinterpret_cast<const unsigned *>(descs + c);
-        unsigned *sdst = reinterpret_cast<unsigned *>(&D);
-        for (int w = threadIdx.x; w < static_cast<int>(sizeof(CavityDesc) / 4); w += blockDim.x)
-            sdst[w] = g[w];
-    }
-    __syncthreads();
-    const int bx = D.bx;
-    const long long b = static_cast<long long>(blockIdx.x) - D.block_start;
-    const int tx = static_cast<int>(threadIdx.x) % bx, ty = static_cast<int>(threadIdx.x) / bx;
-    const int tix = static_cast<int>(b % D.tiles_x);
-    const long long r = b / D.tiles_x;
-    const int tiy = static_cast<int>(r % D.tiles_y);
-    const int z = static_cast<int>(r / D.tiles_y);
-    const int x = tix * bx + tx, y = tiy * D.by + ty;
-    if (x >= D.nx || y >= D.ny) return;
+    int x, y, z;
+    if (!locate_cell(D, descs, blockmap, x, y, z)) return;
     ensemble_cell<T, SR>(srcb + D.offset, dstb + D.offset, D, x, y, z, salt);
+}
+
+// In-place scheme (see step_inplace.cu): phase 0 pulls from the neighbours'
+// swapped slots and pushes to theirs, phase 1 works on the cell's own slots.
+// The buffer's tail holds two step counters: phase p reads word p and writes
+// word p ^ 1.
+template <typename T, bool SR, int PHASE>
+__global__ void __launch_bounds__(256, kMinBlocksEnsInplace)
+    ensemble_inplace_kernel(T *__restrict__ buf, const CavityDesc *__restrict__ descs,
+                            const int *__restrict__ blockmap, long long counter_at)
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;");
+    unsigned salt = 0;
+    if constexpr (SR) {
+        unsigned *ctr = reinterpret_cast<unsigned *>(buf + counter_at);
+        const unsigned step = ctr[PHASE];
+        if (blockIdx.x == 0 && threadIdx.x == 0) ctr[PHASE ^ 1] = step + 1u;
+        salt = pcg_hash(step);
+    }
+    __shared__ CavityDesc D;
+    int x, y, z;
+    if (!locate_cell(D, descs, blockmap, x, y, z)) return;
+    T *A = buf + D.offset;
+    const int nx = D.nx, ny = D.ny, nz = D.nz;
+    const unsigned plane = D.plane;
+    const unsigned self = (static_cast<unsigned>(z) * ny + y) * nx + x;
+    const bool dir_x = D.wall != 1, dir_z = D.wall == 2;
+    const SwappedOffsets O{plane, static_cast<unsigned>(nx), D.nxy};
+    float d[19], g[7];
+    if constexpr (PHASE == 0)
+        pull_offsets<kRuntimeWall, T>(A, O, nx, ny, nz, D.inv_ny, self, x, y, z, d, g, dir_x, dir_z);
+    else
+        pull_offsets<kRuntimeWall, T>(A, LocalOffsets{plane}, nx, ny, nz, D.inv_ny, self, x, y, z, d,
+                                      g, dir_x, dir_z);
+    collide_pairs(D.C, d, g);
+    const unsigned base = SR ? pcg_hash(self ^ salt) : 0u;
+    // The store offsets equal the load offsets (each cell writes the slots it
+    // read); left to itself the compiler keeps all 26 of them live through the
+    // collision and spills.  Re-reading the strides from shared memory after
+    // a compiler barrier makes it recompute them at the stores instead.
+    asm volatile("" ::: "memory");
+    const unsigned splane = D.plane;
+    if constexpr (PHASE == 1) {
+        store_cell_to<T, SR>(A, d, g, base, [&](auto I) -> unsigned {
+            return self + plane_opp<decltype(I)::value>() * splane;
+        });
+    } else {
+        const SwappedOffsets SO{splane, static_cast<unsigned>(D.nx), D.nxy};
+        const unsigned edge = face_bits(x, y, z, D.nx, D.ny, D.nz);
+        store_cell_to<T, SR>(A, d, g, base, [&](auto I) -> unsigned {
+            constexpr int q = decltype(I)::value;
+            constexpr unsigned faces = leaving_faces<q>();
+            if constexpr (faces == 0) return self + SO.template sn<q>();
+            else return self + ((edge & faces) ? SO.template sb<q>() : SO.template sn<q>());
+        });
+    }
 }
 
 // ---------------------------------------------------------------- residual
 
-__device__ __forceinline__ Geometry geometry_of(const CavityDesc &D)
+__device__ __forceinline__ Geometry geometry_of(const CavityDesc &D, int layout)
 {
     Geometry G;
     G.nx = D.nx;
     G.ny = D.ny;
     G.nz = D.nz;
-    G.layout = lbm::kLayoutAB;
+    G.layout = layout;
     G.plane = D.plane;
     G.inv_ny = D.inv_ny;
     return G;
@@ -134,7 +213,7 @@ __device__ __forceinline__ Macro pulled_macro(const T *src, const Geometry &G, i
 template <typename T>
 __global__ void __launch_bounds__(kEnsRedThreads)
     ensemble_residual_kernel(const T *__restrict__ srcb, const CavityDesc *__restrict__ descs,
-                             const int *__restrict__ redmap, float *__restrict__ snapb,
+                             const int *__restrict__ redmap, int layout, float *__restrict__ snapb,
                              int have_prev, double *__restrict__ partials)
 {
     const int c = redmap[blockIdx.x];
@@ -146,7 +225,7 @@ __global__ void __launch_bounds__(kEnsRedThreads)
     const int z = static_cast<int>(r / D.red_tiles_y);
     double v[4] = {0.0, 0.0, 0.0, 0.0};
     if (x < D.nx && y < D.ny) {
-        const Geometry G = geometry_of(D);
+        const Geometry G = geometry_of(D, layout);
         const T *src = srcb + D.offset;
         Macro m;
         switch (D.wall) {
@@ -222,12 +301,12 @@ __device__ __forceinline__ float pulled_T(const T *src, const Geometry &G, int x
 template <typename T>
 __global__ void __launch_bounds__(kEnsRedThreads)
     ensemble_nusselt_kernel(const T *__restrict__ srcb, const CavityDesc *__restrict__ descs,
-                            int wall, int max_nz, double *__restrict__ partials)
+                            int layout, int wall, int max_nz, double *__restrict__ partials)
 {
     const int c = blockIdx.y, z = blockIdx.x;
     const CavityDesc &D = descs[c];
     if (z >= D.nz) return;  // uniform per block
-    const Geometry G = geometry_of(D);
+    const Geometry G = geometry_of(D, layout);
     const T *src = srcb + D.offset;
     const int y1 = wall == 0 ? 0 : D.ny - 1;
     const int y2 = wall == 0 ? 1 : D.ny - 2;
@@ -325,7 +404,40 @@ cudaError_t launch_ensemble_step(int storage, bool stochastic, const void *src, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_ensemble_residual(int storage, const void *src, const CavityDesc *descs,
+cudaError_t launch_ensemble_inplace(int storage, bool stochastic, void *buf, int phase,
+                                    const CavityDesc *descs, const int *blockmap, long long blocks,
+                                    int threads, long long counter_at, cudaStream_t s, bool pdl)
+{
+    if (phase != 0 && phase != 1) return cudaErrorInvalidValue;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(static_cast<unsigned>(blocks));
+    cfg.blockDim = dim3(threads);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    cudaError_t e = dispatch(1, storage, [&](auto, auto *tp) {
+        using T = std::remove_pointer_t<decltype(tp)>;
+        T *A = static_cast<T *>(buf);
+        if constexpr (!std::is_same_v<T, float>) {
+            if (stochastic)
+                return phase == 0 ? cudaLaunchKernelEx(&cfg, ensemble_inplace_kernel<T, true, 0>, A,
+                                                       descs, blockmap, counter_at)
+                                  : cudaLaunchKernelEx(&cfg, ensemble_inplace_kernel<T, true, 1>, A,
+                                                       descs, blockmap, counter_at);
+        }
+        return phase == 0 ? cudaLaunchKernelEx(&cfg, ensemble_inplace_kernel<T, false, 0>, A, descs,
+                                               blockmap, counter_at)
+                          : cudaLaunchKernelEx(&cfg, ensemble_inplace_kernel<T, false, 1>, A, descs,
+                                               blockmap, counter_at);
+    });
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ensemble_residual(int storage, const void *src, int layout, const CavityDesc *descs,
                                      const int *redmap, long long red_blocks, int count,
                                      float *snap, int have_prev, int K, double *partials,
                                      double *result, cudaStream_t s)
@@ -333,7 +445,7 @@ cudaError_t launch_ensemble_residual(int storage, const void *src, const CavityD
     cudaError_t e = dispatch(1, storage, [&](auto, auto *tp) {
         using T = std::remove_pointer_t<decltype(tp)>;
         ensemble_residual_kernel<T><<<static_cast<unsigned>(red_blocks), dim3(32, 8), 0, s>>>(
-            static_cast<const T *>(src), descs, redmap, snap, have_prev, partials);
+            static_cast<const T *>(src), descs, redmap, layout, snap, have_prev, partials);
         return cudaSuccess;
     });
     if (e != cudaSuccess) return e;
@@ -343,14 +455,14 @@ cudaError_t launch_ensemble_residual(int storage, const void *src, const CavityD
     return cudaGetLastError();
 }
 
-cudaError_t launch_ensemble_nusselt(int storage, const void *src, const CavityDesc *descs,
+cudaError_t launch_ensemble_nusselt(int storage, const void *src, int layout, const CavityDesc *descs,
                                     int count, int max_nz, int wall, double *partials,
                                     double *out, cudaStream_t s)
 {
     cudaError_t e = dispatch(1, storage, [&](auto, auto *tp) {
         using T = std::remove_pointer_t<decltype(tp)>;
         ensemble_nusselt_kernel<T><<<dim3(max_nz, count), kEnsRedThreads, 0, s>>>(
-            static_cast<const T *>(src), descs, wall, max_nz, partials);
+            static_cast<const T *>(src), descs, layout, wall, max_nz, partials);
         return cudaSuccess;
     });
     if (e != cudaSuccess) return e;
@@ -385,6 +497,9 @@ struct dmrt_ensemble {
     long long total_cells = 0;
     void *buf[2] = {nullptr, nullptr};
     int cur = 0;
+    bool inplace = false;  // one buffer, in-place streaming (buf[0])
+    int parity = 0;        // in-place: layout of the state (steps mod 2)
+    long long device_bytes = 0;
     float *snap = nullptr;
     double *partials = nullptr;
     size_t npartials = 0;
@@ -528,8 +643,21 @@ void drop_graphs(dmrt_ensemble_t *e)
         }
 }
 
+// The alternating state of the ensemble: the current buffer (A-B) or the
+// layout parity (in-place).
+int &phase(dmrt_ensemble_t *e) { return e->inplace ? e->parity : e->cur; }
+
+int state_layout(const dmrt_ensemble_t *e)
+{
+    return !e->inplace ? lbm::kLayoutAB : (e->parity ? lbm::kLayoutStreamed : lbm::kLayoutSwapped);
+}
+
 cudaError_t launch_one_step(dmrt_ensemble_t *e, int from)
 {
+    if (e->inplace)
+        return lbm::launch_ensemble_inplace(e->storage, e->stochastic, e->buf[0], from, e->d_desc,
+                                            e->d_blockmap, e->step_blocks, e->threads,
+                                            e->total_elems, e->stream, e->use_pdl);
     return lbm::launch_ensemble_step(e->storage, e->stochastic, e->buf[from], e->buf[from ^ 1],
                                      e->d_desc, e->d_blockmap, e->step_blocks, e->threads,
                                      e->total_elems, e->stream, e->use_pdl);
@@ -565,7 +693,7 @@ bool capture_interval(dmrt_ensemble_t *e, int start)
 dmrt_status run_residual(dmrt_ensemble_t *e)
 {
     ECK(e,
-        lbm::launch_ensemble_residual(e->storage, e->buf[e->cur], e->d_desc, e->d_redmap,
+        lbm::launch_ensemble_residual(e->storage, e->buf[e->cur], state_layout(e), e->d_desc, e->d_redmap,
                                       e->red_blocks, e->count, e->snap, e->snaps > 0 ? 1 : 0, e->K,
                                       e->partials, e->dres, e->stream),
         "ensemble residual");
@@ -586,17 +714,18 @@ dmrt_status run_steps(dmrt_ensemble_t *e, long n)
             ECK(e, cudaEventRecord(e0, e->stream), "cudaEventRecord");
         }
         bool graphed = false;
+        int &ph = phase(e);
         if (chunk == e->K && e->K <= kEnsMaxGraphSteps && e->use_graphs) {
-            if (!e->graph[e->cur] && !capture_interval(e, e->cur)) e->use_graphs = false;
-            if (e->graph[e->cur]) {
-                ECK(e, cudaGraphLaunch(e->graph[e->cur], e->stream), "cudaGraphLaunch");
-                if (e->K & 1) e->cur ^= 1;
+            if (!e->graph[ph] && !capture_interval(e, ph)) e->use_graphs = false;
+            if (e->graph[ph]) {
+                ECK(e, cudaGraphLaunch(e->graph[ph], e->stream), "cudaGraphLaunch");
+                if (e->K & 1) ph ^= 1;
                 graphed = true;
             }
         }
         for (long s = 0; s < chunk && !graphed; ++s) {
-            ECK(e, launch_one_step(e, e->cur), "ensemble step");
-            e->cur ^= 1;
+            ECK(e, launch_one_step(e, ph), "ensemble step");
+            ph ^= 1;
         }
         e->steps += chunk;
         e->step_launches += chunk;
@@ -619,16 +748,19 @@ dmrt_status ensure_staging(dmrt_ensemble_t *e, size_t floats)
 {
     if (e->staging_floats >= floats) return DMRT_OK;
     if (e->staging) cudaFree(e->staging);
+    e->device_bytes -= static_cast<long long>(e->staging_floats * sizeof(float));
     e->staging = nullptr;
     e->staging_floats = 0;
     ECK(e, cudaMalloc(&e->staging, floats * sizeof(float)), "cudaMalloc(staging)");
     e->staging_floats = floats;
+    e->device_bytes += static_cast<long long>(floats * sizeof(float));
     return DMRT_OK;
 }
 
-lbm::Geometry member_geometry(const lbm::CavityDesc &D)
+lbm::Geometry member_geometry(const dmrt_ensemble_t *e, const lbm::CavityDesc &D)
 {
     lbm::Geometry G{};
+    G.layout = state_layout(e);
     G.nx = D.nx;
     G.ny = D.ny;
     G.nz = D.nz;
@@ -653,14 +785,15 @@ dmrt_status dmrt_ensemble_create(dmrt_ensemble_t **out, int count, const dmrt_ca
     if (!out) return DMRT_ERR_ARG;
     *out = nullptr;
     if (count < 1 || !cav) return DMRT_ERR_ARG;
-    int storage = DMRT_STORE_F32, K = 100, rounding = DMRT_ROUND_AUTO;
+    int storage = DMRT_STORE_F32, K = 100, rounding = DMRT_ROUND_AUTO, streaming = DMRT_STREAM_AB;
     if (opts) {
         storage = opts->storage;
         rounding = opts->rounding;
+        streaming = opts->streaming;
         if (opts->residual_interval > 0) K = opts->residual_interval;
         if (opts->residual_interval < 0) return DMRT_ERR_ARG;
-        if (opts->streaming != DMRT_STREAM_AB) return DMRT_ERR_ARG;
     }
+    if (streaming != DMRT_STREAM_AB && streaming != DMRT_STREAM_INPLACE) return DMRT_ERR_ARG;
     if (storage < DMRT_STORE_F32 || storage > DMRT_STORE_F16) return DMRT_ERR_ARG;
     if (rounding < DMRT_ROUND_AUTO || rounding > DMRT_ROUND_STOCHASTIC) return DMRT_ERR_ARG;
 
@@ -674,6 +807,7 @@ dmrt_status dmrt_ensemble_create(dmrt_ensemble_t **out, int count, const dmrt_ca
     e->count = count;
     e->storage = storage;
     e->stochastic = storage != DMRT_STORE_F32 && rounding != DMRT_ROUND_NEAREST;
+    e->inplace = streaming == DMRT_STREAM_INPLACE;
     e->K = K;
     e->in.assign(cav, cav + count);
     e->desc.resize(count);
@@ -728,12 +862,15 @@ dmrt_status dmrt_ensemble_create(dmrt_ensemble_t **out, int count, const dmrt_ca
 
     cudaError_t c;
     const size_t buf_bytes = static_cast<size_t>(offset) * lbm::storage_bytes(storage) + 256;
-    for (int b = 0; b < 2; ++b) {
+    const int nbuf = e->inplace ? 1 : 2;
+    for (int b = 0; b < nbuf; ++b) {
         c = cudaMalloc(&e->buf[b], buf_bytes);
         if (c != cudaSuccess) return bail(c == cudaErrorMemoryAllocation ? DMRT_ERR_OOM : DMRT_ERR_CUDA);
+        e->device_bytes += static_cast<long long>(buf_bytes);
     }
     if (cudaMalloc(&e->snap, static_cast<size_t>(snap_off) * sizeof(float)) != cudaSuccess)
         return bail(DMRT_ERR_OOM);
+    e->device_bytes += snap_off * static_cast<long long>(sizeof(float));
     e->npartials = std::max<size_t>(static_cast<size_t>(red_start) * 4,
                                     static_cast<size_t>(count) * e->max_nz * 3);
     if (cudaMalloc(&e->partials, e->npartials * sizeof(double)) != cudaSuccess) return bail(DMRT_ERR_OOM);
@@ -743,6 +880,8 @@ dmrt_status dmrt_ensemble_create(dmrt_ensemble_t **out, int count, const dmrt_ca
     if (cudaMalloc(&e->d_desc, static_cast<size_t>(count) * sizeof(lbm::CavityDesc)) != cudaSuccess)
         return bail(DMRT_ERR_OOM);
     if (cudaMalloc(&e->d_redmap, redmap.size() * sizeof(int)) != cudaSuccess) return bail(DMRT_ERR_OOM);
+    e->device_bytes += static_cast<long long>(e->npartials * sizeof(double) + count * 5 * sizeof(double) +
+                                              count * sizeof(lbm::CavityDesc) + redmap.size() * sizeof(int));
     if (cudaStreamCreateWithFlags(&e->own, cudaStreamNonBlocking) != cudaSuccess)
         return bail(DMRT_ERR_CUDA);
     e->stream = e->own;
@@ -750,7 +889,7 @@ dmrt_status dmrt_ensemble_create(dmrt_ensemble_t **out, int count, const dmrt_ca
                         cudaMemcpyHostToDevice, e->stream) != cudaSuccess)
         return bail(DMRT_ERR_CUDA);
     if (upload_layout(e, map) != DMRT_OK) return bail(DMRT_ERR_CUDA);
-    for (int b = 0; b < 2; ++b)
+    for (int b = 0; b < nbuf; ++b)
         if (cudaMemsetAsync(e->buf[b], 0, buf_bytes, e->stream) != cudaSuccess) return bail(DMRT_ERR_CUDA);
     if (cudaStreamSynchronize(e->stream) != cudaSuccess) return bail(DMRT_ERR_CUDA);
     *out = e;
@@ -838,17 +977,53 @@ dmrt_status dmrt_ensemble_autotune(dmrt_ensemble_t *e, int trials, char *report,
     EDeviceGuard dg(e->device);
     ECK(e, cudaStreamSynchronize(e->stream), "cudaStreamSynchronize");
     drop_graphs(e);
+    // In-place ensembles are timed on a scratch copy of their buffer (each
+    // launch rewrites its input); two-buffer ones on the live buffers, where
+    // every launch recomputes the same next state from buf[cur].
+    void *live = e->buf[0];
+    void *scratch = nullptr;
+    if (e->inplace) {
+        const size_t bytes = static_cast<size_t>(e->total_elems) * lbm::storage_bytes(e->storage) + 256;
+        cudaError_t c = cudaMalloc(&scratch, bytes);
+        if (c != cudaSuccess) {
+            cudaGetLastError();
+            return efail(e, DMRT_ERR_OOM, "autotune of an in-place ensemble needs a scratch copy "
+                                          "of %zu bytes", bytes);
+        }
+        c = cudaMemcpyAsync(scratch, live, bytes, cudaMemcpyDeviceToDevice, e->stream);
+        if (c != cudaSuccess) {
+            cudaFree(scratch);
+            return ecuda(e, c, "copy to scratch");
+        }
+        e->buf[0] = scratch;
+    }
+    struct Restore {
+        dmrt_ensemble_t *e;
+        void *live, *scratch;
+        ~Restore()
+        {
+            if (!scratch) return;
+            cudaStreamSynchronize(e->stream);
+            e->buf[0] = live;
+            cudaFree(scratch);
+        }
+    } restore{e, live, scratch};
     cudaEvent_t t0, t1;
     ECK(e, cudaEventCreate(&t0), "cudaEventCreate");
     ECK(e, cudaEventCreate(&t1), "cudaEventCreate");
-    // time `trials` launches of the current layout of `which` (state kept:
-    // every launch recomputes the same next state from buf[cur])
+    int ph = phase(e);
+    auto one = [&]() {
+        const cudaError_t c = launch_one_step(e, ph);
+        if (e->inplace) ph ^= 1;  // the scratch state advances
+        return c;
+    };
+    // time `trials` launches of the current layout of `which`
     auto time_layout = [&](const std::vector<int> &which, float *ms) -> dmrt_status {
         dmrt_status st = upload_layout(e, layout_step(e, which));
         if (st != DMRT_OK) return st;
-        ECK(e, launch_one_step(e, e->cur), "autotune warm-up");
+        ECK(e, one(), "autotune warm-up");
         ECK(e, cudaEventRecord(t0, e->stream), "cudaEventRecord");
-        for (int t = 0; t < trials; ++t) ECK(e, launch_one_step(e, e->cur), "autotune launch");
+        for (int t = 0; t < trials; ++t) ECK(e, one(), "autotune launch");
         ECK(e, cudaEventRecord(t1, e->stream), "cudaEventRecord");
         ECK(e, cudaEventSynchronize(t1), "cudaEventSynchronize");
         ECK(e, cudaEventElapsedTime(ms, t0, t1), "cudaEventElapsedTime");
@@ -979,7 +1154,7 @@ dmrt_status dmrt_ensemble_nusselt(dmrt_ensemble_t *e, int wall, double *out)
     if (!e || !out || (wall != 0 && wall != 1)) return DMRT_ERR_ARG;
     EDeviceGuard dg(e->device);
     ECK(e,
-        lbm::launch_ensemble_nusselt(e->storage, e->buf[e->cur], e->d_desc, e->count, e->max_nz,
+        lbm::launch_ensemble_nusselt(e->storage, e->buf[e->cur], state_layout(e), e->d_desc, e->count, e->max_nz,
                                      wall, e->partials, e->dnu, e->stream),
         "ensemble nusselt");
     e->total_launches += 2;
@@ -996,7 +1171,7 @@ dmrt_status dmrt_ensemble_fields(dmrt_ensemble_t *e, int member, float *rho, flo
     if (!e || member < 0 || member >= e->count) return DMRT_ERR_ARG;
     EDeviceGuard dg(e->device);
     const lbm::CavityDesc &D = e->desc[member];
-    const lbm::Geometry G = member_geometry(D);
+    const lbm::Geometry G = member_geometry(e, D);
     const size_t cells = static_cast<size_t>(D.nx) * D.ny * D.nz;
     float *dr = rho, *du = u, *dt = theta;
     if (!on_device) {
@@ -1025,7 +1200,7 @@ dmrt_status dmrt_ensemble_init_fields(dmrt_ensemble_t *e, int member, const floa
     if (!e || member < 0 || member >= e->count || !rho || !u || !theta) return DMRT_ERR_ARG;
     EDeviceGuard dg(e->device);
     const lbm::CavityDesc &D = e->desc[member];
-    const lbm::Geometry G = member_geometry(D);
+    const lbm::Geometry G = member_geometry(e, D);
     const size_t cells = static_cast<size_t>(D.nx) * D.ny * D.nz;
     const float *dr = rho, *du = u, *dt = theta;
     if (!on_device) {
@@ -1055,7 +1230,7 @@ dmrt_status dmrt_ensemble_get_populations(dmrt_ensemble_t *e, int member, float 
     if (!f && !g) return DMRT_OK;
     EDeviceGuard dg(e->device);
     const lbm::CavityDesc &D = e->desc[member];
-    const lbm::Geometry G = member_geometry(D);
+    const lbm::Geometry G = member_geometry(e, D);
     const size_t cells = static_cast<size_t>(D.nx) * D.ny * D.nz;
     float *df = f, *dgp = g;
     if (!on_device) {
@@ -1092,6 +1267,8 @@ dmrt_status dmrt_ensemble_member_params(const dmrt_ensemble_t *e, int member, dm
     out->tau_nu = 3.0 * e->nu[member] + 0.5;
     out->tau_alpha = 0.5 + 4.0 * e->alpha[member];
     out->steps = e->steps;
+    out->streaming = e->inplace ? DMRT_STREAM_INPLACE : DMRT_STREAM_AB;
+    out->device_bytes = e->device_bytes;
     return DMRT_OK;
 }
 

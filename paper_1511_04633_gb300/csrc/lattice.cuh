@@ -81,56 +81,35 @@ __host__ __device__ __forceinline__ unsigned pcg_hash(unsigned v)
 
 constexpr unsigned kWeyl = 0x9E3779B9u;  // 2^32 / golden ratio
 
+// The rounding itself is the hardware's stochastic-rounding conversion
+// (cvt.rs, PTX ISA 8.7, sm_100a and later), which adds the random bits below
+// the kept mantissa bits and truncates; one instruction per value.  Measured
+// on GB300 it made the FP16 step 23 % and the BF16 step 5 % faster than the
+// same rounding done with integer instructions.  Only the converted value of
+// the pair's low half is kept.
 template <typename T>
 struct StoreSR;
 
-// DMRT_SR_HW = 1: round with the hardware's stochastic-rounding conversion
-// (cvt.rs, PTX ISA 8.7, sm_100a and later) fed with the same random word;
-// 0: the integer formulations below.
-#ifndef DMRT_SR_HW
-#define DMRT_SR_HW 0
-#endif
-
-// bfloat16 keeps the high 16 bits of the FP32 pattern: adding 16 random bits
-// below them and truncating rounds the magnitude up with the right
-// probability (a carry into the exponent is the correct next value).
 template <>
 struct StoreSR<__nv_bfloat16> {
     static __device__ __forceinline__ void st(__nv_bfloat16 *p, float v, unsigned r)
     {
-#if DMRT_SR_HW
         unsigned pair;
         asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(pair) : "f"(0.0f), "f"(v), "r"(r));
         *reinterpret_cast<unsigned short *>(p) = static_cast<unsigned short>(pair);
-#else
-        const unsigned bits = __float_as_uint(v) + (r >> 16);
-        *reinterpret_cast<unsigned short *>(p) = static_cast<unsigned short>(bits >> 16);
-#endif
     }
 };
 
-// half: add uniform noise in [-ulp/2, ulp/2) of the half value, then round to
-// nearest, which rounds up with probability (v - lower) / ulp.  The ulp of a
-// half with the FP32 exponent e is 2^(e - 127 - 10), and 2^-24 in the half
-// subnormal range.
+// half: the value times the 2^10 storage scale (exact), rounded likewise.
 template <>
 struct StoreSR<__half> {
     static __device__ __forceinline__ void st(__half *p, float v, unsigned r)
     {
-#if DMRT_SR_HW
         unsigned pair;
         asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;"
             : "=r"(pair)
             : "f"(0.0f), "f"(v * Store<__half>::kScale), "r"(r));
         *reinterpret_cast<unsigned short *>(p) = static_cast<unsigned short>(pair);
-        return;
-#endif
-        const float s = v * Store<__half>::kScale;
-        const int e = static_cast<int>((__float_as_uint(s) >> 23) & 0xFFu);
-        const int ue = e - 10 > 103 ? e - 10 : 103;
-        const float ulp = __uint_as_float(static_cast<unsigned>(ue) << 23);
-        const float u = static_cast<float>(r >> 8) * (1.0f / 16777216.0f) - 0.5f;
-        *p = __float2half_rn(fmaf(u, ulp, s));
     }
 };
 

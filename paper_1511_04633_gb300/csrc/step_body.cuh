@@ -286,6 +286,88 @@ __device__ __forceinline__ void pull_offsets(const T *__restrict__ src, const Of
     });
 }
 
+// ---------------------------------------------------------------- in-place streaming
+
+// Direction q of the 26 planes (0..18 D3Q19, 19..25 D3Q7): velocity and the
+// plane of the opposite direction.
+template <int Q>
+__device__ constexpr int plane_ex() { return Q < 19 ? q19_ex(Q) : q7_ex(Q - 19); }
+template <int Q>
+__device__ constexpr int plane_ey() { return Q < 19 ? q19_ey(Q) : q7_ey(Q - 19); }
+template <int Q>
+__device__ constexpr int plane_ez() { return Q < 19 ? q19_ez(Q) : q7_ez(Q - 19); }
+template <int Q>
+__device__ constexpr int plane_opp() { return Q < 19 ? q19_opp(Q) : 19 + q7_opp(Q - 19); }
+
+// The box faces a cell touches, one bit each: x = 0, x = nx-1, y = 0,
+// y = ny-1, z = 0, z = nz-1.
+__device__ __forceinline__ unsigned face_bits(int x, int y, int z, int nx, int ny, int nz)
+{
+    return (x == 0 ? 1u : 0u) | (x == nx - 1 ? 2u : 0u) | (y == 0 ? 4u : 0u) |
+           (y == ny - 1 ? 8u : 0u) | (z == 0 ? 16u : 0u) | (z == nz - 1 ? 32u : 0u);
+}
+
+// Faces (face_bits) that x + e_Q crosses when x touches them.
+template <int Q>
+__device__ constexpr unsigned leaving_faces()
+{
+    constexpr int ex = plane_ex<Q>(), ey = plane_ey<Q>(), ez = plane_ez<Q>();
+    return (ex == 1 ? 2u : (ex == -1 ? 1u : 0u)) | (ey == 1 ? 8u : (ey == -1 ? 4u : 0u)) |
+           (ez == 1 ? 32u : (ez == -1 ? 16u : 0u));
+}
+
+// Phase-1 loads of the in-place scheme: population q of a cell arrives in its
+// own slot of plane q.
+struct LocalOffsets {
+    unsigned plane;
+    template <int Q>
+    __device__ __forceinline__ unsigned nb() const { return Q * plane; }
+    template <int Q>
+    __device__ __forceinline__ unsigned bb() const { return Q * plane; }
+};
+
+// Phase-0 offsets of the in-place scheme computed from the strides: S_q(x -
+// e_q) sits in plane opp(q) at x - e_q (nb), the bounce-back source S_opp(x)
+// in plane q at x (bb); the value leaving x along q goes to plane q at x +
+// e_q (sn), or to plane opp(q) at x when that link leaves the box (sb).
+struct SwappedOffsets {
+    unsigned plane, nx, nxy;
+    template <int Q>
+    __device__ __forceinline__ int off() const
+    {
+        return plane_ex<Q>() + plane_ey<Q>() * static_cast<int>(nx) +
+               plane_ez<Q>() * static_cast<int>(nxy);
+    }
+    template <int Q>
+    __device__ __forceinline__ unsigned nb() const
+    {
+        return plane_opp<Q>() * plane - static_cast<unsigned>(off<Q>());
+    }
+    template <int Q>
+    __device__ __forceinline__ unsigned bb() const { return Q * plane; }
+    template <int Q>
+    __device__ __forceinline__ unsigned sn() const { return Q * plane + static_cast<unsigned>(off<Q>()); }
+    template <int Q>
+    __device__ __forceinline__ unsigned sb() const { return plane_opp<Q>() * plane; }
+};
+
+// Store the 26 post-collision values of one cell at A + addr(q), rounding
+// stochastically with bits keyed by the direction q as store_cell does.
+template <typename T, bool SR, typename Addr>
+__device__ __forceinline__ void store_cell_to(T *A, const float d[19], const float g[7],
+                                              unsigned base, Addr &&addr)
+{
+    static_for<0, 26>([&](auto I) {
+        constexpr int q = decltype(I)::value;
+        float v;
+        if constexpr (q < 19) v = d[q];
+        else v = g[q - 19];
+        T *p = A + addr(I);
+        if constexpr (SR) StoreSR<T>::st(p, v, base + q * kWeyl);
+        else Store<T>::st(p, v);
+    });
+}
+
 // Store the 26 post-collision values of one cell; SR selects stochastic
 // rounding with the random word `base` (one Weyl step per plane).
 template <typename T, bool SR>

@@ -38,15 +38,6 @@ namespace {
 #define DMRT_INPLACE_MIN_BLOCKS1 3
 #endif
 
-// Phase-1 loads: population q of a cell arrives in its own slot of plane q.
-struct LocalOffsets {
-    unsigned plane;
-    template <int Q>
-    __device__ __forceinline__ unsigned nb() const { return Q * plane; }
-    template <int Q>
-    __device__ __forceinline__ unsigned bb() const { return Q * plane; }
-};
-
 // Cell index of (x + dx, y + dy, z + dz) in a periodic box.
 __device__ __forceinline__ unsigned wrapped_cell(const StepGeometry &S, int x, int y, int z)
 {
@@ -73,24 +64,6 @@ __device__ __forceinline__ void load_periodic(const T *A, const StepGeometry &S,
         const float v = Store<T>::ld(A + a);
         if constexpr (q < 19) d[q] = v;
         else g[q - 19] = v;
-    });
-}
-
-// Store the 26 post-collision values of one cell at addr(q) (plane and cell
-// of the slot), rounding stochastically with bits keyed by the direction q
-// as in the two-buffer store.
-template <typename T, bool SR, typename Addr>
-__device__ __forceinline__ void store_cell_to(T *A, const float d[19], const float g[7],
-                                              unsigned base, Addr &&addr)
-{
-    static_for<0, 26>([&](auto I) {
-        constexpr int q = decltype(I)::value;
-        float v;
-        if constexpr (q < 19) v = d[q];
-        else v = g[q - 19];
-        T *p = A + addr(I);
-        if constexpr (SR) StoreSR<T>::st(p, v, base + q * kWeyl);
-        else Store<T>::st(p, v);
     });
 }
 
@@ -139,20 +112,10 @@ __global__ void __launch_bounds__(256, PHASE == 0 ? DMRT_INPLACE_MIN_BLOCKS0 : D
             return q * S.plane + wrapped_cell(S, x + ex, y + ey, z + ez);
         });
     } else {
-        // the box faces the cell touches, one bit each (kept in one register
-        // across the collision): x = 0, x = nx-1, y = 0, y = ny-1, z = 0, z = nz-1
-        const unsigned edge = (x == 0 ? 1u : 0u) | (x == S.nx - 1 ? 2u : 0u) |
-                              (y == 0 ? 4u : 0u) | (y == S.ny - 1 ? 8u : 0u) |
-                              (z == 0 ? 16u : 0u) | (z == S.nz - 1 ? 32u : 0u);
+        const unsigned edge = face_bits(x, y, z, S.nx, S.ny, S.nz);
         store_cell_to<T, SR>(A, d, g, base, [&](auto I) -> unsigned {
             constexpr int q = decltype(I)::value;
-            constexpr int ex = q < 19 ? q19_ex(q) : q7_ex(q - 19);
-            constexpr int ey = q < 19 ? q19_ey(q) : q7_ey(q - 19);
-            constexpr int ez = q < 19 ? q19_ez(q) : q7_ez(q - 19);
-            // faces that x + e_q crosses
-            constexpr unsigned faces = (ex == 1 ? 2u : (ex == -1 ? 1u : 0u)) |
-                                       (ey == 1 ? 8u : (ey == -1 ? 4u : 0u)) |
-                                       (ez == 1 ? 32u : (ez == -1 ? 16u : 0u));
+            constexpr unsigned faces = leaving_faces<q>();
             if constexpr (faces == 0) return self + static_cast<unsigned>(SI.sn[q]);
             else return self + static_cast<unsigned>((edge & faces) ? SI.sb[q] : SI.sn[q]);
         });

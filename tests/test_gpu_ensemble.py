@@ -118,3 +118,84 @@ def test_ensemble_rejects_periodic_members_and_bad_indices(dm):
     with pytest.raises(dm.DmrtError) as ei:
         dm.dmrt_ensemble_fields(ens.e, 1, rho=rho)
     assert ei.value.status == dm.ERR_ARG
+
+
+# ------------------------------------------------------------------ in-place ensembles
+
+def _same_members(a, b, count, walls=True):
+    for k in range(count):
+        fa, ga = a.populations(k)
+        fb, gb = b.populations(k)
+        assert np.array_equal(fa, fb) and np.array_equal(ga, gb), k
+        for x, y in zip(a.fields(k), b.fields(k)):
+            assert np.array_equal(x, y), k
+    if walls:
+        assert np.array_equal(np.asarray(a.nusselt(0)), np.asarray(b.nusselt(0)))
+        assert np.array_equal(np.asarray(a.nusselt(1)), np.asarray(b.nusselt(1)))
+
+
+@pytest.mark.parametrize("storage", [0, 1, 2], ids=["f32", "bf16", "f16"])
+@pytest.mark.parametrize("K", [6, 7])
+def test_in_place_ensemble_is_bitwise_the_two_buffer_ensemble(dm, storage, K):
+    """Odd and even step counts, graph-replayed intervals of odd and even K,
+    residuals: the in-place ensemble returns exactly what the two-buffer one
+    does."""
+    ab = dm.Ensemble(MEMBERS, storage=storage, residual_interval=K)
+    ip = dm.Ensemble(MEMBERS, storage=storage, residual_interval=K, streaming=dm.STREAM_INPLACE)
+    for n in (1, 2, 3 * K, 5 * K + 1):
+        ab.step(n)
+        ip.step(n)
+        _same_members(ab, ip, len(MEMBERS))
+    assert np.array_equal(np.asarray(ab.residual()), np.asarray(ip.residual()))
+
+
+def test_in_place_ensemble_members_match_single_in_place_cavities(dm):
+    ip = dm.Ensemble(MEMBERS[:3], storage=1, streaming=dm.STREAM_INPLACE)
+    ip.step(77)
+    for k, m in enumerate(MEMBERS[:3]):
+        single = dm.Cavity(m["grid"], m["Ra"], wall_type=m["wall"], storage=1,
+                           streaming=dm.STREAM_INPLACE)
+        single.step(77)
+        fe, ge = ip.populations(k)
+        fs, gs = single.populations()
+        assert np.array_equal(fe, fs) and np.array_equal(ge, gs), k
+
+
+def test_in_place_ensemble_init_fields_in_both_layouts(dm):
+    """A member's new state is written in whatever layout the ensemble is in
+    (here after an odd and an even step count)."""
+    ab = dm.Ensemble(MEMBERS, storage=1)
+    ip = dm.Ensemble(MEMBERS, storage=1, streaming=dm.STREAM_INPLACE)
+    for steps, member in ((5, 1), (4, 3)):
+        m = MEMBERS[member]
+        rho, u, th = inputs.random_fields(m["grid"], seed=steps)
+        for e in (ab, ip):
+            e.step(steps)
+            e.init_fields(member, rho, u, th)
+            e.step(3)
+        _same_members(ab, ip, len(MEMBERS))
+
+
+def test_in_place_ensemble_autotune_keeps_the_state(dm):
+    ip = dm.Ensemble(MEMBERS, streaming=dm.STREAM_INPLACE)
+    ip.step(41)  # the streamed layout
+    before = [ip.populations(k) for k in range(len(MEMBERS))]
+    report = ip.autotune(trials=2)
+    assert "chosen threads=" in report
+    for k in range(len(MEMBERS)):
+        f, g = ip.populations(k)
+        assert np.array_equal(f, before[k][0]) and np.array_equal(g, before[k][1])
+    ab = dm.Ensemble(MEMBERS)
+    ab.step(41)
+    ip.step(20)
+    ab.step(20)
+    _same_members(ab, ip, len(MEMBERS))
+
+
+def test_in_place_ensemble_holds_half_the_populations(dm):
+    ab = dm.Ensemble(MEMBERS)
+    ip = dm.Ensemble(MEMBERS, streaming=dm.STREAM_INPLACE)
+    pa, pi = ab.params(0), ip.params(0)
+    assert pi["streaming"] == dm.STREAM_INPLACE
+    elems = sum((m["grid"][0] * m["grid"][1] * m["grid"][2] + 63) // 64 * 64 * 26 for m in MEMBERS)
+    assert pa["device_bytes"] - pi["device_bytes"] == elems * 4 + 256

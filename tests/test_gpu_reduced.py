@@ -74,6 +74,34 @@ def test_ra1e6_type3_trajectory_against_the_oracle(dm, storage):
     assert abs(nu[0] - no[0]) <= 2 * u16 * no[0]
 
 
+@pytest.fixture(scope="module")
+def config3_reduced_oracle():
+    """The Type 3, Ra = 1e6 cavity of the 256^3 reduced-precision workload at
+    64^3, 600 steps from rest (the FP64 oracle cannot run 256^3)."""
+    o = oracle.Oracle.physical((64, 64, 64), 3, 1e6)
+    o.step(600)
+    _, uo, to = o.fields()
+    no, _ = o.nusselt(0)
+    return uo, to, no
+
+
+@pytest.mark.parametrize("storage", [0, 1, 2], ids=["f32", "bf16", "f16"])
+def test_config3_at_64cube_against_the_oracle(dm, config3_reduced_oracle, storage):
+    uo, to, no = config3_reduced_oracle
+    c = dm.Cavity((64, 64, 64), 1e6, wall_type=3, storage=storage)
+    c.step(600)
+    _, u, t = c.fields()
+    nu = c.nusselt(0)
+    if storage == 0:
+        assert np.abs(t - to).max() <= 1e-5 and np.abs(u - uo).max() <= 1e-5
+        assert abs(nu[0] - no[0]) <= 1e-4 * no[0]
+    else:
+        u16 = U16[storage]
+        assert np.abs(t - to).max() <= 2 * u16
+        assert np.abs(u - uo).max() <= 2 * u16 * UC
+        assert abs(nu[0] - no[0]) <= 2 * u16 * no[0]
+
+
 @pytest.mark.parametrize("storage", [1, 2], ids=["bf16", "f16"])
 def test_steady_nusselt_matches_fp32(dm, storage):
     """Type 1, 50^3, Ra = 1e4: the FP32 steady state against the time mean
