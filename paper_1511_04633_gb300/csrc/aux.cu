@@ -251,8 +251,8 @@ __global__ void set_populations_kernel(const float *__restrict__ f, const float 
     const long long cells = static_cast<long long>(G.nx) * G.ny * G.nz;
     for (long long c = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; c < cells;
          c += static_cast<long long>(gridDim.x) * blockDim.x) {
-        int x, y, z;
-        cell_xyz(G, c, x, y, z);
+        int x = 0, y = 0, z = 0;  // only the streamed layout needs the coordinates
+        if (G.layout == kLayoutStreamed) cell_xyz(G, c, x, y, z);
         static_for<0, 19>([&](auto I) {
             constexpr int i = decltype(I)::value;
             Store<T>::st(dst + state_index(G, periodic, i, c, x, y, z), f[i * cells + c] - q19_w(i));
@@ -269,8 +269,8 @@ __global__ void get_populations_kernel(const T *__restrict__ src, float *f, floa
     const long long cells = static_cast<long long>(G.nx) * G.ny * G.nz;
     for (long long c = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; c < cells;
          c += static_cast<long long>(gridDim.x) * blockDim.x) {
-        int x, y, z;
-        cell_xyz(G, c, x, y, z);
+        int x = 0, y = 0, z = 0;  // only the streamed layout needs the coordinates
+        if (G.layout == kLayoutStreamed) cell_xyz(G, c, x, y, z);
         if (f)
             static_for<0, 19>([&](auto I) {
                 constexpr int i = decltype(I)::value;
@@ -292,8 +292,8 @@ __global__ void init_fields_kernel(const float *__restrict__ rho, const float *_
     const long long cells = static_cast<long long>(G.nx) * G.ny * G.nz;
     for (long long c = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; c < cells;
          c += static_cast<long long>(gridDim.x) * blockDim.x) {
-        int x, y, z;
-        cell_xyz(G, c, x, y, z);
+        int x = 0, y = 0, z = 0;  // only the streamed layout needs the coordinates
+        if (G.layout == kLayoutStreamed) cell_xyz(G, c, x, y, z);
         const float r = rho[c];
         const float dr = r - 1.0f;
         const float vx = u[c], vy = u[cells + c], vz = u[2 * cells + c];

@@ -46,12 +46,15 @@ namespace {
 
 constexpr int kEnsRedThreads = 256;
 constexpr int kMinBlocksEns = 4;
-// the in-place phases need their store offsets beside the collision's values
-// (as the single-cavity in-place kernels): 80 registers
-#ifndef DMRT_ENS_INPLACE_MIN_BLOCKS
-#define DMRT_ENS_INPLACE_MIN_BLOCKS 3
+// Minimum resident 256-thread blocks per SM of the in-place phases (4 caps a
+// kernel at 64 registers, 3 at 80).  Measured on GB300 (64 members, FP32):
+// 64 registers everywhere gave 805 us per step, 80 registers 842 us.
+#ifndef DMRT_ENS_INPLACE_MIN_BLOCKS0
+#define DMRT_ENS_INPLACE_MIN_BLOCKS0 4
 #endif
-constexpr int kMinBlocksEnsInplace = DMRT_ENS_INPLACE_MIN_BLOCKS;
+#ifndef DMRT_ENS_INPLACE_MIN_BLOCKS1
+#define DMRT_ENS_INPLACE_MIN_BLOCKS1 4
+#endif
 
 // ---------------------------------------------------------------- step
 
@@ -133,7 +136,7 @@ __global__ void __launch_bounds__(256, kMinBlocksEns)
 // The buffer's tail holds two step counters: phase p reads word p and writes
 // word p ^ 1.
 template <typename T, bool SR, int PHASE>
-__global__ void __launch_bounds__(256, kMinBlocksEnsInplace)
+__global__ void __launch_bounds__(256, PHASE == 0 ? DMRT_ENS_INPLACE_MIN_BLOCKS0 : DMRT_ENS_INPLACE_MIN_BLOCKS1)
     ensemble_inplace_kernel(T *__restrict__ buf, const CavityDesc *__restrict__ descs,
                             const int *__restrict__ blockmap, long long counter_at)
 {
