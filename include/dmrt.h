@@ -369,7 +369,7 @@ typedef struct dmrt_surrogate dmrt_surrogate_t;
 typedef struct dmrt_surrogate_cfg {
     int grid;        /* n: edge of the cubic grid; n / 2^depth a multiple of 8 */
     int depth;       /* pooling levels D, 1..3 */
-    int channels[4]; /* c_0..c_D, each dividing 256 and <= 128 */
+    int channels[4]; /* c_0..c_D, each 4, 8, 16, 32, 64 or 128 */
     int storage;     /* DMRT_STORE_F32 or DMRT_STORE_BF16 */
     int max_batch;   /* largest batch of one call */
     unsigned seed;   /* initial weights: He-uniform from a PCG hash of the seed

@@ -369,6 +369,349 @@ __global__ void __launch_bounds__(128) wgrad_mma_kernel(const __nv_bfloat16 *__r
         }
 }
 
+// Tensor-core weight gradient of a 3^3 convolution, all 27 taps per block:
+// dw[tap][co][ci] = sum over voxels v of dy[v][co] x[v + tap][ci].  A block
+// owns 16 output x 16 input channels and a run of 8 x 8 x 4 voxel tiles of
+// one sample.  Per tile it stages dy (256 voxels) and the x halo (10 x 10 x 6
+// voxels) once, unmodified (channels-last rows padded to 24 elements, which
+// keeps the 8 rows of every ldmatrix conflict-free), and every tap reads the
+// shifted x rows straight from the halo: ldmatrix takes one row address per
+// thread, so the shift costs nothing.  The transposed 8 x 8 loads
+// (ldmatrix .trans) turn the channels-last rows into the A = dy^T (co x
+// voxels) and B = x_tap (voxels x ci) fragments of mma.m16n8k16.  Warp w
+// accumulates taps w, w + 8, w + 16 (and w + 24 < 27) for both 8-channel
+// halves of ci: 6 or 8 accumulator tiles.  The block's sums over its tiles go
+// to partials[chunk][tap][co][ci], summed in chunk order afterwards.
+constexpr int kWtX = 8, kWtY = 8, kWtZ = 4;                  // voxel tile
+constexpr int kWtHX = kWtX + 2, kWtHY = kWtY + 2, kWtHZ = kWtZ + 2;
+constexpr int kWtVox = kWtX * kWtY * kWtZ;                   // 256
+constexpr int kWtHalo = kWtHX * kWtHY * kWtHZ;               // 600
+constexpr int kWtRow = 24;                                   // bf16 per staged row
+
+__device__ __forceinline__ void ldsm_x4_trans(unsigned (&r)[4], const void *p)
+{
+    const unsigned a = static_cast<unsigned>(__cvta_generic_to_shared(p));
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(a));
+}
+
+__global__ void __launch_bounds__(256) wgrad_taps_kernel(const __nv_bfloat16 *__restrict__ x,
+                                                         const __nv_bfloat16 *__restrict__ dy,
+                                                         float *__restrict__ partials, int n,
+                                                         int cin, int cout, int tiles_per_sample,
+                                                         int total_tiles, int tiles_per_block)
+{
+    __shared__ __align__(16) __nv_bfloat16 xs[kWtHalo][kWtRow];
+    __shared__ __align__(16) __nv_bfloat16 gs[kWtVox][kWtRow];
+    const int ci_tiles = cin > 8 ? cin / 16 : 1;
+    const int co0 = (blockIdx.x / ci_tiles) * 16, ci0 = (blockIdx.x % ci_tiles) * 16;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int ntap = warp + 24 < 27 ? 4 : 3;
+    float acc[4][2][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
+    const int tx_n = n / kWtX, ty_n = n / kWtY;
+    const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
+    // ldmatrix row of this thread: matrix j = lane / 8, row r = lane % 8
+    const int mj = lane >> 3, mr = lane & 7;
+    const int t_begin = blockIdx.y * tiles_per_block;
+    const int t_end = min(t_begin + tiles_per_block, total_tiles);
+    for (int tile = t_begin; tile < t_end; ++tile) {
+        const int b = tile / tiles_per_sample;
+        int r = tile % tiles_per_sample;
+        const int x0 = (r % tx_n) * kWtX;
+        r /= tx_n;
+        const int y0 = (r % ty_n) * kWtY;
+        const int z0 = (r / ty_n) * kWtZ;
+        const long long sample = static_cast<long long>(b) * n * n * n;
+        // x halo: 600 voxels x 2 granules of 8 channels (zero outside the
+        // grid and beyond cin)
+        for (int e = t; e < kWtHalo * 2; e += 256) {
+            const int half = e & 1, h = e >> 1;
+            const int hx = h % kWtHX, hy = (h / kWtHX) % kWtHY, hz = h / (kWtHX * kWtHY);
+            const int gx = x0 + hx - 1, gy = y0 + hy - 1, gz = z0 + hz - 1;
+            const int c = ci0 + 8 * half;
+            uint4 v = zero4;
+            if (gx >= 0 && gx < n && gy >= 0 && gy < n && gz >= 0 && gz < n && c < cin)
+                v = *reinterpret_cast<const uint4 *>(
+                    x + (sample + (static_cast<long long>(gz) * n + gy) * n + gx) * cin + c);
+            *reinterpret_cast<uint4 *>(&xs[h][8 * half]) = v;
+        }
+        // dy tile: 256 voxels x 2 granules
+        for (int e = t; e < kWtVox * 2; e += 256) {
+            const int half = e & 1, vi = e >> 1;
+            const int vx = vi % kWtX, vy = (vi / kWtX) % kWtY, vz = vi / (kWtX * kWtY);
+            const uint4 v = *reinterpret_cast<const uint4 *>(
+                dy + (sample + (static_cast<long long>(z0 + vz) * n + y0 + vy) * n + x0 + vx) * cout +
+                co0 + 8 * half);
+            *reinterpret_cast<uint4 *>(&gs[vi][8 * half]) = v;
+        }
+        __syncthreads();
+#pragma unroll 2
+        for (int ks = 0; ks < kWtVox / 16; ++ks) {
+            // k-step ks: voxels 16 ks .. 16 ks + 15 = two x-rows (z, y), (z, y + 1)
+            const int vz = ks / (kWtY / 2), vy = 2 * (ks % (kWtY / 2));
+            unsigned a[4];
+            // A = dy^T: matrices (v 0-7, co 0-7), (v 0-7, co 8-15), (v 8-15, co 0-7), (v 8-15, co 8-15)
+            ldsm_x4_trans(a, &gs[16 * ks + 8 * (mj >> 1) + mr][8 * (mj & 1)]);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                if (i < ntap) {
+                    const int tap = warp + 8 * i;
+                    const int dz = tap / 9, dyy = (tap / 3) % 3, dx = tap % 3;
+                    // B rows: voxel row (mj & 1) of the k-step, x = mr, shifted by the tap;
+                    // matrices (v 0-7, ci 0-7), (v 8-15, ci 0-7), (v 0-7, ci 8-15), (v 8-15, ci 8-15)
+                    const int h = ((vz + dz) * kWtHY + vy + (mj & 1) + dyy) * kWtHX + mr + dx;
+                    unsigned bb[4];
+                    ldsm_x4_trans(bb, &xs[h][8 * (mj >> 1)]);
+                    mma_bf16_16816(acc[i][0], a, bb[0], bb[1]);
+                    mma_bf16_16816(acc[i][1], a, bb[2], bb[3]);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    // acc[i][j]: rows co0 + g (+8), columns ci0 + 8 j + 2 tig (+1)
+    const int g = lane >> 2, tig = lane & 3;
+    float *out = partials + static_cast<long long>(blockIdx.y) * 27 * cout * cin;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        if (i >= ntap) continue;
+        const int tap = warp + 8 * i;
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int co = co0 + g + 8 * (q >> 1);
+                const int ci = ci0 + 8 * j + 2 * tig + (q & 1);
+                if (ci < cin)
+                    out[(static_cast<long long>(tap) * cout + co) * cin + ci] = acc[i][j][q];
+            }
+    }
+}
+
+// Weight gradient of a 1^3 convolution with few channels (the output head):
+// dw[co][ci] = sum over voxels of dy[v][co] x[v][ci] on CUDA cores.  Each
+// thread sums a strided set of voxels into CO x CI registers; the block
+// reduces its threads in a fixed tree and writes partials[block][co][ci].
+template <typename TI, int CO, int CI>
+__global__ void __launch_bounds__(256) wgrad_small_kernel(const TI *__restrict__ x,
+                                                          const float *__restrict__ dy,
+                                                          float *__restrict__ partials, long long voxels,
+                                                          int cin, int cout, long long chunk)
+{
+    float acc[CO][CI];
+#pragma unroll
+    for (int o = 0; o < CO; ++o)
+#pragma unroll
+        for (int i = 0; i < CI; ++i) acc[o][i] = 0.f;
+    const long long v0 = blockIdx.x * chunk;
+    const long long v1 = v0 + chunk < voxels ? v0 + chunk : voxels;
+    for (long long v = v0 + threadIdx.x; v < v1; v += 256) {
+        float xv[CI], gv[CO];
+#pragma unroll
+        for (int i = 0; i < CI; ++i) xv[i] = i < cin ? ldf(x + v * cin + i) : 0.f;
+#pragma unroll
+        for (int o = 0; o < CO; ++o) gv[o] = o < cout ? dy[v * cout + o] : 0.f;
+#pragma unroll
+        for (int o = 0; o < CO; ++o)
+#pragma unroll
+            for (int i = 0; i < CI; ++i) acc[o][i] = fmaf(gv[o], xv[i], acc[o][i]);
+    }
+    // fixed-order reduction: warp shuffle tree, then the 8 warps in order
+    __shared__ float red[8][CO * CI];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 0; o < CO; ++o)
+#pragma unroll
+        for (int i = 0; i < CI; ++i) {
+            float v = acc[o][i];
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+            if (lane == 0) red[warp][o * CI + i] = v;
+        }
+    __syncthreads();
+    for (int k = threadIdx.x; k < CO * CI; k += 256) {
+        const int o = k / CI, i = k % CI;
+        if (o >= cout || i >= cin) continue;
+        float v = 0.f;
+        for (int w = 0; w < 8; ++w) v += red[w][k];
+        partials[(static_cast<long long>(blockIdx.x) * cout + o) * cin + i] = v;
+    }
+}
+
+__device__ __forceinline__ void ldsm_x4(unsigned (&r)[4], const void *p)
+{
+    const unsigned a = static_cast<unsigned>(__cvta_generic_to_shared(p));
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(a));
+}
+
+template <typename T>
+__device__ __forceinline__ void st2(T *p, float a, float b);
+template <>
+__device__ __forceinline__ void st2<float>(float *p, float a, float b)
+{
+    *reinterpret_cast<float2 *>(p) = make_float2(a, b);
+}
+template <>
+__device__ __forceinline__ void st2<__nv_bfloat16>(__nv_bfloat16 *p, float a, float b)
+{
+    *reinterpret_cast<__nv_bfloat162 *>(p) = __floats2bfloat162_rn(a, b);
+}
+
+// Tensor-core 3^3 convolution (implicit GEMM, mma.m16n8k16, FP32
+// accumulation) over 8 x 8 x 4 voxel tiles: a block owns one tile of one
+// sample and 8 NT output channels.  For every 16 input channels it stages
+// the x halo (10 x 10 x 6 voxels) and the weights of all 27 taps for its
+// channels (rows padded to 24 elements: conflict-free ldmatrix), then runs
+// the 27 taps as shifted GEMMs: ldmatrix takes one row address per thread,
+// so tap (dz, dy, dx) just reads the halo rows shifted by it.  Warp w owns
+// voxel rows 32 w .. 32 w + 31 (two m16 tiles) and all NT n8 tiles.
+// Dynamic shared memory: (600 + 27 * 8 NT) rows of 24 bfloat16.
+template <int NT, typename TO>
+__global__ void __launch_bounds__(256) conv3d_tc_kernel(const __nv_bfloat16 *__restrict__ x,
+                                                        const __nv_bfloat16 *__restrict__ w,
+                                                        const float *__restrict__ bias,
+                                                        TO *__restrict__ y, int n, int cin, int cout,
+                                                        int act)
+{
+    constexpr int CO = 8 * NT;
+    extern __shared__ __align__(16) unsigned char conv_smem[];
+    __nv_bfloat16(*xs)[kWtRow] = reinterpret_cast<__nv_bfloat16(*)[kWtRow]>(conv_smem);
+    __nv_bfloat16(*ws)[kWtRow] = xs + kWtHalo;  // [tap * CO + co]
+    const int tx_n = n / kWtX, ty_n = n / kWtY, tz_n = n / kWtZ;
+    int r = blockIdx.x;
+    const int x0 = (r % tx_n) * kWtX;
+    r /= tx_n;
+    const int y0 = (r % ty_n) * kWtY;
+    r /= ty_n;
+    const int z0 = (r % tz_n) * kWtZ;
+    const int b = r / tz_n;
+    const int co0 = blockIdx.y * CO;
+    const long long sample = static_cast<long long>(b) * n * n * n;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int mj = lane >> 3, mr = lane & 7;
+    float acc[2][NT][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < NT; ++j)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
+    const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
+    for (int ci0 = 0; ci0 < cin; ci0 += 16) {
+        for (int e = t; e < kWtHalo * 2; e += 256) {
+            const int half = e & 1, h = e >> 1;
+            const int hx = h % kWtHX, hy = (h / kWtHX) % kWtHY, hz = h / (kWtHX * kWtHY);
+            const int gx = x0 + hx - 1, gy = y0 + hy - 1, gz = z0 + hz - 1;
+            const int c = ci0 + 8 * half;
+            uint4 v = zero4;
+            if (gx >= 0 && gx < n && gy >= 0 && gy < n && gz >= 0 && gz < n && c < cin)
+                v = *reinterpret_cast<const uint4 *>(
+                    x + (sample + (static_cast<long long>(gz) * n + gy) * n + gx) * cin + c);
+            *reinterpret_cast<uint4 *>(&xs[h][8 * half]) = v;
+        }
+        for (int e = t; e < 27 * CO * 2; e += 256) {
+            const int half = e & 1, row = e >> 1;
+            const int co = row % CO, tap = row / CO;
+            const int c = ci0 + 8 * half;
+            uint4 v = zero4;
+            if (co0 + co < cout && c < cin)
+                v = *reinterpret_cast<const uint4 *>(w + (static_cast<long long>(tap) * cout + co0 + co) * cin + c);
+            *reinterpret_cast<uint4 *>(&ws[row][8 * half]) = v;
+        }
+        __syncthreads();
+#pragma unroll 1
+        for (int tap = 0; tap < 27; ++tap) {
+            const int dz = tap / 9, dyy = (tap / 3) % 3, dx = tap % 3;
+            unsigned a[2][4];
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                // m16 tile 2 warp + i: voxel x-rows (vz, vy) and (vz, vy + 1)
+                const int mt = 2 * warp + i;
+                const int vz = mt / (kWtY / 2), vy = 2 * (mt % (kWtY / 2));
+                const int h = ((vz + dz) * kWtHY + vy + (mj & 1) + dyy) * kWtHX + mr + dx;
+                ldsm_x4(a[i], &xs[h][8 * (mj >> 1)]);
+            }
+#pragma unroll
+            for (int j = 0; j < NT; j += 2) {
+                // n8 tiles j, j + 1: matrices (co j, ci 0-7), (co j, ci 8-15), (co j+1, ...)
+                unsigned bb[4];
+                ldsm_x4(bb, &ws[tap * CO + 8 * (j + (mj >> 1)) + mr][8 * (mj & 1)]);
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+                    mma_bf16_16816(acc[i][j], a[i], bb[0], bb[1]);
+                    mma_bf16_16816(acc[i][j + 1], a[i], bb[2], bb[3]);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    const int g = lane >> 2, tig = lane & 3;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const int mt = 2 * warp + i;
+        const int vz = mt / (kWtY / 2), vy = 2 * (mt % (kWtY / 2));
+#pragma unroll
+        for (int hrow = 0; hrow < 2; ++hrow) {
+            const long long vox = sample + (static_cast<long long>(z0 + vz) * n + y0 + vy + hrow) * n + x0 + g;
+            TO *yo = y + vox * cout;
+#pragma unroll
+            for (int j = 0; j < NT; ++j) {
+                const int co = co0 + 8 * j + 2 * tig;
+                if (co >= cout) continue;
+                float v0 = acc[i][j][2 * hrow] + (bias ? bias[co] : 0.f);
+                float v1 = acc[i][j][2 * hrow + 1] + (bias ? bias[co + 1] : 0.f);
+                if (act) {
+                    v0 = v0 > 0.f ? v0 : kSlope * v0;
+                    v1 = v1 > 0.f ? v1 : kSlope * v1;
+                }
+                st2(yo + co, v0, v1);
+            }
+        }
+    }
+}
+
+// A 1^3 convolution with few channels (the output head and its input
+// gradient) on CUDA cores: one voxel per thread, the weights and bias in
+// shared memory, y[v][co] = act(sum_ci x[v][ci] w[co][ci] + b[co]).
+template <typename TI, typename TW, typename TO, int CI, int CO>
+__global__ void __launch_bounds__(256) conv1x1_small_kernel(const TI *__restrict__ x, const TW *__restrict__ w,
+                                                            const float *__restrict__ bias, TO *__restrict__ y,
+                                                            long long voxels, int cin, int cout, int act)
+{
+    __shared__ float ws[CO][CI];
+    __shared__ float bs[CO];
+    for (int e = threadIdx.x; e < CO * CI; e += blockDim.x) {
+        const int o = e / CI, i = e % CI;
+        ws[o][i] = (o < cout && i < cin) ? ldf(w + o * cin + i) : 0.f;
+    }
+    for (int o = threadIdx.x; o < CO; o += blockDim.x) bs[o] = (bias && o < cout) ? bias[o] : 0.f;
+    __syncthreads();
+    for (long long v = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; v < voxels;
+         v += static_cast<long long>(gridDim.x) * blockDim.x) {
+        float xv[CI];
+#pragma unroll
+        for (int i = 0; i < CI; ++i) xv[i] = i < cin ? ldf(x + v * cin + i) : 0.f;
+#pragma unroll
+        for (int o = 0; o < CO; ++o) {
+            if (o >= cout) break;
+            float r = bs[o];
+#pragma unroll
+            for (int i = 0; i < CI; ++i) r = fmaf(xv[i], ws[o][i], r);
+            if (act) r = r > 0.f ? r : kSlope * r;
+            stf(y + v * cout + o, r);
+        }
+    }
+}
+
 // out = bfloat16(in)
 __global__ void narrow_kernel(const float *__restrict__ in, __nv_bfloat16 *__restrict__ out, long long len)
 {
@@ -444,28 +787,70 @@ __global__ void __launch_bounds__(256) conv3d_wgrad_kernel(const TI *__restrict_
         if (k < nco) out[(co0 + k * step) * cin + ci] = acc[k];
 }
 
-// out[i] = sum over chunks (in order) of partials[chunk][i]
-__global__ void sum_chunks_kernel(const float *__restrict__ partials, float *__restrict__ out,
-                                  long long len, int chunks)
+// out[i] = sum over chunks of partials[chunk][i], in a fixed order: a block
+// covers E consecutive elements (E = 32, or the power of two >= len when len
+// is smaller) with 256 / E lanes of chunks; lane l adds chunks l, l + L, ...
+// into four interleaved sums (chunk c goes to sum (c / L) % 4), and the lanes
+// are then added in order.  Threads with consecutive elements read
+// consecutive floats of one chunk.
+__global__ void __launch_bounds__(256) sum_chunks_kernel(const float *__restrict__ partials,
+                                                         float *__restrict__ out, long long len,
+                                                         int chunks, int E)
 {
-    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < len;
-         i += static_cast<long long>(gridDim.x) * blockDim.x) {
-        float s = 0.f;
-        for (int c = 0; c < chunks; ++c) s += partials[c * len + i];
-        out[i] = s;
+    __shared__ float red[256];
+    const int L = 256 / E;
+    const int e = threadIdx.x % E, lane = threadIdx.x / E;
+    const long long i = static_cast<long long>(blockIdx.x) * E + e;
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+    if (i < len) {
+        int c = lane;
+        for (; c + 3 * L < chunks; c += 4 * L) {
+            s0 += partials[static_cast<long long>(c) * len + i];
+            s1 += partials[static_cast<long long>(c + L) * len + i];
+            s2 += partials[static_cast<long long>(c + 2 * L) * len + i];
+            s3 += partials[static_cast<long long>(c + 3 * L) * len + i];
+        }
+        for (; c < chunks; c += L) s0 += partials[static_cast<long long>(c) * len + i];
+    }
+    red[threadIdx.x] = (s0 + s1) + (s2 + s3);
+    __syncthreads();
+    if (lane == 0 && i < len) {
+        float tot = 0.f;
+        for (int l = 0; l < L; ++l) tot += red[l * E + e];
+        out[i] = tot;
     }
 }
 
 // Bias gradient partials: per block of voxels, the sum of dy over them.
-__global__ void bias_grad_kernel(const float *__restrict__ dy, float *__restrict__ partials,
-                                 long long voxels, int cout, int chunk)
+// Thread t adds channel t % cout of voxels lane, lane + lanes, ... (lane =
+// t / cout, lanes = 256 / cout; four interleaved sums), so a warp reads
+// consecutive floats; the lanes are then summed in order.
+__global__ void __launch_bounds__(256) bias_grad_kernel(const float *__restrict__ dy,
+                                                        float *__restrict__ partials, long long voxels,
+                                                        int cout, long long chunk)
 {
+    __shared__ float red[256];
+    const int lanes = 256 / cout;
+    const int c = threadIdx.x % cout, lane = threadIdx.x / cout;
     const long long v0 = static_cast<long long>(blockIdx.x) * chunk;
     const long long v1 = v0 + chunk < voxels ? v0 + chunk : voxels;
-    for (int c = threadIdx.x; c < cout; c += blockDim.x) {
-        float s = 0.f;
-        for (long long v = v0; v < v1; ++v) s += dy[v * cout + c];
-        partials[static_cast<long long>(blockIdx.x) * cout + c] = s;
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+    if (lane < lanes) {
+        long long v = v0 + lane;
+        for (; v + 3 * lanes < v1; v += 4 * lanes) {
+            s0 += dy[v * cout + c];
+            s1 += dy[(v + lanes) * cout + c];
+            s2 += dy[(v + 2 * lanes) * cout + c];
+            s3 += dy[(v + 3 * lanes) * cout + c];
+        }
+        for (; v < v1; v += lanes) s0 += dy[v * cout + c];
+    }
+    red[threadIdx.x] = (s0 + s1) + (s2 + s3);
+    __syncthreads();
+    if (threadIdx.x < cout) {
+        float tot = 0.f;
+        for (int l = 0; l < lanes; ++l) tot += red[l * cout + threadIdx.x];
+        partials[static_cast<long long>(blockIdx.x) * cout + threadIdx.x] = tot;
     }
 }
 
@@ -476,6 +861,32 @@ __global__ void act_backward_kernel(const T *__restrict__ yout, float *__restric
     for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < len;
          i += static_cast<long long>(gridDim.x) * blockDim.x)
         if (!(ldf(yout + i) > 0.f)) dy[i] *= kSlope;
+}
+
+// The leaky-ReLU backward (when act) fused with the bfloat16 copy of the
+// resulting gradient: dy[i] *= slope where the output was not positive, then
+// dyn[i] = bfloat16(dy[i]).  Four elements per thread (len % 4 == 0).
+template <typename T>
+__global__ void act_backward_narrow_kernel(const T *__restrict__ yout, float *__restrict__ dy,
+                                           __nv_bfloat16 *__restrict__ dyn, long long len4, int act)
+{
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < len4;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        float4 g = reinterpret_cast<float4 *>(dy)[i];
+        if (act) {
+            const long long e = 4 * i;
+            if (!(ldf(yout + e) > 0.f)) g.x *= kSlope;
+            if (!(ldf(yout + e + 1) > 0.f)) g.y *= kSlope;
+            if (!(ldf(yout + e + 2) > 0.f)) g.z *= kSlope;
+            if (!(ldf(yout + e + 3) > 0.f)) g.w *= kSlope;
+            reinterpret_cast<float4 *>(dy)[i] = g;
+        }
+        __nv_bfloat162 lo = __floats2bfloat162_rn(g.x, g.y), hi = __floats2bfloat162_rn(g.z, g.w);
+        uint2 pk;
+        pk.x = *reinterpret_cast<unsigned *>(&lo);
+        pk.y = *reinterpret_cast<unsigned *>(&hi);
+        reinterpret_cast<uint2 *>(dyn)[i] = pk;
+    }
 }
 
 // wt[tap][ci][co] = w[K^3 - 1 - tap][co][ci] (weights of the transposed
@@ -497,27 +908,77 @@ __global__ void flip_transpose_kernel(const TW *__restrict__ w, TW *__restrict__
 
 // ---------------------------------------------------------------- pooling, upsampling, skips
 
+// Four consecutive channels as one access (c % 4 == 0).
+struct F4 {
+    float v[4];
+};
+template <typename T>
+__device__ __forceinline__ F4 ld4(const T *p);
+template <>
+__device__ __forceinline__ F4 ld4<float>(const float *p)
+{
+    const float4 q = *reinterpret_cast<const float4 *>(p);
+    return F4{{q.x, q.y, q.z, q.w}};
+}
+template <>
+__device__ __forceinline__ F4 ld4<__nv_bfloat16>(const __nv_bfloat16 *p)
+{
+    const uint2 q = *reinterpret_cast<const uint2 *>(p);
+    const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&q.x));
+    const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&q.y));
+    return F4{{a.x, a.y, b.x, b.y}};
+}
+template <typename T>
+__device__ __forceinline__ void st4(T *p, const F4 &f);
+template <>
+__device__ __forceinline__ void st4<float>(float *p, const F4 &f)
+{
+    *reinterpret_cast<float4 *>(p) = make_float4(f.v[0], f.v[1], f.v[2], f.v[3]);
+}
+template <>
+__device__ __forceinline__ void st4<__nv_bfloat16>(__nv_bfloat16 *p, const F4 &f)
+{
+    __nv_bfloat162 a = __floats2bfloat162_rn(f.v[0], f.v[1]), b = __floats2bfloat162_rn(f.v[2], f.v[3]);
+    uint2 q;
+    q.x = *reinterpret_cast<unsigned *>(&a);
+    q.y = *reinterpret_cast<unsigned *>(&b);
+    *reinterpret_cast<uint2 *>(p) = q;
+}
+
+// Element i of a [batch][n][n][n][c] tensor handled as (voxel, group of 4
+// channels): i = voxel * c4 + q.  Voxel coordinates from the flat index.
+__device__ __forceinline__ void voxel_xyz(long long v, int n, int &x, int &y, int &z, long long &b)
+{
+    x = static_cast<int>(v % n);
+    v /= n;
+    y = static_cast<int>(v % n);
+    v /= n;
+    z = static_cast<int>(v % n);
+    b = v / n;
+}
+
+// 2 x 2 x 2 average pooling, n -> n / 2 (channels in groups of 4)
 template <typename T>
 __global__ void avgpool2_kernel(const T *__restrict__ x, T *__restrict__ y, int batch, int n, int c)
 {
-    const int m = n / 2;
-    const long long len = static_cast<long long>(batch) * m * m * m * c;
+    const int m = n / 2, c4 = c / 4;
+    const long long len = static_cast<long long>(batch) * m * m * m * c4;
     for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < len;
          i += static_cast<long long>(gridDim.x) * blockDim.x) {
-        const int ch = static_cast<int>(i % c);
-        long long r = i / c;
-        const int ox = static_cast<int>(r % m);
-        r /= m;
-        const int oy = static_cast<int>(r % m);
-        r /= m;
-        const int oz = static_cast<int>(r % m);
-        const long long b = r / m;
-        float s = 0.f;
+        const int q = static_cast<int>(i % c4);
+        int ox, oy, oz;
+        long long b;
+        voxel_xyz(i / c4, m, ox, oy, oz, b);
+        F4 s{{0.f, 0.f, 0.f, 0.f}};
         for (int k = 0; k < 8; ++k) {
             const int zz = 2 * oz + (k >> 2), yy = 2 * oy + ((k >> 1) & 1), xx = 2 * ox + (k & 1);
-            s += ldf(x + (((b * n + zz) * n + yy) * n + xx) * c + ch);
+            const F4 a = ld4(x + (((b * n + zz) * n + yy) * n + xx) * c + 4 * q);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) s.v[j] += a.v[j];
         }
-        stf(y + i, 0.125f * s);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) s.v[j] *= 0.125f;
+        st4(y + 4 * i, s);
     }
 }
 
@@ -525,19 +986,18 @@ __global__ void avgpool2_kernel(const T *__restrict__ x, T *__restrict__ y, int 
 __global__ void avgpool2_backward_kernel(const float *__restrict__ dy, float *__restrict__ dx,
                                          int batch, int n, int c)
 {
-    const int m = n / 2;
-    const long long len = static_cast<long long>(batch) * n * n * n * c;
+    const int m = n / 2, c4 = c / 4;
+    const long long len = static_cast<long long>(batch) * n * n * n * c4;
     for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < len;
          i += static_cast<long long>(gridDim.x) * blockDim.x) {
-        const int ch = static_cast<int>(i % c);
-        long long r = i / c;
-        const int xx = static_cast<int>(r % n);
-        r /= n;
-        const int yy = static_cast<int>(r % n);
-        r /= n;
-        const int zz = static_cast<int>(r % n);
-        const long long b = r / n;
-        dx[i] = 0.125f * dy[(((b * m + zz / 2) * m + yy / 2) * m + xx / 2) * c + ch];
+        const int q = static_cast<int>(i % c4);
+        int xx, yy, zz;
+        long long b;
+        voxel_xyz(i / c4, n, xx, yy, zz, b);
+        F4 a = ld4(dy + (((b * m + zz / 2) * m + yy / 2) * m + xx / 2) * c + 4 * q);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) a.v[j] *= 0.125f;
+        st4(dx + 4 * i, a);
     }
 }
 
@@ -546,21 +1006,21 @@ template <typename T>
 __global__ void up2_add_kernel(const T *__restrict__ x, const T *__restrict__ skip, T *__restrict__ y,
                                int batch, int n, int c)
 {
-    const int m = 2 * n;
-    const long long len = static_cast<long long>(batch) * m * m * m * c;
+    const int m = 2 * n, c4 = c / 4;
+    const long long len = static_cast<long long>(batch) * m * m * m * c4;
     for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < len;
          i += static_cast<long long>(gridDim.x) * blockDim.x) {
-        const int ch = static_cast<int>(i % c);
-        long long r = i / c;
-        const int xx = static_cast<int>(r % m);
-        r /= m;
-        const int yy = static_cast<int>(r % m);
-        r /= m;
-        const int zz = static_cast<int>(r % m);
-        const long long b = r / m;
-        float v = ldf(x + (((b * n + zz / 2) * n + yy / 2) * n + xx / 2) * c + ch);
-        if (skip) v += ldf(skip + i);
-        stf(y + i, v);
+        const int q = static_cast<int>(i % c4);
+        int xx, yy, zz;
+        long long b;
+        voxel_xyz(i / c4, m, xx, yy, zz, b);
+        F4 v = ld4(x + (((b * n + zz / 2) * n + yy / 2) * n + xx / 2) * c + 4 * q);
+        if (skip) {
+            const F4 sk = ld4(skip + 4 * i);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) v.v[j] += sk.v[j];
+        }
+        st4(y + 4 * i, v);
     }
 }
 
@@ -568,32 +1028,38 @@ __global__ void up2_add_kernel(const T *__restrict__ x, const T *__restrict__ sk
 __global__ void up2_backward_kernel(const float *__restrict__ dy, float *__restrict__ dx, int batch,
                                     int n, int c)
 {
-    const int m = 2 * n;
-    const long long len = static_cast<long long>(batch) * n * n * n * c;
+    const int m = 2 * n, c4 = c / 4;
+    const long long len = static_cast<long long>(batch) * n * n * n * c4;
     for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < len;
          i += static_cast<long long>(gridDim.x) * blockDim.x) {
-        const int ch = static_cast<int>(i % c);
-        long long r = i / c;
-        const int ox = static_cast<int>(r % n);
-        r /= n;
-        const int oy = static_cast<int>(r % n);
-        r /= n;
-        const int oz = static_cast<int>(r % n);
-        const long long b = r / n;
-        float s = 0.f;
+        const int q = static_cast<int>(i % c4);
+        int ox, oy, oz;
+        long long b;
+        voxel_xyz(i / c4, n, ox, oy, oz, b);
+        F4 s{{0.f, 0.f, 0.f, 0.f}};
         for (int k = 0; k < 8; ++k) {
             const int zz = 2 * oz + (k >> 2), yy = 2 * oy + ((k >> 1) & 1), xx = 2 * ox + (k & 1);
-            s += dy[(((b * m + zz) * m + yy) * m + xx) * c + ch];
+            const F4 a = ld4(dy + (((b * m + zz) * m + yy) * m + xx) * c + 4 * q);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) s.v[j] += a.v[j];
         }
-        dx[i] = s;
+        st4(dx + 4 * i, s);
     }
 }
 
-__global__ void add_inplace_kernel(float *__restrict__ a, const float *__restrict__ b, long long len)
+// a += b, four floats per thread (len % 4 == 0)
+__global__ void add_inplace_kernel(float *__restrict__ a, const float *__restrict__ b, long long len4)
 {
-    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < len;
-         i += static_cast<long long>(gridDim.x) * blockDim.x)
-        a[i] += b[i];
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < len4;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        float4 x = reinterpret_cast<float4 *>(a)[i];
+        const float4 y = reinterpret_cast<const float4 *>(b)[i];
+        x.x += y.x;
+        x.y += y.y;
+        x.z += y.z;
+        x.w += y.w;
+        reinterpret_cast<float4 *>(a)[i] = x;
+    }
 }
 
 // ---------------------------------------------------------------- loss, optimiser, features
@@ -668,26 +1134,28 @@ template <typename T>
 __global__ void features_kernel(const double *__restrict__ ra, const int *__restrict__ wall,
                                 T *__restrict__ out, int batch, int n)
 {
+    // the per-sample feature (log10 Ra - 4.5) / 1.5, once per block (FP64 is slow)
+    extern __shared__ float feat_ra[];
+    for (int b = threadIdx.x; b < batch; b += blockDim.x)
+        feat_ra[b] = static_cast<float>((log10(ra[b]) - 4.5) / 1.5);
+    __syncthreads();
     const long long vox = static_cast<long long>(n) * n * n;
     const long long len = batch * vox;
+    const float h = 1.0f / n;
     for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < len;
          i += static_cast<long long>(gridDim.x) * blockDim.x) {
-        const long long b = i / vox;
-        long long r = i % vox;
-        const int xx = static_cast<int>(r % n);
+        const int b = static_cast<int>(i / vox);
+        int r = static_cast<int>(i - b * vox);
+        const int xx = r % n;
         r /= n;
-        const int yy = static_cast<int>(r % n);
-        const int zz = static_cast<int>(r / n);
-        T *o = out + i * kFeatures;
-        const float h = 1.0f / n;
-        stf(o + 0, static_cast<float>((log10(ra[b]) - 4.5) / 1.5));
-        stf(o + 1, wall[b] == 1 ? 1.f : 0.f);
-        stf(o + 2, wall[b] == 2 ? 1.f : 0.f);
-        stf(o + 3, wall[b] == 3 ? 1.f : 0.f);
-        stf(o + 4, 2.f * (xx + 0.5f) * h - 1.f);
-        stf(o + 5, 2.f * (yy + 0.5f) * h - 1.f);
-        stf(o + 6, 2.f * (zz + 0.5f) * h - 1.f);
-        stf(o + 7, 0.5f - (yy + 0.5f) * h);
+        const int yy = r % n;
+        const int zz = r / n;
+        const int wl = wall[b];
+        const F4 lo{{feat_ra[b], wl == 1 ? 1.f : 0.f, wl == 2 ? 1.f : 0.f, wl == 3 ? 1.f : 0.f}};
+        const F4 hi{{2.f * (xx + 0.5f) * h - 1.f, 2.f * (yy + 0.5f) * h - 1.f, 2.f * (zz + 0.5f) * h - 1.f,
+                     0.5f - (yy + 0.5f) * h}};
+        st4(out + i * kFeatures, lo);
+        st4(out + i * kFeatures + 4, hi);
     }
 }
 
@@ -770,6 +1238,22 @@ __global__ void target_kernel(const float *__restrict__ u, const float *__restri
     }
 }
 
+// Elements per block of sum_chunks_kernel and its grid: one thread per
+// element when there are few chunks, else 32 elements (fewer when len is
+// smaller) with the remaining threads as lanes over the chunks.
+int sum_width(long long len, int chunks)
+{
+    if (chunks <= 16) return 256;
+    int e = 1;
+    while (e < 32 && e < len) e *= 2;
+    return e;
+}
+unsigned sum_blocks(long long len, int chunks)
+{
+    const int e = sum_width(len, chunks);
+    return static_cast<unsigned>((len + e - 1) / e);
+}
+
 unsigned flat_blocks(long long len)
 {
     long long b = (len + 255) / 256;
@@ -787,6 +1271,12 @@ cudaError_t conv3d(const TI *x, const TW *w, const float *bias, TO *y, int batch
                    int cout, int k, int act, cudaStream_t s)
 {
     if (n % kTile != 0 || (k != 1 && k != 3)) return cudaErrorInvalidValue;
+    if (k == 1 && cin <= 16 && cout <= 16 && (cin < 8 || cout < 8)) {
+        const long long voxels = static_cast<long long>(batch) * n * n * n;
+        conv1x1_small_kernel<TI, TW, TO, 16, 16><<<flat_blocks(voxels), 256, 0, s>>>(x, w, bias, y, voxels, cin,
+                                                                                  cout, act);
+        return cudaGetLastError();
+    }
     const int tiles = n / kTile;
     dim3 grid(static_cast<unsigned>(tiles) * tiles * n * batch, (cout + kCoTile - 1) / kCoTile);
     if constexpr (std::is_same_v<TI, __nv_bfloat16> && std::is_same_v<TW, __nv_bfloat16>) {
@@ -794,6 +1284,25 @@ cudaError_t conv3d(const TI *x, const TW *w, const float *bias, TO *y, int batch
         // channel count and both base pointers must keep 16-byte alignment
         const bool aligned =
             ((reinterpret_cast<unsigned long long>(x) | reinterpret_cast<unsigned long long>(w)) & 15ull) == 0;
+        if (k == 3 && aligned && (cin == 8 || cin % 16 == 0) && cout % 16 == 0 && n % kWtX == 0 &&
+            n % kWtZ == 0) {
+            const unsigned vtiles = static_cast<unsigned>(batch) * (n / kWtX) * (n / kWtY) * (n / kWtZ);
+            // the dynamic shared memory exceeds the 48 KB default: opt in (per
+            // call, so every device the kernel runs on gets the attribute)
+            cudaError_t e;
+            if (cout % 32 == 0) {
+                const int smem = (kWtHalo + 27 * 32) * kWtRow * 2;
+                e = cudaFuncSetAttribute(conv3d_tc_kernel<4, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+                if (e != cudaSuccess) return e;
+                conv3d_tc_kernel<4, TO><<<dim3(vtiles, cout / 32), 256, smem, s>>>(x, w, bias, y, n, cin, cout, act);
+            } else {
+                const int smem = (kWtHalo + 27 * 16) * kWtRow * 2;
+                e = cudaFuncSetAttribute(conv3d_tc_kernel<2, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+                if (e != cudaSuccess) return e;
+                conv3d_tc_kernel<2, TO><<<dim3(vtiles, cout / 16), 256, smem, s>>>(x, w, bias, y, n, cin, cout, act);
+            }
+            return cudaGetLastError();
+        }
         if (cin % 8 == 0 && aligned) {
             if (k == 3)
                 conv3d_mma_kernel<3, TO><<<grid, 128, 0, s>>>(x, w, bias, y, n, cin, cout, act);
@@ -816,6 +1325,30 @@ cudaError_t conv3d_wgrad_bf16(const __nv_bfloat16 *x, const __nv_bfloat16 *dy, f
     const bool aligned =
         ((reinterpret_cast<unsigned long long>(x) | reinterpret_cast<unsigned long long>(dy)) & 15ull) == 0;
     if (cin % 8 != 0 || cout % 8 != 0 || !aligned || (k != 1 && k != 3)) return cudaErrorInvalidValue;
+    if (k == 3 && cout % 16 == 0 && (cin == 8 || cin % 16 == 0) && n % kWtX == 0 && n % kWtZ == 0) {
+        const int ci_tiles = cin > 8 ? cin / 16 : 1;
+        const long long blocks_per_chunk = static_cast<long long>(cout / 16) * ci_tiles;
+        const long long pairs = static_cast<long long>(cin) * cout;
+        const int tiles_per_sample = (n / kWtX) * (n / kWtY) * (n / kWtZ);
+        const long long total_tiles = static_cast<long long>(batch) * tiles_per_sample;
+        // one wave of 3 resident blocks per SM: fewer chunks keep the final
+        // sum over chunks short
+        long long chunks = (152 * 3 + blocks_per_chunk - 1) / blocks_per_chunk;
+        if (chunks > total_tiles) chunks = total_tiles;
+        while (chunks > 1 && static_cast<size_t>(chunks * 27 * pairs) > scratch_floats) chunks /= 2;
+        if (static_cast<size_t>(chunks * 27 * pairs) > scratch_floats) return cudaErrorInvalidValue;
+        const long long per = (total_tiles + chunks - 1) / chunks;
+        chunks = (total_tiles + per - 1) / per;
+        dim3 grid(static_cast<unsigned>(blocks_per_chunk), static_cast<unsigned>(chunks));
+        wgrad_taps_kernel<<<grid, 256, 0, s>>>(x, dy, scratch, n, cin, cout, tiles_per_sample,
+                                               static_cast<int>(total_tiles), static_cast<int>(per));
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        const long long len = 27 * pairs;
+        sum_chunks_kernel<<<sum_blocks(len, static_cast<int>(chunks)), 256, 0, s>>>(
+        scratch, dw, len, static_cast<int>(chunks), sum_width(len, static_cast<int>(chunks)));
+        return cudaGetLastError();
+    }
     const long long total = static_cast<long long>(batch) * n * n * n;
     const int taps = k * k * k;
     const int cogs = (cout + 63) / 64, cigs = (cin + 31) / 32;
@@ -838,7 +1371,8 @@ cudaError_t conv3d_wgrad_bf16(const __nv_bfloat16 *x, const __nv_bfloat16 *dy, f
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const long long len = taps * pairs;
-    sum_chunks_kernel<<<flat_blocks(len), 256, 0, s>>>(scratch, dw, len, static_cast<int>(chunks));
+    sum_chunks_kernel<<<sum_blocks(len, static_cast<int>(chunks)), 256, 0, s>>>(
+        scratch, dw, len, static_cast<int>(chunks), sum_width(len, static_cast<int>(chunks)));
     return cudaGetLastError();
 }
 
@@ -847,8 +1381,27 @@ cudaError_t conv3d_wgrad(const TI *x, const float *dy, float *dw, float *scratch
                          size_t scratch_floats, int batch, int n, int cin, int cout, int k,
                          cudaStream_t s)
 {
-    if (cin > 128 || cout > 128 || 256 % cin != 0) return cudaErrorInvalidValue;
     const long long total = static_cast<long long>(batch) * n * n * n;
+    if (k == 1 && cout <= 8 && cin <= 16) {
+        long long blocks = 152 * 4;
+        if (blocks > total) blocks = total;
+        const long long pairs = static_cast<long long>(cin) * cout;
+        while (blocks > 1 && static_cast<size_t>(blocks * pairs) > scratch_floats) blocks /= 2;
+        const long long chunk = (total + blocks - 1) / blocks;
+        blocks = (total + chunk - 1) / chunk;
+        if (cout <= 5)
+            wgrad_small_kernel<TI, 5, 16><<<static_cast<unsigned>(blocks), 256, 0, s>>>(x, dy, scratch, total, cin,
+                                                                                        cout, chunk);
+        else
+            wgrad_small_kernel<TI, 8, 16><<<static_cast<unsigned>(blocks), 256, 0, s>>>(x, dy, scratch, total, cin,
+                                                                                        cout, chunk);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        sum_chunks_kernel<<<sum_blocks(pairs, static_cast<int>(blocks)), 256, 0, s>>>(
+        scratch, dw, pairs, static_cast<int>(blocks), sum_width(pairs, static_cast<int>(blocks)));
+        return cudaGetLastError();
+    }
+    if (cin > 128 || cout > 128 || 256 % cin != 0) return cudaErrorInvalidValue;
     const int taps = k * k * k;
     const long long pairs = static_cast<long long>(cin) * cout;
     // chunks of voxels: enough blocks to fill the GPU, bounded by the scratch
@@ -866,22 +1419,36 @@ cudaError_t conv3d_wgrad(const TI *x, const float *dy, float *dw, float *scratch
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const long long len = taps * pairs;
-    sum_chunks_kernel<<<flat_blocks(len), 256, 0, s>>>(scratch, dw, len, static_cast<int>(chunks));
+    sum_chunks_kernel<<<sum_blocks(len, static_cast<int>(chunks)), 256, 0, s>>>(
+        scratch, dw, len, static_cast<int>(chunks), sum_width(len, static_cast<int>(chunks)));
     return cudaGetLastError();
 }
 
 cudaError_t bias_grad(const float *dy, float *db, float *scratch, size_t scratch_floats,
                       long long voxels, int cout, cudaStream_t s)
 {
-    long long blocks = 152 * 4;
+    if (cout < 1 || cout > 256) return cudaErrorInvalidValue;
+    long long blocks = 152 * 2;
     if (blocks > voxels) blocks = voxels;
     while (blocks > 1 && static_cast<size_t>(blocks * cout) > scratch_floats) blocks /= 2;
-    const int chunk = static_cast<int>((voxels + blocks - 1) / blocks);
+    const long long chunk = (voxels + blocks - 1) / blocks;
     blocks = (voxels + chunk - 1) / chunk;
-    bias_grad_kernel<<<static_cast<unsigned>(blocks), 128, 0, s>>>(dy, scratch, voxels, cout, chunk);
+    bias_grad_kernel<<<static_cast<unsigned>(blocks), 256, 0, s>>>(dy, scratch, voxels, cout, chunk);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    sum_chunks_kernel<<<flat_blocks(cout), 256, 0, s>>>(scratch, db, cout, static_cast<int>(blocks));
+    sum_chunks_kernel<<<sum_blocks(cout, static_cast<int>(blocks)), 256, 0, s>>>(
+        scratch, db, cout, static_cast<int>(blocks), sum_width(cout, static_cast<int>(blocks)));
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t act_backward_narrow(const T *yout, float *dy, __nv_bfloat16 *dyn, long long len, int act,
+                                cudaStream_t s)
+{
+    const bool aligned =
+        ((reinterpret_cast<unsigned long long>(dy) & 15ull) | (reinterpret_cast<unsigned long long>(dyn) & 7ull)) == 0;
+    if (len % 4 != 0 || !aligned) return cudaErrorInvalidValue;
+    act_backward_narrow_kernel<T><<<flat_blocks(len / 4), 256, 0, s>>>(yout, dy, dyn, len / 4, act);
     return cudaGetLastError();
 }
 
@@ -904,14 +1471,16 @@ cudaError_t flip_transpose(const TW *w, TW *wt, int k, int cout, int cin, cudaSt
 template <typename T>
 cudaError_t avgpool2(const T *x, T *y, int batch, int n, int c, cudaStream_t s)
 {
-    const long long len = static_cast<long long>(batch) * (n / 2) * (n / 2) * (n / 2) * c;
+    if (c % 4 != 0) return cudaErrorInvalidValue;
+    const long long len = static_cast<long long>(batch) * (n / 2) * (n / 2) * (n / 2) * (c / 4);
     avgpool2_kernel<T><<<flat_blocks(len), 256, 0, s>>>(x, y, batch, n, c);
     return cudaGetLastError();
 }
 
 cudaError_t avgpool2_backward(const float *dy, float *dx, int batch, int n, int c, cudaStream_t s)
 {
-    const long long len = static_cast<long long>(batch) * n * n * n * c;
+    if (c % 4 != 0) return cudaErrorInvalidValue;
+    const long long len = static_cast<long long>(batch) * n * n * n * (c / 4);
     avgpool2_backward_kernel<<<flat_blocks(len), 256, 0, s>>>(dy, dx, batch, n, c);
     return cudaGetLastError();
 }
@@ -919,21 +1488,24 @@ cudaError_t avgpool2_backward(const float *dy, float *dx, int batch, int n, int 
 template <typename T>
 cudaError_t up2_add(const T *x, const T *skip, T *y, int batch, int n, int c, cudaStream_t s)
 {
-    const long long len = static_cast<long long>(batch) * 8LL * n * n * n * c;
+    if (c % 4 != 0) return cudaErrorInvalidValue;
+    const long long len = static_cast<long long>(batch) * 8LL * n * n * n * (c / 4);
     up2_add_kernel<T><<<flat_blocks(len), 256, 0, s>>>(x, skip, y, batch, n, c);
     return cudaGetLastError();
 }
 
 cudaError_t up2_backward(const float *dy, float *dx, int batch, int n, int c, cudaStream_t s)
 {
-    const long long len = static_cast<long long>(batch) * n * n * n * c;
+    if (c % 4 != 0) return cudaErrorInvalidValue;
+    const long long len = static_cast<long long>(batch) * n * n * n * (c / 4);
     up2_backward_kernel<<<flat_blocks(len), 256, 0, s>>>(dy, dx, batch, n, c);
     return cudaGetLastError();
 }
 
 cudaError_t add_inplace(float *a, const float *b, long long len, cudaStream_t s)
 {
-    add_inplace_kernel<<<flat_blocks(len), 256, 0, s>>>(a, b, len);
+    if (len % 4 != 0) return cudaErrorInvalidValue;
+    add_inplace_kernel<<<flat_blocks(len / 4), 256, 0, s>>>(a, b, len / 4);
     return cudaGetLastError();
 }
 
@@ -970,7 +1542,9 @@ cudaError_t copy_to_store(const float *master, TW *wstore, long long len, cudaSt
 template <typename T>
 cudaError_t features(const double *ra, const int *wall, T *out, int batch, int n, cudaStream_t s)
 {
-    features_kernel<T><<<flat_blocks(static_cast<long long>(batch) * n * n * n), 256, 0, s>>>(
+    const size_t smem = static_cast<size_t>(batch) * sizeof(float);
+    if (smem > 48 * 1024) return cudaErrorInvalidValue;
+    features_kernel<T><<<flat_blocks(static_cast<long long>(batch) * n * n * n), 256, smem, s>>>(
         ra, wall, out, batch, n);
     return cudaGetLastError();
 }
@@ -1022,6 +1596,8 @@ cudaError_t target_from_fields(const float *u, const float *theta, const float *
     template cudaError_t conv3d_wgrad<T>(const T *, const float *, float *, float *, size_t, int, \
                                          int, int, int, int, cudaStream_t);                     \
     template cudaError_t act_backward<T>(const T *, float *, long long, cudaStream_t);          \
+    template cudaError_t act_backward_narrow<T>(const T *, float *, __nv_bfloat16 *, long long, int, \
+                                                cudaStream_t);                                  \
     template cudaError_t flip_transpose<T>(const T *, T *, int, int, int, cudaStream_t);        \
     template cudaError_t avgpool2<T>(const T *, T *, int, int, int, cudaStream_t);              \
     template cudaError_t up2_add<T>(const T *, const T *, T *, int, int, int, cudaStream_t);    \

@@ -38,6 +38,12 @@ cudaError_t bias_grad(const float *dy, float *db, float *scratch, size_t scratch
 template <typename T>
 cudaError_t act_backward(const T *yout, float *dy, long long len, cudaStream_t s);
 
+// act_backward (if act) and then dyn = bfloat16(dy), in one pass; len % 4 == 0,
+// dy 16-byte and dyn 8-byte aligned.
+template <typename T>
+cudaError_t act_backward_narrow(const T *yout, float *dy, __nv_bfloat16 *dyn, long long len, int act,
+                                cudaStream_t s);
+
 // weights of the transposed convolution (input gradient = conv3d with them)
 template <typename TW>
 cudaError_t flip_transpose(const TW *w, TW *wt, int k, int cout, int cin, cudaStream_t s);

@@ -226,13 +226,24 @@ dmrt_status conv_bwd(dmrt_surrogate_t *s, const Layer &L, const void *in, const 
 {
     const int e = edge(s, L.level);
     const long long vox = static_cast<long long>(batch) * e * e * e;
-    if (L.act)
-        SCK(s, lbm::nn::act_backward<T>(static_cast<const T *>(outv), gin, vox * L.cout, s->stream),
-            "act_backward");
     bool wgrad_done = false;
+    bool act_done = false;
     if constexpr (std::is_same_v<T, __nv_bfloat16>) {
         // bf16 storage: the output gradient in bf16 feeds the tensor cores
-        SCK(s, lbm::nn::narrow(gin, s->gnarrow, vox * L.cout, s->stream), "narrow");
+        // (the activation backward and the narrowing in one pass when the
+        // length allows; otherwise one after the other)
+        if ((vox * L.cout) % 4 == 0 &&
+            lbm::nn::act_backward_narrow<T>(static_cast<const T *>(outv), gin, s->gnarrow, vox * L.cout, L.act,
+                                            s->stream) == cudaSuccess) {
+            act_done = true;
+        } else {
+            cudaGetLastError();
+            if (L.act)
+                SCK(s, lbm::nn::act_backward<T>(static_cast<const T *>(outv), gin, vox * L.cout, s->stream),
+                    "act_backward");
+            act_done = true;
+            SCK(s, lbm::nn::narrow(gin, s->gnarrow, vox * L.cout, s->stream), "narrow");
+        }
         if (L.cin % 8 == 0 && L.cout % 8 == 0) {
             SCK(s,
                 lbm::nn::conv3d_wgrad_bf16(static_cast<const __nv_bfloat16 *>(in), s->gnarrow, s->grad + L.w_off,
@@ -241,6 +252,9 @@ dmrt_status conv_bwd(dmrt_surrogate_t *s, const Layer &L, const void *in, const 
             wgrad_done = true;
         }
     }
+    if (L.act && !act_done)
+        SCK(s, lbm::nn::act_backward<T>(static_cast<const T *>(outv), gin, vox * L.cout, s->stream),
+            "act_backward");
     if (!wgrad_done)
         SCK(s,
             lbm::nn::conv3d_wgrad<T>(static_cast<const T *>(in), gin, s->grad + L.w_off, s->scratch,
@@ -362,7 +376,7 @@ dmrt_status dmrt_surrogate_create(dmrt_surrogate_t **out, const dmrt_surrogate_c
     if (cfg->storage != DMRT_STORE_F32 && cfg->storage != DMRT_STORE_BF16) return DMRT_ERR_ARG;
     for (int l = 0; l <= cfg->depth; ++l) {
         const int c = cfg->channels[l];
-        if (c < 1 || c > 128 || 256 % c != 0) return DMRT_ERR_ARG;
+        if (c < 4 || c > 128 || 256 % c != 0) return DMRT_ERR_ARG;  // 4, 8, 16, 32, 64 or 128
     }
     dmrt_surrogate_t *s = new (std::nothrow) dmrt_surrogate();
     if (!s) return DMRT_ERR_OOM;

@@ -141,3 +141,28 @@ def test_surrogate_rejects_bad_configurations(env):
     for grid, depth, ch in ((20, 1, (8, 16)), (16, 2, (8, 16, 32)), (16, 1, (12, 16))):
         with pytest.raises(dm.DmrtError):
             dm.Surrogate(grid, depth, ch)
+
+
+@pytest.mark.parametrize("channels", [(16, 32), (8, 16)])
+def test_bf16_gradients_per_layer(env, channels):
+    """The bf16 path (tensor-core convolutions, weight gradients over all 27
+    taps per block) against the FP64 oracle evaluated at the bf16-rounded
+    parameters, layer by layer: the gradients may differ only by the bf16
+    rounding of activations and output gradients."""
+    torch, dm = env
+    n = 16
+    sur = dm.Surrogate(n, 1, channels, storage=dm.STORE_BF16, max_batch=2)
+    net = S.UNet(n, 1, channels)
+    p = inputs.random_weights(net.count, seed=31, scale=0.3)
+    sur.set_params(p)
+    pb = torch.from_numpy(p).to(torch.bfloat16).float().numpy().astype(np.float64)
+    ra, wall = [4e3, 6e5], [3, 2]
+    t = inputs.random_targets((2, n, n, n, 5), seed=32)
+    g_gpu, _ = sur.gradients(ra, wall, torch.from_numpy(t.reshape(2, -1, 5)).cuda())
+    _, g_ref = net.loss_and_grad(pb, S.features(ra, wall, n), t.astype(np.float64))
+    for (wo, bo), (cin, cout, k, _) in zip(net.offsets, net.layers):
+        seg = slice(wo, bo)  # weights
+        a, b = g_gpu[seg], g_ref[seg]
+        cos = float(np.dot(a, b) / (np.linalg.norm(a) * np.linalg.norm(b)))
+        rel = np.linalg.norm(a - b) / np.linalg.norm(b)
+        assert cos >= 0.995 and rel <= 5e-2, (cin, cout, k, cos, rel)
