@@ -16,6 +16,7 @@ Orchestration only: every arithmetic step runs in the library's kernels;
 torch provides device memory.
 
     python -m paper_1511_04633_gb300.surrogate --grid 32 --train 48 --epochs 30
+    python -m paper_1511_04633_gb300.surrogate --time-steps 3     # time the training step
 """
 
 from __future__ import annotations
@@ -173,6 +174,36 @@ def compare_warm_start(sur, grid, Ra, wall, tol=1e-7, nu_rtol=1e-3, max_steps=2_
     }
 
 
+def time_steps(args):
+    """Wall time of training steps and predictions of the configured network
+    on zero targets (one warm-up step first)."""
+    import torch
+
+    ch = tuple(int(c) for c in args.channels.split(","))
+    sur = dmrt.Surrogate(args.grid, args.depth, ch,
+                         dmrt.STORE_BF16 if args.storage == "bf16" else dmrt.STORE_F32,
+                         max_batch=args.batch, seed=args.seed)
+    t = torch.zeros((args.batch, args.grid ** 3, 5), device="cuda")
+    ra = [10.0 ** (3 + 3 * k / max(args.batch - 1, 1)) for k in range(args.batch)]
+    wall = [1 + k % 3 for k in range(args.batch)]
+    sur.train_step(ra, wall, t, 1e-4)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.time_steps):
+        sur.train_step(ra, wall, t, 1e-4)
+    torch.cuda.synchronize()
+    step = (time.perf_counter() - t0) / args.time_steps
+    t0 = time.perf_counter()
+    for _ in range(args.time_steps):
+        sur.predict(ra[:1], wall[:1])
+    torch.cuda.synchronize()
+    pred = (time.perf_counter() - t0) / args.time_steps
+    res = {"train_step_ms": step * 1e3, "predict_ms": pred * 1e3, "params": sur.param_count,
+           "grid": args.grid, "batch": args.batch}
+    print(json.dumps(res), flush=True)
+    return res
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description="train the warm-start surrogate and measure its gain")
     ap.add_argument("--grid", type=int, default=64, help="network (and training cavity) grid")
@@ -190,8 +221,13 @@ def main(argv=None):
     ap.add_argument("--max-steps", type=int, default=200_000)
     ap.add_argument("--seed", type=int, default=2024)
     ap.add_argument("--out", type=str, default="")
+    ap.add_argument("--time-steps", type=int, default=0,
+                    help="only time this many training steps (zero targets) and predictions")
     args = ap.parse_args(argv)
     import torch
+
+    if args.time_steps > 0:
+        return time_steps(args)
 
     lo, hi = (float(v) for v in args.ra.split(","))
     draws = inputs.ensemble_draws(args.train + args.test, seed=args.seed, edges=(args.grid,),
