@@ -109,6 +109,35 @@ def test_config4_ensemble_draws_build_and_step(dm):
     assert min(taus) > 0.5
 
 
+@pytest.mark.parametrize("streaming", [0, 1], ids=["ab", "inplace"])
+def test_config4_full_ensemble_step_matches_the_oracle(dm, streaming):
+    """The 64-member ensemble in the benchmark's launch configuration
+    (autotuned): after 150 steps from rest, one more step of sampled members
+    (the largest, a Type 3 and the highest Ra) must match the oracle's step
+    from the same state."""
+    draws = inputs.ensemble_draws(64, seed=1234)
+    cav = [{"grid": (d["n"],) * 3, "Ra": d["Ra"], "wall": d["wall"]} for d in draws]
+    ens = dm.Ensemble(cav, streaming=streaming)
+    ens.autotune(trials=2)
+    ens.step(150)
+    picks = {max(range(64), key=lambda k: cav[k]["grid"][0]),
+             next(k for k in range(64) if cav[k]["wall"] == 3),
+             max(range(64), key=lambda k: cav[k]["Ra"])}
+    orcs = {}
+    for k in picks:
+        f, g = ens.populations(k)
+        o = oracle.Oracle.physical(cav[k]["grid"], cav[k]["wall"], cav[k]["Ra"])
+        o.set_populations(f.astype(np.float64), g.astype(np.float64))
+        o.step(1)
+        orcs[k] = o
+    ens.step(1)
+    for k, o in orcs.items():
+        fe, ge = ens.populations(k)
+        fo, go = o.populations()
+        assert np.abs(fe - fo).max() <= 1e-6, k
+        assert np.abs(ge - go).max() <= 1e-6, k
+
+
 def test_ensemble_rejects_periodic_members_and_bad_indices(dm):
     with pytest.raises(dm.DmrtError) as ei:
         dm.Ensemble([{"grid": (8, 8, 8), "Ra": 1e4, "wall": 0}])

@@ -182,3 +182,15 @@ def test_full_size_128cube_in_place_matches_two_buffers(dm):
     fi, gi = ip.populations()
     assert np.array_equal(fa, fi) and np.array_equal(ga, gi)
     assert ab.nusselt(0) == ip.nusselt(0)
+
+
+def test_full_size_256cube_in_place_matches_two_buffers(dm):
+    """The 256^3 Type 3 Ra = 1e6 workload: in place and with two buffers,
+    bitwise the same after an odd number of steps."""
+    grid = (256, 256, 256)
+    ab, ip = _twins(dm, grid, 3, Ra=1e6)
+    for h in (ab, ip):
+        h.step(21)
+    for x, y in zip(ab.fields(), ip.fields()):
+        assert np.array_equal(x, y)
+    assert ab.nusselt(0) == ip.nusselt(0)

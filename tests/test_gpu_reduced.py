@@ -200,3 +200,29 @@ def test_round_to_nearest_storage(dm, storage):
     else:
         ref = ((v * np.float32(1024.0)).astype(np.float16).astype(np.float32) / np.float32(1024.0))
     assert np.array_equal(y, ref)
+
+
+@pytest.mark.parametrize("storage", [1, 2], ids=["bf16", "f16"])
+def test_config3_full_size_one_step_matches_the_oracle(dm, storage):
+    """The reduced-precision workload at full size (256^3, Type 3, Ra = 1e6)
+    in the launch shape the benchmark times: after 100 GPU steps from rest,
+    one more GPU step must equal the oracle's step from the same stored state
+    up to the rounding of one 16-bit store (below one unit in the last place
+    of the stored value) plus FP32 round-off."""
+    grid = (256, 256, 256)
+    gpu = dm.Cavity(grid, 1e6, wall_type=3, storage=storage)
+    gpu.step(100)
+    f, g = gpu.populations()
+    orc = oracle.Oracle.physical(grid, 3, 1e6)
+    orc.set_populations(f.astype(np.float64), g.astype(np.float64))
+    del f, g
+    gpu.step(1)
+    orc.step(1)
+    rel = 2.0 ** -7 if storage == 1 else 2.0 ** -10
+    w = oracle.weights19()[:, None, None, None]
+    fg, gg = gpu.populations()
+    fo, go = orc.populations()
+    # deviations from the rest equilibrium are what the 16-bit store holds
+    dg, do = fg.astype(np.float64) - w, fo - w
+    assert np.all(np.abs(dg - do) <= rel * np.abs(do) + 1e-6)
+    assert np.all(np.abs(gg.astype(np.float64) - go) <= rel * np.abs(go) + 1e-6)
