@@ -456,6 +456,22 @@ def test_mirror_symmetry_in_x(orc, wall):
         np.testing.assert_allclose(a, flip(a), atol=1e-13)
 
 
+def test_hot_fluid_rises_along_the_hot_wall(orc):
+    """Buoyancy along +z for theta > theta_ref (Eqs. (15), (16)) and the hot
+    wall at y = 0 (Eq. (6)): the flow climbs along the hot wall and sinks
+    along the cold one, and convection raises Nu above the conduction value
+    of 1 (Sec. 4: Nu > 1 for every Ra of Tables 1-8)."""
+    o = orc.Oracle.physical((12, 12, 12), 1, 2e4)
+    o.step(2500)
+    _, u, T = o.fields()
+    w_hot = u[2][:, 0, :].mean()      # first fluid layer at the hot wall
+    w_cold = u[2][:, -1, :].mean()    # ... at the cold wall
+    assert w_hot > 0 > w_cold
+    assert T[:, 0, :].mean() > 0 > T[:, -1, :].mean()
+    (nu3, _, _), _ = o.nusselt(0)
+    assert nu3 > 1.05
+
+
 # ------------------------------------------------------------------ Nusselt, residual
 
 def test_nusselt_is_exact_for_quadratic_profiles(orc):
