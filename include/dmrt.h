@@ -430,6 +430,12 @@ const char *dmrt_surrogate_last_error(const dmrt_surrogate_t *s);
 dmrt_status dmrt_nn_conv3d(const void *x, const void *w, const float *bias, void *y, int batch, int n,
                            int cin, int cout, int k, int act, int storage, int out_f32, void *stream);
 
+/* Diagnostic of the tensor-core convolutions: the number of launches whose
+ * bounded wait for the tensor cores ran out (their output was not written;
+ * it stays 0 in a healthy run).  reset != 0 clears the count.  -1 on a CUDA
+ * error.  Synchronises the device. */
+int dmrt_nn_tensor_core_errors(int reset);
+
 /* Round n float32 values to a population storage format and back, exactly
  * as the step kernel stores populations: in and out are device arrays of n
  * floats (may alias); storage is a dmrt_storage, rounding a dmrt_rounding

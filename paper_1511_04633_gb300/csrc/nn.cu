@@ -12,10 +12,12 @@
 // training is bitwise repeatable.
 #include <cuda_bf16.h>
 
+#include <cstdlib>
 #include <type_traits>
 
 #include "internal.h"
 #include "nn.h"
+#include "umma.cuh"
 
 namespace lbm {
 namespace nn {
@@ -712,6 +714,141 @@ __global__ void __launch_bounds__(256) conv1x1_small_kernel(const TI *__restrict
     }
 }
 
+// 3^3 convolution on the 5th-generation tensor cores (tcgen05.mma with the
+// accumulator in tensor memory).  A CTA of 4 warps owns a tile of 8 x 16
+// voxels of one z-plane (M = 128 GEMM rows) and CO output channels (N).  Per
+// 16 input channels it stages the x halo (10 x 18 x 3 voxels) and the
+// weights of all 27 taps in the canonical K-major core-matrix layout (8 rows
+// x 16 bytes per core matrix):
+//   halo   [kg 2][z 3][y 18][x 10] x 16 B: the 8 rows of a core matrix are 8
+//          consecutive x voxels, so tap (dz, dy, dx) is the same descriptor
+//          shifted by ((dz * 18 + dy) * 10 + dx) * 16 bytes; SBO (next 8 rows
+//          = next y row) = 160 B, LBO (next 8 channels) = 540 * 16 B;
+//   weights [tap 27][kg 2][co CO] x 16 B: SBO (next 8 channels out) = 128 B,
+//          LBO (next 8 channels in) = CO * 16 B.
+// One thread issues the 27 MMAs (K = 16 each) and commits them to an
+// mbarrier; everyone waits (bounded) before the buffers are restaged.  The
+// epilogue reads each thread's accumulator row (TMEM lane = voxel) with
+// tcgen05.ld and writes bias + activation.  A wait that runs out sets *err.
+constexpr int kUmX = 8, kUmY = 16;
+constexpr int kUmHX = kUmX + 2, kUmHY = kUmY + 2, kUmHZ = 3;
+constexpr int kUmHalo = kUmHX * kUmHY * kUmHZ;                // 540 voxels
+constexpr unsigned kUmHaloOff = 128;                         // after the barrier and TMEM slot
+constexpr unsigned kUmHaloBytes = 2u * kUmHalo * 16u;        // 17280
+template <int CO>
+constexpr unsigned um_smem_bytes()
+{
+    return kUmHaloOff + kUmHaloBytes + 27u * 2u * CO * 16u;
+}
+constexpr unsigned kUmWaitPolls = 1u << 22;  // ~0.3 s of polling before giving up
+// TMEM columns a CTA allocates (the accumulator needs CO, at least 32);
+// DMRT_UMMA_TMEM_COLS raises it (a power of two up to 512).
+#ifndef DMRT_UMMA_TMEM_COLS
+#define DMRT_UMMA_TMEM_COLS 0
+#endif
+
+template <int CO, typename TO>
+__global__ void __launch_bounds__(128, 1) conv3d_umma_kernel(const __nv_bfloat16 *__restrict__ x,
+                                                             const __nv_bfloat16 *__restrict__ w,
+                                                             const float *__restrict__ bias,
+                                                             TO *__restrict__ y, int n, int cin, int cout,
+                                                             int act, int *err)
+{
+    extern __shared__ __align__(1024) unsigned char um_smem[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(um_smem);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(um_smem + 8);
+    unsigned char *halo = um_smem + kUmHaloOff;
+    unsigned char *wsm = halo + kUmHaloBytes;
+    constexpr uint32_t kCols = DMRT_UMMA_TMEM_COLS > (CO < 32 ? 32 : CO) ? DMRT_UMMA_TMEM_COLS : (CO < 32 ? 32 : CO);
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int tx_n = n / kUmX, ty_n = n / kUmY;
+    int r = blockIdx.x;
+    const int x0 = (r % tx_n) * kUmX;
+    r /= tx_n;
+    const int y0 = (r % ty_n) * kUmY;
+    r /= ty_n;
+    const int z = r % n;
+    const int b = r / n;
+    const int co0 = blockIdx.y * CO;
+    const long long sample = static_cast<long long>(b) * n * n * n;
+    if (t == 0) umma::mbar_init(bar, 1);
+    if (warp == 0) umma::tmem_alloc(tslot, kCols);
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+    const uint32_t tmem = *tslot;
+    constexpr uint32_t idesc = umma::idesc_bf16_f32(128, CO);
+    const uint32_t halo_s = umma::smem_u32(halo), w_s = umma::smem_u32(wsm);
+    const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
+    bool ok = true;
+    uint32_t phase = 0;
+    for (int ci0 = 0; ci0 < cin && ok; ci0 += 16) {
+        for (int e = t; e < kUmHalo * 2; e += 128) {
+            const int kg = e / kUmHalo, h = e % kUmHalo;
+            const int hx = h % kUmHX, hy = (h / kUmHX) % kUmHY, hz = h / (kUmHX * kUmHY);
+            const int gx = x0 + hx - 1, gy = y0 + hy - 1, gz = z + hz - 1;
+            const int c = ci0 + 8 * kg;
+            uint4 v = zero4;
+            if (gx >= 0 && gx < n && gy >= 0 && gy < n && gz >= 0 && gz < n && c < cin)
+                v = *reinterpret_cast<const uint4 *>(
+                    x + (sample + (static_cast<long long>(gz) * n + gy) * n + gx) * cin + c);
+            *reinterpret_cast<uint4 *>(halo + (kg * kUmHalo + h) * 16) = v;
+        }
+        for (int e = t; e < 27 * 2 * CO; e += 128) {
+            const int co = e % CO, kg = (e / CO) % 2, tap = e / (2 * CO);
+            const int c = ci0 + 8 * kg;
+            uint4 v = zero4;
+            if (co0 + co < cout && c < cin)
+                v = *reinterpret_cast<const uint4 *>(w + (static_cast<long long>(tap) * cout + co0 + co) * cin + c);
+            *reinterpret_cast<uint4 *>(wsm + ((tap * 2 + kg) * CO + co) * 16) = v;
+        }
+        umma::fence_proxy_async_smem();
+        umma::fence_before_sync();
+        __syncthreads();
+        if (t == 0) {
+            umma::fence_after_sync();
+            for (int tap = 0; tap < 27; ++tap) {
+                const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
+                const uint64_t ad = umma::smem_desc(halo_s + ((dz * kUmHY + dy) * kUmHX + dx) * 16,
+                                                    kUmHalo * 16, kUmHX * 16);
+                const uint64_t bd = umma::smem_desc(w_s + tap * 2 * CO * 16, CO * 16, 128);
+                umma::mma_bf16(tmem, ad, bd, idesc, (ci0 > 0 || tap > 0) ? 1u : 0u);
+            }
+            umma::commit(bar);
+        }
+        // the MMAs read the staged tiles: wait for them before restaging
+        if (!umma::mbar_wait(bar, phase, kUmWaitPolls)) ok = false;
+        phase ^= 1u;
+        umma::fence_after_sync();
+        __syncthreads();
+    }
+    if (ok) {
+        const int m = 32 * warp + lane;  // TMEM lane = GEMM row = voxel (x fastest)
+        const long long vox = sample + (static_cast<long long>(z) * n + y0 + m / kUmX) * n + x0 + m % kUmX;
+        TO *yo = y + vox * cout + co0;
+#pragma unroll
+        for (int c16 = 0; c16 < CO; c16 += 16) {
+            float v[16];
+            umma::ld_32x32b_x16(tmem + (static_cast<uint32_t>(32 * warp) << 16) + c16, v);
+#pragma unroll
+            for (int j = 0; j < 16; j += 2) {
+                const int co = co0 + c16 + j;
+                float a = v[j] + (bias ? bias[co] : 0.f), bb = v[j + 1] + (bias ? bias[co + 1] : 0.f);
+                if (act) {
+                    a = a > 0.f ? a : kSlope * a;
+                    bb = bb > 0.f ? bb : kSlope * bb;
+                }
+                st2(yo + c16 + j, a, bb);
+            }
+        }
+    } else if (t == 0) {
+        atomicExch(err, 1);
+    }
+    umma::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) umma::tmem_dealloc(tmem, kCols);
+}
+
 // out = bfloat16(in)
 __global__ void narrow_kernel(const float *__restrict__ in, __nv_bfloat16 *__restrict__ out, long long len)
 {
@@ -1238,6 +1375,36 @@ __global__ void target_kernel(const float *__restrict__ u, const float *__restri
     }
 }
 
+// Device word counting tcgen05 waits that ran out (see conv3d_umma_kernel).
+__device__ int g_umma_err;
+
+int *umma_error_word()
+{
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_umma_err) != cudaSuccess) return nullptr;
+    return static_cast<int *>(p);
+}
+
+// The tcgen05 convolution is used unless DMRT_NN_NO_TCGEN05 is set in the
+// environment (read once).
+bool umma_enabled()
+{
+    static const bool on = std::getenv("DMRT_NN_NO_TCGEN05") == nullptr;
+    return on;
+}
+
+// Dynamic shared memory of conv3d_umma_kernel<CO>.  DMRT_UMMA_SMEM (bytes)
+// overrides it with a larger allocation.
+#ifndef DMRT_UMMA_SMEM
+#define DMRT_UMMA_SMEM 0
+#endif
+template <int CO>
+unsigned umma_smem()
+{
+    const unsigned need = um_smem_bytes<CO>();
+    return DMRT_UMMA_SMEM > need ? DMRT_UMMA_SMEM : need;
+}
+
 // Elements per block of sum_chunks_kernel and its grid: one thread per
 // element when there are few chunks, else 32 elements (fewer when len is
 // smaller) with the remaining threads as lanes over the chunks.
@@ -1266,6 +1433,16 @@ unsigned flat_blocks(long long len)
 
 // ---------------------------------------------------------------- launchers
 
+int tensor_core_errors(bool reset)
+{
+    int *p = umma_error_word();
+    if (!p) return -1;
+    int v = 0;
+    if (cudaMemcpy(&v, p, sizeof v, cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
+    if (reset && cudaMemset(p, 0, sizeof v) != cudaSuccess) return -1;
+    return v;
+}
+
 template <typename TI, typename TW, typename TO>
 cudaError_t conv3d(const TI *x, const TW *w, const float *bias, TO *y, int batch, int n, int cin,
                    int cout, int k, int act, cudaStream_t s)
@@ -1284,6 +1461,33 @@ cudaError_t conv3d(const TI *x, const TW *w, const float *bias, TO *y, int batch
         // channel count and both base pointers must keep 16-byte alignment
         const bool aligned =
             ((reinterpret_cast<unsigned long long>(x) | reinterpret_cast<unsigned long long>(w)) & 15ull) == 0;
+        if (k == 3 && aligned && (cin == 8 || cin % 16 == 0) && cout % 16 == 0 && n % kUmY == 0 &&
+            umma_enabled()) {
+            const unsigned tiles = static_cast<unsigned>(batch) * (n / kUmX) * (n / kUmY) * n;
+            int *err = umma_error_word();
+            if (!err) return cudaErrorInvalidValue;
+            cudaError_t e;
+            if (cout % 64 == 0) {
+                const unsigned smem = umma_smem<64>();
+                e = cudaFuncSetAttribute(conv3d_umma_kernel<64, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+                if (e != cudaSuccess) return e;
+                conv3d_umma_kernel<64, TO><<<dim3(tiles, cout / 64), 128, smem, s>>>(x, w, bias, y, n, cin, cout, act,
+                                                                                   err);
+            } else if (cout % 32 == 0) {
+                const unsigned smem = umma_smem<32>();
+                e = cudaFuncSetAttribute(conv3d_umma_kernel<32, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+                if (e != cudaSuccess) return e;
+                conv3d_umma_kernel<32, TO><<<dim3(tiles, cout / 32), 128, smem, s>>>(x, w, bias, y, n, cin, cout, act,
+                                                                                   err);
+            } else {
+                const unsigned smem = umma_smem<16>();
+                e = cudaFuncSetAttribute(conv3d_umma_kernel<16, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+                if (e != cudaSuccess) return e;
+                conv3d_umma_kernel<16, TO><<<dim3(tiles, cout / 16), 128, smem, s>>>(x, w, bias, y, n, cin, cout, act,
+                                                                                   err);
+            }
+            return cudaGetLastError();
+        }
         if (k == 3 && aligned && (cin == 8 || cin % 16 == 0) && cout % 16 == 0 && n % kWtX == 0 &&
             n % kWtZ == 0) {
             const unsigned vtiles = static_cast<unsigned>(batch) * (n / kWtX) * (n / kWtY) * (n / kWtZ);

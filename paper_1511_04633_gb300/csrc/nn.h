@@ -31,6 +31,10 @@ cudaError_t conv3d_wgrad_bf16(const __nv_bfloat16 *x, const __nv_bfloat16 *dy, f
                               size_t scratch_floats, int batch, int n, int cin, int cout, int k,
                               cudaStream_t s);
 
+// Number of tcgen05 convolution launches whose bounded wait ran out (their
+// output is not written); reset = true clears it.  -1 on a CUDA error.
+int tensor_core_errors(bool reset);
+
 cudaError_t bias_grad(const float *dy, float *db, float *scratch, size_t scratch_floats,
                       long long voxels, int cout, cudaStream_t s);
 

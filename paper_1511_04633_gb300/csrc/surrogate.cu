@@ -666,6 +666,8 @@ const char *dmrt_surrogate_last_error(const dmrt_surrogate_t *s)
     return s->err.c_str();
 }
 
+int dmrt_nn_tensor_core_errors(int reset) { return lbm::nn::tensor_core_errors(reset != 0); }
+
 dmrt_status dmrt_nn_conv3d(const void *x, const void *w, const float *bias, void *y, int batch, int n,
                            int cin, int cout, int k, int act, int storage, int out_f32, void *stream)
 {

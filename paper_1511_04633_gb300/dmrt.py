@@ -103,6 +103,7 @@ def load(build_if_missing: bool = True):
             "dmrt_nusselt_flux": ([vp, i, P(d)], i),
             "dmrt_nusselt_noalloc": ([vp, i, i, i, i, vp, P(d)], i),
             "dmrt_round_to_storage": ([i, i, vp, vp, ctypes.c_longlong, ctypes.c_uint, vp], i),
+            "dmrt_nn_tensor_core_errors": ([i], i),
             "dmrt_residual": ([vp, P(d)], i),
             "dmrt_run_to_steady": ([vp, d, l_, P(l_), P(d)], i),
             "dmrt_set_populations": ([vp, vp, vp, i], i),
@@ -293,6 +294,11 @@ def dmrt_round_to_storage(x, storage: int, rounding: int = ROUND_AUTO, seed: int
     check(None, load().dmrt_round_to_storage(storage, rounding, p, q, x.numel(), seed, raw),
           "dmrt_round_to_storage")
     return out
+
+
+def dmrt_nn_tensor_core_errors(reset: bool = False) -> int:
+    """Launches of the tcgen05 convolution whose bounded wait ran out."""
+    return int(load().dmrt_nn_tensor_core_errors(1 if reset else 0))
 
 
 def dmrt_residual(h) -> float:

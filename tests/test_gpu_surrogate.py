@@ -89,6 +89,7 @@ def test_tensor_core_convolution_matches_the_definition(env, k, cin, cout, out_f
     b = torch.from_numpy(inputs.random_weights(cout, seed=23, scale=0.5))
     y = torch.empty((batch, n, n, n, cout), dtype=torch.float32 if out_f32 else torch.bfloat16, device="cuda")
     dm.dmrt_nn_conv3d(x.cuda(), w.cuda(), b.cuda(), y, batch, n, cin, cout, k, act=1)
+    assert dm.dmrt_nn_tensor_core_errors(reset=True) == 0
     ref = S.leaky(S.conv3d(x.double().numpy(), w.double().numpy().reshape(k ** 3, cout, cin), b.double().numpy(), k))
     got = y.double().cpu().numpy()
     scale = np.abs(ref).max()
