@@ -12,6 +12,7 @@
 // training is bitwise repeatable.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cstdlib>
 #include <type_traits>
 
@@ -743,6 +744,9 @@ constexpr unsigned um_smem_bytes()
 constexpr unsigned kUmWaitPolls = 1u << 22;  // ~0.3 s of polling before giving up
 // TMEM columns a CTA allocates (the accumulator needs CO, at least 32);
 // DMRT_UMMA_TMEM_COLS raises it (a power of two up to 512).
+#ifndef DMRT_UMMA_CTAS_PER_SM
+#define DMRT_UMMA_CTAS_PER_SM 4
+#endif
 #ifndef DMRT_UMMA_TMEM_COLS
 #define DMRT_UMMA_TMEM_COLS 0
 #endif
@@ -844,6 +848,153 @@ __global__ void __launch_bounds__(128, 1) conv3d_umma_kernel(const __nv_bfloat16
     } else if (t == 0) {
         atomicExch(err, 1);
     }
+    umma::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) umma::tmem_dealloc(tmem, kCols);
+}
+
+// The same tcgen05 convolution streamed along z for few channels (cin <= 32,
+// cout <= 32): a CTA keeps the weights of all taps and a ring of four halo
+// planes (10 x 18 voxels, all input channels) resident and walks a run of
+// z-planes of its 8 x 16 tile.  The MMAs of plane z go to one of two TMEM
+// accumulators while the threads write out plane z - 1 from the other and
+// stage halo plane z + 2 into the ring slot plane z - 2 left free, so the
+// tensor cores, the epilogue and the loads overlap.  Ring slot of grid plane
+// g: g mod 4 (planes outside the grid hold zeros).
+template <int KG>
+constexpr unsigned up_plane_bytes()
+{
+    return static_cast<unsigned>(KG) * kUmHX * kUmHY * 16u;
+}
+template <int CO, int KG>
+constexpr unsigned up_smem_bytes()
+{
+    return 128u + 4u * up_plane_bytes<KG>() + 27u * KG * CO * 16u;
+}
+
+template <int CO, int KG, typename TO>
+__global__ void __launch_bounds__(128) conv3d_umma_stream_kernel(const __nv_bfloat16 *__restrict__ x,
+                                                                 const __nv_bfloat16 *__restrict__ w,
+                                                                 const float *__restrict__ bias,
+                                                                 TO *__restrict__ y, int n, int cin, int cout,
+                                                                 int act, int zrun, int *err)
+{
+    extern __shared__ __align__(1024) unsigned char up_smem[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(up_smem);  // [2]
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(up_smem + 16);
+    unsigned char *ring = up_smem + 128;
+    unsigned char *wsm = ring + 4 * up_plane_bytes<KG>();
+    constexpr unsigned kPlane = up_plane_bytes<KG>();
+    constexpr int kRow = kUmHX * kUmHY;  // 180 voxels of a halo plane
+    constexpr uint32_t kCols = 2 * CO < 32 ? 32 : 2 * CO;
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int tx_n = n / kUmX, ty_n = n / kUmY, zs_n = (n + zrun - 1) / zrun;
+    int r = blockIdx.x;
+    const int x0 = (r % tx_n) * kUmX;
+    r /= tx_n;
+    const int y0 = (r % ty_n) * kUmY;
+    r /= ty_n;
+    const int z_begin = (r % zs_n) * zrun;
+    const int b = r / zs_n;
+    const int z_end = min(z_begin + zrun, n);
+    const long long sample = static_cast<long long>(b) * n * n * n;
+    const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
+    if (t == 0) {
+        umma::mbar_init(&bar[0], 1);
+        umma::mbar_init(&bar[1], 1);
+    }
+    if (warp == 0) umma::tmem_alloc(tslot, kCols);
+    // weights of all taps: [tap][kg][co] x 16 B
+    for (int e = t; e < 27 * KG * CO; e += 128) {
+        const int co = e % CO, kg = (e / CO) % KG, tap = e / (KG * CO);
+        const int c = 8 * kg;
+        uint4 v = zero4;
+        if (co < cout && c < cin)
+            v = *reinterpret_cast<const uint4 *>(w + (static_cast<long long>(tap) * cout + co) * cin + c);
+        *reinterpret_cast<uint4 *>(wsm + ((tap * KG + kg) * CO + co) * 16) = v;
+    }
+    auto stage = [&](int g) {  // grid plane g into ring slot g mod 4
+        unsigned char *dst = ring + static_cast<unsigned>((g + 4) & 3) * kPlane;
+        for (int e = t; e < KG * kRow; e += 128) {
+            const int kg = e / kRow, h = e % kRow;
+            const int gx = x0 + h % kUmHX - 1, gy = y0 + h / kUmHX - 1;
+            const int c = 8 * kg;
+            uint4 v = zero4;
+            if (g >= 0 && g < n && gx >= 0 && gx < n && gy >= 0 && gy < n && c < cin)
+                v = *reinterpret_cast<const uint4 *>(
+                    x + (sample + (static_cast<long long>(g) * n + gy) * n + gx) * cin + c);
+            *reinterpret_cast<uint4 *>(dst + (kg * kRow + h) * 16) = v;
+        }
+    };
+    stage(z_begin - 1);
+    stage(z_begin);
+    stage(z_begin + 1);
+    umma::fence_proxy_async_smem();
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+    const uint32_t tmem = *tslot;
+    constexpr uint32_t idesc = umma::idesc_bf16_f32(128, CO);
+    const uint32_t ring_s = umma::smem_u32(ring), w_s = umma::smem_u32(wsm);
+    uint32_t uses0 = 0u, uses1 = 0u;  // completed phases of each accumulator's barrier
+    bool ok = true;
+    auto epilogue = [&](int zz, int buf) {
+        const int m = 32 * warp + lane;  // TMEM lane = GEMM row = voxel (x fastest)
+        const long long vox = sample + (static_cast<long long>(zz) * n + y0 + m / kUmX) * n + x0 + m % kUmX;
+        TO *yo = y + vox * cout;
+#pragma unroll
+        for (int c16 = 0; c16 < CO; c16 += 16) {
+            float v[16];
+            umma::ld_32x32b_x16(tmem + (static_cast<uint32_t>(32 * warp) << 16) + buf * CO + c16, v);
+#pragma unroll
+            for (int j = 0; j < 16; j += 2) {
+                const int co = c16 + j;
+                float a = v[j] + (bias ? bias[co] : 0.f), bb = v[j + 1] + (bias ? bias[co + 1] : 0.f);
+                if (act) {
+                    a = a > 0.f ? a : kSlope * a;
+                    bb = bb > 0.f ? bb : kSlope * bb;
+                }
+                st2(yo + co, a, bb);
+            }
+        }
+    };
+    for (int z = z_begin; z < z_end && ok; ++z) {
+        const int buf = z & 1;
+        if (t == 0) {
+            for (int tap = 0; tap < 27; ++tap) {
+                const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
+                const uint32_t plane = ring_s + static_cast<uint32_t>((z - 1 + dz + 4) & 3) * kPlane +
+                                       (dy * kUmHX + dx) * 16;
+#pragma unroll
+                for (int kc = 0; kc < KG / 2; ++kc) {
+                    const uint64_t ad = umma::smem_desc(plane + 2 * kc * kRow * 16, kRow * 16, kUmHX * 16);
+                    const uint64_t bd = umma::smem_desc(w_s + (tap * KG + 2 * kc) * CO * 16, CO * 16, 128);
+                    umma::mma_bf16(tmem + buf * CO, ad, bd, idesc, (tap > 0 || kc > 0) ? 1u : 0u);
+                }
+            }
+            umma::commit(&bar[buf]);
+        }
+        if (z > z_begin) {
+            // plane z - 1: its MMAs read the slot plane z + 2 goes to
+            uint32_t &u = buf ? uses0 : uses1;  // the barrier of plane z - 1
+            if (!umma::mbar_wait(&bar[buf ^ 1], u & 1u, kUmWaitPolls)) ok = false;
+            ++u;
+            umma::fence_after_sync();
+            if (ok) epilogue(z - 1, buf ^ 1);
+        }
+        if (ok && z + 1 < z_end) stage(z + 2);
+        umma::fence_proxy_async_smem();
+        umma::fence_before_sync();
+        __syncthreads();
+        umma::fence_after_sync();
+    }
+    if (ok) {
+        const int zl = z_end - 1, buf = zl & 1;
+        if (!umma::mbar_wait(&bar[buf], (buf ? uses1 : uses0) & 1u, kUmWaitPolls)) ok = false;
+        umma::fence_after_sync();
+        if (ok) epilogue(zl, buf);
+    }
+    if (!ok && t == 0) atomicExch(err, 1);
     umma::fence_before_sync();
     __syncthreads();
     if (warp == 0) umma::tmem_dealloc(tmem, kCols);
@@ -1461,6 +1612,29 @@ cudaError_t conv3d(const TI *x, const TW *w, const float *bias, TO *y, int batch
         // channel count and both base pointers must keep 16-byte alignment
         const bool aligned =
             ((reinterpret_cast<unsigned long long>(x) | reinterpret_cast<unsigned long long>(w)) & 15ull) == 0;
+        if (k == 3 && aligned && (cin == 8 || cin == 16 || cin == 32) && (cout == 16 || cout == 32) &&
+            n % kUmY == 0 && umma_enabled()) {
+            // stream along z: about DMRT_UMMA_CTAS_PER_SM CTAs per SM, runs of at least 2 planes
+            const long long xy = static_cast<long long>(batch) * (n / kUmX) * (n / kUmY);
+            int zs = static_cast<int>((DMRT_UMMA_CTAS_PER_SM * 152 + xy - 1) / xy);
+            zs = std::max(1, std::min(zs, n / 2));
+            const int zrun = (n + zs - 1) / zs;
+            zs = (n + zrun - 1) / zrun;
+            const unsigned grid = static_cast<unsigned>(xy * zs);
+            int *err = umma_error_word();
+            if (!err) return cudaErrorInvalidValue;
+            cudaError_t e = cudaSuccess;
+            auto go = [&](auto kernel, unsigned smem) {
+                e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+                if (e == cudaSuccess) kernel<<<grid, 128, smem, s>>>(x, w, bias, y, n, cin, cout, act, zrun, err);
+            };
+            if (cout == 16 && cin <= 16) go(conv3d_umma_stream_kernel<16, 2, TO>, up_smem_bytes<16, 2>());
+            else if (cout == 16) go(conv3d_umma_stream_kernel<16, 4, TO>, up_smem_bytes<16, 4>());
+            else if (cin <= 16) go(conv3d_umma_stream_kernel<32, 2, TO>, up_smem_bytes<32, 2>());
+            else go(conv3d_umma_stream_kernel<32, 4, TO>, up_smem_bytes<32, 4>());
+            if (e != cudaSuccess) return e;
+            return cudaGetLastError();
+        }
         if (k == 3 && aligned && (cin == 8 || cin % 16 == 0) && cout % 16 == 0 && n % kUmY == 0 &&
             umma_enabled()) {
             const unsigned tiles = static_cast<unsigned>(batch) * (n / kUmX) * (n / kUmY) * n;

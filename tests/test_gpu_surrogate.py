@@ -167,3 +167,22 @@ def test_bf16_gradients_per_layer(env, channels):
         cos = float(np.dot(a, b) / (np.linalg.norm(a) * np.linalg.norm(b)))
         rel = np.linalg.norm(a - b) / np.linalg.norm(b)
         assert cos >= 0.995 and rel <= 5e-2, (cin, cout, k, cos, rel)
+
+
+@pytest.mark.parametrize("cin,cout", [(16, 16), (32, 32), (8, 32)])
+@pytest.mark.parametrize("out_f32", [False, True])
+def test_tensor_core_convolution_on_a_64_grid(env, cin, cout, out_f32):
+    """The tcgen05 convolution streamed along z (runs of 7 planes and a last
+    run of one on a 64^3 grid) against the definition."""
+    torch, dm = env
+    n, batch, k = 64, 1, 3
+    x = torch.from_numpy(inputs.random_targets((batch, n, n, n, cin), seed=41)).to(torch.bfloat16)
+    w = torch.from_numpy(inputs.random_weights(k ** 3 * cout * cin, seed=42, scale=0.2)).to(torch.bfloat16)
+    b = torch.from_numpy(inputs.random_weights(cout, seed=43, scale=0.5))
+    y = torch.empty((batch, n, n, n, cout), dtype=torch.float32 if out_f32 else torch.bfloat16, device="cuda")
+    dm.dmrt_nn_conv3d(x.cuda(), w.cuda(), b.cuda(), y, batch, n, cin, cout, k, act=1)
+    assert dm.dmrt_nn_tensor_core_errors(reset=True) == 0
+    ref = S.leaky(S.conv3d(x.double().numpy(), w.double().numpy().reshape(k ** 3, cout, cin), b.double().numpy(), k))
+    got = y.double().cpu().numpy()
+    tol = 2e-5 if out_f32 else 8e-3
+    assert np.abs(got - ref).max() <= tol * np.abs(ref).max()
