@@ -55,6 +55,18 @@ constexpr int kMinBlocksEns = 4;
 #ifndef DMRT_ENS_INPLACE_MIN_BLOCKS1
 #define DMRT_ENS_INPLACE_MIN_BLOCKS1 4
 #endif
+// DMRT_ENS_INPLACE_BLOCK128 = N: the in-place phases are compiled for blocks
+// of 128 threads with N resident per SM (e.g. 7 gives 72 registers), and
+// autotuning tries only 128-thread blocks for in-place ensembles.
+#ifndef DMRT_ENS_INPLACE_BLOCK128
+#define DMRT_ENS_INPLACE_BLOCK128 0
+#endif
+#if DMRT_ENS_INPLACE_BLOCK128
+#define DMRT_ENS_INPLACE_BOUNDS(PHASE) __launch_bounds__(128, DMRT_ENS_INPLACE_BLOCK128)
+#else
+#define DMRT_ENS_INPLACE_BOUNDS(PHASE) \
+    __launch_bounds__(256, PHASE == 0 ? DMRT_ENS_INPLACE_MIN_BLOCKS0 : DMRT_ENS_INPLACE_MIN_BLOCKS1)
+#endif
 
 // ---------------------------------------------------------------- step
 
@@ -136,7 +148,7 @@ __global__ void __launch_bounds__(256, kMinBlocksEns)
 // The buffer's tail holds two step counters: phase p reads word p and writes
 // word p ^ 1.
 template <typename T, bool SR, int PHASE>
-__global__ void __launch_bounds__(256, PHASE == 0 ? DMRT_ENS_INPLACE_MIN_BLOCKS0 : DMRT_ENS_INPLACE_MIN_BLOCKS1)
+__global__ void DMRT_ENS_INPLACE_BOUNDS(PHASE)
     ensemble_inplace_kernel(T *__restrict__ buf, const CavityDesc *__restrict__ descs,
                             const int *__restrict__ blockmap, long long counter_at)
 {
@@ -1042,6 +1054,7 @@ dmrt_status dmrt_ensemble_autotune(dmrt_ensemble_t *e, int trials, char *report,
     std::vector<int> best_bx(e->count);
     std::string rep;
     for (int threads : {128, 256}) {
+        if (DMRT_ENS_INPLACE_BLOCK128 && e->inplace && threads != 128) continue;
         e->threads = threads;
         for (auto &g : groups) {
             int best = -1;

@@ -37,6 +37,17 @@ namespace {
 #ifndef DMRT_INPLACE_MIN_BLOCKS1
 #define DMRT_INPLACE_MIN_BLOCKS1 3
 #endif
+// DMRT_INPLACE_BLOCK128 = N: compile both phases for the 128-thread blocks
+// the cavities use, with N resident per SM (e.g. 7 gives 72 registers).
+#ifndef DMRT_INPLACE_BLOCK128
+#define DMRT_INPLACE_BLOCK128 0
+#endif
+#if DMRT_INPLACE_BLOCK128
+#define DMRT_INPLACE_BOUNDS(PHASE) __launch_bounds__(128, DMRT_INPLACE_BLOCK128)
+#else
+#define DMRT_INPLACE_BOUNDS(PHASE) \
+    __launch_bounds__(256, PHASE == 0 ? DMRT_INPLACE_MIN_BLOCKS0 : DMRT_INPLACE_MIN_BLOCKS1)
+#endif
 
 // Cell index of (x + dx, y + dy, z + dz) in a periodic box.
 __device__ __forceinline__ unsigned wrapped_cell(const StepGeometry &S, int x, int y, int z)
@@ -68,7 +79,7 @@ __device__ __forceinline__ void load_periodic(const T *A, const StepGeometry &S,
 }
 
 template <int WALL, typename T, bool SR, int PHASE>
-__global__ void __launch_bounds__(256, PHASE == 0 ? DMRT_INPLACE_MIN_BLOCKS0 : DMRT_INPLACE_MIN_BLOCKS1)
+__global__ void DMRT_INPLACE_BOUNDS(PHASE)
     step_inplace_kernel(T *__restrict__ A, const InplaceGeometry SI, const CollideParams C)
 {
     const StepGeometry &S = SI.load;
