@@ -59,7 +59,7 @@ constexpr int kMinBlocksEns = 4;
 // of 128 threads with N resident per SM (e.g. 7 gives 72 registers), and
 // autotuning tries only 128-thread blocks for in-place ensembles.
 #ifndef DMRT_ENS_INPLACE_BLOCK128
-#define DMRT_ENS_INPLACE_BLOCK128 0
+#define DMRT_ENS_INPLACE_BLOCK128 7  // 72 registers, no spills; measured 1 % faster than 64
 #endif
 #if DMRT_ENS_INPLACE_BLOCK128
 #define DMRT_ENS_INPLACE_BOUNDS(PHASE) __launch_bounds__(128, DMRT_ENS_INPLACE_BLOCK128)

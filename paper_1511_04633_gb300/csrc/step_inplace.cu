@@ -26,8 +26,9 @@ namespace lbm {
 
 namespace {
 
-// Minimum resident 256-thread blocks per SM of each phase (4 caps a kernel
-// at 64 registers, 3 at 80).  The phase-0 kernel needs its store offsets
+// Minimum resident 256-thread blocks per SM of each FP32 phase (4 caps a
+// kernel at 64 registers, 3 at 80; the kernels launch 128-thread blocks, so
+// the bound below asks for twice as many of those).  The phase-0 kernel needs its store offsets
 // beside the collision's values and spills ~50 bytes at 64 registers;
 // measured on GB300 (128^3, FP32), 80 registers for both phases give
 // 67.7 us per step against 75.2 us at 64.
@@ -43,10 +44,12 @@ namespace {
 #define DMRT_INPLACE_BLOCK128 0
 #endif
 #if DMRT_INPLACE_BLOCK128
-#define DMRT_INPLACE_BOUNDS(PHASE) __launch_bounds__(128, DMRT_INPLACE_BLOCK128)
+#define DMRT_INPLACE_BOUNDS(PHASE, T) __launch_bounds__(128, DMRT_INPLACE_BLOCK128)
 #else
-#define DMRT_INPLACE_BOUNDS(PHASE) \
-    __launch_bounds__(256, PHASE == 0 ? DMRT_INPLACE_MIN_BLOCKS0 : DMRT_INPLACE_MIN_BLOCKS1)
+// the 16-bit phases run at 72 registers (7 blocks of 128 threads), measured
+// 3 % faster than at 80; the FP32 phases at 80 (measured 3 % faster than 72)
+#define DMRT_INPLACE_BOUNDS(PHASE, T) \
+    __launch_bounds__(128, std::is_same_v<T, float> ? 2 * (PHASE == 0 ? DMRT_INPLACE_MIN_BLOCKS0 : DMRT_INPLACE_MIN_BLOCKS1) : 7)
 #endif
 
 // Cell index of (x + dx, y + dy, z + dz) in a periodic box.
@@ -79,7 +82,7 @@ __device__ __forceinline__ void load_periodic(const T *A, const StepGeometry &S,
 }
 
 template <int WALL, typename T, bool SR, int PHASE>
-__global__ void DMRT_INPLACE_BOUNDS(PHASE)
+__global__ void DMRT_INPLACE_BOUNDS(PHASE, T)
     step_inplace_kernel(T *__restrict__ A, const InplaceGeometry SI, const CollideParams C)
 {
     const StepGeometry &S = SI.load;
