@@ -1177,6 +1177,59 @@ __global__ void act_backward_narrow_kernel(const T *__restrict__ yout, float *__
     }
 }
 
+// act_backward_narrow_kernel that also sums the bias gradient: with a grid
+// of a fixed number of blocks the grid stride is a multiple of the cout / 4
+// channel groups, so every thread sees the same four channels and sums them;
+// each block adds its threads per channel group in thread order and writes
+// partials[block][cout].
+template <typename T>
+__global__ void __launch_bounds__(256) act_backward_narrow_bias_kernel(const T *__restrict__ yout,
+                                                                       float *__restrict__ dy,
+                                                                       __nv_bfloat16 *__restrict__ dyn,
+                                                                       long long len4, int act, int c4,
+                                                                       float *__restrict__ partials)
+{
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < len4;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        float4 g = reinterpret_cast<float4 *>(dy)[i];
+        if (act) {
+            const long long e = 4 * i;
+            if (!(ldf(yout + e) > 0.f)) g.x *= kSlope;
+            if (!(ldf(yout + e + 1) > 0.f)) g.y *= kSlope;
+            if (!(ldf(yout + e + 2) > 0.f)) g.z *= kSlope;
+            if (!(ldf(yout + e + 3) > 0.f)) g.w *= kSlope;
+            reinterpret_cast<float4 *>(dy)[i] = g;
+        }
+        __nv_bfloat162 lo = __floats2bfloat162_rn(g.x, g.y), hi = __floats2bfloat162_rn(g.z, g.w);
+        uint2 pk;
+        pk.x = *reinterpret_cast<unsigned *>(&lo);
+        pk.y = *reinterpret_cast<unsigned *>(&hi);
+        reinterpret_cast<uint2 *>(dyn)[i] = pk;
+        acc.x += g.x;
+        acc.y += g.y;
+        acc.z += g.z;
+        acc.w += g.w;
+    }
+    __shared__ float4 red[256];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    if (static_cast<int>(threadIdx.x) < c4) {
+        float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int k = threadIdx.x; k < 256; k += c4) {
+            t.x += red[k].x;
+            t.y += red[k].y;
+            t.z += red[k].z;
+            t.w += red[k].w;
+        }
+        float *o = partials + static_cast<long long>(blockIdx.x) * 4 * c4 + 4 * threadIdx.x;
+        o[0] = t.x;
+        o[1] = t.y;
+        o[2] = t.z;
+        o[3] = t.w;
+    }
+}
+
 // wt[tap][ci][co] = w[K^3 - 1 - tap][co][ci] (weights of the transposed
 // convolution, in the storage type).
 template <typename TW>
@@ -1831,6 +1884,23 @@ cudaError_t act_backward_narrow(const T *yout, float *dy, __nv_bfloat16 *dyn, lo
 }
 
 template <typename T>
+cudaError_t act_backward_narrow_bias(const T *yout, float *dy, __nv_bfloat16 *dyn, long long voxels, int cout,
+                                     int act, float *db, float *scratch, size_t scratch_floats, cudaStream_t s)
+{
+    constexpr int kBlocks = 152 * 4;
+    const bool aligned =
+        ((reinterpret_cast<unsigned long long>(dy) & 15ull) | (reinterpret_cast<unsigned long long>(dyn) & 7ull)) == 0;
+    if (cout % 4 != 0 || 256 % (cout / 4) != 0 || !aligned || static_cast<size_t>(kBlocks) * cout > scratch_floats)
+        return cudaErrorInvalidValue;
+    const long long len4 = voxels * cout / 4;
+    act_backward_narrow_bias_kernel<T><<<kBlocks, 256, 0, s>>>(yout, dy, dyn, len4, act, cout / 4, scratch);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    sum_chunks_kernel<<<sum_blocks(cout, kBlocks), 256, 0, s>>>(scratch, db, cout, kBlocks, sum_width(cout, kBlocks));
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t act_backward(const T *yout, float *dy, long long len, cudaStream_t s)
 {
     act_backward_kernel<T><<<flat_blocks(len), 256, 0, s>>>(yout, dy, len);
@@ -1976,6 +2046,8 @@ cudaError_t target_from_fields(const float *u, const float *theta, const float *
     template cudaError_t act_backward<T>(const T *, float *, long long, cudaStream_t);          \
     template cudaError_t act_backward_narrow<T>(const T *, float *, __nv_bfloat16 *, long long, int, \
                                                 cudaStream_t);                                  \
+    template cudaError_t act_backward_narrow_bias<T>(const T *, float *, __nv_bfloat16 *, long long, int, int, \
+                                                     float *, float *, size_t, cudaStream_t);   \
     template cudaError_t flip_transpose<T>(const T *, T *, int, int, int, cudaStream_t);        \
     template cudaError_t avgpool2<T>(const T *, T *, int, int, int, cudaStream_t);              \
     template cudaError_t up2_add<T>(const T *, const T *, T *, int, int, int, cudaStream_t);    \

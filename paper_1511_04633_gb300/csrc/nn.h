@@ -48,6 +48,13 @@ template <typename T>
 cudaError_t act_backward_narrow(const T *yout, float *dy, __nv_bfloat16 *dyn, long long len, int act,
                                 cudaStream_t s);
 
+// act_backward_narrow over voxels x cout values plus the bias gradient db[co]
+// = sum over voxels of dy[v][co], in a fixed order; cout % 4 == 0 and cout / 4
+// dividing 256; `scratch` holds 608 * cout partial sums.
+template <typename T>
+cudaError_t act_backward_narrow_bias(const T *yout, float *dy, __nv_bfloat16 *dyn, long long voxels, int cout,
+                                     int act, float *db, float *scratch, size_t scratch_floats, cudaStream_t s);
+
 // weights of the transposed convolution (input gradient = conv3d with them)
 template <typename TW>
 cudaError_t flip_transpose(const TW *w, TW *wt, int k, int cout, int cin, cudaStream_t s);

@@ -59,6 +59,8 @@ struct dmrt_surrogate {
     float *target = nullptr;
     float *scratch = nullptr;
     size_t scratch_floats = 0;
+    float *bscratch = nullptr;  // partial sums of the bias gradients
+    size_t bscratch_floats = 0;
     double *dpart = nullptr, *dloss = nullptr;
     double *dra = nullptr;
     int *dwall = nullptr;
@@ -228,13 +230,20 @@ dmrt_status conv_bwd(dmrt_surrogate_t *s, const Layer &L, const void *in, const 
     const long long vox = static_cast<long long>(batch) * e * e * e;
     bool wgrad_done = false;
     bool act_done = false;
+    bool bias_done = false;
     if constexpr (std::is_same_v<T, __nv_bfloat16>) {
         // bf16 storage: the output gradient in bf16 feeds the tensor cores
-        // (the activation backward and the narrowing in one pass when the
-        // length allows; otherwise one after the other)
-        if ((vox * L.cout) % 4 == 0 &&
-            lbm::nn::act_backward_narrow<T>(static_cast<const T *>(outv), gin, s->gnarrow, vox * L.cout, L.act,
-                                            s->stream) == cudaSuccess) {
+        // (the activation backward, the narrowing and the bias gradient in
+        // one pass when the channel count allows; otherwise separately)
+        if (lbm::nn::act_backward_narrow_bias<T>(static_cast<const T *>(outv), gin, s->gnarrow, vox, L.cout, L.act,
+                                                 s->grad + L.b_off, s->bscratch, s->bscratch_floats,
+                                                 s->stream) == cudaSuccess) {
+            act_done = true;
+            bias_done = true;
+        } else if ((vox * L.cout) % 4 == 0 &&
+                   lbm::nn::act_backward_narrow<T>(static_cast<const T *>(outv), gin, s->gnarrow, vox * L.cout,
+                                                   L.act, s->stream) == cudaSuccess) {
+            cudaGetLastError();
             act_done = true;
         } else {
             cudaGetLastError();
@@ -260,8 +269,9 @@ dmrt_status conv_bwd(dmrt_surrogate_t *s, const Layer &L, const void *in, const 
             lbm::nn::conv3d_wgrad<T>(static_cast<const T *>(in), gin, s->grad + L.w_off, s->scratch,
                                      s->scratch_floats, batch, e, L.cin, L.cout, L.k, s->stream),
             "conv3d_wgrad");
-    SCK(s, lbm::nn::bias_grad(gin, s->grad + L.b_off, s->scratch, s->scratch_floats, vox, L.cout, s->stream),
-        "bias_grad");
+    if (!bias_done)
+        SCK(s, lbm::nn::bias_grad(gin, s->grad + L.b_off, s->scratch, s->scratch_floats, vox, L.cout, s->stream),
+            "bias_grad");
     if (gout) {
         SCK(s, lbm::nn::flip_transpose<T>(W<T>(s, L), static_cast<T *>(s->wt), L.k, L.cout, L.cin, s->stream),
             "flip_transpose");
@@ -432,7 +442,9 @@ dmrt_status dmrt_surrogate_create(dmrt_surrogate_t **out, const dmrt_surrogate_c
          dalloc(reinterpret_cast<void **>(&s->gnarrow), gmax * 2) &&
          dalloc(reinterpret_cast<void **>(&s->target), static_cast<size_t>(Bm) * voxels(s, 0) * kOut * 4);
     s->scratch_floats = std::max<size_t>(static_cast<size_t>(27) * 128 * 128 * 64, 4u << 20);
+    s->bscratch_floats = static_cast<size_t>(152) * 4 * 128;
     ok = ok && dalloc(reinterpret_cast<void **>(&s->scratch), s->scratch_floats * 4) &&
+         dalloc(reinterpret_cast<void **>(&s->bscratch), s->bscratch_floats * 4) &&
          dalloc(reinterpret_cast<void **>(&s->dpart), 512 * sizeof(double)) &&
          dalloc(reinterpret_cast<void **>(&s->dloss), sizeof(double)) &&
          dalloc(reinterpret_cast<void **>(&s->dra), Bm * sizeof(double)) &&
@@ -453,7 +465,7 @@ void dmrt_surrogate_destroy(dmrt_surrogate_t *s)
     SGuard g(s->device);
     if (s->stream) cudaStreamSynchronize(s->stream);
     void *ptrs[] = {s->master, s->grad, s->m1, s->m2, s->wstore, s->wt, s->x0, s->out, s->g0, s->g1,
-                    s->g2, s->gnarrow, s->target, s->scratch, s->dpart, s->dloss, s->dra, s->dwall};
+                    s->g2, s->gnarrow, s->target, s->scratch, s->bscratch, s->dpart, s->dloss, s->dra, s->dwall};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (auto *v : {&s->a, &s->s, &s->m, &s->h, &s->dd, &s->pin})
