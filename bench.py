@@ -56,12 +56,14 @@ def workload(args) -> str:
             f"residual + hot-wall Nu")
 
 
-STEP_KERNEL_SOURCES = ["paper_1511_04633_gb300/csrc/step.cu",
-                       "paper_1511_04633_gb300/csrc/step_body.cuh",
-                       "paper_1511_04633_gb300/csrc/lattice.cuh"]
-INPLACE_KERNEL_SOURCES = ["paper_1511_04633_gb300/csrc/step_inplace.cu",
-                          "paper_1511_04633_gb300/csrc/step_body.cuh",
-                          "paper_1511_04633_gb300/csrc/lattice.cuh"]
+_BODY = ["paper_1511_04633_gb300/csrc/step_body.cuh", "paper_1511_04633_gb300/csrc/lattice.cuh",
+         "paper_1511_04633_gb300/csrc/vec2.cuh"]
+# sources of each step kernel: one cell per thread (two buffers), two cells
+# per thread (two buffers), in place
+KERNEL_SOURCES = {"ab": ["paper_1511_04633_gb300/csrc/step.cu"] + _BODY,
+                  "pair": ["paper_1511_04633_gb300/csrc/step_pair.cu"] + _BODY,
+                  "inplace": ["paper_1511_04633_gb300/csrc/step_inplace.cu"] + _BODY}
+STEP_KERNEL_SOURCES = KERNEL_SOURCES["ab"]
 
 
 # ---------------------------------------------------------------- distributed plumbing
@@ -170,18 +172,18 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def step_kernel_digest(streaming: str = "ab") -> str:
+def step_kernel_digest(scheme: str = "ab") -> str:
     h = hashlib.sha256()
-    for rel in (STEP_KERNEL_SOURCES if streaming == "ab" else INPLACE_KERNEL_SOURCES):
+    for rel in KERNEL_SOURCES[scheme]:
         with open(os.path.join(ROOT, rel), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(storage: str = "f32", wall: int = 2, streaming: str = "ab"):
+def profiled_traffic(storage: str = "f32", wall: int = 2, scheme: str = "ab"):
     """DRAM bytes per step-kernel launch from the committed ncu summary, only
     if it was taken on the current kernel sources for this storage, wall and
-    streaming scheme."""
+    kernel scheme ("ab", "pair" or "inplace")."""
     path = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
     try:
         with open(path) as fh:
@@ -190,9 +192,9 @@ def profiled_traffic(storage: str = "f32", wall: int = 2, streaming: str = "ab")
         return None
     recs = t if isinstance(t, list) else [t]
     for rec in recs:
-        if (rec.get("source_digest") == step_kernel_digest(streaming)
+        if (rec.get("source_digest") == step_kernel_digest(scheme)
                 and rec.get("storage", "f32") == storage and rec.get("wall", 2) == wall
-                and rec.get("streaming", "ab") == streaming):
+                and rec.get("scheme", "ab") == scheme):
             return rec.get("dram_bytes_per_launch")
     return None
 
@@ -272,9 +274,11 @@ def run_dmrt(args, rank, local, world):
     cells = grid[0] * grid[1] * grid[2]
     storage = STORAGES[args.storage]
     cav = dmrt.Cavity(grid, args.ra, PR, MA, args.wall, storage=storage,
-                      streaming=STREAMINGS[args.streaming])
+                      streaming=STREAMINGS[args.streaming], cells_per_thread=args.cells_per_thread)
     dmrt.dmrt_set_stream(cav.h, stream)
     inner = args.inner
+    cpt = cav.params["cells_per_thread"]
+    scheme = "inplace" if args.streaming == "inplace" else ("pair" if cpt == 2 else "ab")
 
     def one_step():
         dmrt.dmrt_step(cav.h, inner)
@@ -310,7 +314,7 @@ def run_dmrt(args, rank, local, world):
     bytes_per_cell = stats["bytes_per_cell"]
     achieved = bytes_per_cell * cells / launch_s / 1e9
     peak, peak_src = measured_peaks()
-    traffic = profiled_traffic(args.storage, args.wall, args.streaming)
+    traffic = profiled_traffic(args.storage, args.wall, scheme)
 
     # end to end through the C ABI with host buffers: upload the start fields
     # from pinned memory, step, read the fields and Nu back
@@ -370,11 +374,14 @@ def run_dmrt(args, rank, local, world):
                    "l2": f"inputs larger than L2 ({nbuf} x {bytes_per_cell / 2 * cells / 1e6:.0f} MB "
                          f"population buffer)" if bytes_per_cell / 2 * cells > 129e6
                          else "inputs fit in L2: not a DRAM measurement",
+                   "cells_per_thread": cpt,
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
-                     "kernel": (f"step_kernel<{args.wall}, {args.storage}>" if args.streaming == "ab"
-                                else f"step_inplace_kernel<{args.wall}, {args.storage}> (both phases)"),
+                     "kernel": {"ab": f"step_kernel<{args.wall}, {args.storage}>",
+                                "pair": f"step_pair_kernel<{args.wall}, {args.storage}>",
+                                "inplace": f"step_inplace_kernel<{args.wall}, {args.storage}> "
+                                           "(both phases)"}[scheme],
                      "bytes_per_cell": bytes_per_cell, "launch_us": launch_s * 1e6},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": h2d,
@@ -400,7 +407,8 @@ def run_to_steady(dmrt, torch, stream, grid, storage, args, launch_s, seconds=40
     about `seconds` of kernel time), then a 1000-step window timed on the
     converged state."""
     tol = STEADY_TOL[storage]
-    cav = dmrt.Cavity(grid, args.ra, PR, MA, args.wall, storage=storage, streaming=STREAMINGS[args.streaming])
+    cav = dmrt.Cavity(grid, args.ra, PR, MA, args.wall, storage=storage, streaming=STREAMINGS[args.streaming],
+                      cells_per_thread=args.cells_per_thread)
     dmrt.dmrt_set_stream(cav.h, stream)
     budget = max(10_000, int(seconds / max(launch_s, 1e-7)) // 100 * 100)
     torch.cuda.synchronize()
@@ -536,6 +544,8 @@ def main(argv=None):
     ap.add_argument("--streaming", choices=sorted(STREAMINGS), default="ab",
                     help="two population buffers, or one updated in place")
     ap.add_argument("--grid", type=int, default=GRID[0], help="cubic cavity edge")
+    ap.add_argument("--cells-per-thread", type=int, choices=[0, 1, 2], default=0,
+                    help="step kernel: 0 = the library's choice, 1 or 2 cells per thread")
     ap.add_argument("--wall", type=int, choices=[1, 2, 3], default=WALL)
     ap.add_argument("--ra", type=float, default=RA)
     ap.add_argument("--ensemble", action="store_true",

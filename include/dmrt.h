@@ -98,6 +98,14 @@ typedef struct dmrt_opts {
     int residual_interval; /* K of the convergence residual; 0 = 100 */
     int rounding;          /* dmrt_rounding; default DMRT_ROUND_AUTO */
     int streaming;         /* dmrt_streaming; default DMRT_STREAM_AB */
+    int cells_per_thread;  /* cells one thread of the step kernel updates:
+                            * 0 = auto, 1, or 2 (two neighbouring cells of a
+                            * row, collided together in packed FP32x2
+                            * arithmetic; needs a walled box and an even nx,
+                            * else DMRT_ERR_ARG).  Either streaming scheme.
+                            * The stored values are bitwise the same either
+                            * way.  Auto takes 2 for 16-bit storage where
+                            * allowed.  Ensembles accept 0 or 1. */
 } dmrt_opts;
 
 /* Derived lattice parameters of a handle (read-only view). */
@@ -108,6 +116,7 @@ typedef struct dmrt_params {
     long steps;                /* time steps taken since creation / last reset */
     int streaming;             /* dmrt_streaming */
     long long device_bytes;    /* device memory the handle holds now */
+    int cells_per_thread;      /* 1 or 2: the step kernel in use */
 } dmrt_params;
 
 /* Counters for profiling and for the benchmark's launch count. */

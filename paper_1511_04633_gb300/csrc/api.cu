@@ -31,6 +31,7 @@ struct dmrt {
     lbm::StepGeometry S{};
     CollideParams C{};
     lbm::BlockShape block{32, 4};
+    int cells_per_thread = 1;  // 2: the paired step kernels (walled box, even nx)
 
     void *buf[2] = {nullptr, nullptr};   // ping-pong population buffers (storage type)
     int cur = 0;                          // buffer holding the current state
@@ -141,9 +142,15 @@ int &phase(dmrt_t *h) { return h->inplace ? h->parity : h->cur; }
 // One fused step from state `ph`.
 cudaError_t launch_one_step(dmrt_t *h, int ph)
 {
+    if (h->inplace && h->cells_per_thread == 2)
+        return lbm::launch_step_inplace_pair(h->wall, h->storage, h->stochastic, h->buf[0], ph,
+                                             h->SI, h->G, h->C, h->stream, h->use_pdl);
     if (h->inplace)
         return lbm::launch_step_inplace(h->wall, h->storage, h->stochastic, h->buf[0], ph, h->SI,
                                         h->G, h->C, h->block, h->stream, h->use_pdl);
+    if (h->cells_per_thread == 2)
+        return lbm::launch_step_pair(h->wall, h->storage, h->stochastic, h->buf[ph], h->buf[ph ^ 1],
+                                     h->S, h->G, h->C, h->stream, h->use_pdl);
     return lbm::launch_step(h->wall, h->storage, h->stochastic, h->buf[ph], h->buf[ph ^ 1], h->S,
                             h->G, h->C, h->block, h->stream, h->use_pdl);
 }
@@ -334,13 +341,16 @@ dmrt_status create_common(dmrt_t **out, const int grid[3], double nu, double alp
         !std::isfinite(gbeta))
         return DMRT_ERR_ARG;
     int storage = DMRT_STORE_F32, K = 100, rounding = DMRT_ROUND_AUTO, streaming = DMRT_STREAM_AB;
+    int cpt = 0;
     if (opts) {
         storage = opts->storage;
         rounding = opts->rounding;
         streaming = opts->streaming;
+        cpt = opts->cells_per_thread;
         if (opts->residual_interval > 0) K = opts->residual_interval;
         if (opts->residual_interval < 0) return DMRT_ERR_ARG;
     }
+    if (cpt < 0 || cpt > 2) return DMRT_ERR_ARG;
     if (rounding < DMRT_ROUND_AUTO || rounding > DMRT_ROUND_STOCHASTIC) return DMRT_ERR_ARG;
     if (streaming != DMRT_STREAM_AB && streaming != DMRT_STREAM_INPLACE) return DMRT_ERR_ARG;
     if (storage != DMRT_STORE_F32 && storage != DMRT_STORE_BF16 && storage != DMRT_STORE_F16)
@@ -371,6 +381,15 @@ dmrt_status create_common(dmrt_t **out, const int grid[3], double nu, double alp
     lbm::fill_step_geometry(h->G, h->S);
     lbm::fill_inplace_geometry(h->G, h->SI);
     fill_rates(h);
+    // two cells per thread: the paired kernels serve walled boxes with even
+    // nx; auto takes them for 16-bit storage, whose one-cell kernels are
+    // bound by instruction issue rather than by HBM
+    const bool pair_ok = lbm::step_pair_supported(wall_type, h->G);
+    if (cpt == 2 && !pair_ok) {
+        delete h;
+        return DMRT_ERR_ARG;
+    }
+    h->cells_per_thread = (cpt == 2 || (cpt == 0 && pair_ok && storage != DMRT_STORE_F32)) ? 2 : 1;
 #ifdef DMRT_BLOCK_X
     h->block = {DMRT_BLOCK_X, DMRT_BLOCK_Y};
 #else
@@ -849,6 +868,7 @@ dmrt_status dmrt_get_params(const dmrt_t *h, dmrt_params *out)
     out->steps = h->steps;
     out->streaming = h->inplace ? DMRT_STREAM_INPLACE : DMRT_STREAM_AB;
     out->device_bytes = h->device_bytes;
+    out->cells_per_thread = h->cells_per_thread;
     return DMRT_OK;
 }
 

@@ -30,6 +30,15 @@ cudaError_t launch_step(int wall, int storage, bool stochastic, const void *src,
                         const StepGeometry &S, const Geometry &G, const CollideParams &C,
                         BlockShape b, cudaStream_t s, bool pdl);
 
+// The same step with two neighbouring cells of a row per thread (x0 even):
+// bitwise the values of launch_step, in packed FP32x2 arithmetic.  Needs a
+// walled box (wall 1..3) and an even nx (step_pair_supported); the launcher
+// picks its own block shape.
+bool step_pair_supported(int wall, const Geometry &G);
+cudaError_t launch_step_pair(int wall, int storage, bool stochastic, const void *src, void *dst,
+                             const StepGeometry &S, const Geometry &G, const CollideParams &C,
+                             cudaStream_t s, bool pdl);
+
 // In-place streaming (one buffer).  The state alternates between two
 // layouts (see kLayoutSwapped / kLayoutStreamed): phase 0 reads the swapped
 // layout and leaves the streamed one, phase 1 the reverse.  Both phases do
@@ -41,6 +50,11 @@ void fill_inplace_geometry(const Geometry &G, InplaceGeometry &SI);
 cudaError_t launch_step_inplace(int wall, int storage, bool stochastic, void *buf, int phase,
                                 const InplaceGeometry &SI, const Geometry &G,
                                 const CollideParams &C, BlockShape b, cudaStream_t s, bool pdl);
+// Both in-place phases with two cells per thread (same conditions as
+// launch_step_pair); bitwise the values of launch_step_inplace.
+cudaError_t launch_step_inplace_pair(int wall, int storage, bool stochastic, void *buf, int phase,
+                                     const InplaceGeometry &SI, const Geometry &G,
+                                     const CollideParams &C, cudaStream_t s, bool pdl);
 
 // Fields of the pulled populations (any output may be null).
 cudaError_t launch_fields(int wall, int storage, const void *src, const Geometry &G, float *rho,

@@ -280,6 +280,14 @@ struct InplaceGeometry {
 
 // ---------------------------------------------------------------- pull with walls
 
+// theta on a linear wall (Types 2 and 3, Eqs. (7), (10)) at the height of row
+// y: 1/2 - (y + 1/2)/ny, with one rounding in a fixed form, so every kernel
+// that applies the wall rule gets the same value.
+__device__ __forceinline__ float theta_linear(int y, float inv_ny)
+{
+    return __fmaf_rn(-(static_cast<float>(y) + 0.5f), inv_ny, 0.5f);
+}
+
 // Wall rule of a D3Q7 link that leaves the box through a face on `axis`
 // (0 = x, 1 = y, 2 = z): true for a Dirichlet wall (anti-bounce-back).
 template <int WALL>
@@ -350,7 +358,7 @@ __device__ __forceinline__ void pull_g(const T *__restrict__ src, const Geometry
     const long long P = G.plane;
     const int self = (z * ny + y) * nx + x;
     const T *gs = src + 19 * P;
-    const float th_lin = 0.5f - (static_cast<float>(y) + 0.5f) * G.inv_ny;
+    const float th_lin = theta_linear(y, G.inv_ny);
     const int L = G.layout;
     static_for<0, 7>([&](auto I) {
         constexpr int i = decltype(I)::value;

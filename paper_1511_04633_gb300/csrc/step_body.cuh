@@ -15,66 +15,82 @@
 #pragma once
 
 #include "internal.h"
+#include "vec2.cuh"
 
 namespace lbm {
 
-// Collision of one cell in place: d holds f - w, g the energy populations
-// (pulled); on return both hold the post-collision values of Eqs. (14), (29).
-__device__ __forceinline__ void collide_pairs(const CollideParams &C, float d[19], float g[7])
+// Collision of one cell (V = float) or of two cells at once (V = F2), in
+// place: d holds f - w, g the energy populations (pulled); on return both
+// hold the post-collision values of Eqs. (14), (29).  Both forms give the same
+// bits given one rule that the code below keeps: no product is added or
+// subtracted as a separate operation.  ptxas fuses a packed multiply into a
+// following packed add or subtract (an FMA, one rounding fewer) even with
+// explicit rounding modes, and the compiler may do the same to float code;
+// so every such pair is written as fma(), and a product that is subtracted
+// enters as the product of a negated factor.
+template <typename V>
+__device__ __forceinline__ void collide(const CollideParams &C, V d[19], V g[7])
 {
     // ---- opposite-velocity pairs (i, opp(i)): sums s and differences a
-    const float s1 = d[1] + d[2], a1 = d[1] - d[2];          // (+-1, 0, 0)
-    const float s3 = d[3] + d[4], a3 = d[3] - d[4];          // (0, +-1, 0)
-    const float s5 = d[5] + d[6], a5 = d[5] - d[6];          // (0, 0, +-1)
-    const float s7 = d[7] + d[10], a7 = d[7] - d[10];        // +-(1, 1, 0)
-    const float s8 = d[8] + d[9], a8 = d[8] - d[9];          // +-(-1, 1, 0)
-    const float s11 = d[11] + d[14], a11 = d[11] - d[14];    // +-(1, 0, 1)
-    const float s12 = d[12] + d[13], a12 = d[12] - d[13];    // +-(-1, 0, 1)
-    const float s15 = d[15] + d[18], a15 = d[15] - d[18];    // +-(0, 1, 1)
-    const float s16 = d[16] + d[17], a16 = d[16] - d[17];    // +-(0, -1, 1)
+    const V s1 = d[1] + d[2], a1 = d[1] - d[2];          // (+-1, 0, 0)
+    const V s3 = d[3] + d[4], a3 = d[3] - d[4];          // (0, +-1, 0)
+    const V s5 = d[5] + d[6], a5 = d[5] - d[6];          // (0, 0, +-1)
+    const V s7 = d[7] + d[10], a7 = d[7] - d[10];        // +-(1, 1, 0)
+    const V s8 = d[8] + d[9], a8 = d[8] - d[9];          // +-(-1, 1, 0)
+    const V s11 = d[11] + d[14], a11 = d[11] - d[14];    // +-(1, 0, 1)
+    const V s12 = d[12] + d[13], a12 = d[12] - d[13];    // +-(-1, 0, 1)
+    const V s15 = d[15] + d[18], a15 = d[15] - d[18];    // +-(0, 1, 1)
+    const V s16 = d[16] + d[17], a16 = d[16] - d[17];    // +-(0, -1, 1)
 
     // ---- conserved moments (Eqs. (20), (30))
-    const float SF = s1 + s3 + s5;                 // faces
-    const float A = s7 + s8, B = s11 + s12, Cyz = s15 + s16;  // xy, xz, yz edges
-    const float SE = A + B + Cyz;                  // edges
-    const float drho = d[0] + SF + SE;
-    const float X1 = a7 - a8, X2 = a11 - a12;
-    const float Y1 = a7 + a8, Y2 = a15 - a16;
-    const float Z1 = a11 + a12, Z2 = a15 + a16;
-    const float Ex = X1 + X2, Ey = Y1 + Y2, Ez = Z1 + Z2;
-    const float jx = a1 + Ex, jy = a3 + Ey, jz = a5 + Ez;
+    const V SF = (s1 + s3) + s5;                 // faces
+    const V A = s7 + s8, B = s11 + s12, Cyz = s15 + s16;  // xy, xz, yz edges
+    const V SE = (A + B) + Cyz;                  // edges
+    const V drho = (d[0] + SF) + SE;
+    const V X1 = a7 - a8, X2 = a11 - a12;
+    const V Y1 = a7 + a8, Y2 = a15 - a16;
+    const V Z1 = a11 + a12, Z2 = a15 + a16;
+    const V Ex = X1 + X2, Ey = Y1 + Y2, Ez = Z1 + Z2;
+    const V jx = a1 + Ex, jy = a3 + Ey, jz = a5 + Ez;
 
-    const float tsx = g[1] + g[2], tax = g[1] - g[2];
-    const float tsy = g[3] + g[4], tay = g[3] - g[4];
-    const float tsz = g[5] + g[6], taz = g[5] - g[6];
-    const float tsm = tsx + tsy + tsz;
-    const float T = g[0] + tsm;
+    const V tsx = g[1] + g[2], tax = g[1] - g[2];
+    const V tsy = g[3] + g[4], tay = g[3] - g[4];
+    const V tsz = g[5] + g[6], taz = g[5] - g[6];
+    const V tsm = (tsx + tsy) + tsz;
+    const V T = g[0] + tsm;
 
-    const float rho = 1.0f + drho;
-    const float ir = 1.0f / rho;
-    const float vx = jx * ir, vy = jy * ir, vz = jz * ir;
-    const float jxx = jx * jx, jyy = jy * jy, jzz = jz * jz;
-    const float jj = jxx + jyy + jzz;
+    const V rho = drho + V(1.0f);
+    const V ir = recip(rho);
+    const V vx = jx * ir, vy = jy * ir, vz = jz * ir;
+    const V njx = jx * V(-1.0f), njy = jy * V(-1.0f), njz = jz * V(-1.0f);
+    const V jj = fma(jx, jx, fma(jy, jy, jz * jz));  // |j|^2
+    const V pww = fma(jy, jy, njz * jz);             // jy^2 - jz^2
 
     // ---- non-equilibrium parts m_k - m_k^eq (Eq. (24), rho0 = 1; the rest
-    // moments of w cancel between m and m^eq)
-    const float n1 = (-30.0f * d[0] - 11.0f * SF + 8.0f * SE) - (-11.0f * drho + 19.0f * jj);
-    const float n2 = (12.0f * d[0] - 4.0f * SF + SE) - (3.0f * drho - 5.5f * jj);
-    const float n4 = (-4.0f * a1 + Ex) + (2.0f / 3.0f) * jx;
-    const float n6 = (-4.0f * a3 + Ey) + (2.0f / 3.0f) * jy;
-    const float n8 = (-4.0f * a5 + Ez) + (2.0f / 3.0f) * jz;
-    const float s35 = s3 + s5, AB = A + B;
-    const float pxx = 2.0f * jxx - (jyy + jzz);
-    const float n9 = (2.0f * s1 - s35 + AB - 2.0f * Cyz) - pxx;
-    const float n10 = (-4.0f * s1 + 2.0f * s35 + AB - 2.0f * Cyz) + 0.5f * pxx;
-    const float d35 = s3 - s5, dAB = A - B;
-    const float pww = jyy - jzz;
-    const float n11 = (d35 + dAB) - pww;
-    const float n12 = (-2.0f * d35 + dAB) + 0.5f * pww;
-    const float n13 = (s7 - s8) - jx * jy;
-    const float n14 = (s15 - s16) - jy * jz;
-    const float n15 = (s11 - s12) - jx * jz;
-    const float n16 = X1 - X2, n17 = Y2 - Y1, n18 = Z1 - Z2;
+    // moments of w cancel between m and m^eq).  With drho = d0 + SF + SE:
+    //   m1 = -30 d0 - 11 SF + 8 SE,  m1eq = -11 drho + 19 jj
+    //   m2 = 12 d0 - 4 SF + SE,      m2eq = 3 drho - 11/2 jj
+    //   m4 = -4 a1 + Ex,             m4eq = -2/3 jx   (m6, m8 alike)
+    //   m9 = 3 (s1 - Cyz) + SE - SF, m9eq = 3 jx^2 - jj
+    //   m10 = -6 s1 - 3 Cyz + 2 SF + SE, m10eq = -m9eq / 2
+    //   m11 = (s3 - s5) + (A - B),   m11eq = jy^2 - jz^2
+    //   m12 = -2 (s3 - s5) + (A - B), m12eq = -m11eq / 2
+    //   m13 = s7 - s8 (m14 = s15 - s16, m15 = s11 - s12), m13eq = jx jy
+    const V n1 = V(19.0f) * ((SE - d[0]) - jj);
+    const V n2 = fma(V(9.0f), d[0], fma(V(-7.0f), SF, fma(V(-2.0f), SE, V(5.5f) * jj)));
+    const V n4 = V(5.0f / 3.0f) * fma(V(-2.0f), a1, Ex);
+    const V n6 = V(5.0f / 3.0f) * fma(V(-2.0f), a3, Ey);
+    const V n8 = V(5.0f / 3.0f) * fma(V(-2.0f), a5, Ez);
+    const V n9 = fma(V(3.0f), fma(njx, jx, s1 - Cyz), (SE - SF) + jj);
+    const V n10 = fma(V(-6.0f), s1,
+                      fma(V(-3.0f), Cyz, fma(V(1.5f), jx * jx, fma(V(-0.5f), jj, fma(V(2.0f), SF, SE)))));
+    const V d35 = s3 - s5, dAB = A - B;
+    const V n11 = (d35 + dAB) - pww;
+    const V n12 = fma(V(-2.0f), d35, fma(V(0.5f), pww, dAB));
+    const V n13 = fma(njx, jy, s7 - s8);
+    const V n14 = fma(njy, jz, s15 - s16);
+    const V n15 = fma(njx, jz, s11 - s12);
+    const V n16 = X1 - X2, n17 = Y2 - Y1, n18 = Z1 - Z2;
 
     // ---- buoyancy in moment space.  With G = (0, 0, G_z) (Eq. (16)) and
     // F_i = G_z (e_iz - V_z) f_eq,i / c_s^2 (Eqs. (15), (17)), the moments
@@ -87,107 +103,129 @@ __device__ __forceinline__ void collide_pairs(const CollideParams &C, float d[19
     //   F^_13 = -3 gv V_x V_y   F^_14 = g V_y (1 - 3 V_z^2)   F^_15 = g V_x (1 - 3 V_z^2)
     //   F^_16 = -3 gv V_x       F^_17 = 3 gv V_y              F^_18 = 3/2 g (V_x^2 - V_y^2)
     // and F^_0 = F^_3 = F^_5 = 0 (the D3Q19 moments of f_eq up to fourth
-    // order are the isotropic ones, which makes these sums exact).
-    const float gr = C.gbeta * (T - C.theta_ref) * rho;
-    const float gv = gr * vz;
-    const float vxx = vx * vx, vyy = vy * vy, vzz = vz * vz;
-    const float vv = vxx + vyy + vzz;
-    const float F1 = gv * (38.0f - 57.0f * vv);
-    const float F2 = gv * (16.5f * vv - 11.0f);
-    const float F4 = 5.0f * gv * vx;
-    const float F6 = 5.0f * gv * vy;
-    const float F7 = gr;
-    const float F8 = gr * (2.5f * (vxx + vyy) - 2.0f / 3.0f);
-    const float F9 = -gv * (6.0f * vxx - 3.0f * (vyy + vzz) + 2.0f);
-    const float F11 = -gv * (3.0f * (vyy - vzz) + 2.0f);
-    const float F13 = -3.0f * gv * vx * vy;
-    const float t1z = 1.0f - 3.0f * vzz;
-    const float F14 = gr * vy * t1z;
-    const float F15 = gr * vx * t1z;
-    const float F16 = -3.0f * gv * vx;
-    const float F17 = 3.0f * gv * vy;
-    const float F18 = 1.5f * gr * (vxx - vyy);
+    // order are the isotropic ones, which makes these sums exact).  Below,
+    // f_k = -F^_k / |M_k|^2 (norms 2394, 252, 40, 40, 10, 40, 36, 144, 12,
+    // 48, 4, 4, 4, 8, 8, 8) with the constants folded in.
+    const V gr = (V(C.gbeta) * (T - V(C.theta_ref))) * rho;
+    const V gv = gr * vz;
+    const V vxy = fma(vx, vx, vy * vy);                  // V_x^2 + V_y^2
+    const V vv = fma(vz, vz, vxy);                       // V^2
+    const V dxy = fma(vx, vx, (vy * V(-1.0f)) * vy);     // V_x^2 - V_y^2
+    const V dyz = fma(vy, vy, (vz * V(-1.0f)) * vz);     // V_y^2 - V_z^2
+    const V gvx = gv * vx, gvy = gv * vy;
+    const V f1 = gv * fma(V(57.0f / 2394.0f), vv, V(-38.0f / 2394.0f));
+    const V f2 = gv * fma(V(-16.5f / 252.0f), vv, V(11.0f / 252.0f));
+    const V f4 = gvx * V(-0.125f);
+    const V f6 = gvy * V(-0.125f);
+    const V f8 = gr * fma(V(-0.0625f), vxy, V(1.0f / 60.0f));
+    const V f9 = gv * fma(V(0.25f), vx * vx, fma(V(-1.0f / 12.0f), vv, V(1.0f / 18.0f)));
+    const V f11 = gv * fma(V(0.25f), dyz, V(1.0f / 6.0f));
+    const V f13 = (gvx * vy) * V(0.75f);
+    const V grz = gr * fma(V(0.75f), vz * vz, V(-0.25f));
+    const V f16 = gvx * V(0.375f);
+    const V f17 = gvy * V(-0.375f);
+    const V f18 = (gr * V(-0.1875f)) * dxy;
 
     // ---- b_k = (s_k (m_k - m_k^eq) - F^_k) / |M_k|^2  (rates come divided)
-    const float b1 = fmaf(C.rs[1], n1, F1 * (-1.0f / 2394.0f));
-    const float b2 = fmaf(C.rs[2], n2, F2 * (-1.0f / 252.0f));
-    const float b4 = fmaf(C.rs[4], n4, F4 * (-1.0f / 40.0f));
-    const float b6 = fmaf(C.rs[6], n6, F6 * (-1.0f / 40.0f));
-    const float b7 = F7 * (-1.0f / 10.0f);
-    const float b8 = fmaf(C.rs[8], n8, F8 * (-1.0f / 40.0f));
-    const float b9 = fmaf(C.rs[9], n9, F9 * (-1.0f / 36.0f));
-    const float b10 = fmaf(C.rs[10], n10, F9 * (1.0f / 144.0f));
-    const float b11 = fmaf(C.rs[11], n11, F11 * (-1.0f / 12.0f));
-    const float b12 = fmaf(C.rs[12], n12, F11 * (1.0f / 48.0f));
-    const float b13 = fmaf(C.rs[13], n13, F13 * -0.25f);
-    const float b14 = fmaf(C.rs[14], n14, F14 * -0.25f);
-    const float b15 = fmaf(C.rs[15], n15, F15 * -0.25f);
-    const float b16 = fmaf(C.rs[16], n16, F16 * -0.125f);
-    const float b17 = fmaf(C.rs[17], n17, F17 * -0.125f);
-    const float b18 = fmaf(C.rs[18], n18, F18 * -0.125f);
+    const V b1 = fma(V(C.rs[1]), n1, f1);
+    const V b2 = fma(V(C.rs[2]), n2, f2);
+    const V b4 = fma(V(C.rs[4]), n4, f4);
+    const V b6 = fma(V(C.rs[6]), n6, f6);
+    const V b7 = gr * V(-0.1f);
+    const V b8 = fma(V(C.rs[8]), n8, f8);
+    const V b9 = fma(V(C.rs[9]), n9, f9);
+    const V b10 = fma(V(C.rs[10]), n10, f9 * V(-0.25f));
+    const V b11 = fma(V(C.rs[11]), n11, f11);
+    const V b12 = fma(V(C.rs[12]), n12, f11 * V(-0.25f));
+    const V b13 = fma(V(C.rs[13]), n13, f13);
+    const V b14 = fma(V(C.rs[14]), n14, grz * vy);
+    const V b15 = fma(V(C.rs[15]), n15, grz * vx);
+    const V b16 = fma(V(C.rs[16]), n16, f16);
+    const V b17 = fma(V(C.rs[17]), n17, f17);
+    const V b18 = fma(V(C.rs[18]), n18, f18);
 
     // ---- back-transform f* = f - M^T b, one even (E) and one odd (O) partial
     // sum per pair: f*_i = f_i - (E + O), f*_opp = f_opp - (E - O)
-    d[0] -= -30.0f * b1 + 12.0f * b2;
-    const float F0 = -11.0f * b1 - 4.0f * b2;  // every face
-    const float G0 = 8.0f * b1 + b2;           // every edge
-    const float Pf = 2.0f * b10 - b9, Qf = b11 - 2.0f * b12;
-    const float Efx = F0 + 2.0f * b9 - 4.0f * b10;
-    const float Efy = F0 + Pf + Qf, Efz = F0 + Pf - Qf;
-    const float Ofx = -4.0f * b4, Ofy = -4.0f * b6, Ofz = b7 - 4.0f * b8;
-    d[1] -= Efx + Ofx;
-    d[2] -= Efx - Ofx;
-    d[3] -= Efy + Ofy;
-    d[4] -= Efy - Ofy;
-    d[5] -= Efz + Ofz;
-    d[6] -= Efz - Ofz;
+    d[0] = fma(V(30.0f), b1, fma(V(-12.0f), b2, d[0]));
+    const V F0 = fma(V(-11.0f), b1, V(-4.0f) * b2);  // every face
+    const V G0 = fma(V(8.0f), b1, b2);               // every edge
+    const V Efx = fma(V(2.0f), b9, fma(V(-4.0f), b10, F0));
+    const V F0P = fma(V(2.0f), b10, F0 - b9);
+    const V Qf = fma(V(-2.0f), b12, b11);
+    const V Efy = F0P + Qf, Efz = F0P - Qf;
+    const V Ofz = fma(V(-4.0f), b8, b7);  // odd parts of x, y: -4 b4, -4 b6
+    d[1] = fma(V(4.0f), b4, d[1] - Efx);
+    d[2] = fma(V(-4.0f), b4, d[2] - Efx);
+    d[3] = fma(V(4.0f), b6, d[3] - Efy);
+    d[4] = fma(V(-4.0f), b6, d[4] - Efy);
+    d[5] = (d[5] - Efz) - Ofz;
+    d[6] = (d[6] - Efz) + Ofz;
 
-    const float H = b9 + b10, K = b11 + b12;
-    const float Exy = G0 + H + K, Exz = G0 + H - K, Eyz = G0 - 2.0f * H;
-    const float b78 = b7 + b8;
-    const float E7 = Exy + b13, O7 = (b4 + b6) + (b16 - b17);        // (1,1,0)
-    const float E8 = Exy - b13, O8 = (b6 - b4) - (b16 + b17);        // (-1,1,0)
-    const float E11 = Exz + b15, O11 = (b78 + b4) + (b18 - b16);     // (1,0,1)
-    const float E12 = Exz - b15, O12 = (b78 - b4) + (b16 + b18);     // (-1,0,1)
-    const float E15 = Eyz + b14, O15 = (b78 + b6) + (b17 - b18);     // (0,1,1)
-    const float E16 = Eyz - b14, O16 = (b78 - b6) - (b17 + b18);     // (0,-1,1)
-    d[7] -= E7 + O7;
-    d[10] -= E7 - O7;
-    d[8] -= E8 + O8;
-    d[9] -= E8 - O8;
-    d[11] -= E11 + O11;
-    d[14] -= E11 - O11;
-    d[12] -= E12 + O12;
-    d[13] -= E12 - O12;
-    d[15] -= E15 + O15;
-    d[18] -= E15 - O15;
-    d[16] -= E16 + O16;
-    d[17] -= E16 - O16;
+    const V H = b9 + b10, K = b11 + b12;
+    const V G0H = G0 + H;
+    const V Exy = G0H + K, Exz = G0H - K, Eyz = fma(V(-2.0f), H, G0);
+    const V b78 = fma(gr, V(-0.1f), b8);  // b7 + b8
+    const V E7 = Exy + b13, O7 = (b4 + b6) + (b16 - b17);        // (1,1,0)
+    const V E8 = Exy - b13, O8 = (b6 - b4) - (b16 + b17);        // (-1,1,0)
+    const V E11 = Exz + b15, O11 = (b78 + b4) + (b18 - b16);     // (1,0,1)
+    const V E12 = Exz - b15, O12 = (b78 - b4) + (b16 + b18);     // (-1,0,1)
+    const V E15 = Eyz + b14, O15 = (b78 + b6) + (b17 - b18);     // (0,1,1)
+    const V E16 = Eyz - b14, O16 = (b78 - b6) - (b17 + b18);     // (0,-1,1)
+    d[7] = (d[7] - E7) - O7;
+    d[10] = (d[10] - E7) + O7;
+    d[8] = (d[8] - E8) - O8;
+    d[9] = (d[9] - E8) + O8;
+    d[11] = (d[11] - E11) - O11;
+    d[14] = (d[14] - E11) + O11;
+    d[12] = (d[12] - E12) - O12;
+    d[13] = (d[13] - E12) + O12;
+    d[15] = (d[15] - E15) - O15;
+    d[18] = (d[18] - E15) + O15;
+    d[16] = (d[16] - E16) - O16;
+    d[17] = (d[17] - E16) + O16;
 
-    // ---- energy: n - n^eq with n^eq = (T, V T, 3/4 T, 0, 0) (Eqs. (33),(34))
-    const float e1 = tax - vx * T, e2 = tay - vy * T, e3 = taz - vz * T;
-    float c1, c2, c3;
+    // ---- energy: n - n^eq with n^eq = (T, V T, 3/4 T, 0, 0) (Eqs. (33),(34)).
+    // The flux parts e = (ta - V T) relax with Q's flux block; with
+    // T = g0 + tsm the even parts are c4 = q4 (21/4 g0 - 7/4 tsm),
+    // c5 = q5 (3 tsx - tsm), c6 = q6 (tsy - tsz) (rates divided by the norms),
+    // and the back-transform subtracts, per pair, an even part (2 c5 - c4 for
+    // x, c6 - c4 - c5 for y, -(c4 + c5 + c6) for z) and +-the relaxed flux.
+    const V nT = T * V(-1.0f);
+    const V e1 = fma(vx, nT, tax), e2 = fma(vy, nT, tay), e3 = fma(vz, nT, taz);
+    const V u4 = fma(V(5.25f), g[0], V(-1.75f) * tsm);
+    const V u5 = fma(V(3.0f), tsx, tsm * V(-1.0f));
+    const V u6 = tsy - tsz;
+    const V c4 = V(C.rq[4]) * u4, nc4 = V(-C.rq[4]) * u4;
+    g[0] = fma(V(-6.0f), c4, g[0]);
+    const V Etx = fma(V(2.0f * C.rq[5]), u5, nc4);     // 2 c5 - c4
+    const V c45 = fma(V(C.rq[5]), u5, c4);             // c4 + c5
+    const V nc45 = fma(V(-C.rq[5]), u5, nc4);          // -(c4 + c5)
+    const V Ety = fma(V(C.rq[6]), u6, nc45);           // c6 - c4 - c5
+    const V P = fma(V(C.rq[6]), u6, c45);              // c4 + c5 + c6
     if (C.aniso) {  // uniform: the full flux block of Q (Eq. (35))
-        c1 = fmaf(C.qa[0], e1, fmaf(C.qa[1], e2, C.qa[2] * e3));
-        c2 = fmaf(C.qa[3], e1, fmaf(C.qa[4], e2, C.qa[5] * e3));
-        c3 = fmaf(C.qa[6], e1, fmaf(C.qa[7], e2, C.qa[8] * e3));
+        const V c1 = fma(V(C.qa[0]), e1, fma(V(C.qa[1]), e2, V(C.qa[2]) * e3));
+        const V c2 = fma(V(C.qa[3]), e1, fma(V(C.qa[4]), e2, V(C.qa[5]) * e3));
+        const V c3 = fma(V(C.qa[6]), e1, fma(V(C.qa[7]), e2, V(C.qa[8]) * e3));
+        g[1] = (g[1] - Etx) - c1;
+        g[2] = (g[2] - Etx) + c1;
+        g[3] = (g[3] - Ety) - c2;
+        g[4] = (g[4] - Ety) + c2;
+        g[5] = (g[5] + P) - c3;
+        g[6] = (g[6] + P) + c3;
     } else {
-        c1 = C.rq[1] * e1;
-        c2 = C.rq[2] * e2;
-        c3 = C.rq[3] * e3;
+        g[1] = fma(V(-C.rq[1]), e1, g[1] - Etx);
+        g[2] = fma(V(C.rq[1]), e1, g[2] - Etx);
+        g[3] = fma(V(-C.rq[2]), e2, g[3] - Ety);
+        g[4] = fma(V(C.rq[2]), e2, g[4] - Ety);
+        g[5] = fma(V(-C.rq[3]), e3, g[5] + P);
+        g[6] = fma(V(C.rq[3]), e3, g[6] + P);
     }
-    const float c4 = C.rq[4] * (6.0f * g[0] - tsm - 0.75f * T);
-    const float c5 = C.rq[5] * (2.0f * tsx - (tsy + tsz));
-    const float c6 = C.rq[6] * (tsy - tsz);
-    g[0] -= 6.0f * c4;
-    const float Etx = 2.0f * c5 - c4;
-    const float Ety = c6 - c4 - c5, Etz = -c4 - c5 - c6;
-    g[1] -= Etx + c1;
-    g[2] -= Etx - c1;
-    g[3] -= Ety + c2;
-    g[4] -= Ety - c2;
-    g[5] -= Etz + c3;
-    g[6] -= Etz - c3;
+}
+
+// One cell per thread: the float form of collide().
+__device__ __forceinline__ void collide_pairs(const CollideParams &C, float d[19], float g[7])
+{
+    collide<float>(C, d, g);
 }
 
 // Neighbour / bounce-back offsets of the 26 planes: from the launch-parameter
@@ -257,7 +295,7 @@ __device__ __forceinline__ void pull_offsets(const T *__restrict__ src, const Of
         d[i] = Store<T>::ld(src + (self + (out ? O.template bb<i>() : O.template nb<i>())));
     });
     g[0] = Store<T>::ld(src + (self + O.template nb<19>()));
-    const float th_lin = 0.5f - (static_cast<float>(y) + 0.5f) * inv_ny;
+    const float th_lin = theta_linear(y, inv_ny);
     static_for<1, 7>([&](auto I) {
         constexpr int i = decltype(I)::value;
         constexpr int ex = q7_ex(i), ey = q7_ey(i);

@@ -37,7 +37,8 @@ class DmrtError(RuntimeError):
 
 class dmrt_opts(ctypes.Structure):
     _fields_ = [("storage", ctypes.c_int), ("residual_interval", ctypes.c_int),
-                ("rounding", ctypes.c_int), ("streaming", ctypes.c_int)]
+                ("rounding", ctypes.c_int), ("streaming", ctypes.c_int),
+                ("cells_per_thread", ctypes.c_int)]
 
 
 class dmrt_params(ctypes.Structure):
@@ -47,7 +48,7 @@ class dmrt_params(ctypes.Structure):
                 ("nu", ctypes.c_double), ("alpha", ctypes.c_double), ("gbeta", ctypes.c_double),
                 ("tau_nu", ctypes.c_double), ("tau_alpha", ctypes.c_double),
                 ("steps", ctypes.c_long), ("streaming", ctypes.c_int),
-                ("device_bytes", ctypes.c_longlong)]
+                ("device_bytes", ctypes.c_longlong), ("cells_per_thread", ctypes.c_int)]
 
 
 class dmrt_stats(ctypes.Structure):
@@ -205,11 +206,11 @@ def check(h, status: int, what: str, ensemble: bool = False, surrogate: bool = F
 
 def dmrt_create(grid, Ra: float, Pr: float = 0.71, Ma: float = 0.1, wall_type: int = 1,
                 storage: int = STORE_F32, residual_interval: int = 0, rounding: int = ROUND_AUTO,
-                streaming: int = STREAM_AB):
+                streaming: int = STREAM_AB, cells_per_thread: int = 0):
     L = load()
     h = ctypes.c_void_p()
     g = (ctypes.c_int * 3)(*grid)
-    opts = dmrt_opts(storage, residual_interval, rounding, streaming)
+    opts = dmrt_opts(storage, residual_interval, rounding, streaming, cells_per_thread)
     check(None, L.dmrt_create_ex(ctypes.byref(h), g, Ra, Pr, Ma, wall_type, ctypes.byref(opts)),
           "dmrt_create")
     return h
@@ -217,11 +218,12 @@ def dmrt_create(grid, Ra: float, Pr: float = 0.71, Ma: float = 0.1, wall_type: i
 
 def dmrt_create_lattice(grid, nu: float, alpha: float, gbeta: float, wall_type: int = 1,
                         storage: int = STORE_F32, residual_interval: int = 0,
-                        rounding: int = ROUND_AUTO, streaming: int = STREAM_AB):
+                        rounding: int = ROUND_AUTO, streaming: int = STREAM_AB,
+                        cells_per_thread: int = 0):
     L = load()
     h = ctypes.c_void_p()
     g = (ctypes.c_int * 3)(*grid)
-    opts = dmrt_opts(storage, residual_interval, rounding, streaming)
+    opts = dmrt_opts(storage, residual_interval, rounding, streaming, cells_per_thread)
     check(None, L.dmrt_create_lattice(ctypes.byref(h), g, nu, alpha, gbeta, wall_type,
                                       ctypes.byref(opts)), "dmrt_create_lattice")
     return h
@@ -389,7 +391,7 @@ class Cavity:
 
     def __init__(self, grid, Ra=None, Pr=0.71, Ma=0.1, wall_type=1, *, lattice=None,
                  storage=STORE_F32, residual_interval=0, rounding=ROUND_AUTO,
-                 streaming=STREAM_AB):
+                 streaming=STREAM_AB, cells_per_thread=0):
         self.grid = tuple(int(v) for v in grid)
         nx, ny, nz = self.grid
         self.shape = (nz, ny, nx)
@@ -397,10 +399,10 @@ class Cavity:
         if lattice is not None:
             nu, alpha, gbeta = lattice
             self.h = dmrt_create_lattice(self.grid, nu, alpha, gbeta, wall_type, storage,
-                                         residual_interval, rounding, streaming)
+                                         residual_interval, rounding, streaming, cells_per_thread)
         else:
             self.h = dmrt_create(self.grid, Ra, Pr, Ma, wall_type, storage, residual_interval,
-                                 rounding, streaming)
+                                 rounding, streaming, cells_per_thread)
 
     def close(self):
         if getattr(self, "h", None):

@@ -44,6 +44,13 @@ def test_create_rejects_bad_arguments_without_touching_the_gpu(grid, Ra, Pr, Ma,
     assert ei.value.status == dmrt.ERR_ARG
 
 
+def test_cells_per_thread_out_of_range_is_rejected_without_touching_the_gpu():
+    for cpt in (-1, 3):
+        with pytest.raises(dmrt.DmrtError) as ei:
+            dmrt.dmrt_create((8, 8, 8), 1e4, cells_per_thread=cpt)
+        assert ei.value.status == dmrt.ERR_ARG
+
+
 def test_create_lattice_rejects_nonpositive_transport():
     for nu, alpha in ((0.0, 0.1), (0.1, -1.0), (float("nan"), 0.1)):
         with pytest.raises(dmrt.DmrtError) as ei:
