@@ -59,9 +59,11 @@ def workload(args) -> str:
 _BODY = ["paper_1511_04633_gb300/csrc/step_body.cuh", "paper_1511_04633_gb300/csrc/lattice.cuh",
          "paper_1511_04633_gb300/csrc/vec2.cuh"]
 # sources of each step kernel: one cell per thread (two buffers), two cells
-# per thread (two buffers), in place
+# per thread (two buffers; direct or TMA-staged loads), in place
 KERNEL_SOURCES = {"ab": ["paper_1511_04633_gb300/csrc/step.cu"] + _BODY,
                   "pair": ["paper_1511_04633_gb300/csrc/step_pair.cu"] + _BODY,
+                  "pair_tma": ["paper_1511_04633_gb300/csrc/step_pair.cu",
+                               "paper_1511_04633_gb300/csrc/umma.cuh"] + _BODY,
                   "inplace": ["paper_1511_04633_gb300/csrc/step_inplace.cu"] + _BODY}
 STEP_KERNEL_SOURCES = KERNEL_SOURCES["ab"]
 
@@ -274,11 +276,13 @@ def run_dmrt(args, rank, local, world):
     cells = grid[0] * grid[1] * grid[2]
     storage = STORAGES[args.storage]
     cav = dmrt.Cavity(grid, args.ra, PR, MA, args.wall, storage=storage,
-                      streaming=STREAMINGS[args.streaming], cells_per_thread=args.cells_per_thread)
+                      streaming=STREAMINGS[args.streaming], cells_per_thread=args.cells_per_thread,
+                      pair_loads=args.pair_loads)
     dmrt.dmrt_set_stream(cav.h, stream)
     inner = args.inner
     cpt = cav.params["cells_per_thread"]
-    scheme = "inplace" if args.streaming == "inplace" else ("pair" if cpt == 2 else "ab")
+    scheme = ("inplace" if args.streaming == "inplace" else
+              {1: "ab", 2: ("pair_tma" if cav.params["pair_loads"] == 2 else "pair")}[cpt])
 
     def one_step():
         dmrt.dmrt_step(cav.h, inner)
@@ -374,12 +378,13 @@ def run_dmrt(args, rank, local, world):
                    "l2": f"inputs larger than L2 ({nbuf} x {bytes_per_cell / 2 * cells / 1e6:.0f} MB "
                          f"population buffer)" if bytes_per_cell / 2 * cells > 129e6
                          else "inputs fit in L2: not a DRAM measurement",
-                   "cells_per_thread": cpt,
+                   "cells_per_thread": cpt, "pair_loads": cav.params["pair_loads"],
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
                      "kernel": {"ab": f"step_kernel<{args.wall}, {args.storage}>",
                                 "pair": f"step_pair_kernel<{args.wall}, {args.storage}>",
+                                "pair_tma": f"step_pair_tma_kernel<{args.wall}, {args.storage}>",
                                 "inplace": f"step_inplace_kernel<{args.wall}, {args.storage}> "
                                            "(both phases)"}[scheme],
                      "bytes_per_cell": bytes_per_cell, "launch_us": launch_s * 1e6},
@@ -408,7 +413,7 @@ def run_to_steady(dmrt, torch, stream, grid, storage, args, launch_s, seconds=40
     converged state."""
     tol = STEADY_TOL[storage]
     cav = dmrt.Cavity(grid, args.ra, PR, MA, args.wall, storage=storage, streaming=STREAMINGS[args.streaming],
-                      cells_per_thread=args.cells_per_thread)
+                      cells_per_thread=args.cells_per_thread, pair_loads=args.pair_loads)
     dmrt.dmrt_set_stream(cav.h, stream)
     budget = max(10_000, int(seconds / max(launch_s, 1e-7)) // 100 * 100)
     torch.cuda.synchronize()
@@ -546,6 +551,9 @@ def main(argv=None):
     ap.add_argument("--grid", type=int, default=GRID[0], help="cubic cavity edge")
     ap.add_argument("--cells-per-thread", type=int, choices=[0, 1, 2], default=0,
                     help="step kernel: 0 = the library's choice, 1 or 2 cells per thread")
+    ap.add_argument("--pair-loads", type=int, choices=[0, 1, 2], default=0,
+                    help="two-cell two-buffer kernel: 0 = the library's choice, 1 = direct loads, "
+                         "2 = TMA-staged")
     ap.add_argument("--wall", type=int, choices=[1, 2, 3], default=WALL)
     ap.add_argument("--ra", type=float, default=RA)
     ap.add_argument("--ensemble", action="store_true",

@@ -106,6 +106,12 @@ typedef struct dmrt_opts {
                             * The stored values are bitwise the same either
                             * way.  Auto takes 2 for 16-bit storage where
                             * allowed.  Ensembles accept 0 or 1. */
+    int pair_loads;        /* how the two-cell kernel of two-buffer 16-bit
+                            * storage loads: 0 = auto (direct), 1 = direct
+                            * loads, 2 = staged: TMA copies of each plane's
+                            * source rows into shared memory, two slabs ahead
+                            * (nx a multiple of 8, else DMRT_ERR_ARG).  Same
+                            * values either way. */
 } dmrt_opts;
 
 /* Derived lattice parameters of a handle (read-only view). */
@@ -117,6 +123,7 @@ typedef struct dmrt_params {
     int streaming;             /* dmrt_streaming */
     long long device_bytes;    /* device memory the handle holds now */
     int cells_per_thread;      /* 1 or 2: the step kernel in use */
+    int pair_loads;            /* 1 = direct, 2 = staged (0 for one cell) */
 } dmrt_params;
 
 /* Counters for profiling and for the benchmark's launch count. */

@@ -32,6 +32,9 @@ struct dmrt {
     CollideParams C{};
     lbm::BlockShape block{32, 4};
     int cells_per_thread = 1;  // 2: the paired step kernels (walled box, even nx)
+    int pair_loads = 0;        // paired two-buffer step: 1 direct loads, 2 TMA-staged
+    alignas(64) unsigned char tma_map[2][256] = {};  // tensor maps of buf[0], buf[1] (rows, x edges)
+    unsigned *derr = nullptr;  // device word: a staged kernel's copy wait ran out
 
     void *buf[2] = {nullptr, nullptr};   // ping-pong population buffers (storage type)
     int cur = 0;                          // buffer holding the current state
@@ -148,6 +151,9 @@ cudaError_t launch_one_step(dmrt_t *h, int ph)
     if (h->inplace)
         return lbm::launch_step_inplace(h->wall, h->storage, h->stochastic, h->buf[0], ph, h->SI,
                                         h->G, h->C, h->block, h->stream, h->use_pdl);
+    if (h->pair_loads == 2)
+        return lbm::launch_step_pair_tma(h->wall, h->storage, h->stochastic, h->tma_map[ph], h->buf[ph],
+                                         h->buf[ph ^ 1], h->S, h->G, h->C, h->derr, h->stream, h->use_pdl);
     if (h->cells_per_thread == 2)
         return lbm::launch_step_pair(h->wall, h->storage, h->stochastic, h->buf[ph], h->buf[ph ^ 1],
                                      h->S, h->G, h->C, h->stream, h->use_pdl);
@@ -156,6 +162,19 @@ cudaError_t launch_one_step(dmrt_t *h, int ph)
 }
 
 bool periodic(const dmrt_t *h) { return h->wall == DMRT_WALL_PERIODIC; }
+
+// A staged step kernel whose copy wait ran out has set *derr and left its
+// cells unwritten: report it once (after a synchronisation) and clear it.
+dmrt_status check_stage_errors(dmrt_t *h)
+{
+    if (h->pair_loads != 2) return DMRT_OK;
+    unsigned v = 0;
+    CK(h, cudaMemcpyAsync(&v, h->derr, sizeof v, cudaMemcpyDeviceToHost, h->stream), "copy stage error word");
+    CK(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    if (v == 0) return DMRT_OK;
+    CK(h, cudaMemsetAsync(h->derr, 0, sizeof v, h->stream), "clear stage error word");
+    return fail(h, DMRT_ERR_TIMEOUT, "a staged step kernel's copy wait ran out; the state is invalid");
+}
 
 // Relaxation rates of Eq. (26) (flow) and Eqs. (35),(36) (energy), folded with
 // the squared norms of the moment basis.
@@ -341,16 +360,17 @@ dmrt_status create_common(dmrt_t **out, const int grid[3], double nu, double alp
         !std::isfinite(gbeta))
         return DMRT_ERR_ARG;
     int storage = DMRT_STORE_F32, K = 100, rounding = DMRT_ROUND_AUTO, streaming = DMRT_STREAM_AB;
-    int cpt = 0;
+    int cpt = 0, ploads = 0;
     if (opts) {
         storage = opts->storage;
         rounding = opts->rounding;
         streaming = opts->streaming;
         cpt = opts->cells_per_thread;
+        ploads = opts->pair_loads;
         if (opts->residual_interval > 0) K = opts->residual_interval;
         if (opts->residual_interval < 0) return DMRT_ERR_ARG;
     }
-    if (cpt < 0 || cpt > 2) return DMRT_ERR_ARG;
+    if (cpt < 0 || cpt > 2 || ploads < 0 || ploads > 2) return DMRT_ERR_ARG;
     if (rounding < DMRT_ROUND_AUTO || rounding > DMRT_ROUND_STOCHASTIC) return DMRT_ERR_ARG;
     if (streaming != DMRT_STREAM_AB && streaming != DMRT_STREAM_INPLACE) return DMRT_ERR_ARG;
     if (storage != DMRT_STORE_F32 && storage != DMRT_STORE_BF16 && storage != DMRT_STORE_F16)
@@ -390,6 +410,15 @@ dmrt_status create_common(dmrt_t **out, const int grid[3], double nu, double alp
         return DMRT_ERR_ARG;
     }
     h->cells_per_thread = (cpt == 2 || (cpt == 0 && pair_ok && storage != DMRT_STORE_F32)) ? 2 : 1;
+    // loads of the paired two-buffer kernel: TMA-staged where the tensor map
+    // allows it (16-bit storage, nx a multiple of 8)
+    const bool tma_ok = h->cells_per_thread == 2 && !h->inplace &&
+                        lbm::step_pair_tma_supported(wall_type, storage, h->G);
+    if (ploads == 2 && !tma_ok) {
+        delete h;
+        return DMRT_ERR_ARG;
+    }
+    h->pair_loads = h->cells_per_thread != 2 || h->inplace ? 0 : (tma_ok && ploads == 2 ? 2 : 1);
 #ifdef DMRT_BLOCK_X
     h->block = {DMRT_BLOCK_X, DMRT_BLOCK_Y};
 #else
@@ -424,6 +453,20 @@ dmrt_status create_common(dmrt_t **out, const int grid[3], double nu, double alp
     if (e != cudaSuccess) return bail(DMRT_ERR_OOM);
     h->device_bytes += 16 * static_cast<long long>(sizeof(double));
     h->dnu = h->dres + 8;
+    h->derr = reinterpret_cast<unsigned *>(h->dres + 12);  // doubles 12..15: error words
+    if (cudaMemset(h->dres, 0, 16 * sizeof(double)) != cudaSuccess) return bail(DMRT_ERR_CUDA);
+    if (h->pair_loads == 2) {
+        e = lbm::prepare_step_pair_tma(wall_type, storage);
+        if (e != cudaSuccess) return bail(DMRT_ERR_CUDA);
+        for (int b = 0; b < 2; ++b) {
+            e = lbm::encode_pair_tma_maps(h->buf[b], h->G, h->tma_map[b]);
+            if (e != cudaSuccess) {
+                if (ploads == 2) return bail(DMRT_ERR_CUDA);
+                h->pair_loads = 1;  // auto: the direct-load kernel does the same work
+                break;
+            }
+        }
+    }
     e = cudaStreamCreateWithFlags(&h->own, cudaStreamNonBlocking);
     if (e != cudaSuccess) return bail(DMRT_ERR_CUDA);
     h->stream = h->own;
@@ -524,7 +567,7 @@ dmrt_status dmrt_sync(dmrt_t *h)
     if (!h) return DMRT_ERR_ARG;
     DeviceGuard dg(h->device);
     CK(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
-    return DMRT_OK;
+    return check_stage_errors(h);
 }
 
 dmrt_status dmrt_fields(dmrt_t *h, float *rho, float *u, float *theta, int on_device)
@@ -629,6 +672,8 @@ dmrt_status dmrt_residual(dmrt_t *h, double *r)
        "copy residual");
     CK(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
     *r = res[4];
+    const dmrt_status se = check_stage_errors(h);
+    if (se != DMRT_OK) return se;
     if (res[5] != 0.0 || !std::isfinite(res[4]))
         return fail(h, DMRT_ERR_DIVERGED, "non-finite fields at step %ld", h->steps);
     return DMRT_OK;
@@ -869,6 +914,7 @@ dmrt_status dmrt_get_params(const dmrt_t *h, dmrt_params *out)
     out->streaming = h->inplace ? DMRT_STREAM_INPLACE : DMRT_STREAM_AB;
     out->device_bytes = h->device_bytes;
     out->cells_per_thread = h->cells_per_thread;
+    out->pair_loads = h->pair_loads;
     return DMRT_OK;
 }
 

@@ -808,6 +808,7 @@ dmrt_status dmrt_ensemble_create(dmrt_ensemble_t **out, int count, const dmrt_ca
         if (opts->residual_interval > 0) K = opts->residual_interval;
         if (opts->residual_interval < 0) return DMRT_ERR_ARG;
         if (opts->cells_per_thread < 0 || opts->cells_per_thread > 1) return DMRT_ERR_ARG;
+        if (opts->pair_loads < 0 || opts->pair_loads > 1) return DMRT_ERR_ARG;
     }
     if (streaming != DMRT_STREAM_AB && streaming != DMRT_STREAM_INPLACE) return DMRT_ERR_ARG;
     if (storage < DMRT_STORE_F32 || storage > DMRT_STORE_F16) return DMRT_ERR_ARG;

@@ -50,6 +50,21 @@ void fill_inplace_geometry(const Geometry &G, InplaceGeometry &SI);
 cudaError_t launch_step_inplace(int wall, int storage, bool stochastic, void *buf, int phase,
                                 const InplaceGeometry &SI, const Geometry &G,
                                 const CollideParams &C, BlockShape b, cudaStream_t s, bool pdl);
+// The two-buffer paired step with its loads staged by TMA into shared memory
+// (16-bit storage, walled box, nx a multiple of 8): bitwise the values of
+// launch_step_pair.  `map` holds the two tensor maps of `src` (the row boxes
+// and the x-face edge boxes; two CUtensorMap, 128 bytes each, 64-byte
+// aligned) made by encode_pair_tma_maps; a copy wait that runs out sets *err
+// (device memory) and the kernel returns early.
+bool step_pair_tma_supported(int wall, int storage, const Geometry &G);
+cudaError_t encode_pair_tma_maps(const void *buf, const Geometry &G, void *maps);
+// Once per device and kernel variant, outside stream capture: allow the
+// staged kernel its shared memory (about 49 KB per block).
+cudaError_t prepare_step_pair_tma(int wall, int storage);
+cudaError_t launch_step_pair_tma(int wall, int storage, bool stochastic, const void *map, const void *src,
+                                 void *dst, const StepGeometry &S, const Geometry &G, const CollideParams &C,
+                                 unsigned *err, cudaStream_t s, bool pdl);
+
 // Both in-place phases with two cells per thread (same conditions as
 // launch_step_pair); bitwise the values of launch_step_inplace.
 cudaError_t launch_step_inplace_pair(int wall, int storage, bool stochastic, void *buf, int phase,

@@ -18,7 +18,11 @@
 // (step_inplace_pair_kernel, the counterpart of step_inplace.cu).  The
 // kernels need an even row length nx (rows then start on even elements, and
 // the planes are padded to 64 elements), which the launchers check.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "step_body.cuh"
+#include "umma.cuh"
 
 namespace lbm {
 
@@ -367,6 +371,230 @@ __global__ void __launch_bounds__(128, DMRT_PAIR_MIN_BLOCKS)
     });
 }
 
+
+// ---------------------------------------------------------------- TMA-staged pairs
+//
+// The paired kernel above holds its loaded values in registers, and at 124
+// registers only 16 warps per SM fit: too few bytes in flight to keep HBM
+// busy.  step_pair_tma_kernel moves the loads into the asynchronous copy
+// engine: a block of 64 x 8 threads owns 8 rows of 128 cells and marches
+// along z.  For each z, one thread issues 26 TMA copies (one 144 x 8 box per
+// plane: the eight source rows y - e_y at slab z - e_z, from 8 elements left
+// of the block's first cell to 8 right of its last) into a ring of three
+// shared-memory stages (60 KB each), two slabs ahead, completing on one
+// mbarrier per stage.  Boxes of 2.3 KB keep the number of TMA operations per
+// cell low; with 2-row boxes of 576 B the kernel ran 25 % slower than with
+// direct loads.
+// Threads then read their values from shared memory, shifted by -e_x.  Boxes
+// that fall outside the box's rows or slabs are filled with zeros by the TMA
+// unit; those links leave the box, and their bounce-back sources (the
+// cell's own slot of the opposite plane) are needed instead.  For the x faces,
+// which every row meets, blocks at x = 0 and x = nx - 1 stage them too: one
+// 8 x 2 box of each opposite plane at the face, with the same mbarrier.  The
+// rarer y and z faces take direct loads issued before the wait.  Every wait is
+// bounded: one that runs out sets *err, the block stops, waits (bounded) for
+// its copies in flight and returns.
+
+constexpr int kTmaPairs = 64;                   // pairs per block row (128 cells)
+constexpr int kTmaRows = 8;                     // rows per block (and per box)
+constexpr int kTmaBoxW = 2 * kTmaPairs + 16;    // box width in elements (16-byte multiple)
+constexpr int kTmaPlaneBytes = kTmaBoxW * kTmaRows * 2;  // one plane's box: 2304 B, a multiple of 128
+constexpr int kTmaEdgeW = 8;                    // edge box width in elements (16 bytes)
+constexpr int kTmaEdgeLinks = 6;                // links with e_x = +1 (or -1): 5 D3Q19, 1 D3Q7
+constexpr int kTmaEdgeSlot = 128;               // one edge box (8 x 8 x 2 B)
+constexpr int kTmaEdgeTx = kTmaEdgeLinks * kTmaEdgeW * kTmaRows * 2;  // bytes of one side's boxes
+constexpr int kTmaStageBytes = kPlanes * kTmaPlaneBytes + 2 * kTmaEdgeLinks * kTmaEdgeSlot;
+constexpr int kTmaStages = 3;
+constexpr uint32_t kTmaStageTx = kPlanes * kTmaBoxW * kTmaRows * 2;  // bytes a stage receives
+constexpr int kTmaSmemBytes = kTmaStages * kTmaStageBytes + kTmaStages * 8 + 128;  // + alignment slack
+constexpr uint32_t kTmaWaitPolls = 1u << 20;    // with a 64 ns sleep each: well over 60 ms
+
+__host__ __device__ constexpr int plane_ex_of(int p) { return p < 19 ? q19_ex(p) : q7_ex(p - 19); }
+
+// Slot of link q among the links with its sign of e_x, in plane order (0..5).
+template <int Q>
+__device__ constexpr int edge_slot()
+{
+    int k = 0;
+    for (int p = 0; p < Q; ++p)
+        if (plane_ex_of(p) == plane_ex_of(Q)) ++k;
+    return k;
+}
+
+// One TMA tile copy of a 4-D box at (x, y, z, plane) into shared memory.
+__device__ __forceinline__ void tma_box(const CUtensorMap *map, unsigned char *dst, uint32_t bar, int x, int y,
+                                        int z, int q)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(umma::smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(q), "r"(bar)
+        : "memory");
+}
+
+// Issue the boxes of slab z into one stage (one thread): the 26 plane boxes
+// and, for a block at the x = 0 (left) or x = nx - 1 (right) face, the edge
+// boxes of the opposite planes of the links leaving through it.
+__device__ __forceinline__ void tma_issue_slab(const CUtensorMap *map, const CUtensorMap *edge,
+                                               unsigned char *stage, uint64_t *bar, int xs, int y0, int z,
+                                               bool left, bool right, int nx)
+{
+    const uint32_t b = umma::smem_u32(bar);
+    const uint32_t tx = kTmaStageTx + (left ? kTmaEdgeTx : 0) + (right ? kTmaEdgeTx : 0);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(tx) : "memory");
+    static_for<0, kPlanes>([&](auto I) {
+        constexpr int q = decltype(I)::value;
+        tma_box(map, stage + q * kTmaPlaneBytes, b, xs - 8, y0 - plane_ey<q>(), z - plane_ez<q>(), q);
+    });
+    unsigned char *eb = stage + kPlanes * kTmaPlaneBytes;
+    static_for<0, kPlanes>([&](auto I) {
+        constexpr int q = decltype(I)::value;
+        if constexpr (plane_ex<q>() == 1) {
+            if (left) tma_box(edge, eb + edge_slot<q>() * kTmaEdgeSlot, b, 0, y0, z, plane_opp<q>());
+        } else if constexpr (plane_ex<q>() == -1) {
+            if (right)
+                tma_box(edge, eb + (kTmaEdgeLinks + edge_slot<q>()) * kTmaEdgeSlot, b, nx - kTmaEdgeW, y0, z,
+                        plane_opp<q>());
+        }
+    });
+}
+
+static_assert(kTmaPlaneBytes % 128 == 0 && kTmaEdgeW * kTmaRows * 2 <= kTmaEdgeSlot, "stage layout");
+
+// 512 threads (64 pairs x 8 rows) at up to 128 registers: one block per SM.
+template <int WALL, typename T, bool SR>
+__global__ void __launch_bounds__(kTmaPairs * kTmaRows, 1)
+    step_pair_tma_kernel(const __grid_constant__ CUtensorMap map, const __grid_constant__ CUtensorMap edge,
+                         const T *__restrict__ src, T *__restrict__ dst, const StepGeometry S,
+                         const CollideParams C, int zper, unsigned *err)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    // stage boxes start on 128-byte boundaries whatever the base alignment
+    unsigned char *smem = smem_raw + ((128u - (umma::smem_u32(smem_raw) & 127u)) & 127u);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + kTmaStages * kTmaStageBytes);
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int xs = blockIdx.x * (2 * kTmaPairs);
+    const int x0 = xs + 2 * tx;
+    const int y0 = blockIdx.y * kTmaRows, y = y0 + ty;
+    const int zb = blockIdx.z * zper;
+    const int ze = min(zb + zper, S.nz);
+    const bool valid = x0 < S.nx && y < S.ny;
+    const bool leader = tx == 0 && ty == 0;
+    const bool left = xs == 0, right = xs + 2 * kTmaPairs >= S.nx;  // the block meets x = 0 / x = nx - 1
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;");
+    if (leader) {
+        for (int k = 0; k < kTmaStages; ++k) umma::mbar_init(&bar[k], 1);
+        for (int k = 0; k < kTmaStages - 1 && zb + k < ze; ++k)
+            tma_issue_slab(&map, &edge, smem + k * kTmaStageBytes, &bar[k], xs, y0, zb + k, left, right, S.nx);
+    }
+    __syncthreads();
+
+    unsigned step = 0;
+    if constexpr (SR) step = *reinterpret_cast<const unsigned *>(src + static_cast<size_t>(kPlanes) * S.plane);
+    const bool xlo = x0 == 0, xhi = x0 + 2 == S.nx, ylo = y == 0, yhi = y == S.ny - 1;
+    const float th_lin = theta_linear(y, S.inv_ny);
+    const int k0 = 2 * tx + 8;  // cell 0's element in a staged row
+    bool ok = true;
+    int j = 0;
+    for (int z = zb; z < ze; ++z, ++j) {
+        const int s = j % kTmaStages;
+        const bool zlo = z == 0, zhi = z == S.nz - 1;
+        const unsigned self = (static_cast<unsigned>(z) * S.ny + y) * S.nx + x0;
+        const T *Bp = src + self;
+        // ---- bounce-back sources of links that leave through a y or z face:
+        // direct loads, issued before the wait so that they overlap it (the x
+        // faces' sources arrive in the edge boxes)
+        float v0[kPlanes], v1[kPlanes];
+        bool o0[kPlanes], o1[kPlanes];
+        static_for<0, kPlanes>([&](auto I) {
+            constexpr int q = decltype(I)::value;
+            constexpr int ex = plane_ex<q>(), ey = plane_ey<q>(), ez = plane_ez<q>();
+            bool oyz = false;
+            if constexpr (ey == 1) oyz = oyz || ylo;
+            if constexpr (ey == -1) oyz = oyz || yhi;
+            if constexpr (ez == 1) oyz = oyz || zlo;
+            if constexpr (ez == -1) oyz = oyz || zhi;
+            const bool xo0 = ex == 1 && xlo, xo1 = ex == -1 && xhi;
+            o0[q] = valid && (oyz || xo0);
+            o1[q] = valid && (oyz || xo1);
+            const unsigned bb = static_cast<unsigned>(S.bb[q]);
+            v0[q] = o0[q] && !xo0 ? Pair<T>::ld1(Bp + bb) : 0.0f;
+            v1[q] = o1[q] && !xo1 ? Pair<T>::ld1((Bp + bb) + 1) : 0.0f;
+        });
+        ok = umma::mbar_wait(&bar[s], (j / kTmaStages) & 1, kTmaWaitPolls);
+        if (!__syncthreads_and(ok)) break;
+        // every thread is past its reads of the stage last used at z - 1: refill it
+        if (leader && z + kTmaStages - 1 < ze)
+            tma_issue_slab(&map, &edge, smem + ((j + kTmaStages - 1) % kTmaStages) * kTmaStageBytes,
+                           &bar[(j + kTmaStages - 1) % kTmaStages], xs, y0, z + kTmaStages - 1, left, right,
+                           S.nx);
+        if (valid) {
+            // ---- values from the staged rows, shifted by -e_x
+            const unsigned char *st = smem + s * kTmaStageBytes + ty * (kTmaBoxW * 2);
+            const unsigned char *eb = smem + s * kTmaStageBytes + kPlanes * kTmaPlaneBytes + ty * (kTmaEdgeW * 2);
+            F2 d[19], g[7];
+            static_for<0, kPlanes>([&](auto I) {
+                constexpr int q = decltype(I)::value;
+                constexpr int ex = plane_ex<q>();
+                const T *row = reinterpret_cast<const T *>(st + q * kTmaPlaneBytes);
+                float a = v0[q], b = v1[q];
+                if constexpr (ex == 0) {
+                    if (!o0[q]) {
+                        const float2 w = Pair<T>::ld2(row + k0);
+                        a = w.x;
+                        b = w.y;
+                    }
+                } else {
+                    if (!o0[q]) a = Pair<T>::ld1(row + k0 - ex);
+                    if (!o1[q]) b = Pair<T>::ld1(row + k0 + 1 - ex);
+                    // x faces: the opposite plane's own slot from the edge box
+                    if constexpr (ex == 1) {
+                        if (xlo) a = Pair<T>::ld1(reinterpret_cast<const T *>(eb + edge_slot<q>() * kTmaEdgeSlot));
+                    } else {
+                        if (xhi)
+                            b = Pair<T>::ld1(reinterpret_cast<const T *>(
+                                                 eb + (kTmaEdgeLinks + edge_slot<q>()) * kTmaEdgeSlot) +
+                                             (kTmaEdgeW - 1));
+                    }
+                }
+                if constexpr (q >= 20 && dirichlet_axis<WALL>(plane_ex<q>() != 0 ? 0 : (plane_ey<q>() != 0 ? 1 : 2))) {
+                    constexpr int axis = plane_ex<q>() != 0 ? 0 : (plane_ey<q>() != 0 ? 1 : 2);
+                    float tw;
+                    if constexpr (axis == 1) tw = (plane_ey<q>() == 1) ? 0.5f : -0.5f;
+                    else tw = th_lin;
+                    a = o0[q] ? fmaf(0.25f, tw, -a) : a;  // anti-bounce-back, 2 w_T,i = 1/4
+                    b = o1[q] ? fmaf(0.25f, tw, -b) : b;
+                }
+                if constexpr (q < 19) d[q] = F2(a, b);
+                else g[q - 19] = F2(a, b);
+            });
+            collide(C, d, g);
+            unsigned r01 = 0;
+            if constexpr (SR) {
+                if (self == 0) *reinterpret_cast<unsigned *>(dst + static_cast<size_t>(kPlanes) * S.plane) = step + 1u;
+                r01 = pair_bits(self, step);
+            }
+            T *Dp = dst + self;
+            const unsigned plane = opaque(S.plane);
+            static_for<0, 26>([&](auto I) {
+                constexpr int q = decltype(I)::value;
+                store2<T, SR>(Dp + q * plane, plane_value<q>(d, g), SR ? plane_bits<q>(r01) : 0u);
+            });
+        }
+    }
+    if (!ok) {
+        // a stage never completed: report it, then give the copies already
+        // issued (slabs j .. j + kTmaStages - 2) a bounded time to land
+        if (leader) {
+            atomicOr(err, 1u);
+            for (int k = 0; k < kTmaStages - 1 && zb + j + k < ze; ++k)
+                umma::mbar_wait(&bar[(j + k) % kTmaStages], ((j + k) / kTmaStages) & 1, kTmaWaitPolls);
+        }
+        __syncthreads();
+    }
+}
+
 }  // namespace
 
 bool step_pair_supported(int wall, const Geometry &G)
@@ -416,6 +644,102 @@ cudaError_t launch_step_pair(int wall, int storage, bool stochastic, const void 
                 if (stochastic) return cudaLaunchKernelEx(&cfg, step_pair_kernel<WL, T, true>, a, b, S, C);
             }
             return cudaLaunchKernelEx(&cfg, step_pair_kernel<WL, T, false>, a, b, S, C);
+        }
+    });
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+bool step_pair_tma_supported(int wall, int storage, const Geometry &G)
+{
+    return step_pair_supported(wall, G) && storage != 0 && G.nx % 8 == 0;
+}
+
+cudaError_t encode_pair_tma_map(const void *buf, const Geometry &G, void *map, int box_width)
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        const cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                               cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    // the buffer as [26 planes][nz][ny][nx] 16-bit elements; strides in bytes
+    const cuuint64_t dims[4] = {static_cast<cuuint64_t>(G.nx), static_cast<cuuint64_t>(G.ny),
+                                static_cast<cuuint64_t>(G.nz), static_cast<cuuint64_t>(kPlanes)};
+    const cuuint64_t strides[3] = {static_cast<cuuint64_t>(G.nx) * 2, static_cast<cuuint64_t>(G.nx) * G.ny * 2,
+                                   static_cast<cuuint64_t>(G.plane) * 2};
+    const cuuint32_t box[4] = {static_cast<cuuint32_t>(box_width), kTmaRows, 1, 1};
+    const cuuint32_t unit[4] = {1, 1, 1, 1};
+    const CUresult r = encode(static_cast<CUtensorMap *>(map), CU_TENSOR_MAP_DATA_TYPE_UINT16, 4,
+                              const_cast<void *>(buf), dims, strides, box, unit, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t prepare_step_pair_tma(int wall, int storage)
+{
+    return dispatch(wall, storage, [&](auto W, auto *tp) {
+        using T = std::remove_pointer_t<decltype(tp)>;
+        constexpr int WL = decltype(W)::value;
+        if constexpr (WL == 0 || std::is_same_v<T, float>) {
+            return cudaErrorInvalidValue;
+        } else {
+            cudaError_t e = cudaFuncSetAttribute(step_pair_tma_kernel<WL, T, true>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, kTmaSmemBytes);
+            if (e != cudaSuccess) return e;
+            return cudaFuncSetAttribute(step_pair_tma_kernel<WL, T, false>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, kTmaSmemBytes);
+        }
+    });
+}
+
+cudaError_t encode_pair_tma_maps(const void *buf, const Geometry &G, void *maps)
+{
+    cudaError_t e = encode_pair_tma_map(buf, G, maps, kTmaBoxW);
+    if (e != cudaSuccess) return e;
+    return encode_pair_tma_map(buf, G, static_cast<unsigned char *>(maps) + sizeof(CUtensorMap), kTmaEdgeW);
+}
+
+cudaError_t launch_step_pair_tma(int wall, int storage, bool stochastic, const void *map, const void *src,
+                                 void *dst, const StepGeometry &S, const Geometry &G, const CollideParams &C,
+                                 unsigned *err, cudaStream_t s, bool pdl)
+{
+    if (!step_pair_tma_supported(wall, storage, G)) return cudaErrorInvalidValue;
+    const int xblocks = (G.nx / 2 + kTmaPairs - 1) / kTmaPairs;
+    const int yblocks = (G.ny + kTmaRows - 1) / kTmaRows;
+    // z chunks: about eight waves of one resident block on each of 152 SMs
+    const int cols = xblocks * yblocks;
+    int zchunks = (8 * 152 + cols / 2) / cols;
+    zchunks = zchunks < 1 ? 1 : (zchunks > G.nz ? G.nz : zchunks);
+    const int zper = (G.nz + zchunks - 1) / zchunks;
+    zchunks = (G.nz + zper - 1) / zper;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(xblocks, yblocks, zchunks);
+    cfg.blockDim = dim3(kTmaPairs, kTmaRows, 1);
+    cfg.dynamicSmemBytes = kTmaSmemBytes;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    const CUtensorMap &m = static_cast<const CUtensorMap *>(map)[0];
+    const CUtensorMap &me = static_cast<const CUtensorMap *>(map)[1];
+    cudaError_t e = dispatch(wall, storage, [&](auto W, auto *tp) {
+        using T = std::remove_pointer_t<decltype(tp)>;
+        constexpr int WL = decltype(W)::value;
+        if constexpr (WL == 0 || std::is_same_v<T, float>) {
+            return cudaErrorInvalidValue;
+        } else {
+            const T *a = static_cast<const T *>(src);
+            T *b = static_cast<T *>(dst);
+            if (stochastic)
+                return cudaLaunchKernelEx(&cfg, step_pair_tma_kernel<WL, T, true>, m, me, a, b, S, C, zper, err);
+            return cudaLaunchKernelEx(&cfg, step_pair_tma_kernel<WL, T, false>, m, me, a, b, S, C, zper, err);
         }
     });
     if (e != cudaSuccess) return e;

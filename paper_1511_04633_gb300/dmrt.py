@@ -38,7 +38,7 @@ class DmrtError(RuntimeError):
 class dmrt_opts(ctypes.Structure):
     _fields_ = [("storage", ctypes.c_int), ("residual_interval", ctypes.c_int),
                 ("rounding", ctypes.c_int), ("streaming", ctypes.c_int),
-                ("cells_per_thread", ctypes.c_int)]
+                ("cells_per_thread", ctypes.c_int), ("pair_loads", ctypes.c_int)]
 
 
 class dmrt_params(ctypes.Structure):
@@ -48,7 +48,8 @@ class dmrt_params(ctypes.Structure):
                 ("nu", ctypes.c_double), ("alpha", ctypes.c_double), ("gbeta", ctypes.c_double),
                 ("tau_nu", ctypes.c_double), ("tau_alpha", ctypes.c_double),
                 ("steps", ctypes.c_long), ("streaming", ctypes.c_int),
-                ("device_bytes", ctypes.c_longlong), ("cells_per_thread", ctypes.c_int)]
+                ("device_bytes", ctypes.c_longlong), ("cells_per_thread", ctypes.c_int),
+                ("pair_loads", ctypes.c_int)]
 
 
 class dmrt_stats(ctypes.Structure):
@@ -206,11 +207,11 @@ def check(h, status: int, what: str, ensemble: bool = False, surrogate: bool = F
 
 def dmrt_create(grid, Ra: float, Pr: float = 0.71, Ma: float = 0.1, wall_type: int = 1,
                 storage: int = STORE_F32, residual_interval: int = 0, rounding: int = ROUND_AUTO,
-                streaming: int = STREAM_AB, cells_per_thread: int = 0):
+                streaming: int = STREAM_AB, cells_per_thread: int = 0, pair_loads: int = 0):
     L = load()
     h = ctypes.c_void_p()
     g = (ctypes.c_int * 3)(*grid)
-    opts = dmrt_opts(storage, residual_interval, rounding, streaming, cells_per_thread)
+    opts = dmrt_opts(storage, residual_interval, rounding, streaming, cells_per_thread, pair_loads)
     check(None, L.dmrt_create_ex(ctypes.byref(h), g, Ra, Pr, Ma, wall_type, ctypes.byref(opts)),
           "dmrt_create")
     return h
@@ -219,11 +220,11 @@ def dmrt_create(grid, Ra: float, Pr: float = 0.71, Ma: float = 0.1, wall_type: i
 def dmrt_create_lattice(grid, nu: float, alpha: float, gbeta: float, wall_type: int = 1,
                         storage: int = STORE_F32, residual_interval: int = 0,
                         rounding: int = ROUND_AUTO, streaming: int = STREAM_AB,
-                        cells_per_thread: int = 0):
+                        cells_per_thread: int = 0, pair_loads: int = 0):
     L = load()
     h = ctypes.c_void_p()
     g = (ctypes.c_int * 3)(*grid)
-    opts = dmrt_opts(storage, residual_interval, rounding, streaming, cells_per_thread)
+    opts = dmrt_opts(storage, residual_interval, rounding, streaming, cells_per_thread, pair_loads)
     check(None, L.dmrt_create_lattice(ctypes.byref(h), g, nu, alpha, gbeta, wall_type,
                                       ctypes.byref(opts)), "dmrt_create_lattice")
     return h
@@ -391,7 +392,7 @@ class Cavity:
 
     def __init__(self, grid, Ra=None, Pr=0.71, Ma=0.1, wall_type=1, *, lattice=None,
                  storage=STORE_F32, residual_interval=0, rounding=ROUND_AUTO,
-                 streaming=STREAM_AB, cells_per_thread=0):
+                 streaming=STREAM_AB, cells_per_thread=0, pair_loads=0):
         self.grid = tuple(int(v) for v in grid)
         nx, ny, nz = self.grid
         self.shape = (nz, ny, nx)
@@ -399,10 +400,11 @@ class Cavity:
         if lattice is not None:
             nu, alpha, gbeta = lattice
             self.h = dmrt_create_lattice(self.grid, nu, alpha, gbeta, wall_type, storage,
-                                         residual_interval, rounding, streaming, cells_per_thread)
+                                         residual_interval, rounding, streaming, cells_per_thread,
+                                         pair_loads)
         else:
             self.h = dmrt_create(self.grid, Ra, Pr, Ma, wall_type, storage, residual_interval,
-                                 rounding, streaming, cells_per_thread)
+                                 rounding, streaming, cells_per_thread, pair_loads)
 
     def close(self):
         if getattr(self, "h", None):

@@ -30,11 +30,13 @@ def dm():
     return dmrt
 
 
-def _pair_and_single(dm, grid, wall, **kw):
-    two = dm.Cavity(grid, wall_type=wall, cells_per_thread=2, **kw)
+def _pair_and_single(dm, grid, wall, pair_loads=0, **kw):
+    two = dm.Cavity(grid, wall_type=wall, cells_per_thread=2, pair_loads=pair_loads, **kw)
     one = dm.Cavity(grid, wall_type=wall, cells_per_thread=1, **kw)
     assert two.params["cells_per_thread"] == 2
     assert one.params["cells_per_thread"] == 1
+    if pair_loads:
+        assert two.params["pair_loads"] == pair_loads
     return two, one
 
 
@@ -49,19 +51,25 @@ def _assert_same(a, b):
 
 
 # grids: the smallest box, one pair per row with ragged y, rows spanning two
-# 64-pair blocks plus a one-pair tail, and a 16-pair row with 8 rows a block
-GRIDS = [(2, 3, 2), (2, 9, 5), (130, 6, 4), (32, 17, 6), (38, 20, 13)]
+# 64-pair blocks plus a one-pair tail, and a 16-pair row with 8 rows a block;
+# rows of a multiple of 8 cells (32, 8, 136: two 64-pair blocks, ragged y)
+# also run with the TMA-staged loads for 16-bit storage
+GRIDS = [(2, 3, 2), (2, 9, 5), (130, 6, 4), (32, 17, 6), (38, 20, 13), (8, 3, 4), (136, 5, 7)]
 
 
+@pytest.mark.parametrize("loads", [1, 2], ids=["direct", "staged"])
 @pytest.mark.parametrize("rounding", [0, 1], ids=["auto", "nearest"])
 @pytest.mark.parametrize("storage", [0, 1, 2], ids=["f32", "bf16", "f16"])
 @pytest.mark.parametrize("wall", [1, 2, 3])
 @pytest.mark.parametrize("grid", GRIDS, ids=lambda g: "x".join(map(str, g)))
-def test_bitwise_equal_to_one_cell_kernel(dm, grid, wall, storage, rounding):
+def test_bitwise_equal_to_one_cell_kernel(dm, grid, wall, storage, rounding, loads):
     if storage == 0 and rounding == 1:
         pytest.skip("FP32 storage has one rounding mode")
+    if loads == 2 and (storage == 0 or grid[0] % 8):
+        pytest.skip("staged loads need 16-bit storage and rows of a multiple of 8 cells")
     rnd = dm.ROUND_NEAREST if rounding == 1 else dm.ROUND_AUTO
-    two, one = _pair_and_single(dm, grid, wall, lattice=LATTICE, storage=storage, rounding=rnd)
+    two, one = _pair_and_single(dm, grid, wall, pair_loads=loads, lattice=LATTICE, storage=storage,
+                                rounding=rnd)
     f = inputs.random_populations(grid, 19, seed=500 + wall)
     g = inputs.random_thermal_populations(grid, seed=600 + wall)
     for h in (two, one):
@@ -91,12 +99,16 @@ def test_inplace_bitwise_equal_to_one_cell_kernels(dm, grid, wall, storage):
         _assert_same(two, one)
 
 
+@pytest.mark.parametrize("loads", [1, 2], ids=["direct", "staged"])
 @pytest.mark.parametrize("storage", [0, 1, 2], ids=["f32", "bf16", "f16"])
-def test_graph_replayed_intervals_from_rest(dm, storage):
+def test_graph_replayed_intervals_from_rest(dm, storage, loads):
     """Whole residual intervals replay captured graphs of the paired kernel;
     a developing Type 2 flow from rest stays bitwise with the one-cell run."""
+    if loads == 2 and storage == 0:
+        pytest.skip("staged loads need 16-bit storage")
     grid = (48, 40, 36)
-    two, one = _pair_and_single(dm, grid, 2, Ra=1e5, storage=storage, residual_interval=50)
+    two, one = _pair_and_single(dm, grid, 2, pair_loads=loads, Ra=1e5, storage=storage,
+                                residual_interval=50)
     for h in (two, one):
         h.step(7)
         h.step(400)
@@ -143,6 +155,20 @@ def test_auto_choice_and_rejected_requests(dm):
         assert ei.value.status == dm.ERR_ARG
     with pytest.raises(dm.DmrtError):
         dm.Cavity((16, 8, 8), lattice=LATTICE, cells_per_thread=3)
+    # staged loads: on request, for 16-bit two-buffer storage with rows of a
+    # multiple of 8 cells; auto takes the direct loads
+    assert dm.Cavity((16, 8, 8), 1e4, storage=dm.STORE_BF16).params["pair_loads"] == 1
+    assert dm.Cavity((16, 8, 8), 1e4, storage=dm.STORE_BF16, pair_loads=2).params["pair_loads"] == 2
+    assert dm.Cavity((18, 8, 8), 1e4, storage=dm.STORE_BF16).params["pair_loads"] == 1
+    assert dm.Cavity((16, 8, 8), 1e4, storage=dm.STORE_BF16,
+                     streaming=dm.STREAM_INPLACE).params["pair_loads"] == 0
+    assert dm.Cavity((16, 8, 8), 1e4).params["pair_loads"] == 0
+    for kw in (dict(grid=(18, 8, 8), storage=dm.STORE_BF16), dict(grid=(16, 8, 8)),
+               dict(grid=(16, 8, 8), storage=dm.STORE_BF16, streaming=dm.STREAM_INPLACE)):
+        grid = kw.pop("grid")
+        with pytest.raises(dm.DmrtError) as ei:
+            dm.Cavity(grid, lattice=LATTICE, cells_per_thread=2, pair_loads=2, **kw)
+        assert ei.value.status == dm.ERR_ARG
     with pytest.raises(dm.DmrtError):
         dm.dmrt_create((16, 8, 8), 1e4, cells_per_thread=-1)
 
@@ -163,11 +189,36 @@ def test_inplace_graph_intervals_match_two_buffers(dm, storage):
     assert ab.residual() == ip.residual()
 
 
-def test_full_size_step_of_the_256_cube_bf16(dm):
+@pytest.mark.parametrize("storage", [1, 2], ids=["bf16", "f16"])
+@pytest.mark.parametrize("wall", [1, 2, 3])
+def test_staged_loads_over_several_slabs(dm, storage, wall):
+    """A 256 x 192 x 24 box gives every staged block four slabs in a row (the
+    three-stage ring wraps); direct and staged loads and one cell per thread
+    agree bitwise after 1, 2 and 5 steps from random populations."""
+    grid = (256, 192, 24)
+    kw = dict(wall_type=wall, lattice=LATTICE, storage=storage)
+    staged = dm.Cavity(grid, cells_per_thread=2, pair_loads=2, **kw)
+    direct = dm.Cavity(grid, cells_per_thread=2, pair_loads=1, **kw)
+    one = dm.Cavity(grid, cells_per_thread=1, **kw)
+    assert staged.params["pair_loads"] == 2 and direct.params["pair_loads"] == 1
+    f = inputs.random_populations(grid, 19, seed=900 + wall)
+    g = inputs.random_thermal_populations(grid, seed=910 + wall)
+    for h in (staged, direct, one):
+        h.set_populations(f, g)
+    for n in (1, 1, 3):
+        for h in (staged, direct, one):
+            h.step(n)
+        _assert_same(staged, direct)
+        _assert_same(staged, one)
+    staged.sync()
+
+
+@pytest.mark.parametrize("loads", [1, 2], ids=["direct", "staged"])
+def test_full_size_step_of_the_256_cube_bf16(dm, loads):
     """The 256^3 Type 3 Ra = 1e6 BF16 cavity of the benchmark: 30 steps from
     rest, paired and one-cell kernels bitwise equal on every plane."""
     grid = (256, 256, 256)
-    two, one = _pair_and_single(dm, grid, 3, Ra=1e6, storage=dm.STORE_BF16)
+    two, one = _pair_and_single(dm, grid, 3, pair_loads=loads, Ra=1e6, storage=dm.STORE_BF16)
     for h in (two, one):
         h.step(30)
     fa, ga = two.populations()
