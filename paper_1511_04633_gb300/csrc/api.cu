@@ -188,7 +188,10 @@ void fill_rates(dmrt_t *h)
     s[4] = s[6] = s[8] = 1.2;
     s[16] = s[17] = s[18] = 1.98;
     s[9] = s[11] = s[13] = s[14] = s[15] = s_nu;
-    for (int k = 0; k < 19; ++k) h->C.rs[k] = static_cast<float>(s[k] / lbm::m19_norm2(k));
+    for (int k = 0; k < 19; ++k) {
+        h->C.rs[k] = static_cast<float>(s[k] / lbm::m19_norm2(k));
+        h->C.ws[k] = static_cast<float>((1.0 - s[k]) / lbm::m19_norm2(k));
+    }
     const double tau_a = 0.5 + 4.0 * h->alpha;  // eps = 1/4, dt = dx = 1
     double q[7] = {1.0, 1.0 / tau_a, 1.0 / tau_a, 1.0 / tau_a, 1.0, 1.0, 1.0};
     for (int k = 0; k < 7; ++k) h->C.rq[k] = static_cast<float>(q[k] / lbm::m7_norm2(k));

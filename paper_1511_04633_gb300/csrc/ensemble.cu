@@ -591,7 +591,10 @@ void fill_rates_desc(lbm::CavityDesc &D, double nu, double alpha, double gbeta)
     s[4] = s[6] = s[8] = 1.2;
     s[16] = s[17] = s[18] = 1.98;
     s[9] = s[11] = s[13] = s[14] = s[15] = s_nu;
-    for (int k = 0; k < 19; ++k) D.C.rs[k] = static_cast<float>(s[k] / lbm::m19_norm2(k));
+    for (int k = 0; k < 19; ++k) {
+        D.C.rs[k] = static_cast<float>(s[k] / lbm::m19_norm2(k));
+        D.C.ws[k] = static_cast<float>((1.0 - s[k]) / lbm::m19_norm2(k));
+    }
     const double tau_a = 0.5 + 4.0 * alpha;  // Eq. (36), eps = 1/4
     const double q[7] = {1.0, 1.0 / tau_a, 1.0 / tau_a, 1.0 / tau_a, 1.0, 1.0, 1.0};
     for (int k = 0; k < 7; ++k) D.C.rq[k] = static_cast<float>(q[k] / lbm::m7_norm2(k));

@@ -228,6 +228,7 @@ __host__ __device__ constexpr int m7_norm2(int k)
 // back-transform M^-1 = M^T diag(1/|M_k|^2) needs no further scaling.
 struct CollideParams {
     float rs[19];     // s_k / |M_k|^2 (Eq. (26)); entries 0,3,5,7 unused
+    float ws[19];     // (1 - s_k) / |M_k|^2; entries 0,3,5,7 unused
     float rq[7];      // q_k / |N_k|^2 (Eqs. (35),(36)); entry 0 unused
     float gbeta;      // g beta dT (lattice units)
     float theta_ref;  // reference temperature of Eq. (16)

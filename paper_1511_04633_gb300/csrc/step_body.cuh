@@ -62,35 +62,33 @@ __device__ __forceinline__ void collide(const CollideParams &C, V d[19], V g[7])
     const V rho = drho + V(1.0f);
     const V ir = recip(rho);
     const V vx = jx * ir, vy = jy * ir, vz = jz * ir;
-    const V njx = jx * V(-1.0f), njy = jy * V(-1.0f), njz = jz * V(-1.0f);
+    const V njz = jz * V(-1.0f);
     const V jj = fma(jx, jx, fma(jy, jy, jz * jz));  // |j|^2
     const V pww = fma(jy, jy, njz * jz);             // jy^2 - jz^2
 
-    // ---- non-equilibrium parts m_k - m_k^eq (Eq. (24), rho0 = 1; the rest
-    // moments of w cancel between m and m^eq).  With drho = d0 + SF + SE:
-    //   m1 = -30 d0 - 11 SF + 8 SE,  m1eq = -11 drho + 19 jj
-    //   m2 = 12 d0 - 4 SF + SE,      m2eq = 3 drho - 11/2 jj
-    //   m4 = -4 a1 + Ex,             m4eq = -2/3 jx   (m6, m8 alike)
-    //   m9 = 3 (s1 - Cyz) + SE - SF, m9eq = 3 jx^2 - jj
-    //   m10 = -6 s1 - 3 Cyz + 2 SF + SE, m10eq = -m9eq / 2
-    //   m11 = (s3 - s5) + (A - B),   m11eq = jy^2 - jz^2
-    //   m12 = -2 (s3 - s5) + (A - B), m12eq = -m11eq / 2
-    //   m13 = s7 - s8 (m14 = s15 - s16, m15 = s11 - s12), m13eq = jx jy
-    const V n1 = V(19.0f) * ((SE - d[0]) - jj);
-    const V n2 = fma(V(9.0f), d[0], fma(V(-7.0f), SF, fma(V(-2.0f), SE, V(5.5f) * jj)));
-    const V n4 = V(5.0f / 3.0f) * fma(V(-2.0f), a1, Ex);
-    const V n6 = V(5.0f / 3.0f) * fma(V(-2.0f), a3, Ey);
-    const V n8 = V(5.0f / 3.0f) * fma(V(-2.0f), a5, Ez);
-    const V n9 = fma(V(3.0f), fma(njx, jx, s1 - Cyz), (SE - SF) + jj);
-    const V n10 = fma(V(-6.0f), s1,
-                      fma(V(-3.0f), Cyz, fma(V(1.5f), jx * jx, fma(V(-0.5f), jj, fma(V(2.0f), SF, SE)))));
+    // ---- moments m_k of the deviations (Eqs. (21), (22)): the moments of w
+    // are the rest equilibrium moments and cancel against those of m^eq.
+    //   m1 = -30 d0 - 11 SF + 8 SE     m2 = 12 d0 - 4 SF + SE
+    //   m4 = -4 a1 + Ex (m6, m8 alike) m9 = 3 (s1 - Cyz) + SE - SF
+    //   m10 = -6 s1 - 3 Cyz + 2 SF + SE
+    //   m11 = (s3 - s5) + (A - B)      m12 = -2 (s3 - s5) + (A - B)
+    //   m13 = s7 - s8, m14 = s15 - s16, m15 = s11 - s12
+    //   m16 = X1 - X2, m17 = Y2 - Y1, m18 = Z1 - Z2
+    // and their equilibria (Eq. (24), rho0 = 1), with j^2 = jj:
+    //   m1eq = -11 drho + 19 jj   m2eq = 3 drho - 11/2 jj   m4eq = -2/3 jx
+    //   m9eq = 3 jx^2 - jj        m10eq = -m9eq / 2
+    //   m11eq = jy^2 - jz^2       m12eq = -m11eq / 2
+    //   m13eq = jx jy, m14eq = jy jz, m15eq = jx jz, m16-18eq = 0
     const V d35 = s3 - s5, dAB = A - B;
-    const V n11 = (d35 + dAB) - pww;
-    const V n12 = fma(V(-2.0f), d35, fma(V(0.5f), pww, dAB));
-    const V n13 = fma(njx, jy, s7 - s8);
-    const V n14 = fma(njy, jz, s15 - s16);
-    const V n15 = fma(njx, jz, s11 - s12);
-    const V n16 = X1 - X2, n17 = Y2 - Y1, n18 = Z1 - Z2;
+    const V m1 = fma(V(-30.0f), d[0], fma(V(-11.0f), SF, V(8.0f) * SE));
+    const V m2 = fma(V(12.0f), d[0], fma(V(-4.0f), SF, SE));
+    const V m4 = fma(V(-4.0f), a1, Ex), m6 = fma(V(-4.0f), a3, Ey), m8 = fma(V(-4.0f), a5, Ez);
+    const V m9 = fma(V(3.0f), s1 - Cyz, SE - SF);
+    const V m10 = fma(V(-6.0f), s1, fma(V(-3.0f), Cyz, fma(V(2.0f), SF, SE)));
+    const V m11 = d35 + dAB, m12 = fma(V(-2.0f), d35, dAB);
+    const V m13 = s7 - s8, m14 = s15 - s16, m15 = s11 - s12;
+    const V m16 = X1 - X2, m17 = Y2 - Y1, m18 = Z1 - Z2;
+    const V meq9 = fma(V(3.0f) * jx, jx, jj * V(-1.0f));
 
     // ---- buoyancy in moment space.  With G = (0, 0, G_z) (Eq. (16)) and
     // F_i = G_z (e_iz - V_z) f_eq,i / c_s^2 (Eqs. (15), (17)), the moments
@@ -104,114 +102,116 @@ __device__ __forceinline__ void collide(const CollideParams &C, V d[19], V g[7])
     //   F^_16 = -3 gv V_x       F^_17 = 3 gv V_y              F^_18 = 3/2 g (V_x^2 - V_y^2)
     // and F^_0 = F^_3 = F^_5 = 0 (the D3Q19 moments of f_eq up to fourth
     // order are the isotropic ones, which makes these sums exact).  Below,
-    // f_k = -F^_k / |M_k|^2 (norms 2394, 252, 40, 40, 10, 40, 36, 144, 12,
-    // 48, 4, 4, 4, 8, 8, 8) with the constants folded in.
-    const V gr = (V(C.gbeta) * (T - V(C.theta_ref))) * rho;
+    // h_k = F^_k / |M_k|^2 with |M_k|^2 = 2394, 252, 40, 40, 10, 40, 36, 72,
+    // 12, 24, 4, 4, 4, 8, 8, 8 (k = 1, 2, 4, 6, 7, 8, 9, ..., 18), constants
+    // folded in.
+    const V gbt = V(C.gbeta) * (T - V(C.theta_ref));
+    const V gr = gbt * rho;
     const V gv = gr * vz;
     const V vxy = fma(vx, vx, vy * vy);                  // V_x^2 + V_y^2
     const V vv = fma(vz, vz, vxy);                       // V^2
     const V dxy = fma(vx, vx, (vy * V(-1.0f)) * vy);     // V_x^2 - V_y^2
     const V dyz = fma(vy, vy, (vz * V(-1.0f)) * vz);     // V_y^2 - V_z^2
     const V gvx = gv * vx, gvy = gv * vy;
-    const V f1 = gv * fma(V(57.0f / 2394.0f), vv, V(-38.0f / 2394.0f));
-    const V f2 = gv * fma(V(-16.5f / 252.0f), vv, V(11.0f / 252.0f));
-    const V f4 = gvx * V(-0.125f);
-    const V f6 = gvy * V(-0.125f);
-    const V f8 = gr * fma(V(-0.0625f), vxy, V(1.0f / 60.0f));
-    const V f9 = gv * fma(V(0.25f), vx * vx, fma(V(-1.0f / 12.0f), vv, V(1.0f / 18.0f)));
-    const V f11 = gv * fma(V(0.25f), dyz, V(1.0f / 6.0f));
-    const V f13 = (gvx * vy) * V(0.75f);
-    const V grz = gr * fma(V(0.75f), vz * vz, V(-0.25f));
-    const V f16 = gvx * V(0.375f);
-    const V f17 = gvy * V(-0.375f);
-    const V f18 = (gr * V(-0.1875f)) * dxy;
+    const V h9 = gv * fma(V(-0.25f), vx * vx, fma(V(1.0f / 12.0f), vv, V(-1.0f / 18.0f)));
+    const V h11 = gv * fma(V(-0.25f), dyz, V(-1.0f / 6.0f));
+    const V grz = gr * fma(V(-0.75f), vz * vz, V(0.25f));
 
-    // ---- b_k = (s_k (m_k - m_k^eq) - F^_k) / |M_k|^2  (rates come divided)
-    const V b1 = fma(V(C.rs[1]), n1, f1);
-    const V b2 = fma(V(C.rs[2]), n2, f2);
-    const V b4 = fma(V(C.rs[4]), n4, f4);
-    const V b6 = fma(V(C.rs[6]), n6, f6);
-    const V b7 = gr * V(-0.1f);
-    const V b8 = fma(V(C.rs[8]), n8, f8);
-    const V b9 = fma(V(C.rs[9]), n9, f9);
-    const V b10 = fma(V(C.rs[10]), n10, f9 * V(-0.25f));
-    const V b11 = fma(V(C.rs[11]), n11, f11);
-    const V b12 = fma(V(C.rs[12]), n12, f11 * V(-0.25f));
-    const V b13 = fma(V(C.rs[13]), n13, f13);
-    const V b14 = fma(V(C.rs[14]), n14, grz * vy);
-    const V b15 = fma(V(C.rs[15]), n15, grz * vx);
-    const V b16 = fma(V(C.rs[16]), n16, f16);
-    const V b17 = fma(V(C.rs[17]), n17, f17);
-    const V b18 = fma(V(C.rs[18]), n18, f18);
+    // ---- post-collision moments over their norms, c_k = m*_k / |M_k|^2 with
+    // m*_k = m_k - s_k (m_k - m_k^eq) + F^_k (Eqs. (19), (24), (26)):
+    // c_k = w_k m_k + r_k m_k^eq + h_k, w_k = (1 - s_k)/|M_k|^2, r_k = s_k/|M_k|^2.
+    // The conserved moments keep m*_0 = drho, m*_3,5 = j_x,y, m*_7 = j_z + g.
+    const V c1 = fma(m1, V(C.ws[1]), fma(V(C.rs[1]), fma(V(-11.0f), drho, V(19.0f) * jj),
+                                       gv * fma(V(-57.0f / 2394.0f), vv, V(38.0f / 2394.0f))));
+    const V c2 = fma(m2, V(C.ws[2]), fma(V(C.rs[2]), fma(V(3.0f), drho, V(-5.5f) * jj),
+                                       gv * fma(V(16.5f / 252.0f), vv, V(-11.0f / 252.0f))));
+    const V c4 = fma(m4, V(C.ws[4]), fma(V(C.rs[4]), jx * V(-2.0f / 3.0f), gvx * V(0.125f)));
+    const V c6 = fma(m6, V(C.ws[6]), fma(V(C.rs[6]), jy * V(-2.0f / 3.0f), gvy * V(0.125f)));
+    const V c8 = fma(m8, V(C.ws[8]), fma(V(C.rs[8]), jz * V(-2.0f / 3.0f),
+                                       gr * fma(V(0.0625f), vxy, V(-1.0f / 60.0f))));
+    const V c9 = fma(m9, V(C.ws[9]), fma(V(C.rs[9]), meq9, h9));
+    const V c10 = fma(m10, V(C.ws[10]), fma(V(C.rs[10]), meq9 * V(-0.5f), h9 * V(-0.25f)));
+    const V c11 = fma(m11, V(C.ws[11]), fma(V(C.rs[11]), pww, h11));
+    const V c12 = fma(m12, V(C.ws[12]), fma(V(C.rs[12]), pww * V(-0.5f), h11 * V(-0.25f)));
+    const V c13 = fma(m13, V(C.ws[13]), fma(V(C.rs[13]), jx * jy, (gvx * vy) * V(-0.75f)));
+    const V c14 = fma(m14, V(C.ws[14]), fma(V(C.rs[14]), jy * jz, grz * vy));
+    const V c15 = fma(m15, V(C.ws[15]), fma(V(C.rs[15]), jx * jz, grz * vx));
+    const V c16 = fma(m16, V(C.ws[16]), gvx * V(-0.375f));
+    const V c17 = fma(m17, V(C.ws[17]), gvy * V(0.375f));
+    const V c18 = fma(m18, V(C.ws[18]), (gr * V(0.1875f)) * dxy);
 
-    // ---- back-transform f* = f - M^T b, one even (E) and one odd (O) partial
-    // sum per pair: f*_i = f_i - (E + O), f*_opp = f_opp - (E - O)
-    d[0] = fma(V(30.0f), b1, fma(V(-12.0f), b2, d[0]));
-    const V F0 = fma(V(-11.0f), b1, V(-4.0f) * b2);  // every face
-    const V G0 = fma(V(8.0f), b1, b2);               // every edge
-    const V Efx = fma(V(2.0f), b9, fma(V(-4.0f), b10, F0));
-    const V F0P = fma(V(2.0f), b10, F0 - b9);
-    const V Qf = fma(V(-2.0f), b12, b11);
-    const V Efy = F0P + Qf, Efz = F0P - Qf;
-    const V Ofz = fma(V(-4.0f), b8, b7);  // odd parts of x, y: -4 b4, -4 b6
-    d[1] = fma(V(4.0f), b4, d[1] - Efx);
-    d[2] = fma(V(-4.0f), b4, d[2] - Efx);
-    d[3] = fma(V(4.0f), b6, d[3] - Efy);
-    d[4] = fma(V(-4.0f), b6, d[4] - Efy);
-    d[5] = (d[5] - Efz) - Ofz;
-    d[6] = (d[6] - Efz) + Ofz;
+    // ---- back-transform f* = M^T c (M^-1 = M^T diag(1/|M_k|^2)), one even (E)
+    // and one odd (O) partial sum per pair: f*_i = E + O, f*_opp = E - O.
+    // c0 = drho/19, c3 = jx/10, c5 = jy/10, c7 = (jz + g)/10 enter through fma.
+    d[0] = fma(V(-30.0f), c1, fma(V(12.0f), c2, drho * V(1.0f / 19.0f)));
+    const V Fc = fma(V(-11.0f), c1, fma(V(-4.0f), c2, drho * V(1.0f / 19.0f)));  // every face
+    const V Gc = fma(V(8.0f), c1, fma(drho, V(1.0f / 19.0f), c2));                // every edge
+    const V Efx = fma(V(2.0f), c9, fma(V(-4.0f), c10, Fc));
+    const V FP = fma(V(2.0f), c10, Fc - c9);
+    const V Q = fma(V(-2.0f), c12, c11);
+    const V Efy = FP + Q, Efz = FP - Q;
+    const V jzg = fma(gbt, rho, jz);  // j_z + g
+    const V Ofx = fma(V(-4.0f), c4, jx * V(0.1f));
+    const V Ofy = fma(V(-4.0f), c6, jy * V(0.1f));
+    const V Ofz = fma(V(-4.0f), c8, jzg * V(0.1f));
+    d[1] = Efx + Ofx;
+    d[2] = Efx - Ofx;
+    d[3] = Efy + Ofy;
+    d[4] = Efy - Ofy;
+    d[5] = Efz + Ofz;
+    d[6] = Efz - Ofz;
 
-    const V H = b9 + b10, K = b11 + b12;
-    const V G0H = G0 + H;
-    const V Exy = G0H + K, Exz = G0H - K, Eyz = fma(V(-2.0f), H, G0);
-    const V b78 = fma(gr, V(-0.1f), b8);  // b7 + b8
-    const V E7 = Exy + b13, O7 = (b4 + b6) + (b16 - b17);        // (1,1,0)
-    const V E8 = Exy - b13, O8 = (b6 - b4) - (b16 + b17);        // (-1,1,0)
-    const V E11 = Exz + b15, O11 = (b78 + b4) + (b18 - b16);     // (1,0,1)
-    const V E12 = Exz - b15, O12 = (b78 - b4) + (b16 + b18);     // (-1,0,1)
-    const V E15 = Eyz + b14, O15 = (b78 + b6) + (b17 - b18);     // (0,1,1)
-    const V E16 = Eyz - b14, O16 = (b78 - b6) - (b17 + b18);     // (0,-1,1)
-    d[7] = (d[7] - E7) - O7;
-    d[10] = (d[10] - E7) + O7;
-    d[8] = (d[8] - E8) - O8;
-    d[9] = (d[9] - E8) + O8;
-    d[11] = (d[11] - E11) - O11;
-    d[14] = (d[14] - E11) + O11;
-    d[12] = (d[12] - E12) - O12;
-    d[13] = (d[13] - E12) + O12;
-    d[15] = (d[15] - E15) - O15;
-    d[18] = (d[18] - E15) + O15;
-    d[16] = (d[16] - E16) - O16;
-    d[17] = (d[17] - E16) + O16;
+    const V H = c9 + c10, K = c11 + c12;
+    const V GH = Gc + H;
+    const V Exy = GH + K, Exz = GH - K, Eyz = fma(V(-2.0f), H, Gc);
+    const V cx = fma(jx, V(0.1f), c4), cy = fma(jy, V(0.1f), c6), cz = fma(jzg, V(0.1f), c8);
+    const V E7 = Exy + c13, O7 = (cx + cy) + (c16 - c17);        // (1,1,0)
+    const V E8 = Exy - c13, O8 = (cy - cx) - (c16 + c17);        // (-1,1,0)
+    const V E11 = Exz + c15, O11 = (cx + cz) + (c18 - c16);      // (1,0,1)
+    const V E12 = Exz - c15, O12 = (cz - cx) + (c16 + c18);      // (-1,0,1)
+    const V E15 = Eyz + c14, O15 = (cy + cz) + (c17 - c18);      // (0,1,1)
+    const V E16 = Eyz - c14, O16 = (cz - cy) - (c17 + c18);      // (0,-1,1)
+    d[7] = E7 + O7;
+    d[10] = E7 - O7;
+    d[8] = E8 + O8;
+    d[9] = E8 - O8;
+    d[11] = E11 + O11;
+    d[14] = E11 - O11;
+    d[12] = E12 + O12;
+    d[13] = E12 - O12;
+    d[15] = E15 + O15;
+    d[18] = E15 - O15;
+    d[16] = E16 + O16;
+    d[17] = E16 - O16;
 
     // ---- energy: n - n^eq with n^eq = (T, V T, 3/4 T, 0, 0) (Eqs. (33),(34)).
     // The flux parts e = (ta - V T) relax with Q's flux block; with
-    // T = g0 + tsm the even parts are c4 = q4 (21/4 g0 - 7/4 tsm),
-    // c5 = q5 (3 tsx - tsm), c6 = q6 (tsy - tsz) (rates divided by the norms),
-    // and the back-transform subtracts, per pair, an even part (2 c5 - c4 for
-    // x, c6 - c4 - c5 for y, -(c4 + c5 + c6) for z) and +-the relaxed flux.
+    // T = g0 + tsm the even parts are t4 = q4 (21/4 g0 - 7/4 tsm),
+    // t5 = q5 (3 tsx - tsm), t6 = q6 (tsy - tsz) (rates divided by the norms),
+    // and the back-transform subtracts, per pair, an even part (2 t5 - t4 for
+    // x, t6 - t4 - t5 for y, -(t4 + t5 + t6) for z) and +-the relaxed flux.
     const V nT = T * V(-1.0f);
     const V e1 = fma(vx, nT, tax), e2 = fma(vy, nT, tay), e3 = fma(vz, nT, taz);
     const V u4 = fma(V(5.25f), g[0], V(-1.75f) * tsm);
     const V u5 = fma(V(3.0f), tsx, tsm * V(-1.0f));
     const V u6 = tsy - tsz;
-    const V c4 = V(C.rq[4]) * u4, nc4 = V(-C.rq[4]) * u4;
-    g[0] = fma(V(-6.0f), c4, g[0]);
-    const V Etx = fma(V(2.0f * C.rq[5]), u5, nc4);     // 2 c5 - c4
-    const V c45 = fma(V(C.rq[5]), u5, c4);             // c4 + c5
-    const V nc45 = fma(V(-C.rq[5]), u5, nc4);          // -(c4 + c5)
-    const V Ety = fma(V(C.rq[6]), u6, nc45);           // c6 - c4 - c5
-    const V P = fma(V(C.rq[6]), u6, c45);              // c4 + c5 + c6
+    const V t4 = V(C.rq[4]) * u4, nt4 = V(-C.rq[4]) * u4;
+    g[0] = fma(V(-6.0f), t4, g[0]);
+    const V Etx = fma(V(2.0f * C.rq[5]), u5, nt4);     // 2 t5 - t4
+    const V t45 = fma(V(C.rq[5]), u5, t4);             // t4 + t5
+    const V nt45 = fma(V(-C.rq[5]), u5, nt4);          // -(t4 + t5)
+    const V Ety = fma(V(C.rq[6]), u6, nt45);           // t6 - t4 - t5
+    const V P = fma(V(C.rq[6]), u6, t45);              // t4 + t5 + t6
     if (C.aniso) {  // uniform: the full flux block of Q (Eq. (35))
-        const V c1 = fma(V(C.qa[0]), e1, fma(V(C.qa[1]), e2, V(C.qa[2]) * e3));
-        const V c2 = fma(V(C.qa[3]), e1, fma(V(C.qa[4]), e2, V(C.qa[5]) * e3));
-        const V c3 = fma(V(C.qa[6]), e1, fma(V(C.qa[7]), e2, V(C.qa[8]) * e3));
-        g[1] = (g[1] - Etx) - c1;
-        g[2] = (g[2] - Etx) + c1;
-        g[3] = (g[3] - Ety) - c2;
-        g[4] = (g[4] - Ety) + c2;
-        g[5] = (g[5] + P) - c3;
-        g[6] = (g[6] + P) + c3;
+        const V t1 = fma(V(C.qa[0]), e1, fma(V(C.qa[1]), e2, V(C.qa[2]) * e3));
+        const V t2 = fma(V(C.qa[3]), e1, fma(V(C.qa[4]), e2, V(C.qa[5]) * e3));
+        const V t3 = fma(V(C.qa[6]), e1, fma(V(C.qa[7]), e2, V(C.qa[8]) * e3));
+        g[1] = (g[1] - Etx) - t1;
+        g[2] = (g[2] - Etx) + t1;
+        g[3] = (g[3] - Ety) - t2;
+        g[4] = (g[4] - Ety) + t2;
+        g[5] = (g[5] + P) - t3;
+        g[6] = (g[6] + P) + t3;
     } else {
         g[1] = fma(V(-C.rq[1]), e1, g[1] - Etx);
         g[2] = fma(V(C.rq[1]), e1, g[2] - Etx);

@@ -259,12 +259,25 @@ __device__ __forceinline__ F2 plane_value(const F2 d[19], const F2 g[7])
     else return g[Q - 19];
 }
 
-// Registers: 128-thread blocks, DMRT_PAIR_MIN_BLOCKS resident per SM (4 caps
-// the kernel at 128 registers: 512 threads, 1024 cells in flight per SM, as
-// many as the one-cell kernel at 64 registers).
-#ifndef DMRT_PAIR_MIN_BLOCKS
-#define DMRT_PAIR_MIN_BLOCKS 4
+// Block shape: 128 threads, and blocks resident per SM per storage type and
+// scheme (the register cap is 65536 / (128 x blocks); the kernels need
+// 108-114 registers unconstrained).  Measured on GB300 at 256^3 Type 3, what
+// counts is warps in flight, more than a small spill: BF16 takes 296 us
+// (two buffers) and 306 us (in place) with 5 blocks (96 registers, 20 warps,
+// 24-56 bytes spilled), 328 us with 18 warps at 108 registers and 331 us with
+// 24 warps at 80; FP16 takes 317 us with 4 blocks (two buffers, 108
+// registers) against 324 us with 5, but 322 us with 5 in place against 340
+// us with 4.  DMRT_PAIR_MIN_BLOCKS overrides the count for experiments.
+constexpr int kPairThreads = 128;
+template <typename T, bool INPLACE>
+constexpr int pair_blocks()
+{
+#ifdef DMRT_PAIR_MIN_BLOCKS
+    return DMRT_PAIR_MIN_BLOCKS;
+#else
+    return std::is_same_v<T, __half> && !INPLACE ? 4 : 5;
 #endif
+}
 
 // Thread -> pair: x0 = 2 (block x * block width + thread x) must be < nx.
 struct PairCoords {
@@ -289,7 +302,7 @@ __device__ __forceinline__ PairCoords pair_coords(const StepGeometry &S)
 }
 
 template <int WALL, typename T, bool SR>
-__global__ void __launch_bounds__(128, DMRT_PAIR_MIN_BLOCKS)
+__global__ void __launch_bounds__(kPairThreads, (pair_blocks<T, false>()))
     step_pair_kernel(const T *__restrict__ src, T *__restrict__ dst, const StepGeometry S,
                      const CollideParams C)
 {
@@ -324,7 +337,7 @@ __global__ void __launch_bounds__(128, DMRT_PAIR_MIN_BLOCKS)
 // an aligned pair for the planes with e_x = 0 and one element per cell for
 // the others (or, where the link leaves the box, plane opp(q) at the cell).
 template <int WALL, typename T, bool SR, int PHASE>
-__global__ void __launch_bounds__(128, DMRT_PAIR_MIN_BLOCKS)
+__global__ void __launch_bounds__(kPairThreads, (pair_blocks<T, true>()))
     step_inplace_pair_kernel(T *__restrict__ A, const InplaceGeometry SI, const CollideParams C)
 {
     const StepGeometry &S = SI.load;
@@ -605,12 +618,13 @@ bool step_pair_supported(int wall, const Geometry &G)
 namespace {
 
 // Launch shape of the paired kernels: one row of up to 128 cells per block
-// row, 128 threads per block.
+// row, kPairThreads threads per block.
 cudaLaunchConfig_t pair_config(const Geometry &G, cudaStream_t s, cudaLaunchAttribute *attr, bool pdl)
 {
+    const int threads = kPairThreads;
     const int pairs = G.nx / 2;
     const int bx = pairs >= 64 ? 64 : (pairs >= 32 ? 32 : 16);
-    const int by = 128 / bx;
+    const int by = threads / bx > 0 ? threads / bx : 1;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((pairs + bx - 1) / bx, (G.ny + by - 1) / by, G.nz);
     cfg.blockDim = dim3(bx, by, 1);
