@@ -405,14 +405,14 @@ dmrt_status create_common(dmrt_t **out, const int grid[3], double nu, double alp
     lbm::fill_inplace_geometry(h->G, h->SI);
     fill_rates(h);
     // two cells per thread: the paired kernels serve walled boxes with even
-    // nx; auto takes them for 16-bit storage, whose one-cell kernels are
-    // bound by instruction issue rather than by HBM
+    // nx, and auto takes them there (measured faster for every storage
+    // format; the one-cell 16-bit kernels are bound by instruction issue)
     const bool pair_ok = lbm::step_pair_supported(wall_type, h->G);
     if (cpt == 2 && !pair_ok) {
         delete h;
         return DMRT_ERR_ARG;
     }
-    h->cells_per_thread = (cpt == 2 || (cpt == 0 && pair_ok && storage != DMRT_STORE_F32)) ? 2 : 1;
+    h->cells_per_thread = (cpt == 2 || (cpt == 0 && pair_ok)) ? 2 : 1;
     // loads of the paired two-buffer kernel: TMA-staged where the tensor map
     // allows it (16-bit storage, nx a multiple of 8)
     const bool tma_ok = h->cells_per_thread == 2 && !h->inplace &&

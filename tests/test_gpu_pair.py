@@ -137,11 +137,12 @@ def test_one_step_parity_with_the_oracle(dm, grid, wall):
 
 
 def test_auto_choice_and_rejected_requests(dm):
-    """Auto takes two cells for 16-bit storage on even rows of walled boxes,
-    one otherwise; two cells on an odd row or a periodic box are refused."""
+    """Auto takes two cells on even rows of walled boxes, one otherwise; two
+    cells on an odd row or a periodic box are refused."""
     assert dm.Cavity((16, 8, 8), 1e4, storage=dm.STORE_BF16).params["cells_per_thread"] == 2
     assert dm.Cavity((15, 8, 8), 1e4, storage=dm.STORE_BF16).params["cells_per_thread"] == 1
-    assert dm.Cavity((16, 8, 8), 1e4).params["cells_per_thread"] == 1
+    assert dm.Cavity((16, 8, 8), 1e4).params["cells_per_thread"] == 2
+    assert dm.Cavity((16, 8, 8), 1e4, wall_type=0).params["cells_per_thread"] == 1
     assert dm.Cavity((16, 8, 8), 1e4, storage=dm.STORE_F16,
                      streaming=dm.STREAM_INPLACE).params["cells_per_thread"] == 2
     assert dm.Cavity((16, 8, 8), 1e4, storage=dm.STORE_F16, wall_type=0,
@@ -162,7 +163,7 @@ def test_auto_choice_and_rejected_requests(dm):
     assert dm.Cavity((18, 8, 8), 1e4, storage=dm.STORE_BF16).params["pair_loads"] == 1
     assert dm.Cavity((16, 8, 8), 1e4, storage=dm.STORE_BF16,
                      streaming=dm.STREAM_INPLACE).params["pair_loads"] == 0
-    assert dm.Cavity((16, 8, 8), 1e4).params["pair_loads"] == 0
+    assert dm.Cavity((16, 8, 8), 1e4).params["pair_loads"] == 1
     for kw in (dict(grid=(18, 8, 8), storage=dm.STORE_BF16), dict(grid=(16, 8, 8)),
                dict(grid=(16, 8, 8), storage=dm.STORE_BF16, streaming=dm.STREAM_INPLACE)):
         grid = kw.pop("grid")
