@@ -453,6 +453,8 @@ def run_ensemble(args, rank, local, world):
     storage = STORAGES[args.storage]
     streaming = STREAMINGS[args.streaming]
     ens = dmrt.Ensemble(cav, storage=storage, streaming=streaming)
+    ens_kernel = ("ensemble_pair_kernel" if ens.params(0)["cells_per_thread"] == 2
+                  else "ensemble_step_kernel") + (" (in place, both phases)" if streaming else "")
     dmrt.dmrt_ensemble_set_stream(ens.e, stream)
     report = ens.autotune(trials=3)
     cells = ens.cells
@@ -522,7 +524,7 @@ def run_ensemble(args, rank, local, world):
                        "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
-                         "kernel": "ensemble_step_kernel", "bytes_per_cell": stats["bytes_per_cell"],
+                         "kernel": ens_kernel, "bytes_per_cell": stats["bytes_per_cell"],
                          "launch_us": launch_s * 1e6},
             "separate_runs": {"value": separate, "unit": "MLUPS",
                               "what": f"the same {len(cav)} cavities as separate handles, "

@@ -104,8 +104,8 @@ typedef struct dmrt_opts {
                             * arithmetic; needs a walled box and an even nx,
                             * else DMRT_ERR_ARG).  Either streaming scheme.
                             * The stored values are bitwise the same either
-                            * way.  Auto takes 2 where allowed.  Ensembles
-                            * accept 0 or 1. */
+                            * way.  Auto takes 2 where allowed; for an
+                            * ensemble, where every member's nx is even. */
     int pair_loads;        /* how the two-cell kernel of two-buffer 16-bit
                             * storage loads: 0 = auto (direct), 1 = direct
                             * loads, 2 = staged: TMA copies of each plane's

@@ -12,7 +12,8 @@
 // cavity's first block index.  The per-cell arithmetic is the single-cavity
 // body (step_body.cuh), and stochastic rounding draws the same bits from the
 // cell index and step number, so a member evolves bitwise like a single
-// handle of the same cavity.
+// handle of the same cavity.  When every member has an even row length the
+// kernels take two cells per thread (pair_body.cuh), as a single cavity does.
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
@@ -24,7 +25,7 @@
 
 #include "dmrt.h"
 #include "reduce.cuh"
-#include "step_body.cuh"
+#include "pair_body.cuh"
 
 namespace lbm {
 
@@ -198,6 +199,121 @@ __global__ void DMRT_ENS_INPLACE_BOUNDS(PHASE)
             else return self + ((edge & faces) ? SO.template sb<q>() : SO.template sn<q>());
         });
     }
+}
+
+// ---------------------------------------------------------------- two cells per thread
+
+// 128-thread blocks, 5 resident per SM (96 registers), as the single-cavity
+// paired kernels of BF16 storage.
+constexpr int kEnsPairBlocks = 5;
+
+// As locate_cell, for tiles of pairs: the thread holds the cells x0, x0 + 1
+// with x0 = 2 (tile x * bx + thread x).
+__device__ __forceinline__ bool locate_pair(CavityDesc &D, const CavityDesc *__restrict__ descs,
+                                            const int *__restrict__ blockmap, int &x0, int &y, int &z)
+{
+    int xp;
+    (void)locate_cell(D, descs, blockmap, xp, y, z);  // its bound is for one cell per thread
+    x0 = 2 * xp;
+    return x0 < D.nx && y < D.ny;
+}
+
+__device__ __forceinline__ PairFaces pair_faces(const CavityDesc &D, int x0, int y, int z)
+{
+    return PairFaces{x0 == 0, x0 + 2 == D.nx, y == 0, y == D.ny - 1, z == 0, z == D.nz - 1};
+}
+
+template <typename T, bool SR>
+__global__ void __launch_bounds__(128, kEnsPairBlocks)
+    ensemble_pair_kernel(const T *__restrict__ srcb, T *__restrict__ dstb, const CavityDesc *__restrict__ descs,
+                         const int *__restrict__ blockmap, long long counter_at)
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;");
+    unsigned salt = 0;
+    if constexpr (SR) {
+        const unsigned step = *reinterpret_cast<const unsigned *>(srcb + counter_at);
+        if (blockIdx.x == 0 && threadIdx.x == 0)
+            *reinterpret_cast<unsigned *>(dstb + counter_at) = step + 1u;
+        salt = pcg_hash(step);
+    }
+    __shared__ CavityDesc D;
+    int x0, y, z;
+    if (!locate_pair(D, descs, blockmap, x0, y, z)) return;
+    const unsigned self = (static_cast<unsigned>(z) * D.ny + y) * D.nx + x0;
+    F2 d[19], g[7];
+    pull_pair<kRuntimeWall, T>(srcb + D.offset + self,
+                               ComputedOffsets{D.plane, static_cast<unsigned>(D.nx), D.nxy},
+                               pair_faces(D, x0, y, z), theta_linear(y, D.inv_ny), d, g, D.wall != 1,
+                               D.wall == 2);
+    collide(D.C, d, g);
+    // re-read the plane stride after a compiler barrier (see ensemble_cell)
+    asm volatile("" ::: "memory");
+    const unsigned r01 = SR ? pair_bits_salted(self, salt) : 0u;
+    T *Dp = dstb + D.offset + self;
+    const unsigned plane = D.plane;
+    static_for<0, 26>([&](auto I) {
+        constexpr int q = decltype(I)::value;
+        store2<T, SR>(Dp + q * plane, plane_value<q>(d, g), SR ? plane_bits<q>(r01) : 0u);
+    });
+}
+
+// In-place scheme with two cells per thread (see step_inplace_pair_kernel).
+template <typename T, bool SR, int PHASE>
+__global__ void __launch_bounds__(128, kEnsPairBlocks)
+    ensemble_inplace_pair_kernel(T *__restrict__ buf, const CavityDesc *__restrict__ descs,
+                                 const int *__restrict__ blockmap, long long counter_at)
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;");
+    unsigned salt = 0;
+    if constexpr (SR) {
+        unsigned *ctr = reinterpret_cast<unsigned *>(buf + counter_at);
+        const unsigned step = ctr[PHASE];
+        if (blockIdx.x == 0 && threadIdx.x == 0) ctr[PHASE ^ 1] = step + 1u;
+        salt = pcg_hash(step);
+    }
+    __shared__ CavityDesc D;
+    int x0, y, z;
+    if (!locate_pair(D, descs, blockmap, x0, y, z)) return;
+    T *A = buf + D.offset;
+    const unsigned self = (static_cast<unsigned>(z) * D.ny + y) * D.nx + x0;
+    const PairFaces P = pair_faces(D, x0, y, z);
+    F2 d[19], g[7];
+    if constexpr (PHASE == 0)
+        pull_pair<kRuntimeWall, T>(A + self, SwappedOffsets{D.plane, static_cast<unsigned>(D.nx), D.nxy}, P,
+                                   theta_linear(y, D.inv_ny), d, g, D.wall != 1, D.wall == 2);
+    else
+        pull_pair<kRuntimeWall, T>(A + self, LocalOffsets{D.plane}, P, theta_linear(y, D.inv_ny), d, g,
+                                   D.wall != 1, D.wall == 2);
+    collide(D.C, d, g);
+    asm volatile("" ::: "memory");
+    const unsigned r01 = SR ? pair_bits_salted(self, salt) : 0u;
+    T *Dp = A + self;
+    const SwappedOffsets SO{D.plane, static_cast<unsigned>(D.nx), D.nxy};
+    static_for<0, 26>([&](auto I) {
+        constexpr int q = decltype(I)::value;
+        const F2 v = plane_value<q>(d, g);
+        const unsigned r = SR ? plane_bits<q>(r01) : 0u;
+        if constexpr (PHASE == 1) {
+            store2<T, SR>(Dp + plane_opp<q>() * SO.plane, v, r);
+        } else {
+            constexpr int ex = plane_ex<q>(), ey = plane_ey<q>(), ez = plane_ez<q>();
+            bool lyz = false;  // the link leaves through a y or z face
+            if constexpr (ey == 1) lyz = lyz || P.yhi;
+            if constexpr (ey == -1) lyz = lyz || P.ylo;
+            if constexpr (ez == 1) lyz = lyz || P.zhi;
+            if constexpr (ez == -1) lyz = lyz || P.zlo;
+            const unsigned sn = SO.template sn<q>(), sb = SO.template sb<q>();
+            if constexpr (ex == 0) {
+                store2<T, SR>(Dp + (lyz ? sb : sn), v, r);
+            } else {
+                const bool l0 = lyz || (ex == -1 && P.xlo);
+                const bool l1 = lyz || (ex == 1 && P.xhi);
+                store_split<T, SR>(Dp + (l0 ? sb : sn), (Dp + (l1 ? sb : sn)) + 1, v, r);
+            }
+        }
+    });
 }
 
 // ---------------------------------------------------------------- residual
@@ -393,7 +509,7 @@ __global__ void __launch_bounds__(kEnsRedThreads)
 
 cudaError_t launch_ensemble_step(int storage, bool stochastic, const void *src, void *dst,
                                  const CavityDesc *descs, const int *blockmap, long long blocks,
-                                 int threads, long long counter_at, cudaStream_t s, bool pdl)
+                                 int threads, long long counter_at, cudaStream_t s, bool pdl, bool pairs)
 {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(static_cast<unsigned>(blocks));
@@ -406,14 +522,20 @@ cudaError_t launch_ensemble_step(int storage, bool stochastic, const void *src, 
     cfg.numAttrs = pdl ? 1 : 0;
     cudaError_t e = dispatch(1, storage, [&](auto, auto *tp) {
         using T = std::remove_pointer_t<decltype(tp)>;
+        const T *a = static_cast<const T *>(src);
+        T *b = static_cast<T *>(dst);
+        if (pairs) {
+            if constexpr (!std::is_same_v<T, float>) {
+                if (stochastic)
+                    return cudaLaunchKernelEx(&cfg, ensemble_pair_kernel<T, true>, a, b, descs, blockmap, counter_at);
+            }
+            return cudaLaunchKernelEx(&cfg, ensemble_pair_kernel<T, false>, a, b, descs, blockmap, counter_at);
+        }
         if constexpr (!std::is_same_v<T, float>) {
             if (stochastic)
-                return cudaLaunchKernelEx(&cfg, ensemble_step_kernel<T, true>,
-                                          static_cast<const T *>(src), static_cast<T *>(dst), descs,
-                                          blockmap, counter_at);
+                return cudaLaunchKernelEx(&cfg, ensemble_step_kernel<T, true>, a, b, descs, blockmap, counter_at);
         }
-        return cudaLaunchKernelEx(&cfg, ensemble_step_kernel<T, false>, static_cast<const T *>(src),
-                                  static_cast<T *>(dst), descs, blockmap, counter_at);
+        return cudaLaunchKernelEx(&cfg, ensemble_step_kernel<T, false>, a, b, descs, blockmap, counter_at);
     });
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
@@ -421,7 +543,7 @@ cudaError_t launch_ensemble_step(int storage, bool stochastic, const void *src, 
 
 cudaError_t launch_ensemble_inplace(int storage, bool stochastic, void *buf, int phase,
                                     const CavityDesc *descs, const int *blockmap, long long blocks,
-                                    int threads, long long counter_at, cudaStream_t s, bool pdl)
+                                    int threads, long long counter_at, cudaStream_t s, bool pdl, bool pairs)
 {
     if (phase != 0 && phase != 1) return cudaErrorInvalidValue;
     cudaLaunchConfig_t cfg = {};
@@ -436,6 +558,19 @@ cudaError_t launch_ensemble_inplace(int storage, bool stochastic, void *buf, int
     cudaError_t e = dispatch(1, storage, [&](auto, auto *tp) {
         using T = std::remove_pointer_t<decltype(tp)>;
         T *A = static_cast<T *>(buf);
+        if (pairs) {
+            if constexpr (!std::is_same_v<T, float>) {
+                if (stochastic)
+                    return phase == 0 ? cudaLaunchKernelEx(&cfg, ensemble_inplace_pair_kernel<T, true, 0>, A,
+                                                           descs, blockmap, counter_at)
+                                      : cudaLaunchKernelEx(&cfg, ensemble_inplace_pair_kernel<T, true, 1>, A,
+                                                           descs, blockmap, counter_at);
+            }
+            return phase == 0 ? cudaLaunchKernelEx(&cfg, ensemble_inplace_pair_kernel<T, false, 0>, A, descs,
+                                                   blockmap, counter_at)
+                              : cudaLaunchKernelEx(&cfg, ensemble_inplace_pair_kernel<T, false, 1>, A, descs,
+                                                   blockmap, counter_at);
+        }
         if constexpr (!std::is_same_v<T, float>) {
             if (stochastic)
                 return phase == 0 ? cudaLaunchKernelEx(&cfg, ensemble_inplace_kernel<T, true, 0>, A,
@@ -513,6 +648,7 @@ struct dmrt_ensemble {
     void *buf[2] = {nullptr, nullptr};
     int cur = 0;
     bool inplace = false;  // one buffer, in-place streaming (buf[0])
+    bool pairs = false;    // two cells per thread (every member has an even nx)
     int parity = 0;        // in-place: layout of the state (steps mod 2)
     long long device_bytes = 0;
     float *snap = nullptr;
@@ -602,14 +738,17 @@ void fill_rates_desc(lbm::CavityDesc &D, double nu, double alpha, double gbeta)
     D.C.theta_ref = 0.0f;
 }
 
-// Default tile width: the widest of 128 / 64 / 32 not wider than the cavity
-// (rounded up to 32), limited by the block size.
-int default_bx(int nx, int threads)
+// Default tile width in threads: the widest of 128 / 64 / 32 not wider than
+// the cavity (rounded up to 32), limited by the block size.  With two cells
+// per thread a row holds nx / 2 threads, and tiles of 16 are allowed too.
+int default_bx(int nx, int threads, bool pairs)
 {
-    const int w = (nx + 31) / 32 * 32;
-    int bx = 32;
-    for (int cand : {64, 128})
-        if (cand <= w && cand <= threads) bx = cand;
+    const int units = pairs ? nx / 2 : nx;
+    const int q = pairs ? 16 : 32;
+    const int w = (units + q - 1) / q * q;
+    int bx = q;
+    for (int cand : {32, 64, 128})
+        if (cand > bx && cand <= w && cand <= threads) bx = cand;
     return bx;
 }
 
@@ -622,7 +761,8 @@ std::vector<int> layout_step(dmrt_ensemble_t *e, const std::vector<int> &which)
     for (int c : which) {
         lbm::CavityDesc &D = e->desc[c];
         D.by = e->threads / D.bx;
-        D.tiles_x = (D.nx + D.bx - 1) / D.bx;
+        const int units = e->pairs ? D.nx / 2 : D.nx;  // threads along a row
+        D.tiles_x = (units + D.bx - 1) / D.bx;
         D.tiles_y = (D.ny + D.by - 1) / D.by;
         D.block_start = start;
         const long long nb = static_cast<long long>(D.tiles_x) * D.tiles_y * D.nz;
@@ -675,10 +815,10 @@ cudaError_t launch_one_step(dmrt_ensemble_t *e, int from)
     if (e->inplace)
         return lbm::launch_ensemble_inplace(e->storage, e->stochastic, e->buf[0], from, e->d_desc,
                                             e->d_blockmap, e->step_blocks, e->threads,
-                                            e->total_elems, e->stream, e->use_pdl);
+                                            e->total_elems, e->stream, e->use_pdl, e->pairs);
     return lbm::launch_ensemble_step(e->storage, e->stochastic, e->buf[from], e->buf[from ^ 1],
                                      e->d_desc, e->d_blockmap, e->step_blocks, e->threads,
-                                     e->total_elems, e->stream, e->use_pdl);
+                                     e->total_elems, e->stream, e->use_pdl, e->pairs);
 }
 
 bool capture_interval(dmrt_ensemble_t *e, int start)
@@ -804,15 +944,21 @@ dmrt_status dmrt_ensemble_create(dmrt_ensemble_t **out, int count, const dmrt_ca
     *out = nullptr;
     if (count < 1 || !cav) return DMRT_ERR_ARG;
     int storage = DMRT_STORE_F32, K = 100, rounding = DMRT_ROUND_AUTO, streaming = DMRT_STREAM_AB;
+    int cpt = 0;
     if (opts) {
         storage = opts->storage;
         rounding = opts->rounding;
         streaming = opts->streaming;
+        cpt = opts->cells_per_thread;
         if (opts->residual_interval > 0) K = opts->residual_interval;
         if (opts->residual_interval < 0) return DMRT_ERR_ARG;
-        if (opts->cells_per_thread < 0 || opts->cells_per_thread > 1) return DMRT_ERR_ARG;
+        if (cpt < 0 || cpt > 2) return DMRT_ERR_ARG;
         if (opts->pair_loads < 0 || opts->pair_loads > 1) return DMRT_ERR_ARG;
     }
+    // two cells per thread where every member's rows have an even length
+    bool even = true;
+    for (int c = 0; c < count && cav; ++c) even = even && cav[c].grid[0] % 2 == 0;
+    if (cpt == 2 && !even) return DMRT_ERR_ARG;
     if (streaming != DMRT_STREAM_AB && streaming != DMRT_STREAM_INPLACE) return DMRT_ERR_ARG;
     if (storage < DMRT_STORE_F32 || storage > DMRT_STORE_F16) return DMRT_ERR_ARG;
     if (rounding < DMRT_ROUND_AUTO || rounding > DMRT_ROUND_STOCHASTIC) return DMRT_ERR_ARG;
@@ -828,6 +974,7 @@ dmrt_status dmrt_ensemble_create(dmrt_ensemble_t **out, int count, const dmrt_ca
     e->storage = storage;
     e->stochastic = storage != DMRT_STORE_F32 && rounding != DMRT_ROUND_NEAREST;
     e->inplace = streaming == DMRT_STREAM_INPLACE;
+    e->pairs = cpt == 2 || (cpt == 0 && even);
     e->K = K;
     e->in.assign(cav, cav + count);
     e->desc.resize(count);
@@ -859,7 +1006,7 @@ dmrt_status dmrt_ensemble_create(dmrt_ensemble_t **out, int count, const dmrt_ca
         D.plane = static_cast<unsigned>(plane);
         D.nxy = static_cast<unsigned>(nx) * ny;
         D.inv_ny = 1.0f / static_cast<float>(ny);
-        D.bx = default_bx(nx, e->threads);
+        D.bx = default_bx(nx, e->threads, e->pairs);
         D.offset = offset;
         D.snap_offset = snap_off;
         D.red_tiles_x = (nx + 31) / 32;
@@ -1060,12 +1207,15 @@ dmrt_status dmrt_ensemble_autotune(dmrt_ensemble_t *e, int trials, char *report,
     std::string rep;
     for (int threads : {128, 256}) {
         if (DMRT_ENS_INPLACE_BLOCK128 && e->inplace && threads != 128) continue;
+        if (e->pairs && threads != 128) continue;  // the paired kernels are built for 128
         e->threads = threads;
         for (auto &g : groups) {
             int best = -1;
             float best_ms = INFINITY;
-            for (int bx : {32, 64, 128}) {
-                if (bx > threads || bx > (g.first + 31) / 32 * 32 + 32) continue;
+            const int units = e->pairs ? g.first / 2 : g.first;  // threads along a row
+            for (int bx : {16, 32, 64, 128}) {
+                if (bx == 16 && !e->pairs) continue;
+                if (bx > threads || bx > (units + 15) / 16 * 16 + 32) continue;
                 for (int c : g.second) e->desc[c].bx = bx;
                 float ms = 0.f;
                 dmrt_status st = time_layout(g.second, &ms);
@@ -1289,6 +1439,8 @@ dmrt_status dmrt_ensemble_member_params(const dmrt_ensemble_t *e, int member, dm
     out->tau_alpha = 0.5 + 4.0 * e->alpha[member];
     out->steps = e->steps;
     out->streaming = e->inplace ? DMRT_STREAM_INPLACE : DMRT_STREAM_AB;
+    out->cells_per_thread = e->pairs ? 2 : 1;
+    out->pair_loads = e->pairs && !e->inplace ? 1 : 0;
     out->device_bytes = e->device_bytes;
     return DMRT_OK;
 }

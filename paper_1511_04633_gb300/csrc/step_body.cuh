@@ -232,6 +232,7 @@ __device__ __forceinline__ void collide_pairs(const CollideParams &C, float d[19
 // tables of one cavity.
 struct TableOffsets {
     const StepGeometry &S;
+    static constexpr bool kLocal = false;
     template <int Q>
     __device__ __forceinline__ unsigned nb() const { return static_cast<unsigned>(S.nb[Q]); }
     template <int Q>
@@ -242,6 +243,7 @@ struct TableOffsets {
 // (used where many cavities share one launch).
 struct ComputedOffsets {
     unsigned plane, nx, nxy;
+    static constexpr bool kLocal = false;
     template <int Q>
     __device__ __forceinline__ unsigned nb() const
     {
@@ -358,6 +360,7 @@ __device__ constexpr unsigned leaving_faces()
 // own slot of plane q.
 struct LocalOffsets {
     unsigned plane;
+    static constexpr bool kLocal = true;  // every plane from the cell's own slot
     template <int Q>
     __device__ __forceinline__ unsigned nb() const { return Q * plane; }
     template <int Q>
@@ -370,6 +373,7 @@ struct LocalOffsets {
 // e_q (sn), or to plane opp(q) at x when that link leaves the box (sb).
 struct SwappedOffsets {
     unsigned plane, nx, nxy;
+    static constexpr bool kLocal = false;
     template <int Q>
     __device__ __forceinline__ int off() const
     {

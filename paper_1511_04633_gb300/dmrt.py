@@ -489,7 +489,8 @@ def _echeck(e, status, what):
 
 
 def dmrt_ensemble_create(cavities, storage: int = STORE_F32, residual_interval: int = 0,
-                         rounding: int = ROUND_AUTO, streaming: int = STREAM_AB):
+                         rounding: int = ROUND_AUTO, streaming: int = STREAM_AB,
+                         cells_per_thread: int = 0):
     """cavities: iterable of dicts {"grid": (nx, ny, nz), "Ra", "Pr", "Ma", "wall"}."""
     L = load()
     cav = list(cavities)
@@ -501,7 +502,7 @@ def dmrt_ensemble_create(cavities, storage: int = STORE_F32, residual_interval: 
         arr[k].Ma = c.get("Ma", 0.1)
         arr[k].wall_type = c["wall"]
     e = ctypes.c_void_p()
-    opts = dmrt_opts(storage, residual_interval, rounding, streaming)
+    opts = dmrt_opts(storage, residual_interval, rounding, streaming, cells_per_thread)
     _echeck(None, L.dmrt_ensemble_create(ctypes.byref(e), len(cav), arr, ctypes.byref(opts)),
             "dmrt_ensemble_create")
     return e
@@ -594,10 +595,11 @@ class Ensemble:
     list of dicts {"grid": (nx, ny, nz), "Ra": .., "wall": 1..3, ["Pr", "Ma"]}."""
 
     def __init__(self, cavities, storage=STORE_F32, residual_interval=0, rounding=ROUND_AUTO,
-                 streaming=STREAM_AB):
+                 streaming=STREAM_AB, cells_per_thread=0):
         self.cavities = [dict(c) for c in cavities]
         self.count = len(self.cavities)
-        self.e = dmrt_ensemble_create(self.cavities, storage, residual_interval, rounding, streaming)
+        self.e = dmrt_ensemble_create(self.cavities, storage, residual_interval, rounding, streaming,
+                                      cells_per_thread)
 
     def close(self):
         if getattr(self, "e", None):

@@ -228,3 +228,56 @@ def test_in_place_ensemble_holds_half_the_populations(dm):
     assert pi["streaming"] == dm.STREAM_INPLACE
     elems = sum((m["grid"][0] * m["grid"][1] * m["grid"][2] + 63) // 64 * 64 * 26 for m in MEMBERS)
     assert pa["device_bytes"] - pi["device_bytes"] == elems * 4 + 256
+
+
+# every row length even: the ensemble takes two cells per thread (a 16-wide
+# row gives 8-thread rows of pairs, tiles of 16 threads)
+EVEN = [
+    {"grid": (16, 16, 16), "Ra": 1e4, "wall": 1},
+    {"grid": (20, 18, 16), "Ra": 5e4, "wall": 3},
+    {"grid": (24, 24, 24), "Ra": 1e5, "wall": 2},
+    {"grid": (38, 20, 13), "Ra": 3e4, "wall": 2},
+    {"grid": (12, 12, 12), "Ra": 1e3, "wall": 1},
+    {"grid": (130, 9, 5), "Ra": 2e5, "wall": 3},
+]
+
+
+@pytest.mark.parametrize("streaming", [0, 1], ids=["ab", "inplace"])
+@pytest.mark.parametrize("storage", [0, 1, 2], ids=["f32", "bf16", "f16"])
+def test_paired_members_evolve_bitwise_like_single_cavities(dm, storage, streaming):
+    """Two cells per thread in the ensemble: every member bitwise equal to a
+    single handle and to the same ensemble with one cell per thread, over 73
+    steps (an odd count ends the in-place state in the streamed layout)."""
+    two = dm.Ensemble(EVEN, storage=storage, streaming=streaming)
+    one = dm.Ensemble(EVEN, storage=storage, streaming=streaming, cells_per_thread=1)
+    assert two.params(0)["cells_per_thread"] == 2 and one.params(0)["cells_per_thread"] == 1
+    two.step(73)
+    one.step(73)
+    for k, m in enumerate(EVEN):
+        single = dm.Cavity(m["grid"], m["Ra"], wall_type=m["wall"], storage=storage, streaming=streaming)
+        single.step(73)
+        fe, ge = two.populations(k)
+        fo, go = one.populations(k)
+        fs, gs = single.populations()
+        assert np.array_equal(fe, fo) and np.array_equal(ge, go), k
+        assert np.array_equal(fe, fs) and np.array_equal(ge, gs), k
+
+
+def test_paired_ensemble_autotune_and_requests(dm):
+    """Autotuning the paired ensemble keeps its state; a member with an odd
+    row length means one cell per thread, and asking for two is refused."""
+    ens = dm.Ensemble(EVEN, storage=dm.STORE_BF16)
+    ref = dm.Ensemble(EVEN, storage=dm.STORE_BF16)
+    ens.step(20)
+    ref.step(20)
+    report = ens.autotune(trials=2)
+    assert "threads=128" in report
+    ens.step(30)
+    ref.step(30)
+    for k in range(len(EVEN)):
+        fa, ga = ens.populations(k)
+        fb, gb = ref.populations(k)
+        assert np.array_equal(fa, fb) and np.array_equal(ga, gb), k
+    assert dm.Ensemble(MEMBERS).params(0)["cells_per_thread"] == 1
+    with pytest.raises(dm.DmrtError):
+        dm.Ensemble(MEMBERS, cells_per_thread=2)
