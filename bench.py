@@ -61,8 +61,10 @@ _BODY = ["paper_1511_04633_gb300/csrc/step_body.cuh", "paper_1511_04633_gb300/cs
 # sources of each step kernel: one cell per thread (two buffers), two cells
 # per thread (two buffers; direct or TMA-staged loads), in place
 KERNEL_SOURCES = {"ab": ["paper_1511_04633_gb300/csrc/step.cu"] + _BODY,
-                  "pair": ["paper_1511_04633_gb300/csrc/step_pair.cu"] + _BODY,
+                  "pair": ["paper_1511_04633_gb300/csrc/step_pair.cu",
+                           "paper_1511_04633_gb300/csrc/pair_body.cuh"] + _BODY,
                   "pair_tma": ["paper_1511_04633_gb300/csrc/step_pair.cu",
+                               "paper_1511_04633_gb300/csrc/pair_body.cuh",
                                "paper_1511_04633_gb300/csrc/umma.cuh"] + _BODY,
                   "inplace": ["paper_1511_04633_gb300/csrc/step_inplace.cu"] + _BODY}
 STEP_KERNEL_SOURCES = KERNEL_SOURCES["ab"]
