@@ -246,7 +246,7 @@ __global__ void __launch_bounds__(128, kEnsPairBlocks)
                                ComputedOffsets{D.plane, static_cast<unsigned>(D.nx), D.nxy},
                                pair_faces(D, x0, y, z), theta_linear(y, D.inv_ny), d, g, D.wall != 1,
                                D.wall == 2);
-    collide(D.C, d, g);
+    collide_stored<T>(D.C, d, g);
     // re-read the plane stride after a compiler barrier (see ensemble_cell)
     asm volatile("" ::: "memory");
     const unsigned r01 = SR ? pair_bits_salted(self, salt) : 0u;
@@ -286,7 +286,7 @@ __global__ void __launch_bounds__(128, kEnsPairBlocks)
     else
         pull_pair<kRuntimeWall, T>(A + self, LocalOffsets{D.plane}, P, theta_linear(y, D.inv_ny), d, g,
                                    D.wall != 1, D.wall == 2);
-    collide(D.C, d, g);
+    collide_stored<T>(D.C, d, g);
     asm volatile("" ::: "memory");
     const unsigned r01 = SR ? pair_bits_salted(self, salt) : 0u;
     T *Dp = A + self;

@@ -14,12 +14,15 @@ namespace lbm {
 // the lower address.  A 16-bit pair is packed into one 32-bit word (lane x in
 // the low half), rounded to nearest (pack) or stochastically (pack_sr: bits
 // 15..0 of r round lane x, bits 31..16 lane y; FP16 uses bits 12..0 and
-// 28..16 of them).
+// 28..16 of them).  Loads and stores move the stored numbers as they are:
+// 2^kShift times the populations (FP16: the 2^10 storage scale), the units
+// in which the paired kernels collide (collide<F2, kShift>).
 template <typename T>
 struct Pair;
 
 template <>
 struct Pair<float> {
+    static constexpr int kShift = 0;
     static __device__ __forceinline__ float2 ld2(const float *p) { return *reinterpret_cast<const float2 *>(p); }
     static __device__ __forceinline__ float ld1(const float *p) { return *p; }
     static __device__ __forceinline__ void st2(float *p, F2 v, unsigned) { *reinterpret_cast<float2 *>(p) = v.v; }
@@ -54,6 +57,7 @@ struct Pair16 {
 
 template <>
 struct Pair<__nv_bfloat16> : Pair16<__nv_bfloat16, Pair<__nv_bfloat16>> {
+    static constexpr int kShift = 0;
     static __device__ __forceinline__ float2 ld2(const __nv_bfloat16 *p)
     {
         const unsigned w = *reinterpret_cast<const unsigned *>(p);
@@ -74,30 +78,46 @@ struct Pair<__nv_bfloat16> : Pair16<__nv_bfloat16, Pair<__nv_bfloat16>> {
     }
 };
 
-// half: stored times 2^10 like Store<__half>; the scale is exact both ways
+// half: the stored numbers are 2^10 times the populations (Store<__half>);
+// the paired kernels keep that scale through the collision, so no load or
+// store multiplies by it.
 template <>
 struct Pair<__half> : Pair16<__half, Pair<__half>> {
+    static constexpr int kShift = 10;
+    static_assert(Store<__half>::kScale == static_cast<float>(1 << kShift), "FP16 storage scale");
     static __device__ __forceinline__ float2 ld2(const __half *p)
     {
-        const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(p));
-        return (F2(f) * F2(1.0f / Store<__half>::kScale)).v;
+        return __half22float2(*reinterpret_cast<const __half2 *>(p));
     }
-    static __device__ __forceinline__ float ld1(const __half *p) { return Store<__half>::ld(p); }
+    static __device__ __forceinline__ float ld1(const __half *p) { return __half2float(*p); }
     static __device__ __forceinline__ unsigned pack_rn(F2 v)
     {
-        const F2 s = v * F2(Store<__half>::kScale);
         unsigned w;
-        asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(w) : "f"(s.v.y), "f"(s.v.x));
+        asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(w) : "f"(v.v.y), "f"(v.v.x));
         return w;
     }
     static __device__ __forceinline__ unsigned pack_sr(F2 v, unsigned r)
     {
-        const F2 s = v * F2(Store<__half>::kScale);
         unsigned w;
-        asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(w) : "f"(s.v.y), "f"(s.v.x), "r"(r));
+        asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(w) : "f"(v.v.y), "f"(v.v.x), "r"(r));
         return w;
     }
 };
+
+// Collision of a pair in the units of the stored numbers of format T.
+template <typename T>
+__device__ __forceinline__ void collide_stored(const CollideParams &C, F2 d[19], F2 g[7])
+{
+    collide<F2, Pair<T>::kShift>(C, d, g);
+}
+
+// Coefficient of T_w in the anti-bounce-back rule g = 2 w_T T_w - g* (2 w_T =
+// 1/4, Sec. 3.2), in the units of the stored numbers of format T.
+template <typename T>
+__device__ __forceinline__ constexpr float wall_coef()
+{
+    return 0.25f * static_cast<float>(1 << Pair<T>::kShift);
+}
 
 // Store helpers that hide the float / 16-bit difference in the kernels.
 template <typename T, bool SR>
@@ -206,14 +226,14 @@ __device__ __forceinline__ void pull_pair(const T *Bp, const Off &O, const PairF
             float tw;
             if constexpr (axis == 1) tw = (ey == 1) ? 0.5f : -0.5f;
             else tw = th_lin;
-            v0 = (o0 && dir) ? fmaf(0.25f, tw, -v0) : v0;  // anti-bounce-back, 2 w_T,i = 1/4
-            v1 = (o1 && dir) ? fmaf(0.25f, tw, -v1) : v1;
+            v0 = (o0 && dir) ? fmaf(wall_coef<T>(), tw, -v0) : v0;  // anti-bounce-back
+            v1 = (o1 && dir) ? fmaf(wall_coef<T>(), tw, -v1) : v1;
         } else if constexpr (i != 0 && dirichlet_axis<WALL>(axis)) {
             float tw;
             if constexpr (axis == 1) tw = (ey == 1) ? 0.5f : -0.5f;
             else tw = th_lin;
-            v0 = o0 ? fmaf(0.25f, tw, -v0) : v0;  // anti-bounce-back, 2 w_T,i = 1/4
-            v1 = o1 ? fmaf(0.25f, tw, -v1) : v1;
+            v0 = o0 ? fmaf(wall_coef<T>(), tw, -v0) : v0;  // anti-bounce-back
+            v1 = o1 ? fmaf(wall_coef<T>(), tw, -v1) : v1;
         }
         g[i] = F2(v0, v1);
     });

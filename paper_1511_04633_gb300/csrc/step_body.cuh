@@ -28,9 +28,22 @@ namespace lbm {
 // explicit rounding modes, and the compiler may do the same to float code;
 // so every such pair is written as fma(), and a product that is subtracted
 // enters as the product of a negated factor.
-template <typename V>
+//
+// kShift > 0: d and g hold the populations times S = 2^kShift (the FP16
+// storage scale, so the kernels load and store the stored numbers as they
+// are), and the results are scaled alike.  The collision is linear in the
+// populations except through rho, V and T, which are unscaled (rho, T) or
+// divided by S through 1/rho (V), and through the products of two j
+// components, which carry S^2 and lose one S through their constant factor
+// or one multiply; the force terms take S in their constant factors.
+// Multiplying by a power of two commutes with rounding, so every value is
+// exactly S times its value at kShift = 0.
+template <typename V, int kShift = 0>
 __device__ __forceinline__ void collide(const CollideParams &C, V d[19], V g[7])
 {
+    constexpr bool kScaled = kShift != 0;
+    constexpr float kS = static_cast<float>(1u << kShift), kU = 1.0f / kS;
+
     // ---- opposite-velocity pairs (i, opp(i)): sums s and differences a
     const V s1 = d[1] + d[2], a1 = d[1] - d[2];          // (+-1, 0, 0)
     const V s3 = d[3] + d[4], a3 = d[3] - d[4];          // (0, +-1, 0)
@@ -59,12 +72,25 @@ __device__ __forceinline__ void collide(const CollideParams &C, V d[19], V g[7])
     const V tsm = (tsx + tsy) + tsz;
     const V T = g[0] + tsm;
 
-    const V rho = drho + V(1.0f);
-    const V ir = recip(rho);
+    // rho and T unscaled, 1/rho divided by S (the same values at kShift = 0)
+    V Tu = T, rho, ir;
+    if constexpr (kScaled) {
+        Tu = T * V(kU);
+        rho = fma(drho, V(kU), V(1.0f));
+        ir = recip(rho) * V(kU);
+    } else {
+        rho = drho + V(1.0f);
+        ir = recip(rho);
+    }
     const V vx = jx * ir, vy = jy * ir, vz = jz * ir;
     const V njz = jz * V(-1.0f);
-    const V jj = fma(jx, jx, fma(jy, jy, jz * jz));  // |j|^2
-    const V pww = fma(jy, jy, njz * jz);             // jy^2 - jz^2
+    const V jj = fma(jx, jx, fma(jy, jy, jz * jz));  // S^2 |j|^2
+    const V pww = fma(jy, jy, njz * jz);             // S^2 (jy^2 - jz^2)
+    // S times a product of two j components (identity at kShift = 0)
+    auto unS = [&](V p) {
+        if constexpr (kScaled) return p * V(kU);
+        else return p;
+    };
 
     // ---- moments m_k of the deviations (Eqs. (21), (22)): the moments of w
     // are the rest equilibrium moments and cancel against those of m^eq.
@@ -88,7 +114,7 @@ __device__ __forceinline__ void collide(const CollideParams &C, V d[19], V g[7])
     const V m11 = d35 + dAB, m12 = fma(V(-2.0f), d35, dAB);
     const V m13 = s7 - s8, m14 = s15 - s16, m15 = s11 - s12;
     const V m16 = X1 - X2, m17 = Y2 - Y1, m18 = Z1 - Z2;
-    const V meq9 = fma(V(3.0f) * jx, jx, jj * V(-1.0f));
+    const V meq9 = fma(V(3.0f) * jx, jx, jj * V(-1.0f));  // S^2 m9eq
 
     // ---- buoyancy in moment space.  With G = (0, 0, G_z) (Eq. (16)) and
     // F_i = G_z (e_iz - V_z) f_eq,i / c_s^2 (Eqs. (15), (17)), the moments
@@ -105,7 +131,7 @@ __device__ __forceinline__ void collide(const CollideParams &C, V d[19], V g[7])
     // h_k = F^_k / |M_k|^2 with |M_k|^2 = 2394, 252, 40, 40, 10, 40, 36, 72,
     // 12, 24, 4, 4, 4, 8, 8, 8 (k = 1, 2, 4, 6, 7, 8, 9, ..., 18), constants
     // folded in.
-    const V gbt = V(C.gbeta) * (T - V(C.theta_ref));
+    const V gbt = V(C.gbeta) * (Tu - V(C.theta_ref));
     const V gr = gbt * rho;
     const V gv = gr * vz;
     const V vxy = fma(vx, vx, vy * vy);                  // V_x^2 + V_y^2
@@ -113,32 +139,35 @@ __device__ __forceinline__ void collide(const CollideParams &C, V d[19], V g[7])
     const V dxy = fma(vx, vx, (vy * V(-1.0f)) * vy);     // V_x^2 - V_y^2
     const V dyz = fma(vy, vy, (vz * V(-1.0f)) * vz);     // V_y^2 - V_z^2
     const V gvx = gv * vx, gvy = gv * vy;
-    const V h9 = gv * fma(V(-0.25f), vx * vx, fma(V(1.0f / 12.0f), vv, V(-1.0f / 18.0f)));
-    const V h11 = gv * fma(V(-0.25f), dyz, V(-1.0f / 6.0f));
-    const V grz = gr * fma(V(-0.75f), vz * vz, V(0.25f));
+    const V h9 = gv * fma(V(-0.25f * kS), vx * vx,
+                          fma(V((1.0f / 12.0f) * kS), vv, V((-1.0f / 18.0f) * kS)));
+    const V h11 = gv * fma(V(-0.25f * kS), dyz, V((-1.0f / 6.0f) * kS));
+    const V grz = gr * fma(V(-0.75f * kS), vz * vz, V(0.25f * kS));
 
     // ---- post-collision moments over their norms, c_k = m*_k / |M_k|^2 with
     // m*_k = m_k - s_k (m_k - m_k^eq) + F^_k (Eqs. (19), (24), (26)):
     // c_k = w_k m_k + r_k m_k^eq + h_k, w_k = (1 - s_k)/|M_k|^2, r_k = s_k/|M_k|^2.
     // The conserved moments keep m*_0 = drho, m*_3,5 = j_x,y, m*_7 = j_z + g.
-    const V c1 = fma(m1, V(C.ws[1]), fma(V(C.rs[1]), fma(V(-11.0f), drho, V(19.0f) * jj),
-                                       gv * fma(V(-57.0f / 2394.0f), vv, V(38.0f / 2394.0f))));
-    const V c2 = fma(m2, V(C.ws[2]), fma(V(C.rs[2]), fma(V(3.0f), drho, V(-5.5f) * jj),
-                                       gv * fma(V(16.5f / 252.0f), vv, V(-11.0f / 252.0f))));
-    const V c4 = fma(m4, V(C.ws[4]), fma(V(C.rs[4]), jx * V(-2.0f / 3.0f), gvx * V(0.125f)));
-    const V c6 = fma(m6, V(C.ws[6]), fma(V(C.rs[6]), jy * V(-2.0f / 3.0f), gvy * V(0.125f)));
+    const V c1 = fma(m1, V(C.ws[1]), fma(V(C.rs[1]), fma(V(-11.0f), drho, V(19.0f * kU) * jj),
+                                       gv * fma(V((-57.0f / 2394.0f) * kS), vv,
+                                                V((38.0f / 2394.0f) * kS))));
+    const V c2 = fma(m2, V(C.ws[2]), fma(V(C.rs[2]), fma(V(3.0f), drho, V(-5.5f * kU) * jj),
+                                       gv * fma(V((16.5f / 252.0f) * kS), vv,
+                                                V((-11.0f / 252.0f) * kS))));
+    const V c4 = fma(m4, V(C.ws[4]), fma(V(C.rs[4]), jx * V(-2.0f / 3.0f), gvx * V(0.125f * kS)));
+    const V c6 = fma(m6, V(C.ws[6]), fma(V(C.rs[6]), jy * V(-2.0f / 3.0f), gvy * V(0.125f * kS)));
     const V c8 = fma(m8, V(C.ws[8]), fma(V(C.rs[8]), jz * V(-2.0f / 3.0f),
-                                       gr * fma(V(0.0625f), vxy, V(-1.0f / 60.0f))));
-    const V c9 = fma(m9, V(C.ws[9]), fma(V(C.rs[9]), meq9, h9));
-    const V c10 = fma(m10, V(C.ws[10]), fma(V(C.rs[10]), meq9 * V(-0.5f), h9 * V(-0.25f)));
-    const V c11 = fma(m11, V(C.ws[11]), fma(V(C.rs[11]), pww, h11));
-    const V c12 = fma(m12, V(C.ws[12]), fma(V(C.rs[12]), pww * V(-0.5f), h11 * V(-0.25f)));
-    const V c13 = fma(m13, V(C.ws[13]), fma(V(C.rs[13]), jx * jy, (gvx * vy) * V(-0.75f)));
-    const V c14 = fma(m14, V(C.ws[14]), fma(V(C.rs[14]), jy * jz, grz * vy));
-    const V c15 = fma(m15, V(C.ws[15]), fma(V(C.rs[15]), jx * jz, grz * vx));
-    const V c16 = fma(m16, V(C.ws[16]), gvx * V(-0.375f));
-    const V c17 = fma(m17, V(C.ws[17]), gvy * V(0.375f));
-    const V c18 = fma(m18, V(C.ws[18]), (gr * V(0.1875f)) * dxy);
+                                       gr * fma(V(0.0625f * kS), vxy, V((-1.0f / 60.0f) * kS))));
+    const V c9 = fma(m9, V(C.ws[9]), fma(V(C.rs[9]), unS(meq9), h9));
+    const V c10 = fma(m10, V(C.ws[10]), fma(V(C.rs[10]), meq9 * V(-0.5f * kU), h9 * V(-0.25f)));
+    const V c11 = fma(m11, V(C.ws[11]), fma(V(C.rs[11]), unS(pww), h11));
+    const V c12 = fma(m12, V(C.ws[12]), fma(V(C.rs[12]), pww * V(-0.5f * kU), h11 * V(-0.25f)));
+    const V c13 = fma(m13, V(C.ws[13]), fma(V(C.rs[13]), unS(jx * jy), (gvx * vy) * V(-0.75f * kS)));
+    const V c14 = fma(m14, V(C.ws[14]), fma(V(C.rs[14]), unS(jy * jz), grz * vy));
+    const V c15 = fma(m15, V(C.ws[15]), fma(V(C.rs[15]), unS(jx * jz), grz * vx));
+    const V c16 = fma(m16, V(C.ws[16]), gvx * V(-0.375f * kS));
+    const V c17 = fma(m17, V(C.ws[17]), gvy * V(0.375f * kS));
+    const V c18 = fma(m18, V(C.ws[18]), (gr * V(0.1875f * kS)) * dxy);
 
     // ---- back-transform f* = M^T c (M^-1 = M^T diag(1/|M_k|^2)), one even (E)
     // and one odd (O) partial sum per pair: f*_i = E + O, f*_opp = E - O.
@@ -150,7 +179,9 @@ __device__ __forceinline__ void collide(const CollideParams &C, V d[19], V g[7])
     const V FP = fma(V(2.0f), c10, Fc - c9);
     const V Q = fma(V(-2.0f), c12, c11);
     const V Efy = FP + Q, Efz = FP - Q;
-    const V jzg = fma(gbt, rho, jz);  // j_z + g
+    V gbts = gbt;  // S g_beta (T - T_ref)
+    if constexpr (kScaled) gbts = gbt * V(kS);
+    const V jzg = fma(gbts, rho, jz);  // j_z + g
     const V Ofx = fma(V(-4.0f), c4, jx * V(0.1f));
     const V Ofy = fma(V(-4.0f), c6, jy * V(0.1f));
     const V Ofz = fma(V(-4.0f), c8, jzg * V(0.1f));

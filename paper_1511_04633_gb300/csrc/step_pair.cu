@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(kPairThreads, (pair_blocks<T, false>()))
     if (!c.valid) return;
     F2 d[19], g[7];
     pull_pair<WALL, T>(src + c.self, TableOffsets{S}, c.faces, c.th_lin, d, g);
-    collide(C, d, g);
+    collide_stored<T>(C, d, g);
     // every plane of the pair: one 2-element store at the cells' own slots
     unsigned r01 = 0;
     if constexpr (SR) {
@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(kPairThreads, (pair_blocks<T, true>()))
     F2 d[19], g[7];
     if constexpr (PHASE == 0) pull_pair<WALL, T>(A + c.self, TableOffsets{S}, c.faces, c.th_lin, d, g);
     else pull_pair<WALL, T>(A + c.self, LocalOffsets{S.plane}, c.faces, c.th_lin, d, g);
-    collide(C, d, g);
+    collide_stored<T>(C, d, g);
     unsigned r01 = 0;
     if constexpr (SR) {
         unsigned *ctr = reinterpret_cast<unsigned *>(A + static_cast<size_t>(kPlanes) * S.plane);
@@ -345,13 +345,13 @@ __global__ void __launch_bounds__(kTmaPairs * kTmaRows, 1)
                     float tw;
                     if constexpr (axis == 1) tw = (plane_ey<q>() == 1) ? 0.5f : -0.5f;
                     else tw = th_lin;
-                    a = o0[q] ? fmaf(0.25f, tw, -a) : a;  // anti-bounce-back, 2 w_T,i = 1/4
-                    b = o1[q] ? fmaf(0.25f, tw, -b) : b;
+                    a = o0[q] ? fmaf(wall_coef<T>(), tw, -a) : a;  // anti-bounce-back
+                    b = o1[q] ? fmaf(wall_coef<T>(), tw, -b) : b;
                 }
                 if constexpr (q < 19) d[q] = F2(a, b);
                 else g[q - 19] = F2(a, b);
             });
-            collide(C, d, g);
+            collide_stored<T>(C, d, g);
             unsigned r01 = 0;
             if constexpr (SR) {
                 if (self == 0) *reinterpret_cast<unsigned *>(dst + static_cast<size_t>(kPlanes) * S.plane) = step + 1u;
@@ -392,7 +392,13 @@ cudaLaunchConfig_t pair_config(const Geometry &G, cudaStream_t s, cudaLaunchAttr
 {
     const int threads = kPairThreads;
     const int pairs = G.nx / 2;
-    const int bx = pairs >= 64 ? 64 : (pairs >= 32 ? 32 : 16);
+    // the tile width (in pairs) that launches the fewest idle threads along a
+    // row, the widest of equals: 48 pairs take 3 tiles of 16, not 2 of 32
+    int bx = 16, slots = (pairs + 15) / 16 * 16;
+    for (int cand : {32, 64}) {
+        const int c = (pairs + cand - 1) / cand * cand;
+        if (c <= slots) bx = cand, slots = c;
+    }
     const int by = threads / bx > 0 ? threads / bx : 1;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((pairs + bx - 1) / bx, (G.ny + by - 1) / by, G.nz);
