@@ -66,7 +66,9 @@ KERNEL_SOURCES = {"ab": ["paper_1511_04633_gb300/csrc/step.cu"] + _BODY,
                   "pair_tma": ["paper_1511_04633_gb300/csrc/step_pair.cu",
                                "paper_1511_04633_gb300/csrc/pair_body.cuh",
                                "paper_1511_04633_gb300/csrc/umma.cuh"] + _BODY,
-                  "inplace": ["paper_1511_04633_gb300/csrc/step_inplace.cu"] + _BODY}
+                  "inplace": ["paper_1511_04633_gb300/csrc/step_inplace.cu"] + _BODY,
+                  "inplace_pair": ["paper_1511_04633_gb300/csrc/step_pair.cu",
+                                   "paper_1511_04633_gb300/csrc/pair_body.cuh"] + _BODY}
 STEP_KERNEL_SOURCES = KERNEL_SOURCES["ab"]
 
 
@@ -187,7 +189,7 @@ def step_kernel_digest(scheme: str = "ab") -> str:
 def profiled_traffic(storage: str = "f32", wall: int = 2, scheme: str = "ab"):
     """DRAM bytes per step-kernel launch from the committed ncu summary, only
     if it was taken on the current kernel sources for this storage, wall and
-    kernel scheme ("ab", "pair" or "inplace")."""
+    kernel scheme ("ab", "pair", "pair_tma", "inplace" or "inplace_pair")."""
     path = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
     try:
         with open(path) as fh:
@@ -283,8 +285,10 @@ def run_dmrt(args, rank, local, world):
     dmrt.dmrt_set_stream(cav.h, stream)
     inner = args.inner
     cpt = cav.params["cells_per_thread"]
-    scheme = ("inplace" if args.streaming == "inplace" else
-              {1: "ab", 2: ("pair_tma" if cav.params["pair_loads"] == 2 else "pair")}[cpt])
+    if args.streaming == "inplace":
+        scheme = {1: "inplace", 2: "inplace_pair"}[cpt]
+    else:
+        scheme = {1: "ab", 2: ("pair_tma" if cav.params["pair_loads"] == 2 else "pair")}[cpt]
 
     def one_step():
         dmrt.dmrt_step(cav.h, inner)
@@ -388,7 +392,9 @@ def run_dmrt(args, rank, local, world):
                                 "pair": f"step_pair_kernel<{args.wall}, {args.storage}>",
                                 "pair_tma": f"step_pair_tma_kernel<{args.wall}, {args.storage}>",
                                 "inplace": f"step_inplace_kernel<{args.wall}, {args.storage}> "
-                                           "(both phases)"}[scheme],
+                                           "(both phases)",
+                                "inplace_pair": f"step_inplace_pair_kernel<{args.wall}, {args.storage}> "
+                                                "(both phases)"}[scheme],
                      "bytes_per_cell": bytes_per_cell, "launch_us": launch_s * 1e6},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": h2d,

@@ -28,15 +28,15 @@ namespace lbm {
 
 namespace {
 
-// Block shape: 128 threads, and blocks resident per SM per storage type and
-// scheme (the register cap is 65536 / (128 x blocks); the kernels need
-// 108-114 registers unconstrained).  Measured on GB300 at 256^3 Type 3, what
-// counts is warps in flight, more than a small spill: BF16 takes 296 us
-// (two buffers) and 306 us (in place) with 5 blocks (96 registers, 20 warps,
-// 24-56 bytes spilled), 328 us with 18 warps at 108 registers and 331 us with
-// 24 warps at 80; FP16 takes 317 us with 4 blocks (two buffers, 108
-// registers) against 324 us with 5, but 322 us with 5 in place against 340
-// us with 4.  DMRT_PAIR_MIN_BLOCKS overrides the count for experiments.
+// Block shape: 128 threads, 5 blocks resident per SM (the register cap is
+// 65536 / (128 x 5) = 102, rounded down to 96; the kernels need 108
+// registers unconstrained).  Measured on GB300 at 256^3 Type 3, what counts
+// is warps in flight, more than a small spill: BF16 takes 296 us (two
+// buffers) and 306 us (in place) with 5 blocks (96 registers, 20 warps, 24-56
+// bytes spilled), 328 us with 18 warps at 108 registers and 331 us with 24
+// warps at 80.  FP16, which collides in the stored units, takes 333 us with 5
+// blocks against 341 us with 4 (Type 1: 328 against 352 us; host-timed runs
+// of 200 steps).  DMRT_PAIR_MIN_BLOCKS overrides the count for experiments.
 constexpr int kPairThreads = 128;
 template <typename T, bool INPLACE>
 constexpr int pair_blocks()
@@ -44,7 +44,7 @@ constexpr int pair_blocks()
 #ifdef DMRT_PAIR_MIN_BLOCKS
     return DMRT_PAIR_MIN_BLOCKS;
 #else
-    return std::is_same_v<T, __half> && !INPLACE ? 4 : 5;
+    return 5;
 #endif
 }
 

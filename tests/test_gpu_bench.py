@@ -52,3 +52,6 @@ def test_bench_line_has_the_contract_keys(torch, streaming):
     assert d["gpu_launches"] >= 3 * 20
     assert d["e2e"]["h2d_bytes_per_step"] == 20 * cells
     assert d["config"]["streaming"].startswith("two" if streaming == "ab" else "in place")
+    # a walled box with even rows takes the paired kernels, named as such
+    assert d["config"]["cells_per_thread"] == 2
+    assert r["kernel"].startswith("step_pair_kernel<" if streaming == "ab" else "step_inplace_pair_kernel<")
