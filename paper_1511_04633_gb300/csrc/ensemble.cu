@@ -33,14 +33,19 @@ struct __align__(8) CavityDesc {
     int nx, ny, nz, wall;
     unsigned plane, nxy;
     float inv_ny;
-    int bx, by;              // step tile shape, bx * by = threads per block
+    int bx, by;              // step tile shape, bx * by = threads per block (bx a power of two)
     int tiles_x, tiles_y;    // step tiles along x and y
-    long long block_start;   // first step block of this cavity in the launch
     long long offset;        // element offset of the cavity's slab in each buffer
     long long snap_offset;   // float offset of its 4 snapshot planes
     long long red_start;     // first residual block (32 x 8 tiles)
     int red_tiles_x, red_tiles_y;
     CollideParams C;
+};
+
+// The step tile of one thread block: its cavity and the tile's coordinates,
+// laid out on the host so that a block finds its cells without division.
+struct __align__(16) BlockTile {
+    int member, tx, ty, z;
 };
 
 namespace {
@@ -74,25 +79,25 @@ constexpr int kMinBlocksEns = 4;
 // Stage the descriptor of the block's cavity in shared memory and locate the
 // block's cell: false if the thread lies outside the cavity.
 __device__ __forceinline__ bool locate_cell(CavityDesc &D, const CavityDesc *__restrict__ descs,
-                                            const int *__restrict__ blockmap, int &x, int &y, int &z)
+                                            const BlockTile *__restrict__ blockmap, int &x, int &y,
+                                            int &z)
 {
+    __shared__ BlockTile t;
     {
-        const int c = blockmap[blockIdx.x];
-        const unsigned *g = reinterpret_cast<const unsigned *>(descs + c);
+        const BlockTile *bt = blockmap + blockIdx.x;
+        const unsigned *g = reinterpret_cast<const unsigned *>(descs + bt->member);
         unsigned *sdst = reinterpret_cast<unsigned *>(&D);
         for (int w = threadIdx.x; w < static_cast<int>(sizeof(CavityDesc) / 4); w += blockDim.x)
             sdst[w] = g[w];
+        if (threadIdx.x == 0) t = *bt;
     }
     __syncthreads();
+    // bx is a power of two, but a shift and mask here made ptxas spill about
+    // 50 bytes more in the paired kernels than this division does
     const int bx = D.bx;
-    const long long b = static_cast<long long>(blockIdx.x) - D.block_start;
-    const int tx = static_cast<int>(threadIdx.x) % bx, ty = static_cast<int>(threadIdx.x) / bx;
-    const int tix = static_cast<int>(b % D.tiles_x);
-    const long long r = b / D.tiles_x;
-    const int tiy = static_cast<int>(r % D.tiles_y);
-    z = static_cast<int>(r / D.tiles_y);
-    x = tix * bx + tx;
-    y = tiy * D.by + ty;
+    x = t.tx * bx + static_cast<int>(threadIdx.x) % bx;
+    y = t.ty * D.by + static_cast<int>(threadIdx.x) / bx;
+    z = t.z;
     return x < D.nx && y < D.ny;
 }
 
@@ -123,7 +128,7 @@ __device__ __forceinline__ void ensemble_cell(const T *__restrict__ src, T *__re
 template <typename T, bool SR>
 __global__ void __launch_bounds__(256, kMinBlocksEns)
     ensemble_step_kernel(const T *__restrict__ srcb, T *__restrict__ dstb,
-                         const CavityDesc *__restrict__ descs, const int *__restrict__ blockmap,
+                         const CavityDesc *__restrict__ descs, const BlockTile *__restrict__ blockmap,
                          long long counter_at)
 {
     // programmatic dependent launch (see step.cu)
@@ -151,7 +156,7 @@ __global__ void __launch_bounds__(256, kMinBlocksEns)
 template <typename T, bool SR, int PHASE>
 __global__ void DMRT_ENS_INPLACE_BOUNDS(PHASE)
     ensemble_inplace_kernel(T *__restrict__ buf, const CavityDesc *__restrict__ descs,
-                            const int *__restrict__ blockmap, long long counter_at)
+                            const BlockTile *__restrict__ blockmap, long long counter_at)
 {
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;");
@@ -210,7 +215,7 @@ constexpr int kEnsPairBlocks = 5;
 // As locate_cell, for tiles of pairs: the thread holds the cells x0, x0 + 1
 // with x0 = 2 (tile x * bx + thread x).
 __device__ __forceinline__ bool locate_pair(CavityDesc &D, const CavityDesc *__restrict__ descs,
-                                            const int *__restrict__ blockmap, int &x0, int &y, int &z)
+                                            const BlockTile *__restrict__ blockmap, int &x0, int &y, int &z)
 {
     int xp;
     (void)locate_cell(D, descs, blockmap, xp, y, z);  // its bound is for one cell per thread
@@ -226,7 +231,7 @@ __device__ __forceinline__ PairFaces pair_faces(const CavityDesc &D, int x0, int
 template <typename T, bool SR>
 __global__ void __launch_bounds__(128, kEnsPairBlocks)
     ensemble_pair_kernel(const T *__restrict__ srcb, T *__restrict__ dstb, const CavityDesc *__restrict__ descs,
-                         const int *__restrict__ blockmap, long long counter_at)
+                         const BlockTile *__restrict__ blockmap, long long counter_at)
 {
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;");
@@ -262,7 +267,7 @@ __global__ void __launch_bounds__(128, kEnsPairBlocks)
 template <typename T, bool SR, int PHASE>
 __global__ void __launch_bounds__(128, kEnsPairBlocks)
     ensemble_inplace_pair_kernel(T *__restrict__ buf, const CavityDesc *__restrict__ descs,
-                                 const int *__restrict__ blockmap, long long counter_at)
+                                 const BlockTile *__restrict__ blockmap, long long counter_at)
 {
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;");
@@ -508,7 +513,7 @@ __global__ void __launch_bounds__(kEnsRedThreads)
 // ---------------------------------------------------------------- launchers
 
 cudaError_t launch_ensemble_step(int storage, bool stochastic, const void *src, void *dst,
-                                 const CavityDesc *descs, const int *blockmap, long long blocks,
+                                 const CavityDesc *descs, const BlockTile *blockmap, long long blocks,
                                  int threads, long long counter_at, cudaStream_t s, bool pdl, bool pairs)
 {
     cudaLaunchConfig_t cfg = {};
@@ -542,7 +547,7 @@ cudaError_t launch_ensemble_step(int storage, bool stochastic, const void *src, 
 }
 
 cudaError_t launch_ensemble_inplace(int storage, bool stochastic, void *buf, int phase,
-                                    const CavityDesc *descs, const int *blockmap, long long blocks,
+                                    const CavityDesc *descs, const BlockTile *blockmap, long long blocks,
                                     int threads, long long counter_at, cudaStream_t s, bool pdl, bool pairs)
 {
     if (phase != 0 && phase != 1) return cudaErrorInvalidValue;
@@ -636,7 +641,7 @@ struct dmrt_ensemble {
     std::vector<double> nu, alpha, gbeta;
     std::vector<lbm::CavityDesc> desc;
     lbm::CavityDesc *d_desc = nullptr;
-    int *d_blockmap = nullptr;
+    lbm::BlockTile *d_blockmap = nullptr;
     long long step_blocks = 0;
     size_t blockmap_cap = 0;
     int *d_redmap = nullptr;
@@ -753,35 +758,33 @@ int default_bx(int nx, int threads, bool pairs)
 }
 
 // Lay out step tiles (and block starts) for the members in `which` with the
-// current bx of each; returns the block map.
-std::vector<int> layout_step(dmrt_ensemble_t *e, const std::vector<int> &which)
+// current bx of each; returns the block map (x tiles fastest, then y, then z).
+std::vector<lbm::BlockTile> layout_step(dmrt_ensemble_t *e, const std::vector<int> &which)
 {
-    std::vector<int> map;
-    long long start = 0;
+    std::vector<lbm::BlockTile> map;
     for (int c : which) {
         lbm::CavityDesc &D = e->desc[c];
         D.by = e->threads / D.bx;
         const int units = e->pairs ? D.nx / 2 : D.nx;  // threads along a row
         D.tiles_x = (units + D.bx - 1) / D.bx;
         D.tiles_y = (D.ny + D.by - 1) / D.by;
-        D.block_start = start;
-        const long long nb = static_cast<long long>(D.tiles_x) * D.tiles_y * D.nz;
-        map.insert(map.end(), static_cast<size_t>(nb), c);
-        start += nb;
+        for (int z = 0; z < D.nz; ++z)
+            for (int ty = 0; ty < D.tiles_y; ++ty)
+                for (int tx = 0; tx < D.tiles_x; ++tx) map.push_back(lbm::BlockTile{c, tx, ty, z});
     }
     return map;
 }
 
-dmrt_status upload_layout(dmrt_ensemble_t *e, const std::vector<int> &map)
+dmrt_status upload_layout(dmrt_ensemble_t *e, const std::vector<lbm::BlockTile> &map)
 {
     if (map.size() > e->blockmap_cap) {
         if (e->d_blockmap) cudaFree(e->d_blockmap);
         e->d_blockmap = nullptr;
         e->blockmap_cap = 0;
-        ECK(e, cudaMalloc(&e->d_blockmap, map.size() * sizeof(int)), "cudaMalloc(blockmap)");
+        ECK(e, cudaMalloc(&e->d_blockmap, map.size() * sizeof(lbm::BlockTile)), "cudaMalloc(blockmap)");
         e->blockmap_cap = map.size();
     }
-    ECK(e, cudaMemcpyAsync(e->d_blockmap, map.data(), map.size() * sizeof(int),
+    ECK(e, cudaMemcpyAsync(e->d_blockmap, map.data(), map.size() * sizeof(lbm::BlockTile),
                            cudaMemcpyHostToDevice, e->stream),
         "copy blockmap");
     ECK(e, cudaMemcpyAsync(e->d_desc, e->desc.data(), e->desc.size() * sizeof(lbm::CavityDesc),
@@ -1025,7 +1028,7 @@ dmrt_status dmrt_ensemble_create(dmrt_ensemble_t **out, int count, const dmrt_ca
     e->red_blocks = red_start;
     std::vector<int> all(count);
     for (int c = 0; c < count; ++c) all[c] = c;
-    const std::vector<int> map = layout_step(e, all);
+    const std::vector<lbm::BlockTile> map = layout_step(e, all);
 
     cudaError_t c;
     const size_t buf_bytes = static_cast<size_t>(offset) * lbm::storage_bytes(storage) + 256;
