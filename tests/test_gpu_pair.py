@@ -50,11 +50,13 @@ def _assert_same(a, b):
         assert a.nusselt(w) == b.nusselt(w)
 
 
-# grids: the smallest box, one pair per row with ragged y, rows spanning two
-# 64-pair blocks plus a one-pair tail, and a 16-pair row with 8 rows a block;
-# rows of a multiple of 8 cells (32, 8, 136: two 64-pair blocks, ragged y)
-# also run with the TMA-staged loads for 16-bit storage
-GRIDS = [(2, 3, 2), (2, 9, 5), (130, 6, 4), (32, 17, 6), (38, 20, 13), (8, 3, 4), (136, 5, 7)]
+# grids: the smallest box, one pair per row with ragged y, rows of 65 pairs
+# (five tiles of 16, the last with one pair), a 16-pair row with 8 rows a
+# block, 19 pairs in one tile of 32, 48 pairs in three tiles of 16; rows of a
+# multiple of 8 cells (32, 8, 136, 96) also run with the TMA-staged loads for
+# 16-bit storage
+GRIDS = [(2, 3, 2), (2, 9, 5), (130, 6, 4), (32, 17, 6), (38, 20, 13), (8, 3, 4), (136, 5, 7),
+         (96, 7, 5)]
 
 
 @pytest.mark.parametrize("loads", [1, 2], ids=["direct", "staged"])
