@@ -116,7 +116,7 @@ __device__ __forceinline__ void ensemble_cell(const T *__restrict__ src, T *__re
     const bool dir_z = D.wall == 2;  // Type 2: linear z walls
     pull_offsets<kRuntimeWall, T>(src, ComputedOffsets{plane, static_cast<unsigned>(nx), D.nxy}, nx,
                                   ny, nz, D.inv_ny, self, x, y, z, d, g, dir_x, dir_z);
-    collide_pairs(D.C, d, g);
+    collide_cell(D.C, d, g);
     // re-read the plane stride after a compiler barrier: otherwise the
     // compiler keeps the load offsets live through the collision for the
     // stores and spills (see ensemble_inplace_kernel)
@@ -182,7 +182,7 @@ __global__ void DMRT_ENS_INPLACE_BOUNDS(PHASE)
     else
         pull_offsets<kRuntimeWall, T>(A, LocalOffsets{plane}, nx, ny, nz, D.inv_ny, self, x, y, z, d,
                                       g, dir_x, dir_z);
-    collide_pairs(D.C, d, g);
+    collide_cell(D.C, d, g);
     const unsigned base = SR ? pcg_hash(self ^ salt) : 0u;
     // The store offsets equal the load offsets (each cell writes the slots it
     // read); left to itself the compiler keeps all 26 of them live through the

@@ -32,7 +32,9 @@ namespace lbm {
 //                  g_i stay below ~0.2 in magnitude, so the scale keeps values
 //                  down to ~6e-8 out of the FP16 subnormal range while the
 //                  largest stay far below the FP16 maximum.  The scale is a
-//                  power of two, so it adds no rounding of its own.
+//                  power of two, so it adds no rounding of its own.  (The
+//                  paired step kernels keep it through the collision instead
+//                  of applying it at every load and store: pair_body.cuh.)
 template <typename T>
 struct Store;
 

@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(256, DMRT_STEP_MIN_BLOCKS)
         pull_offsets<WALL, T>(src, TableOffsets{S}, S.nx, S.ny, S.nz, S.inv_ny, self, x, y, z, d,
                               g);
     }
-    collide_pairs(C, d, g);
+    collide_cell(C, d, g);
     unsigned base = 0;
     if constexpr (SR) {
         const size_t counter_at = static_cast<size_t>(kPlanes) * S.plane;

@@ -254,7 +254,7 @@ __device__ __forceinline__ void collide(const CollideParams &C, V d[19], V g[7])
 }
 
 // One cell per thread: the float form of collide().
-__device__ __forceinline__ void collide_pairs(const CollideParams &C, float d[19], float g[7])
+__device__ __forceinline__ void collide_cell(const CollideParams &C, float d[19], float g[7])
 {
     collide<float>(C, d, g);
 }

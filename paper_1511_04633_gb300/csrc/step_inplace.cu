@@ -103,7 +103,7 @@ __global__ void DMRT_INPLACE_BOUNDS(PHASE, T)
         pull_offsets<WALL, T>(A, LocalOffsets{S.plane}, S.nx, S.ny, S.nz, S.inv_ny, self, x, y, z,
                               d, g);
     }
-    collide_pairs(C, d, g);
+    collide_cell(C, d, g);
     unsigned base = 0;
     if constexpr (SR) {
         unsigned *ctr = reinterpret_cast<unsigned *>(A + static_cast<size_t>(kPlanes) * S.plane);

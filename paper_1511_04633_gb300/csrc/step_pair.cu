@@ -4,7 +4,8 @@
 // stores bitwise the same values, with fewer instructions per cell:
 //  - the collision runs on both cells at once in Blackwell's packed f32x2
 //    arithmetic (collide<F2>, step_body.cuh), half the instructions of two
-//    one-cell collisions;
+//    one-cell collisions; FP16 pairs collide in the stored units, 2^10 times
+//    the populations (collide<F2, 10>), so no load or store multiplies;
 //  - the 14 planes whose links have no x component (e_x = 0) arrive as one
 //    aligned 2-element load per pair; the 12 with e_x = +-1 are shifted by one
 //    cell and load each cell's value on its own;
@@ -38,15 +39,11 @@ namespace {
 // blocks against 341 us with 4 (Type 1: 328 against 352 us; host-timed runs
 // of 200 steps).  DMRT_PAIR_MIN_BLOCKS overrides the count for experiments.
 constexpr int kPairThreads = 128;
-template <typename T, bool INPLACE>
-constexpr int pair_blocks()
-{
 #ifdef DMRT_PAIR_MIN_BLOCKS
-    return DMRT_PAIR_MIN_BLOCKS;
+constexpr int kPairBlocks = DMRT_PAIR_MIN_BLOCKS;
 #else
-    return 5;
+constexpr int kPairBlocks = 5;
 #endif
-}
 
 // Thread -> pair: x0 = 2 (block x * block width + thread x) must be < nx.
 struct PairCoords {
@@ -71,7 +68,7 @@ __device__ __forceinline__ PairCoords pair_coords(const StepGeometry &S)
 }
 
 template <int WALL, typename T, bool SR>
-__global__ void __launch_bounds__(kPairThreads, (pair_blocks<T, false>()))
+__global__ void __launch_bounds__(kPairThreads, kPairBlocks)
     step_pair_kernel(const T *__restrict__ src, T *__restrict__ dst, const StepGeometry S,
                      const CollideParams C)
 {
@@ -106,7 +103,7 @@ __global__ void __launch_bounds__(kPairThreads, (pair_blocks<T, false>()))
 // an aligned pair for the planes with e_x = 0 and one element per cell for
 // the others (or, where the link leaves the box, plane opp(q) at the cell).
 template <int WALL, typename T, bool SR, int PHASE>
-__global__ void __launch_bounds__(kPairThreads, (pair_blocks<T, true>()))
+__global__ void __launch_bounds__(kPairThreads, kPairBlocks)
     step_inplace_pair_kernel(T *__restrict__ A, const InplaceGeometry SI, const CollideParams C)
 {
     const StepGeometry &S = SI.load;
