@@ -41,6 +41,9 @@ RA, PR, MA = 1e5, 0.71, 0.1
 LBM_STEPS_PER_STEP = 100
 STORAGES = {"f32": 0, "bf16": 1, "f16": 2}
 METRIC = "MLUPS and % HBM roofline per coupled step"
+# GB300 HBM3e nominal bandwidth (GB/s); the roofline fraction is taken against
+# the measured copy bandwidth, and against this figure beside it
+NOMINAL_HBM_GBS = 7900.0
 WALL_NAMES = {1: "Type 1 (adiabatic side walls)", 2: "Type 2 (linear side walls)",
               3: "Type 3 (linear x walls, adiabatic z walls)"}
 
@@ -388,6 +391,7 @@ def run_dmrt(args, rank, local, world):
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
+                     "nominal_peak": NOMINAL_HBM_GBS, "frac_nominal": achieved / NOMINAL_HBM_GBS,
                      "kernel": {"ab": f"step_kernel<{args.wall}, {args.storage}>",
                                 "pair": f"step_pair_kernel<{args.wall}, {args.storage}>",
                                 "pair_tma": f"step_pair_tma_kernel<{args.wall}, {args.storage}>",
@@ -532,6 +536,7 @@ def run_ensemble(args, rank, local, world):
                        "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
+                         "nominal_peak": NOMINAL_HBM_GBS, "frac_nominal": achieved / NOMINAL_HBM_GBS,
                          "kernel": ens_kernel, "bytes_per_cell": stats["bytes_per_cell"],
                          "launch_us": launch_s * 1e6},
             "separate_runs": {"value": separate, "unit": "MLUPS",

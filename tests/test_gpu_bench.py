@@ -47,6 +47,7 @@ def test_bench_line_has_the_contract_keys(torch, streaming):
     r = d["roofline"]
     assert r["bound"] == "hbm" and r["unit"] == "GB/s" and r["bytes_per_cell"] == 208
     assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-12
+    assert abs(r["frac_nominal"] - r["achieved"] / r["nominal_peak"]) < 1e-12
     assert abs(r["achieved"] - 208 * cells / (r["launch_us"] * 1e-6) / 1e9) <= 1e-6 * r["achieved"]
     # every timed benchmark step launches 20 step kernels, a residual (2) and a Nusselt (2)
     assert d["gpu_launches"] >= 3 * 20
