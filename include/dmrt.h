@@ -318,12 +318,14 @@ dmrt_status dmrt_ensemble_sync(dmrt_ensemble_t *e);
 dmrt_status dmrt_ensemble_set_timing(dmrt_ensemble_t *e, int enabled);
 dmrt_status dmrt_ensemble_get_stats(dmrt_ensemble_t *e, dmrt_stats *out, int reset);
 
-/* Pick the thread-block size (128 or 256 threads) and, per distinct cavity
- * width, the tile width along x (32, 64 or 128 cells) by timing `trials`
- * launches of each candidate on the live buffers (the state is not
- * advanced).  `report` (may be NULL) receives a one-line summary of the
- * choices and times.  Without a call the defaults are 128 threads and the
- * widest tile not wider than the cavity (rounded up to 32). */
+/* Pick the thread-block size (128 or 256 threads; 128 only in place or with two cells
+ * per thread) and, per distinct cavity width, the tile width along x in
+ * threads (32, 64 or 128, and 16 with two cells per thread, where a thread
+ * covers two cells of the row) by timing `trials` launches of each candidate
+ * on the live buffers (the state is not advanced).  `report` (may be NULL)
+ * receives a one-line summary of the choices and times.  Without a call the
+ * defaults are 128 threads and the widest tile not wider than the row's
+ * threads (rounded up to 32, or to 16 with two cells per thread). */
 dmrt_status dmrt_ensemble_autotune(dmrt_ensemble_t *e, int trials, char *report, int report_len);
 
 /* Advance every member n >= 0 steps (residual every K steps, per member). */
