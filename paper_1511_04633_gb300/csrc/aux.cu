@@ -46,7 +46,9 @@ __global__ void fields_kernel(const T *__restrict__ src, const Geometry G, float
 // ---------------------------------------------------------------- residual
 
 // Per block: sums of |dtheta|^2, |theta|^2, |du|^2, |u|^2 against the
-// snapshot, which is then overwritten with the current fields.
+// snapshot, which is then overwritten with the current fields.  Each cell's
+// terms are FP32 (the difference of two floats, then fused squares), summed
+// in FP32 over a warp's 32 cells and in FP64 from there on.
 template <int WALL, typename T>
 __global__ void __launch_bounds__(kRedThreads) residual_kernel(
     const T *__restrict__ src, const Geometry G, float *__restrict__ snap, int have_prev,
@@ -55,7 +57,7 @@ __global__ void __launch_bounds__(kRedThreads) residual_kernel(
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
-    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    float v[4] = {0.0f, 0.0f, 0.0f, 0.0f};
     if (x < G.nx && y < G.ny) {
         float d[19], g[7];
         pull_f<WALL, T>(src, G, x, y, z, d);
@@ -68,19 +70,20 @@ __global__ void __launch_bounds__(kRedThreads) residual_kernel(
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const float prev = snap[k * cells + c];
-            const double dk = have_prev ? static_cast<double>(now[k]) - prev : 0.0;
+            const float dk = have_prev ? now[k] - prev : 0.0f;
             const int slot = (k == 0) ? 0 : 2;
-            v[slot] += dk * dk;
-            v[slot + 1] += static_cast<double>(now[k]) * now[k];
+            v[slot] = __fmaf_rn(dk, dk, v[slot]);
+            v[slot + 1] = __fmaf_rn(now[k], now[k], v[slot + 1]);
             snap[k * cells + c] = now[k];
         }
     }
-    block_sum<4, kRedThreads>(v);
+    double s[4];
+    block_sum_f32<4, kRedThreads>(v, s);
     if (threadIdx.x == 0 && threadIdx.y == 0) {
         const long long b = (static_cast<long long>(blockIdx.z) * gridDim.y + blockIdx.y) *
                                 gridDim.x + blockIdx.x;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) partials[b * 4 + k] = v[k];
+        for (int k = 0; k < 4; ++k) partials[b * 4 + k] = s[k];
     }
 }
 

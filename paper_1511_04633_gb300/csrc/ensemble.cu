@@ -345,7 +345,9 @@ __device__ __forceinline__ Macro pulled_macro(const T *src, const Geometry &G, i
 }
 
 // Per residual block (32 x 8 cells of one cavity): the sums of the A11
-// residual against the cavity's snapshot, which is then refreshed.
+// residual against the cavity's snapshot, which is then refreshed.  The
+// arithmetic is that of residual_kernel (aux.cu): FP32 per cell and over a
+// warp's 32 cells, FP64 from there on.
 template <typename T>
 __global__ void __launch_bounds__(kEnsRedThreads)
     ensemble_residual_kernel(const T *__restrict__ srcb, const CavityDesc *__restrict__ descs,
@@ -359,7 +361,7 @@ __global__ void __launch_bounds__(kEnsRedThreads)
     const long long r = b / D.red_tiles_x;
     const int y = static_cast<int>(r % D.red_tiles_y) * 8 + threadIdx.y;
     const int z = static_cast<int>(r / D.red_tiles_y);
-    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    float v[4] = {0.0f, 0.0f, 0.0f, 0.0f};
     if (x < D.nx && y < D.ny) {
         const Geometry G = geometry_of(D, layout);
         const T *src = srcb + D.offset;
@@ -378,17 +380,18 @@ __global__ void __launch_bounds__(kEnsRedThreads)
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const float prev = snap[k * cells + cell];
-            const double dk = have_prev ? static_cast<double>(now[k]) - prev : 0.0;
+            const float dk = have_prev ? now[k] - prev : 0.0f;
             const int slot = (k == 0) ? 0 : 2;
-            v[slot] += dk * dk;
-            v[slot + 1] += static_cast<double>(now[k]) * now[k];
+            v[slot] = __fmaf_rn(dk, dk, v[slot]);
+            v[slot + 1] = __fmaf_rn(now[k], now[k], v[slot + 1]);
             snap[k * cells + cell] = now[k];
         }
     }
-    block_sum<4, kEnsRedThreads>(v);
+    double s[4];
+    block_sum_f32<4, kEnsRedThreads>(v, s);
     if (threadIdx.x == 0 && threadIdx.y == 0)
 #pragma unroll
-        for (int k = 0; k < 4; ++k) partials[static_cast<long long>(blockIdx.x) * 4 + k] = v[k];
+        for (int k = 0; k < 4; ++k) partials[static_cast<long long>(blockIdx.x) * 4 + k] = s[k];
 }
 
 __device__ double ens_rel_change(double num2, double den2)
