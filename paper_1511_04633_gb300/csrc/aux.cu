@@ -59,18 +59,23 @@ __global__ void __launch_bounds__(kRedThreads) residual_kernel(
     const int z = blockIdx.z;
     float v[4] = {0.0f, 0.0f, 0.0f, 0.0f};
     if (x < G.nx && y < G.ny) {
+        const long long c = (static_cast<long long>(z) * G.ny + y) * G.nx + x;
+        const long long cells = static_cast<long long>(G.nx) * G.ny * G.nz;
+        // the snapshot is read before any of it is written back (and before
+        // the pull), so its four loads overlap the population loads instead
+        // of following one another behind possibly aliasing stores
+        float prev[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) prev[k] = snap[k * cells + c];
         float d[19], g[7];
         pull_f<WALL, T>(src, G, x, y, z, d);
         pull_g<WALL, T>(src, G, x, y, z, g);
         const Macro m = macro_of(d, g);
         const float r = 1.0f + m.drho;
         const float now[4] = {m.T, m.jx / r, m.jy / r, m.jz / r};
-        const long long c = (static_cast<long long>(z) * G.ny + y) * G.nx + x;
-        const long long cells = static_cast<long long>(G.nx) * G.ny * G.nz;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            const float prev = snap[k * cells + c];
-            const float dk = have_prev ? now[k] - prev : 0.0f;
+            const float dk = have_prev ? now[k] - prev[k] : 0.0f;
             const int slot = (k == 0) ? 0 : 2;
             v[slot] = __fmaf_rn(dk, dk, v[slot]);
             v[slot + 1] = __fmaf_rn(now[k], now[k], v[slot + 1]);

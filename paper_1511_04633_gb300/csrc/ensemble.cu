@@ -363,6 +363,13 @@ __global__ void __launch_bounds__(kEnsRedThreads)
     const int z = static_cast<int>(r / D.red_tiles_y);
     float v[4] = {0.0f, 0.0f, 0.0f, 0.0f};
     if (x < D.nx && y < D.ny) {
+        const long long cells = static_cast<long long>(D.nx) * D.ny * D.nz;
+        const long long cell = (static_cast<long long>(z) * D.ny + y) * D.nx + x;
+        float *snap = snapb + D.snap_offset;
+        // snapshot loads first (see residual_kernel)
+        float prev[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) prev[k] = snap[k * cells + cell];
         const Geometry G = geometry_of(D, layout);
         const T *src = srcb + D.offset;
         Macro m;
@@ -374,13 +381,9 @@ __global__ void __launch_bounds__(kEnsRedThreads)
         }
         const float rr = 1.0f + m.drho;
         const float now[4] = {m.T, m.jx / rr, m.jy / rr, m.jz / rr};
-        const long long cells = static_cast<long long>(D.nx) * D.ny * D.nz;
-        const long long cell = (static_cast<long long>(z) * D.ny + y) * D.nx + x;
-        float *snap = snapb + D.snap_offset;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            const float prev = snap[k * cells + cell];
-            const float dk = have_prev ? now[k] - prev : 0.0f;
+            const float dk = have_prev ? now[k] - prev[k] : 0.0f;
             const int slot = (k == 0) ? 0 : 2;
             v[slot] = __fmaf_rn(dk, dk, v[slot]);
             v[slot + 1] = __fmaf_rn(now[k], now[k], v[slot + 1]);
