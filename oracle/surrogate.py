@@ -10,6 +10,12 @@ and pinned by finite differences in tests/test_oracle_surrogate.py.
 
 Tensors are channels-last (batch, z, y, x, c); a k^3 convolution's weights are
 (taps, cout, cin) with taps ordered (dz, dy, dx), dx fastest.
+
+It also holds the warm start's mapping from a prediction to the initial
+fields of a cavity (trilinear resampling between cell-centred grids on the
+unit cube, then the channel scalings), written from its definition and pinned
+in tests/test_oracle_surrogate.py by linear and separable fields and by hand
+computed cell-centre positions.
 """
 
 from __future__ import annotations
@@ -205,3 +211,60 @@ class UNet:
             if l >= 1:
                 gs[l - 1] = gs[l - 1] + avgpool2_backward(gp)
         return loss, grad
+
+
+# ---------------------------------------------------------------- warm-start mapping
+
+def source_positions(N, m):
+    """Where the centres of N output cells fall on an m-cell input axis, in
+    input cell units (0 = the first input centre).  Both grids divide the
+    same unit interval into equal cells with values at the cell centres:
+    output centre (k + 1/2)/N lies (k + 1/2) m / N - 1/2 input cells past the
+    first input centre.  Positions outside [0, m - 1] are clamped, i.e. the
+    field is held constant beyond the outermost input centres."""
+    p = (np.arange(N) + 0.5) * m / N - 0.5
+    return np.clip(p, 0.0, m - 1.0)
+
+
+def _axis_weights(N, m):
+    """Lower neighbour index and the weight of the upper one for each of N
+    output positions (linear interpolation between input centres)."""
+    p = source_positions(N, m)
+    if m == 1:
+        return np.zeros(N, dtype=int), np.zeros(N, dtype=int), np.zeros(N)
+    i0 = np.minimum(np.floor(p).astype(int), m - 2)
+    return i0, i0 + 1, p - i0
+
+
+def trilinear(pred, N):
+    """Trilinear resampling of a channels-last field pred (m, m, m, c) to
+    (N, N, N, c): each output value is the sum over the 8 surrounding input
+    centres of the value times the product of the three 1-D linear weights."""
+    pred = np.asarray(pred, dtype=np.float64)
+    m = pred.shape[0]
+    x0, x1, fx = _axis_weights(N, m)
+    y0, y1, fy = _axis_weights(N, m)
+    z0, z1, fz = _axis_weights(N, m)
+    out = np.zeros((N, N, N, pred.shape[-1]))
+    for zi, zw in ((z0, 1.0 - fz), (z1, fz)):
+        for yi, yw in ((y0, 1.0 - fy), (y1, fy)):
+            for xi, xw in ((x0, 1.0 - fx), (x1, fx)):
+                w = zw[:, None, None] * yw[None, :, None] * xw[None, None, :]
+                out += w[..., None] * pred[np.ix_(zi, yi, xi)]
+    return out
+
+
+def warm_start_fields(pred, N, uc):
+    """Initial fields of an N^3 cavity from one prediction (m^3, 5) or
+    (m, m, m, 5) with channels (u_x, u_y, u_z)/u_c, theta and
+    (rho - 1)/(3 u_c^2): resampled trilinearly, velocities times u_c, density
+    1 + 3 u_c^2 times its channel.  Returns planar (rho (N,N,N),
+    u (3,N,N,N), theta (N,N,N)) indexed [z][y][x]."""
+    pred = np.asarray(pred, dtype=np.float64)
+    m = round(pred.shape[0] ** (1.0 / 3.0)) if pred.ndim == 2 else pred.shape[0]
+    pred = pred.reshape(m, m, m, OUT)
+    f = trilinear(pred, N)
+    u = np.stack([uc * f[..., 0], uc * f[..., 1], uc * f[..., 2]])
+    theta = f[..., 3]
+    rho = 1.0 + 3.0 * uc * uc * f[..., 4]
+    return rho, u, theta

@@ -522,3 +522,40 @@ def test_residual_definition(orc):
     assert abs(r - max(e_t, e_u) / 100) < 1e-15
     z = np.zeros((3, 100))
     assert orc.residual(th1, z, th1, z, 10) == 0.0
+
+
+@pytest.mark.parametrize("nu,alpha", [(0.04, 0.02), (0.02, 0.05)])
+def test_residual_of_decaying_modes_matches_their_decay_rates(orc, nu, alpha):
+    """Reading A11 against what the mathematics fixes.  In a periodic box
+    without gravity, a shear mode u_x = U sin(k y) decays as exp(-nu k^2 t)
+    and a temperature mode theta = Th cos(k y) as exp(-alpha k^2 t), each on
+    its own.  Over K steps the change of a mode decaying at rate lam has norm
+    (exp(lam K) - 1) times its current norm, so the residual must be
+    max(exp(nu k^2 K) - 1, exp(alpha k^2 K) - 1) / K.  The two cases let
+    the velocity and then the temperature term decide the maximum; with
+    lam K near 0.4 a norm taken at the older state (1 - exp(-lam K)), a sum
+    in place of the maximum, or a second division by K all miss by far more
+    than the lattice's O(k^2) departure from the continuum rates (< 1e-3
+    here)."""
+    ny = 64
+    grid = (2, ny, 2)
+    k = 2 * math.pi / ny
+    lam_u, lam_t = nu * k * k, alpha * k * k
+    K = int(0.4 / max(lam_u, lam_t))
+    o = orc.Oracle(grid, 0, nu, alpha, 0.0)
+    y = np.arange(ny)
+    u = np.zeros((3,) + o.shape)
+    u[0] = 1e-3 * np.sin(k * y)[None, :, None]
+    th = np.broadcast_to((0.1 * np.cos(k * y))[None, :, None], o.shape).copy()
+    o.init_fields(np.ones(o.shape), u, th)
+    o.step(200)  # let the non-equilibrium part settle
+    _, u_prev, t_prev = o.fields()
+    o.step(K)
+    _, u_now, t_now = o.fields()
+    r = orc.residual(t_now, u_now, t_prev, u_prev, K)
+    exact = max(math.expm1(lam_u * K), math.expm1(lam_t * K)) / K
+    assert abs(r / exact - 1) < 2e-3
+    # the plausible mistakes named above, evaluated on the same modes
+    older = max(-math.expm1(-lam_u * K), -math.expm1(-lam_t * K)) / K
+    summed = (math.expm1(lam_u * K) + math.expm1(lam_t * K)) / K
+    assert abs(older / exact - 1) > 0.2 and abs(summed / exact - 1) > 0.2

@@ -110,3 +110,62 @@ def test_parameter_count_of_the_config5_network():
              (128, 64), (64, 64), (64, 32), (32, 32), (32, 16), (16, 16)]
     expect = sum(27 * a * b + b for a, b in pairs) + 16 * 5 + 5
     assert net.count == expect == 1317525
+
+
+# ------------------------------------------------------------------ warm-start mapping
+
+def test_cell_centre_positions_by_hand():
+    """Output centre k of an N-cell axis sits at (k + 1/2) m / N - 1/2 input
+    cells; the values below are worked out by hand for m = 4."""
+    np.testing.assert_allclose(S.source_positions(6, 4), [0.0, 0.5, 7 / 6, 11 / 6, 2.5, 3.0], atol=1e-15)
+    np.testing.assert_allclose(S.source_positions(8, 4), [0.0, 0.25, 0.75, 1.25, 1.75, 2.25, 2.75, 3.0],
+                               atol=1e-15)
+    np.testing.assert_allclose(S.source_positions(2, 4), [0.5, 2.5], atol=1e-15)
+    np.testing.assert_allclose(S.source_positions(5, 5), np.arange(5.0), atol=1e-15)
+
+
+@pytest.mark.parametrize("m,N", [(4, 6), (4, 8), (6, 4), (5, 5), (3, 7)])
+def test_trilinear_reproduces_linear_fields(m, N):
+    """Linear interpolation reproduces a linear function, so a field linear in
+    the input index coordinates comes out as the same function of the output
+    cells' (clamped) source positions: exactly, everywhere, each axis with
+    its own slope so that a swapped axis fails."""
+    a, bx, by, bz = 0.3, 1.25, -0.5, 2.0
+    i = np.arange(m, dtype=float)
+    lin = a + bx * i[None, None, :] + by * i[None, :, None] + bz * i[:, None, None]
+    pred = np.stack([lin, -2.0 * lin], axis=-1)
+    p = S.source_positions(N, m)
+    want = a + bx * p[None, None, :] + by * p[None, :, None] + bz * p[:, None, None]
+    out = S.trilinear(pred, N)
+    np.testing.assert_allclose(out[..., 0], want, atol=1e-12)
+    np.testing.assert_allclose(out[..., 1], -2.0 * want, atol=1e-12)
+
+
+def test_trilinear_of_a_separable_field_is_the_product_of_1d_interpolations():
+    """For f = g(x) h(y) k(z) the tensor-product interpolation equals the
+    product of the three 1-D linear interpolations (numpy.interp, which
+    clamps at the ends like the resampling)."""
+    rng = np.random.default_rng(7)
+    m, N = 5, 9
+    gx, hy, kz = rng.normal(size=m), rng.normal(size=m), rng.normal(size=m)
+    f = kz[:, None, None] * hy[None, :, None] * gx[None, None, :]
+    q = (np.arange(N) + 0.5) * m / N - 0.5
+    i = np.arange(m)
+    want = (np.interp(q, i, kz)[:, None, None] * np.interp(q, i, hy)[None, :, None]
+            * np.interp(q, i, gx)[None, None, :])
+    np.testing.assert_allclose(S.trilinear(f[..., None], N)[..., 0], want, atol=1e-12)
+
+
+def test_identity_grid_and_channel_mapping():
+    """N = m returns the input; the channels map to (u_x, u_y, u_z)/u_c, theta
+    and (rho - 1)/(3 u_c^2)."""
+    rng = np.random.default_rng(8)
+    m, uc = 4, 0.05
+    pred = rng.normal(size=(m, m, m, 5))
+    np.testing.assert_allclose(S.trilinear(pred, m), pred, atol=1e-15)
+    rho, u, th = S.warm_start_fields(pred.reshape(-1, 5), m, uc)
+    np.testing.assert_allclose(u[0], uc * pred[..., 0], atol=1e-15)
+    np.testing.assert_allclose(u[1], uc * pred[..., 1], atol=1e-15)
+    np.testing.assert_allclose(u[2], uc * pred[..., 2], atol=1e-15)
+    np.testing.assert_allclose(th, pred[..., 3], atol=1e-15)
+    np.testing.assert_allclose(rho, 1.0 + 3 * uc * uc * pred[..., 4], atol=1e-15)
