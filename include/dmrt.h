@@ -167,9 +167,13 @@ dmrt_status dmrt_set_stream(dmrt_t *h, void *stream);
 /* Advance n >= 0 time steps (Eqs. (14), (19), (29)): each step is one fused
  * kernel that, for every cell, pulls the D3Q19 and D3Q7 populations from its
  * neighbours (bounce-back / anti-bounce-back at walls), collides them in
- * moment space, adds the buoyancy force and stores them.  After every K-th
- * step (K = residual_interval) the convergence residual is computed on the
- * device.  Asynchronous: returns once the work is queued. */
+ * moment space, adds the buoyancy force and stores them.  The last step of
+ * every K-step interval (K = residual_interval; the steps from the states
+ * K - 1, 2K - 1, ... counted from creation) also takes a residual point: it
+ * compares the fields of the state it pulls with the snapshot of the
+ * previous point and reduces the sums of dmrt_residual, in the same pass
+ * (a small kernel then adds the block sums).  Asynchronous: returns once the
+ * work is queued. */
 dmrt_status dmrt_step(dmrt_t *h, long n);
 
 /* Wait for the handle's queued work; reports deferred CUDA errors. */
@@ -217,18 +221,28 @@ dmrt_status dmrt_nusselt_local(dmrt_t *h, int wall, float *local, int on_device)
  * held by every GPU that loads it until the process exits.  nz may be at most
  * 8192; larger nz, nx*ny*nz >= 2^31, ny < 2, a NULL pointer or a wall other
  * than 0 / 1 return DMRT_ERR_ARG before any GPU work.  The call never calls
- * cudaMalloc or cudaFree.  Its first call on a device, with that device
- * current, looks up the array's device address (cudaGetSymbolAddress); make
- * that first call before any stream capture.  Every call shares the one
- * array: each call writes every slot it reads, so nothing carries over, but
- * calls that overlap on the GPU (other streams, other host threads) race and
- * must be serialised by the caller.  DMRT_ERR_CUDA if a CUDA call fails. */
+ * cudaMalloc or cudaFree.  theta must live on the current device: every
+ * call, with that device current, looks up the array's device address there
+ * (cudaGetSymbolAddress, which allocates nothing).  The call ends by
+ * synchronising the stream and copying the result to host memory, so it
+ * must not be called on a stream that is being captured into a CUDA graph.
+ * Every call shares the one array: each call writes every slot it reads, so
+ * nothing carries over, but calls that overlap on the GPU (other streams,
+ * other host threads) race and must be serialised by the caller.
+ * DMRT_ERR_CUDA if a CUDA call fails. */
 dmrt_status dmrt_nusselt_noalloc(const float *theta, int nx, int ny, int nz, int wall,
                                  void *stream, double out[3]);
 
-/* The convergence residual from the last two residual points (K steps
- * apart): r = max(|theta^n - theta^{n-K}|_2 / |theta^n|_2,
- * |u^n - u^{n-K}|_2 / |u^n|_2) / K, in FP64.  +inf until two points exist.
+/* The convergence residual (the paper states no convergence rule; this is
+ * the library's reading of it) from the last two residual points, the
+ * states n and n - K pulled by the last steps of two consecutive intervals
+ * (see dmrt_step): r = max(|theta^n - theta^{n-K}|_2 / |theta^n|_2,
+ * |u^n - u^{n-K}|_2 / |u^n|_2) / K.  Each cell's four terms are FP32 (from
+ * the FP32 fields, exactly those dmrt_fields reports for that state); they
+ * are summed in double-float arithmetic (about 48 significand bits) and r is
+ * formed in FP64, so r carries the rounding of the cells' FP32 terms only (a
+ * few units of 2^-24, relative).  +inf until two points exist; the points
+ * restart after dmrt_set_populations, dmrt_init_fields or a warm start.
  * Returns DMRT_ERR_DIVERGED if the fields hold a NaN or Inf.  Synchronises. */
 dmrt_status dmrt_residual(dmrt_t *h, double *r);
 
@@ -328,7 +342,9 @@ dmrt_status dmrt_ensemble_get_stats(dmrt_ensemble_t *e, dmrt_stats *out, int res
  * threads (rounded up to 32, or to 16 with two cells per thread). */
 dmrt_status dmrt_ensemble_autotune(dmrt_ensemble_t *e, int trials, char *report, int report_len);
 
-/* Advance every member n >= 0 steps (residual every K steps, per member). */
+/* Advance every member n >= 0 steps (residual points as in dmrt_step, per
+ * member: taken by a reduction kernel just before the last step of every
+ * K-step interval, with the sums of a single cavity). */
 dmrt_status dmrt_ensemble_step(dmrt_ensemble_t *e, long n);
 
 /* Per-member residuals r[count] (as dmrt_residual; +inf before two residual

@@ -43,9 +43,11 @@ struct dmrt {
     lbm::InplaceGeometry SI{};
     long long device_bytes = 0;           // device memory held by the handle
     float *snap = nullptr;                // residual snapshot: theta, u (4 planes)
-    double *partials = nullptr;           // reduction scratch
+    double *partials = nullptr;           // reduction scratch (Nu rows; residual block partials)
     size_t npartials = 0;
-    double *dres = nullptr;               // residual result (8 doubles)
+    long long res_blocks = 0;             // blocks of a residual step's grid (its partials)
+    double *dres = nullptr;               // residual result (8 doubles; [6] = points taken,
+                                          // [7] the finishing kernel's ticket word)
     double *dnu = nullptr;                // Nusselt result (3 doubles)
     float *staging = nullptr;             // device staging for host transfers
     size_t staging_floats = 0;
@@ -142,23 +144,46 @@ Geometry state_geometry(const dmrt_t *h)
 // (A-B) or the layout parity (in-place).  Toggles with every step.
 int &phase(dmrt_t *h) { return h->inplace ? h->parity : h->cur; }
 
-// One fused step from state `ph`.
-cudaError_t launch_one_step(dmrt_t *h, int ph)
+// One fused step from state `ph`; with `res` the step also takes the
+// residual point of the state it pulls, and the finishing kernel follows.
+// The staged (TMA) handles take that step with the direct-load paired
+// kernel, which stores bitwise the same populations.
+cudaError_t launch_one_step(dmrt_t *h, int ph, bool res)
 {
+    const lbm::ResidualArgs R{h->snap, reinterpret_cast<float *>(h->partials), h->dres + 6,
+                              static_cast<unsigned>(cell_count(h->G))};
+    const lbm::ResidualArgs *rp = res ? &R : nullptr;
+    cudaError_t e;
     if (h->inplace && h->cells_per_thread == 2)
-        return lbm::launch_step_inplace_pair(h->wall, h->storage, h->stochastic, h->buf[0], ph,
-                                             h->SI, h->G, h->C, h->stream, h->use_pdl);
-    if (h->inplace)
-        return lbm::launch_step_inplace(h->wall, h->storage, h->stochastic, h->buf[0], ph, h->SI,
-                                        h->G, h->C, h->block, h->stream, h->use_pdl);
-    if (h->pair_loads == 2)
-        return lbm::launch_step_pair_tma(h->wall, h->storage, h->stochastic, h->tma_map[ph], h->buf[ph],
-                                         h->buf[ph ^ 1], h->S, h->G, h->C, h->derr, h->stream, h->use_pdl);
-    if (h->cells_per_thread == 2)
-        return lbm::launch_step_pair(h->wall, h->storage, h->stochastic, h->buf[ph], h->buf[ph ^ 1],
-                                     h->S, h->G, h->C, h->stream, h->use_pdl);
-    return lbm::launch_step(h->wall, h->storage, h->stochastic, h->buf[ph], h->buf[ph ^ 1], h->S,
-                            h->G, h->C, h->block, h->stream, h->use_pdl);
+        e = lbm::launch_step_inplace_pair(h->wall, h->storage, h->stochastic, h->buf[0], ph, h->SI, h->G, h->C,
+                                          h->stream, h->use_pdl, rp);
+    else if (h->inplace)
+        e = lbm::launch_step_inplace(h->wall, h->storage, h->stochastic, h->buf[0], ph, h->SI, h->G, h->C,
+                                     h->block, h->stream, h->use_pdl, rp);
+    else if (h->pair_loads == 2 && !res)
+        e = lbm::launch_step_pair_tma(h->wall, h->storage, h->stochastic, h->tma_map[ph], h->buf[ph],
+                                      h->buf[ph ^ 1], h->S, h->G, h->C, h->derr, h->stream, h->use_pdl);
+    else if (h->cells_per_thread == 2)
+        e = lbm::launch_step_pair(h->wall, h->storage, h->stochastic, h->buf[ph], h->buf[ph ^ 1], h->S, h->G,
+                                  h->C, h->stream, h->use_pdl, rp);
+    else
+        e = lbm::launch_step(h->wall, h->storage, h->stochastic, h->buf[ph], h->buf[ph ^ 1], h->S, h->G, h->C,
+                             h->block, h->stream, h->use_pdl, rp);
+    if (e != cudaSuccess || !res) return e;
+    return lbm::launch_residual_finish(R.partials, h->res_blocks, R.partials + 8 * h->res_blocks,
+                                       reinterpret_cast<unsigned *>(h->dres + 7), h->K, h->dres, h->stream);
+}
+
+// Does the step from the current step count take a residual point?  The
+// points are the states pulled by the last step of every K-step interval.
+bool residual_step(const dmrt_t *h, long steps_done) { return (steps_done + 1) % h->K == 0; }
+
+// Forget the residual history (a new state was written).
+dmrt_status reset_residual(dmrt_t *h)
+{
+    h->snaps = 0;
+    CK(h, cudaMemsetAsync(h->dres + 6, 0, sizeof(double), h->stream), "reset residual points");
+    return DMRT_OK;
 }
 
 bool periodic(const dmrt_t *h) { return h->wall == DMRT_WALL_PERIODIC; }
@@ -241,17 +266,6 @@ dmrt_status collect_timing(dmrt_t *h)
     return DMRT_OK;
 }
 
-dmrt_status run_residual(dmrt_t *h)
-{
-    CK(h,
-       lbm::launch_residual(h->wall, h->storage, h->buf[h->cur], state_geometry(h), h->snap,
-                            h->snaps > 0 ? 1 : 0, h->K, h->partials, h->dres, h->stream),
-       "residual kernel");
-    h->total_launches += 2;
-    if (h->snaps < 2) h->snaps++;
-    return DMRT_OK;
-}
-
 // Capture K consecutive step launches starting from state `start` into an
 // executable graph.  Returns false (and leaves graphs off) if the stream
 // cannot be captured, e.g. the legacy default stream.
@@ -265,7 +279,7 @@ bool capture_interval(dmrt_t *h, int start)
     int ph = start;
     bool ok = true;
     for (long s = 0; s < h->K && ok; ++s) {
-        ok = launch_one_step(h, ph) == cudaSuccess;
+        ok = launch_one_step(h, ph, s == h->K - 1) == cudaSuccess;
         ph ^= 1;
     }
     cudaGraph_t graph = nullptr;
@@ -282,8 +296,8 @@ bool capture_interval(dmrt_t *h, int start)
     return true;
 }
 
-// Launch n fused steps, taking a residual point after every K-th step.  A
-// whole interval of K steps replays a captured graph.
+// Launch n fused steps; the last step of every K-step interval also takes
+// a residual point.  A whole interval of K steps replays a captured graph.
 dmrt_status run_steps(dmrt_t *h, long n)
 {
     long done = 0;
@@ -306,16 +320,19 @@ dmrt_status run_steps(dmrt_t *h, long n)
                 if (h->K & 1) ph ^= 1;
                 h->steps += chunk;
                 h->step_launches += chunk;
-                h->total_launches += chunk;
+                h->total_launches += chunk + 1;  // and the residual's finishing kernel
+                if (h->snaps < 2) h->snaps++;
                 graphed = true;
             }
         }
         for (long s = 0; s < chunk && !graphed; ++s) {
-            CK(h, launch_one_step(h, ph), "step kernel");
+            const bool res = residual_step(h, h->steps);
+            CK(h, launch_one_step(h, ph, res), "step kernel");
             ph ^= 1;
             h->steps++;
             h->step_launches++;
-            h->total_launches++;
+            h->total_launches += res ? 2 : 1;
+            if (res && h->snaps < 2) h->snaps++;
         }
         if (h->timing) {
             CK(h, cudaEventRecord(e1, h->stream), "cudaEventRecord");
@@ -323,10 +340,6 @@ dmrt_status run_steps(dmrt_t *h, long n)
             h->ev_counts.push_back(chunk);
         }
         done += chunk;
-        if (h->steps % h->K == 0) {
-            dmrt_status st = run_residual(h);
-            if (st != DMRT_OK) return st;
-        }
     }
     return DMRT_OK;
 }
@@ -447,7 +460,15 @@ dmrt_status create_common(dmrt_t **out, const int grid[3], double nu, double alp
     e = cudaMalloc(&h->snap, static_cast<size_t>(cells) * 4 * sizeof(float));
     if (e != cudaSuccess) return bail(DMRT_ERR_OOM);
     h->device_bytes += cells * 4 * static_cast<long long>(sizeof(float));
-    h->npartials = lbm::residual_partials(h->G) * 4;
+    // residual partials: 8 floats (4 doubles' room) per block of the grid of
+    // the kernel that takes the residual points
+    if (h->cells_per_thread == 2)
+        h->res_blocks = static_cast<long long>(lbm::pair_blocks(h->G));
+    else
+        h->res_blocks = static_cast<long long>((grid[0] + h->block.bx - 1) / h->block.bx) *
+                        ((grid[1] + h->block.by - 1) / h->block.by) * grid[2];
+    // and the finishing kernel's stage after them
+    h->npartials = static_cast<size_t>(h->res_blocks) * 4 + lbm::residual_stage_floats(h->res_blocks) / 2;
     if (h->npartials < 3 * static_cast<size_t>(grid[2])) h->npartials = 3 * grid[2];
     e = cudaMalloc(&h->partials, h->npartials * sizeof(double));
     if (e != cudaSuccess) return bail(DMRT_ERR_OOM);
@@ -737,7 +758,10 @@ dmrt_status dmrt_set_populations(dmrt_t *h, const float *f, const float *g, int 
                                       h->stream),
        "set kernel");
     h->total_launches++;
-    h->snaps = 0;
+    {
+        dmrt_status st = reset_residual(h);
+        if (st != DMRT_OK) return st;
+    }
     CK(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
     return DMRT_OK;
 }
@@ -801,7 +825,10 @@ dmrt_status dmrt_init_fields(dmrt_t *h, const float *rho, const float *u, const 
                                   h->stream),
        "init kernel");
     h->total_launches++;
-    h->snaps = 0;
+    {
+        dmrt_status st = reset_residual(h);
+        if (st != DMRT_OK) return st;
+    }
     if (!on_device) CK(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
     return DMRT_OK;
 }

@@ -9,6 +9,8 @@
 
 #include "internal.h"
 #include "reduce.cuh"
+#include "residual.cuh"
+#include "step_body.cuh"
 
 namespace lbm {
 
@@ -30,67 +32,21 @@ __global__ void fields_kernel(const T *__restrict__ src, const Geometry G, float
     float d[19], g[7];
     pull_f<WALL, T>(src, G, x, y, z, d);
     pull_g<WALL, T>(src, G, x, y, z, g);
-    const Macro m = macro_of(d, g);
-    const float r = 1.0f + m.drho;
+    // the moments as the step kernels form them (step_body.cuh), so a
+    // residual point taken inside a step sees exactly these values
+    const Conserved<float> m = conserved<float>(d, g);
     const long long c = (static_cast<long long>(z) * G.ny + y) * G.nx + x;
     const long long cells = static_cast<long long>(G.nx) * G.ny * G.nz;
-    if (rho) rho[c] = r;
+    if (rho) rho[c] = m.rho;
     if (u) {
-        u[c] = m.jx / r;
-        u[cells + c] = m.jy / r;
-        u[2 * cells + c] = m.jz / r;
+        u[c] = m.vx;
+        u[cells + c] = m.vy;
+        u[2 * cells + c] = m.vz;
     }
-    if (theta) theta[c] = m.T;
+    if (theta) theta[c] = m.Tu;
 }
 
 // ---------------------------------------------------------------- residual
-
-// Per block: sums of |dtheta|^2, |theta|^2, |du|^2, |u|^2 against the
-// snapshot, which is then overwritten with the current fields.  Each cell's
-// terms are FP32 (the difference of two floats, then fused squares), summed
-// in FP32 over a warp's 32 cells and in FP64 from there on.
-template <int WALL, typename T>
-__global__ void __launch_bounds__(kRedThreads) residual_kernel(
-    const T *__restrict__ src, const Geometry G, float *__restrict__ snap, int have_prev,
-    double *__restrict__ partials)
-{
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = blockIdx.z;
-    float v[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-    if (x < G.nx && y < G.ny) {
-        const long long c = (static_cast<long long>(z) * G.ny + y) * G.nx + x;
-        const long long cells = static_cast<long long>(G.nx) * G.ny * G.nz;
-        // the snapshot is read before any of it is written back (and before
-        // the pull), so its four loads overlap the population loads instead
-        // of following one another behind possibly aliasing stores
-        float prev[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) prev[k] = snap[k * cells + c];
-        float d[19], g[7];
-        pull_f<WALL, T>(src, G, x, y, z, d);
-        pull_g<WALL, T>(src, G, x, y, z, g);
-        const Macro m = macro_of(d, g);
-        const float r = 1.0f + m.drho;
-        const float now[4] = {m.T, m.jx / r, m.jy / r, m.jz / r};
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const float dk = have_prev ? now[k] - prev[k] : 0.0f;
-            const int slot = (k == 0) ? 0 : 2;
-            v[slot] = __fmaf_rn(dk, dk, v[slot]);
-            v[slot + 1] = __fmaf_rn(now[k], now[k], v[slot + 1]);
-            snap[k * cells + c] = now[k];
-        }
-    }
-    double s[4];
-    block_sum_f32<4, kRedThreads>(v, s);
-    if (threadIdx.x == 0 && threadIdx.y == 0) {
-        const long long b = (static_cast<long long>(blockIdx.z) * gridDim.y + blockIdx.y) *
-                                gridDim.x + blockIdx.x;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) partials[b * 4 + k] = s[k];
-    }
-}
 
 __device__ double rel_change(double num2, double den2)
 {
@@ -98,24 +54,98 @@ __device__ double rel_change(double num2, double den2)
     return sqrt(num2) / sqrt(den2);
 }
 
-__global__ void __launch_bounds__(kFinThreads) residual_finish(const double *__restrict__ partials,
-                                                                 long long nparts, int have_prev,
-                                                                 int K, double *result)
+// Block sum (fixed order) of four double-float values per thread; warp 0
+// ends with the totals, lane 0 holding them.
+template <int THREADS>
+__device__ __forceinline__ void df_block_sum(DF v[4])
 {
-    double v[4] = {0.0, 0.0, 0.0, 0.0};
-    for (long long p = threadIdx.x; p < nparts; p += kFinThreads)
+    __shared__ DF sh[THREADS / 32][4];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) v[k] += partials[p * 4 + k];
-    block_sum<4, kFinThreads>(v);
+    for (int k = 0; k < 4; ++k) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] = df_add(v[k], df_shfl_down(v[k], o));
+    }
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) sh[warp][k] = v[k];
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            v[k] = lane < THREADS / 32 ? sh[lane][k] : DF{0.0f, 0.0f};
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v[k] = df_add(v[k], df_shfl_down(v[k], o));
+        }
+    }
+}
+
+constexpr int kGatherThreads = 256;
+constexpr int kGatherPer = 8;  // partials per thread of a gathering block
+
+// Finishes a residual point: adds the step kernel's `nparts` block partials
+// (residual.cuh: hi, lo of the four sums per block) in double-float
+// arithmetic and forms r (reading A11).  Each block adds 2048 consecutive
+// partials (thread t takes t, t + 256, ...; then a fixed tree) into
+// stage[block]; the block that finishes last (a ticket counter) adds the
+// stage entries in index order, so the result does not depend on which
+// block that is.  The totals become FP64 (hi + lo).  result[6] counts the
+// points since the last reset (capped at 2); *ticket is left at 0.
+__global__ void __launch_bounds__(kGatherThreads)
+    residual_finish(const float *__restrict__ partials, long long nparts, float *stage, unsigned *ticket,
+                    int K, double *result)
+{
+    DF v[4] = {};
+    const long long base = static_cast<long long>(blockIdx.x) * (kGatherThreads * kGatherPer);
+#pragma unroll
+    for (int i = 0; i < kGatherPer; ++i) {
+        const long long p = base + i * kGatherThreads + threadIdx.x;
+        if (p < nparts) {
+            const float4 a = *reinterpret_cast<const float4 *>(partials + p * 8);
+            const float4 b = *reinterpret_cast<const float4 *>(partials + p * 8 + 4);
+            v[0] = df_add(v[0], DF{a.x, a.y});
+            v[1] = df_add(v[1], DF{a.z, a.w});
+            v[2] = df_add(v[2], DF{b.x, b.y});
+            v[3] = df_add(v[3], DF{b.z, b.w});
+        }
+    }
+    df_block_sum<kGatherThreads>(v);
+    __shared__ bool last;
     if (threadIdx.x == 0) {
+        float *q = stage + 8 * static_cast<size_t>(blockIdx.x);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            q[2 * k] = v[k].hi;
+            q[2 * k + 1] = v[k].lo;
+        }
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    DF w[4] = {};
+    for (unsigned p = threadIdx.x; p < gridDim.x; p += kGatherThreads) {
+        const volatile float *q = stage + 8 * static_cast<size_t>(p);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) w[k] = df_add(w[k], DF{q[2 * k], q[2 * k + 1]});
+    }
+    df_block_sum<kGatherThreads>(w);
+    if (threadIdx.x == 0) {
+        const double points = result[6];
+        double tot[4];
         bool finite = true;
         for (int k = 0; k < 4; ++k) {
-            result[k] = v[k];
-            finite = finite && isfinite(v[k]);
+            tot[k] = static_cast<double>(w[k].hi) + static_cast<double>(w[k].lo);
+            result[k] = tot[k];
+            finite = finite && isfinite(tot[k]);
         }
-        double r = have_prev ? fmax(rel_change(v[0], v[1]), rel_change(v[2], v[3])) / K : INFINITY;
+        const double r =
+            points > 0.0 ? fmax(rel_change(tot[0], tot[1]), rel_change(tot[2], tot[3])) / K : INFINITY;
         result[4] = finite ? r : NAN;
         result[5] = finite ? 0.0 : 1.0;
+        result[6] = fmin(points + 1.0, 2.0);
+        *ticket = 0u;
     }
 }
 
@@ -372,28 +402,19 @@ cudaError_t launch_fields(int wall, int storage, const void *src, const Geometry
     return cudaGetLastError();
 }
 
-size_t residual_partials(const Geometry &G)
+size_t residual_stage_floats(long long nparts)
 {
-    dim3 grid = cell_grid(G, kRedBlock);
-    return static_cast<size_t>(grid.x) * grid.y * grid.z;
+    const long long blocks = (nparts + kGatherThreads * kGatherPer - 1) / (kGatherThreads * kGatherPer);
+    return static_cast<size_t>(blocks < 1 ? 1 : blocks) * 8;
 }
 
-cudaError_t launch_residual(int wall, int storage, const void *src, const Geometry &G,
-                            float *snap, int have_prev, int K, double *partials, double *result,
-                            cudaStream_t s)
+cudaError_t launch_residual_finish(const float *partials, long long nparts, float *stage, unsigned *ticket,
+                                  int K, double *result, cudaStream_t s)
 {
-    const dim3 grid = cell_grid(G, kRedBlock);
-    cudaError_t e = dispatch(wall, storage, [&](auto W, auto *tp) {
-        using T = std::remove_pointer_t<decltype(tp)>;
-        residual_kernel<decltype(W)::value, T>
-            <<<grid, kRedBlock, 0, s>>>(static_cast<const T *>(src), G, snap, have_prev, partials);
-        return cudaSuccess;
-    });
-    if (e != cudaSuccess) return e;
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    const long long nparts = static_cast<long long>(grid.x) * grid.y * grid.z;
-    residual_finish<<<1, kFinThreads, 0, s>>>(partials, nparts, have_prev, K, result);
+    long long blocks = (nparts + kGatherThreads * kGatherPer - 1) / (kGatherThreads * kGatherPer);
+    if (blocks < 1) blocks = 1;
+    residual_finish<<<static_cast<unsigned>(blocks), kGatherThreads, 0, s>>>(partials, nparts, stage, ticket, K,
+                                                                              result);
     return cudaGetLastError();
 }
 

@@ -336,23 +336,24 @@ __device__ __forceinline__ Geometry geometry_of(const CavityDesc &D, int layout)
 }
 
 template <int WALL, typename T>
-__device__ __forceinline__ Macro pulled_macro(const T *src, const Geometry &G, int x, int y, int z)
+__device__ __forceinline__ Conserved<float> pulled_moments(const T *src, const Geometry &G, int x, int y, int z)
 {
     float d[19], g[7];
     pull_f<WALL, T>(src, G, x, y, z, d);
     pull_g<WALL, T>(src, G, x, y, z, g);
-    return macro_of(d, g);
+    return conserved<float>(d, g);
 }
 
-// Per residual block (32 x 8 cells of one cavity): the sums of the A11
-// residual against the cavity's snapshot, which is then refreshed.  The
-// arithmetic is that of residual_kernel (aux.cu): FP32 per cell and over a
-// warp's 32 cells, FP64 from there on.
+// Per residual block (32 x 8 cells of one cavity): a residual point of the
+// current state (reading A11) against the cavity's snapshot, which is then
+// refreshed.  The fields are the moments as the step kernels form them and
+// the sums are those of a single cavity's step kernel (residual.cuh): FP32
+// terms per cell, double-float sums, one partial per block.
 template <typename T>
 __global__ void __launch_bounds__(kEnsRedThreads)
     ensemble_residual_kernel(const T *__restrict__ srcb, const CavityDesc *__restrict__ descs,
                              const int *__restrict__ redmap, int layout, float *__restrict__ snapb,
-                             int have_prev, double *__restrict__ partials)
+                             const double *__restrict__ points, float *__restrict__ partials)
 {
     const int c = redmap[blockIdx.x];
     const CavityDesc &D = descs[c];
@@ -361,40 +362,25 @@ __global__ void __launch_bounds__(kEnsRedThreads)
     const long long r = b / D.red_tiles_x;
     const int y = static_cast<int>(r % D.red_tiles_y) * 8 + threadIdx.y;
     const int z = static_cast<int>(r / D.red_tiles_y);
-    float v[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    DF acc[4] = {};
     if (x < D.nx && y < D.ny) {
-        const long long cells = static_cast<long long>(D.nx) * D.ny * D.nz;
-        const long long cell = (static_cast<long long>(z) * D.ny + y) * D.nx + x;
-        float *snap = snapb + D.snap_offset;
-        // snapshot loads first (see residual_kernel)
+        const unsigned cells = static_cast<unsigned>(D.nx) * D.ny * D.nz;
+        const unsigned cell = (static_cast<unsigned>(z) * D.ny + y) * D.nx + x;
+        const ResidualArgs R{snapb + D.snap_offset, partials, points, cells};
         float prev[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) prev[k] = snap[k * cells + cell];
+        residual_cell_load(R, cell, prev);  // with the populations' loads
         const Geometry G = geometry_of(D, layout);
         const T *src = srcb + D.offset;
-        Macro m;
+        Conserved<float> m;
         switch (D.wall) {
-        case 0: m = pulled_macro<0, T>(src, G, x, y, z); break;
-        case 1: m = pulled_macro<1, T>(src, G, x, y, z); break;
-        case 2: m = pulled_macro<2, T>(src, G, x, y, z); break;
-        default: m = pulled_macro<3, T>(src, G, x, y, z); break;
+        case 0: m = pulled_moments<0, T>(src, G, x, y, z); break;
+        case 1: m = pulled_moments<1, T>(src, G, x, y, z); break;
+        case 2: m = pulled_moments<2, T>(src, G, x, y, z); break;
+        default: m = pulled_moments<3, T>(src, G, x, y, z); break;
         }
-        const float rr = 1.0f + m.drho;
-        const float now[4] = {m.T, m.jx / rr, m.jy / rr, m.jz / rr};
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const float dk = have_prev ? now[k] - prev[k] : 0.0f;
-            const int slot = (k == 0) ? 0 : 2;
-            v[slot] = __fmaf_rn(dk, dk, v[slot]);
-            v[slot + 1] = __fmaf_rn(now[k], now[k], v[slot + 1]);
-            snap[k * cells + cell] = now[k];
-        }
+        residual_cell(R, cell, prev, m.Tu, m.vx, m.vy, m.vz, acc);
     }
-    double s[4];
-    block_sum_f32<4, kEnsRedThreads>(v, s);
-    if (threadIdx.x == 0 && threadIdx.y == 0)
-#pragma unroll
-        for (int k = 0; k < 4; ++k) partials[static_cast<long long>(blockIdx.x) * 4 + k] = s[k];
+    residual_block_store(acc, partials);
 }
 
 __device__ double ens_rel_change(double num2, double den2)
@@ -403,26 +389,63 @@ __device__ double ens_rel_change(double num2, double den2)
     return sqrt(num2) / sqrt(den2);
 }
 
-// One block per cavity: its residual blocks summed in index order.
-__global__ void __launch_bounds__(kEnsRedThreads)
-    ensemble_residual_finish(const CavityDesc *__restrict__ descs, const double *__restrict__ partials,
-                             int have_prev, int K, double *result)
+// One block per member: its residual blocks' partials summed in index
+// order in double-float arithmetic (as residual_finish does for a single
+// cavity), the totals in FP64, r of reading A11.  *points counts the
+// residual points since the last reset (capped at 2); the block that
+// finishes last (a ticket counter, left at 0) raises it, after every block
+// has read it.
+constexpr int kEnsFinThreads = 256;
+
+__global__ void __launch_bounds__(kEnsFinThreads)
+    ensemble_residual_finish(const CavityDesc *__restrict__ descs, const float *__restrict__ partials, int K,
+                             double *result, double *points, unsigned *ticket)
 {
     const int c = blockIdx.x;
+    const bool have_prev = *points > 0.0;
     const CavityDesc &D = descs[c];
     const long long nb = static_cast<long long>(D.red_tiles_x) * D.red_tiles_y * D.nz;
-    double v[4] = {0.0, 0.0, 0.0, 0.0};
-    for (long long p = threadIdx.x; p < nb; p += kEnsRedThreads)
+    DF v[4] = {};
+    for (long long p = threadIdx.x; p < nb; p += kEnsFinThreads) {
+        const float4 a = *reinterpret_cast<const float4 *>(partials + (D.red_start + p) * 8);
+        const float4 b = *reinterpret_cast<const float4 *>(partials + (D.red_start + p) * 8 + 4);
+        v[0] = df_add(v[0], DF{a.x, a.y});
+        v[1] = df_add(v[1], DF{a.z, a.w});
+        v[2] = df_add(v[2], DF{b.x, b.y});
+        v[3] = df_add(v[3], DF{b.z, b.w});
+    }
+    __shared__ DF sh[kEnsFinThreads / 32][4];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) v[k] += partials[(D.red_start + p) * 4 + k];
-    block_sum<4, kEnsRedThreads>(v);
-    if (threadIdx.x == 0) {
+    for (int k = 0; k < 4; ++k) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] = df_add(v[k], df_shfl_down(v[k], o));
+    }
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) sh[warp][k] = v[k];
+    __syncthreads();
+    if (warp != 0) return;
+    double tot[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        DF w = lane < kEnsFinThreads / 32 ? sh[lane][k] : DF{0.0f, 0.0f};
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) w = df_add(w, df_shfl_down(w, o));
+        tot[k] = static_cast<double>(w.hi) + static_cast<double>(w.lo);
+    }
+    if (lane == 0) {
         bool finite = true;
-        for (int k = 0; k < 4; ++k) finite = finite && isfinite(v[k]);
+        for (int k = 0; k < 4; ++k) finite = finite && isfinite(tot[k]);
         const double rr =
-            have_prev ? fmax(ens_rel_change(v[0], v[1]), ens_rel_change(v[2], v[3])) / K : INFINITY;
+            have_prev ? fmax(ens_rel_change(tot[0], tot[1]), ens_rel_change(tot[2], tot[3])) / K : INFINITY;
         result[c * 2 + 0] = finite ? rr : NAN;
         result[c * 2 + 1] = finite ? 0.0 : 1.0;
+        __threadfence();
+        if (atomicAdd(ticket, 1u) == gridDim.x - 1) {
+            *points = fmin(*points + 1.0, 2.0);
+            *ticket = 0u;
+        }
     }
 }
 
@@ -598,21 +621,24 @@ cudaError_t launch_ensemble_inplace(int storage, bool stochastic, void *buf, int
     return cudaGetLastError();
 }
 
+// points: the count of residual points (device), followed by the finishing
+// kernel's ticket word.
 cudaError_t launch_ensemble_residual(int storage, const void *src, int layout, const CavityDesc *descs,
                                      const int *redmap, long long red_blocks, int count,
-                                     float *snap, int have_prev, int K, double *partials,
-                                     double *result, cudaStream_t s)
+                                     float *snap, int K, float *partials, double *result, double *points,
+                                     cudaStream_t s)
 {
     cudaError_t e = dispatch(1, storage, [&](auto, auto *tp) {
         using T = std::remove_pointer_t<decltype(tp)>;
         ensemble_residual_kernel<T><<<static_cast<unsigned>(red_blocks), dim3(32, 8), 0, s>>>(
-            static_cast<const T *>(src), descs, redmap, layout, snap, have_prev, partials);
+            static_cast<const T *>(src), descs, redmap, layout, snap, points, partials);
         return cudaSuccess;
     });
     if (e != cudaSuccess) return e;
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    ensemble_residual_finish<<<count, kEnsRedThreads, 0, s>>>(descs, partials, have_prev, K, result);
+    ensemble_residual_finish<<<count, kEnsFinThreads, 0, s>>>(descs, partials, K, result, points,
+                                                              reinterpret_cast<unsigned *>(points + 1));
     return cudaGetLastError();
 }
 
@@ -819,8 +845,26 @@ int state_layout(const dmrt_ensemble_t *e)
     return !e->inplace ? lbm::kLayoutAB : (e->parity ? lbm::kLayoutStreamed : lbm::kLayoutSwapped);
 }
 
-cudaError_t launch_one_step(dmrt_ensemble_t *e, int from)
+// A residual point of every member's state `from` (the buffer, or the
+// in-place layout) and its finishing kernel.
+cudaError_t launch_residual_point(dmrt_ensemble_t *e, int from)
 {
+    const int layout = !e->inplace ? lbm::kLayoutAB : (from ? lbm::kLayoutStreamed : lbm::kLayoutSwapped);
+    return lbm::launch_ensemble_residual(e->storage, e->buf[e->inplace ? 0 : from], layout, e->d_desc,
+                                         e->d_redmap, e->red_blocks, e->count, e->snap, e->K,
+                                         reinterpret_cast<float *>(e->partials), e->dres, e->dres + 5 * e->count,
+                                         e->stream);
+}
+
+// One step of every member from state `from`; with `res` a residual point of
+// that state is taken first (the points are the states that the last step
+// of every K-step interval starts from, as in a single cavity).
+cudaError_t launch_one_step(dmrt_ensemble_t *e, int from, bool res = false)
+{
+    if (res) {
+        const cudaError_t c = launch_residual_point(e, from);
+        if (c != cudaSuccess) return c;
+    }
     if (e->inplace)
         return lbm::launch_ensemble_inplace(e->storage, e->stochastic, e->buf[0], from, e->d_desc,
                                             e->d_blockmap, e->step_blocks, e->threads,
@@ -840,7 +884,7 @@ bool capture_interval(dmrt_ensemble_t *e, int start)
     int cur = start;
     bool ok = true;
     for (long s = 0; s < e->K && ok; ++s) {
-        ok = launch_one_step(e, cur) == cudaSuccess;
+        ok = launch_one_step(e, cur, s == e->K - 1) == cudaSuccess;
         cur ^= 1;
     }
     cudaGraph_t graph = nullptr;
@@ -855,18 +899,6 @@ bool capture_interval(dmrt_ensemble_t *e, int start)
     }
     e->graph[start] = exec;
     return true;
-}
-
-dmrt_status run_residual(dmrt_ensemble_t *e)
-{
-    ECK(e,
-        lbm::launch_ensemble_residual(e->storage, e->buf[e->cur], state_layout(e), e->d_desc, e->d_redmap,
-                                      e->red_blocks, e->count, e->snap, e->snaps > 0 ? 1 : 0, e->K,
-                                      e->partials, e->dres, e->stream),
-        "ensemble residual");
-    e->total_launches += 2;
-    if (e->snaps < 2) e->snaps++;
-    return DMRT_OK;
 }
 
 dmrt_status run_steps(dmrt_ensemble_t *e, long n)
@@ -890,23 +922,23 @@ dmrt_status run_steps(dmrt_ensemble_t *e, long n)
                 graphed = true;
             }
         }
+        bool took = graphed;  // a whole interval ends with a residual point
         for (long s = 0; s < chunk && !graphed; ++s) {
-            ECK(e, launch_one_step(e, ph), "ensemble step");
+            const bool res = (e->steps + s + 1) % e->K == 0;
+            ECK(e, launch_one_step(e, ph, res), "ensemble step");
+            took = took || res;
             ph ^= 1;
         }
         e->steps += chunk;
         e->step_launches += chunk;
-        e->total_launches += chunk;
+        e->total_launches += chunk + (took ? 2 : 0);
+        if (took && e->snaps < 2) e->snaps++;
         if (e->timing) {
             ECK(e, cudaEventRecord(e1, e->stream), "cudaEventRecord");
             e->ev_pending.emplace_back(e0, e1);
             e->ev_counts.push_back(chunk);
         }
         done += chunk;
-        if (e->steps % e->K == 0) {
-            dmrt_status st = run_residual(e);
-            if (st != DMRT_OK) return st;
-        }
     }
     return DMRT_OK;
 }
@@ -1050,13 +1082,17 @@ dmrt_status dmrt_ensemble_create(dmrt_ensemble_t **out, int count, const dmrt_ca
     e->npartials = std::max<size_t>(static_cast<size_t>(red_start) * 4,
                                     static_cast<size_t>(count) * e->max_nz * 3);
     if (cudaMalloc(&e->partials, e->npartials * sizeof(double)) != cudaSuccess) return bail(DMRT_ERR_OOM);
-    if (cudaMalloc(&e->dres, static_cast<size_t>(count) * 5 * sizeof(double)) != cudaSuccess)
+    // 2 residual and 3 Nusselt doubles per member, then the count of residual
+    // points and the residual finishing kernel's ticket word
+    if (cudaMalloc(&e->dres, (static_cast<size_t>(count) * 5 + 2) * sizeof(double)) != cudaSuccess)
         return bail(DMRT_ERR_OOM);
+    if (cudaMemset(e->dres, 0, (static_cast<size_t>(count) * 5 + 2) * sizeof(double)) != cudaSuccess)
+        return bail(DMRT_ERR_CUDA);
     e->dnu = e->dres + 2 * count;
     if (cudaMalloc(&e->d_desc, static_cast<size_t>(count) * sizeof(lbm::CavityDesc)) != cudaSuccess)
         return bail(DMRT_ERR_OOM);
     if (cudaMalloc(&e->d_redmap, redmap.size() * sizeof(int)) != cudaSuccess) return bail(DMRT_ERR_OOM);
-    e->device_bytes += static_cast<long long>(e->npartials * sizeof(double) + count * 5 * sizeof(double) +
+    e->device_bytes += static_cast<long long>(e->npartials * sizeof(double) + (count * 5 + 2) * sizeof(double) +
                                               count * sizeof(lbm::CavityDesc) + redmap.size() * sizeof(int));
     if (cudaStreamCreateWithFlags(&e->own, cudaStreamNonBlocking) != cudaSuccess)
         return bail(DMRT_ERR_CUDA);
@@ -1399,6 +1435,7 @@ dmrt_status dmrt_ensemble_init_fields(dmrt_ensemble_t *e, int member, const floa
         "init kernel");
     e->total_launches++;
     e->snaps = 0;
+    ECK(e, cudaMemsetAsync(e->dres + 5 * e->count, 0, sizeof(double), e->stream), "reset residual points");
     ECK(e, cudaStreamSynchronize(e->stream), "cudaStreamSynchronize");
     return DMRT_OK;
 }

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include "lattice.cuh"
+#include "residual.cuh"
 
 namespace lbm {
 
@@ -25,10 +26,13 @@ void fill_step_geometry(const Geometry &G, StepGeometry &S);
 // stochastic: 16-bit stores round stochastically (ignored for FP32).
 // pdl: launch with programmatic stream serialisation (the kernel waits for
 // the previous grid itself).  Each buffer holds kPlanes * plane elements and
-// then one 32-bit step counter (used by stochastic rounding).
+// then one 32-bit step counter (used by stochastic rounding).  res: when not
+// null, the step also takes a residual point of the state it pulls (one
+// partial per block of the launch's grid; residual.cuh), to be finished by
+// launch_residual_finish.
 cudaError_t launch_step(int wall, int storage, bool stochastic, const void *src, void *dst,
                         const StepGeometry &S, const Geometry &G, const CollideParams &C,
-                        BlockShape b, cudaStream_t s, bool pdl);
+                        BlockShape b, cudaStream_t s, bool pdl, const ResidualArgs *res = nullptr);
 
 // The same step with two neighbouring cells of a row per thread (x0 even):
 // bitwise the values of launch_step, in packed FP32x2 arithmetic.  Needs a
@@ -37,7 +41,9 @@ cudaError_t launch_step(int wall, int storage, bool stochastic, const void *src,
 bool step_pair_supported(int wall, const Geometry &G);
 cudaError_t launch_step_pair(int wall, int storage, bool stochastic, const void *src, void *dst,
                              const StepGeometry &S, const Geometry &G, const CollideParams &C,
-                             cudaStream_t s, bool pdl);
+                             cudaStream_t s, bool pdl, const ResidualArgs *res = nullptr);
+// Blocks of the paired kernels' grid (the residual partials they write).
+size_t pair_blocks(const Geometry &G);
 
 // In-place streaming (one buffer).  The state alternates between two
 // layouts (see kLayoutSwapped / kLayoutStreamed): phase 0 reads the swapped
@@ -49,7 +55,8 @@ cudaError_t launch_step_pair(int wall, int storage, bool stochastic, const void 
 void fill_inplace_geometry(const Geometry &G, InplaceGeometry &SI);
 cudaError_t launch_step_inplace(int wall, int storage, bool stochastic, void *buf, int phase,
                                 const InplaceGeometry &SI, const Geometry &G,
-                                const CollideParams &C, BlockShape b, cudaStream_t s, bool pdl);
+                                const CollideParams &C, BlockShape b, cudaStream_t s, bool pdl,
+                                const ResidualArgs *res = nullptr);
 // The two-buffer paired step with its loads staged by TMA into shared memory
 // (16-bit storage, walled box, nx a multiple of 8): bitwise the values of
 // launch_step_pair.  `map` holds the two tensor maps of `src` (the row boxes
@@ -69,19 +76,23 @@ cudaError_t launch_step_pair_tma(int wall, int storage, bool stochastic, const v
 // launch_step_pair); bitwise the values of launch_step_inplace.
 cudaError_t launch_step_inplace_pair(int wall, int storage, bool stochastic, void *buf, int phase,
                                      const InplaceGeometry &SI, const Geometry &G,
-                                     const CollideParams &C, cudaStream_t s, bool pdl);
+                                     const CollideParams &C, cudaStream_t s, bool pdl,
+                                     const ResidualArgs *res = nullptr);
 
 // Fields of the pulled populations (any output may be null).
 cudaError_t launch_fields(int wall, int storage, const void *src, const Geometry &G, float *rho,
                           float *u, float *theta, cudaStream_t s);
 
-// Residual: compare (theta, u) with `snap`, refresh `snap`, reduce in FP64.
-// `partials` needs residual_partials(G) * 4 doubles; `result` 8 doubles:
-// [0..3] = sums |dtheta|^2, |theta|^2, |du|^2, |u|^2; [4] = r; [5] = nonfinite.
-size_t residual_partials(const Geometry &G);
-cudaError_t launch_residual(int wall, int storage, const void *src, const Geometry &G,
-                            float *snap, int have_prev, int K, double *partials, double *result,
-                            cudaStream_t s);
+// The end of a residual point taken by a step kernel: adds its `nparts`
+// block partials (8 floats each) and writes `result` (8 doubles): [0..3] =
+// sums |dtheta|^2, |theta|^2, |du|^2, |u|^2; [4] = r; [5] = nonfinite;
+// [6] = points taken since the last reset (read, then raised, capped at 2;
+// the step kernels read it through ResidualArgs::points).  `stage` needs
+// residual_stage_floats(nparts) floats; *ticket (device) must be 0 and is
+// left at 0.
+size_t residual_stage_floats(long long nparts);
+cudaError_t launch_residual_finish(const float *partials, long long nparts, float *stage, unsigned *ticket,
+                                  int K, double *result, cudaStream_t s);
 
 // Nusselt numbers of wall 0 (hot) / 1 (cold): `partials` needs 3 * nz doubles,
 // `out3` 3 doubles; `local` (nullable) receives the [z][x] map.

@@ -434,28 +434,6 @@ __device__ __forceinline__ long long state_index(const Geometry &G, bool periodi
 
 // ---------------------------------------------------------------- moments
 
-// Macroscopic moments of pulled populations (Eqs. (20), (30)).
-struct Macro {
-    float drho, jx, jy, jz, T;
-};
-
-__device__ __forceinline__ Macro macro_of(const float d[19], const float g[7])
-{
-    Macro m{0.f, 0.f, 0.f, 0.f, 0.f};
-    static_for<0, 19>([&](auto I) {
-        constexpr int i = decltype(I)::value;
-        m.drho += d[i];
-        if constexpr (q19_ex(i) == 1) m.jx += d[i];
-        if constexpr (q19_ex(i) == -1) m.jx -= d[i];
-        if constexpr (q19_ey(i) == 1) m.jy += d[i];
-        if constexpr (q19_ey(i) == -1) m.jy -= d[i];
-        if constexpr (q19_ez(i) == 1) m.jz += d[i];
-        if constexpr (q19_ez(i) == -1) m.jz -= d[i];
-    });
-    static_for<0, 7>([&](auto I) { m.T += g[decltype(I)::value]; });
-    return m;
-}
-
 // ---------------------------------------------------------------- host dispatch
 
 // Calls f(std::integral_constant<int, WALL>{}, (T *)nullptr) for the runtime

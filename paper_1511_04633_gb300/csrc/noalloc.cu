@@ -10,11 +10,10 @@
 // loads the library keeps that array until the process exits.
 //
 // Host code must not pass the array's name to a kernel: on the host the name
-// is only a stand-in, not a device address.  The first call on each device,
-// with that device current, looks up the real address with
-// cudaGetSymbolAddress and caches it; later calls reuse it.
-#include <mutex>
-
+// is only a stand-in, not a device address.  Every call, with the caller's
+// device current, looks up the real address with cudaGetSymbolAddress (which
+// allocates nothing); nothing is cached, so the call stays correct after the
+// caller resets the device or tears down its context.
 #include "dmrt.h"
 
 namespace {
@@ -22,18 +21,10 @@ namespace {
 // Largest nz (number of z rows of the wall) one call accepts.
 constexpr int kNoAllocMaxRows = 8192;
 constexpr int kNoAllocThreads = 256;
-constexpr int kMaxDevices = 64;
 
 // [0, 3*kNoAllocMaxRows): per-row (sum, centre-column sum, max) of local Nu;
 // [3*kNoAllocMaxRows, +3): Nu_3D, Nu_2D, Nu_max of the last call.
 static __device__ __align__(256) double g_nu_scratch[3 * kNoAllocMaxRows + 4];
-
-struct DeviceSlot {
-    bool ready;
-    double *scratch;
-};
-DeviceSlot g_slots[kMaxDevices];
-std::mutex g_slots_mu;
 
 __device__ __forceinline__ double nu_warp_sum(double v)
 {
@@ -123,23 +114,13 @@ __global__ void __launch_bounds__(kNoAllocThreads) nu_finish_noalloc(int nx, int
     }
 }
 
-// Device address of the scratch array on the current device (looked up once
-// per device).
+// Device address of the scratch array on the current device.
 cudaError_t scratch_address(double **out)
 {
-    int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
+    double *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(reinterpret_cast<void **>(&p), g_nu_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_slots_mu);
-    if (!g_slots[dev].ready) {
-        double *p = nullptr;
-        e = cudaGetSymbolAddress(reinterpret_cast<void **>(&p), g_nu_scratch);
-        if (e != cudaSuccess) return e;
-        g_slots[dev].scratch = p;
-        g_slots[dev].ready = true;
-    }
-    *out = g_slots[dev].scratch;
+    *out = p;
     return cudaSuccess;
 }
 

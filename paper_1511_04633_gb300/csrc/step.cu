@@ -9,6 +9,7 @@
 // contiguous run (shifted by one element for the +-x links) and every store
 // a full aligned run.  The neighbour and bounce-back offsets of all 26 planes
 // come precomputed in the launch parameters.
+#include "residual.cuh"
 #include "step_body.cuh"
 
 namespace lbm {
@@ -29,10 +30,12 @@ namespace {
 // (`counter_at` elements in): every step reads it from its source buffer and
 // one thread writes it, plus one, to the destination, so a replayed graph
 // still draws fresh bits each step and runs stay bitwise reproducible.
-template <int WALL, typename T, bool SR>
+// RES: this step also takes a residual point of the state it pulls (the
+// fields of the pulled populations against the snapshot, residual.cuh).
+template <int WALL, typename T, bool SR, bool RES>
 __global__ void __launch_bounds__(256, DMRT_STEP_MIN_BLOCKS)
     step_kernel(const T *__restrict__ src, T *__restrict__ dst, const StepGeometry S,
-                const Geometry G, const CollideParams C)
+                const Geometry G, const CollideParams C, const ResidualArgs R)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -44,25 +47,34 @@ __global__ void __launch_bounds__(256, DMRT_STEP_MIN_BLOCKS)
     // plain launch.
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;");
-    if (x >= S.nx || y >= S.ny) return;
-    const unsigned self = (static_cast<unsigned>(z) * S.ny + y) * S.nx + x;
-    float d[19], g[7];
-    if constexpr (WALL == 0) {
-        pull_f<0, T>(src, G, x, y, z, d);
-        pull_g<0, T>(src, G, x, y, z, g);
-    } else {
-        pull_offsets<WALL, T>(src, TableOffsets{S}, S.nx, S.ny, S.nz, S.inv_ny, self, x, y, z, d,
-                              g);
+    DF acc[4] = {};
+    if (x < S.nx && y < S.ny) {
+        const unsigned self = (static_cast<unsigned>(z) * S.ny + y) * S.nx + x;
+        float d[19], g[7];
+        float prev[4];
+        if constexpr (RES) residual_cell_load(R, self, prev);
+        if constexpr (WALL == 0) {
+            pull_f<0, T>(src, G, x, y, z, d);
+            pull_g<0, T>(src, G, x, y, z, g);
+        } else {
+            pull_offsets<WALL, T>(src, TableOffsets{S}, S.nx, S.ny, S.nz, S.inv_ny, self, x, y, z, d,
+                                  g);
+        }
+        const Conserved<float> m0 = conserved<float>(d, g);
+        // the fields a residual point compares, used after the stores
+        const float th = m0.Tu, ux = m0.vx, uy = m0.vy, uz = m0.vz;
+        collide_from<float>(C, d, g, m0);
+        unsigned base = 0;
+        if constexpr (SR) {
+            const size_t counter_at = static_cast<size_t>(kPlanes) * S.plane;
+            const unsigned step = *reinterpret_cast<const unsigned *>(src + counter_at);
+            if (self == 0) *reinterpret_cast<unsigned *>(dst + counter_at) = step + 1u;
+            base = pcg_hash(self ^ pcg_hash(step));
+        }
+        store_cell<T, SR>(dst, self, S.plane, d, g, base);
+        if constexpr (RES) residual_cell(R, self, prev, th, ux, uy, uz, acc);
     }
-    collide_cell(C, d, g);
-    unsigned base = 0;
-    if constexpr (SR) {
-        const size_t counter_at = static_cast<size_t>(kPlanes) * S.plane;
-        const unsigned step = *reinterpret_cast<const unsigned *>(src + counter_at);
-        if (self == 0) *reinterpret_cast<unsigned *>(dst + counter_at) = step + 1u;
-        base = pcg_hash(self ^ pcg_hash(step));
-    }
-    store_cell<T, SR>(dst, self, S.plane, d, g, base);
+    if constexpr (RES) residual_block_store(acc, R.partials);
 }
 
 }  // namespace
@@ -89,8 +101,10 @@ void fill_step_geometry(const Geometry &G, StepGeometry &S)
 
 cudaError_t launch_step(int wall, int storage, bool stochastic, const void *src, void *dst,
                         const StepGeometry &S, const Geometry &G, const CollideParams &C,
-                        BlockShape b, cudaStream_t s, bool pdl)
+                        BlockShape b, cudaStream_t s, bool pdl, const ResidualArgs *res)
 {
+    // the residual's block reduction works on whole warps
+    if (res && (b.bx * b.by) % 32 != 0) return cudaErrorInvalidValue;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((G.nx + b.bx - 1) / b.bx, (G.ny + b.by - 1) / b.by, G.nz);
     cfg.blockDim = dim3(b.bx, b.by, 1);
@@ -101,17 +115,21 @@ cudaError_t launch_step(int wall, int storage, bool stochastic, const void *src,
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = pdl ? 1 : 0;
+    const ResidualArgs R = res ? *res : ResidualArgs{};
     cudaError_t e = dispatch(wall, storage, [&](auto W, auto *tp) {
         using T = std::remove_pointer_t<decltype(tp)>;
         constexpr int WL = decltype(W)::value;
+        const T *a = static_cast<const T *>(src);
+        T *d = static_cast<T *>(dst);
+        auto go = [&](auto sr) {
+            constexpr bool SRv = decltype(sr)::value;
+            if (res) return cudaLaunchKernelEx(&cfg, step_kernel<WL, T, SRv, true>, a, d, S, G, C, R);
+            return cudaLaunchKernelEx(&cfg, step_kernel<WL, T, SRv, false>, a, d, S, G, C, R);
+        };
         if constexpr (!std::is_same_v<T, float>) {
-            if (stochastic)
-                return cudaLaunchKernelEx(&cfg, step_kernel<WL, T, true>,
-                                          static_cast<const T *>(src), static_cast<T *>(dst), S,
-                                          G, C);
+            if (stochastic) return go(std::true_type{});
         }
-        return cudaLaunchKernelEx(&cfg, step_kernel<WL, T, false>, static_cast<const T *>(src),
-                                  static_cast<T *>(dst), S, G, C);
+        return go(std::false_type{});
     });
     if (e != cudaSuccess) return e;
     return cudaGetLastError();

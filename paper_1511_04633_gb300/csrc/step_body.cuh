@@ -19,27 +19,23 @@
 
 namespace lbm {
 
-// Collision of one cell (V = float) or of two cells at once (V = F2), in
-// place: d holds f - w, g the energy populations (pulled); on return both
-// hold the post-collision values of Eqs. (14), (29).  Both forms give the same
-// bits given one rule that the code below keeps: no product is added or
-// subtracted as a separate operation.  ptxas fuses a packed multiply into a
-// following packed add or subtract (an FMA, one rounding fewer) even with
-// explicit rounding modes, and the compiler may do the same to float code;
-// so every such pair is written as fma(), and a product that is subtracted
-// enters as the product of a negated factor.
-//
-// kShift > 0: d and g hold the populations times S = 2^kShift (the FP16
-// storage scale, so the kernels load and store the stored numbers as they
-// are), and the results are scaled alike.  The collision is linear in the
-// populations except through rho, V and T, which are unscaled (rho, T) or
-// divided by S through 1/rho (V), and through the products of two j
-// components, which carry S^2 and lose one S through their constant factor
-// or one multiply; the force terms take S in their constant factors.
-// Multiplying by a power of two commutes with rounding, so every value is
-// exactly S times its value at kShift = 0.
+// The pulled populations' pair sums and differences and their conserved
+// moments (Eqs. (20), (30)), in the order in which the collision forms them:
+// rho = 1 + drho, j, T, and V = j / rho as j times the reciprocal of rho.
+// The fields the library reports (fields, residual) are these values, so a
+// residual point taken inside a step kernel and one taken from a pull of the
+// stored state agree bitwise cell by cell.  With kShift > 0 the sums carry
+// the storage scale S = 2^kShift; Tu, rho and V are unscaled and ir
+// is 1/rho divided by S (see collide_from below).
+template <typename V>
+struct Conserved {
+    V s1, a1, s3, a3, s5, a5, s7, a7, s8, a8, s11, a11, s12, a12, s15, a15, s16, a16;
+    V SF, A, B, Cyz, SE, drho, X1, X2, Y1, Y2, Z1, Z2, Ex, Ey, Ez, jx, jy, jz;
+    V tsx, tax, tsy, tay, tsz, taz, tsm, T, Tu, rho, ir, vx, vy, vz;
+};
+
 template <typename V, int kShift = 0>
-__device__ __forceinline__ void collide(const CollideParams &C, V d[19], V g[7])
+__device__ __forceinline__ Conserved<V> conserved(const V d[19], const V g[7])
 {
     constexpr bool kScaled = kShift != 0;
     constexpr float kS = static_cast<float>(1u << kShift), kU = 1.0f / kS;
@@ -83,6 +79,44 @@ __device__ __forceinline__ void collide(const CollideParams &C, V d[19], V g[7])
         ir = recip(rho);
     }
     const V vx = jx * ir, vy = jy * ir, vz = jz * ir;
+    return Conserved<V>{s1, a1, s3, a3, s5, a5, s7, a7, s8, a8, s11, a11, s12, a12, s15, a15, s16, a16,
+                        SF, A, B, Cyz, SE, drho, X1, X2, Y1, Y2, Z1, Z2, Ex, Ey, Ez, jx, jy, jz,
+                        tsx, tax, tsy, tay, tsz, taz, tsm, T, Tu, rho, ir, vx, vy, vz};
+}
+
+// Collision of one cell (V = float) or of two cells at once (V = F2), in
+// place: d holds f - w, g the energy populations (pulled); on return both
+// hold the post-collision values of Eqs. (14), (29).  Both forms give the same
+// bits given one rule that the code below keeps: no product is added or
+// subtracted as a separate operation.  ptxas fuses a packed multiply into a
+// following packed add or subtract (an FMA, one rounding fewer) even with
+// explicit rounding modes, and the compiler may do the same to float code;
+// so every such pair is written as fma(), and a product that is subtracted
+// enters as the product of a negated factor.
+//
+// kShift > 0: d and g hold the populations times S = 2^kShift (the FP16
+// storage scale, so the kernels load and store the stored numbers as they
+// are), and the results are scaled alike.  The collision is linear in the
+// populations except through rho, V and T, which are unscaled (rho, T) or
+// divided by S through 1/rho (V), and through the products of two j
+// components, which carry S^2 and lose one S through their constant factor
+// or one multiply; the force terms take S in their constant factors.
+// Multiplying by a power of two commutes with rounding, so every value is
+// exactly S times its value at kShift = 0.
+template <typename V, int kShift = 0>
+__device__ __forceinline__ void collide_from(const CollideParams &C, V d[19], V g[7], const Conserved<V> &m0)
+{
+    constexpr bool kScaled = kShift != 0;
+    constexpr float kS = static_cast<float>(1u << kShift), kU = 1.0f / kS;
+    const V s1 = m0.s1, a1 = m0.a1, s3 = m0.s3, a3 = m0.a3, s5 = m0.s5, a5 = m0.a5;
+    const V s7 = m0.s7, a7 = m0.a7, s8 = m0.s8, a8 = m0.a8, s11 = m0.s11, a11 = m0.a11;
+    const V s12 = m0.s12, a12 = m0.a12, s15 = m0.s15, a15 = m0.a15, s16 = m0.s16, a16 = m0.a16;
+    const V SF = m0.SF, A = m0.A, B = m0.B, Cyz = m0.Cyz, SE = m0.SE, drho = m0.drho;
+    const V X1 = m0.X1, X2 = m0.X2, Y1 = m0.Y1, Y2 = m0.Y2, Z1 = m0.Z1, Z2 = m0.Z2;
+    const V Ex = m0.Ex, Ey = m0.Ey, Ez = m0.Ez, jx = m0.jx, jy = m0.jy, jz = m0.jz;
+    const V tsx = m0.tsx, tax = m0.tax, tsy = m0.tsy, tay = m0.tay, tsz = m0.tsz, taz = m0.taz;
+    const V tsm = m0.tsm, T = m0.T, Tu = m0.Tu, rho = m0.rho, ir = m0.ir, vx = m0.vx;
+    const V vy = m0.vy, vz = m0.vz;
     const V njz = jz * V(-1.0f);
     const V jj = fma(jx, jx, fma(jy, jy, jz * jz));  // S^2 |j|^2
     const V pww = fma(jy, jy, njz * jz);             // S^2 (jy^2 - jz^2)
@@ -251,6 +285,13 @@ __device__ __forceinline__ void collide(const CollideParams &C, V d[19], V g[7])
         g[5] = fma(V(-C.rq[3]), e3, g[5] + P);
         g[6] = fma(V(C.rq[3]), e3, g[6] + P);
     }
+}
+
+// Collision of the pulled populations d, g (see collide_from).
+template <typename V, int kShift = 0>
+__device__ __forceinline__ void collide(const CollideParams &C, V d[19], V g[7])
+{
+    collide_from<V, kShift>(C, d, g, conserved<V, kShift>(d, g));
 }
 
 // One cell per thread: the float form of collide().

@@ -20,6 +20,7 @@
 // two-buffer kernel, and the stochastic-rounding bits are keyed by the
 // producing cell and direction: the stored values are bitwise those of the
 // two-buffer scheme, only their addresses differ.
+#include "residual.cuh"
 #include "step_body.cuh"
 
 namespace lbm {
@@ -81,9 +82,11 @@ __device__ __forceinline__ void load_periodic(const T *A, const StepGeometry &S,
     });
 }
 
-template <int WALL, typename T, bool SR, int PHASE>
+// RES: this step also takes a residual point of the state it pulls.
+template <int WALL, typename T, bool SR, int PHASE, bool RES>
 __global__ void DMRT_INPLACE_BOUNDS(PHASE, T)
-    step_inplace_kernel(T *__restrict__ A, const InplaceGeometry SI, const CollideParams C)
+    step_inplace_kernel(T *__restrict__ A, const InplaceGeometry SI, const CollideParams C,
+                        const ResidualArgs R)
 {
     const StepGeometry &S = SI.load;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -92,48 +95,57 @@ __global__ void DMRT_INPLACE_BOUNDS(PHASE, T)
     // programmatic dependent launch, as in the two-buffer kernel
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;");
-    if (x >= S.nx || y >= S.ny) return;
-    const unsigned self = (static_cast<unsigned>(z) * S.ny + y) * S.nx + x;
-    float d[19], g[7];
-    if constexpr (WALL == 0) {
-        load_periodic<T, PHASE>(A, S, x, y, z, self, d, g);
-    } else if constexpr (PHASE == 0) {
-        pull_offsets<WALL, T>(A, TableOffsets{S}, S.nx, S.ny, S.nz, S.inv_ny, self, x, y, z, d, g);
-    } else {
-        pull_offsets<WALL, T>(A, LocalOffsets{S.plane}, S.nx, S.ny, S.nz, S.inv_ny, self, x, y, z,
-                              d, g);
+    DF acc[4] = {};
+    if (x < S.nx && y < S.ny) {
+        const unsigned self = (static_cast<unsigned>(z) * S.ny + y) * S.nx + x;
+        float d[19], g[7];
+        float prev[4];
+        if constexpr (RES) residual_cell_load(R, self, prev);
+        if constexpr (WALL == 0) {
+            load_periodic<T, PHASE>(A, S, x, y, z, self, d, g);
+        } else if constexpr (PHASE == 0) {
+            pull_offsets<WALL, T>(A, TableOffsets{S}, S.nx, S.ny, S.nz, S.inv_ny, self, x, y, z, d, g);
+        } else {
+            pull_offsets<WALL, T>(A, LocalOffsets{S.plane}, S.nx, S.ny, S.nz, S.inv_ny, self, x, y, z,
+                                  d, g);
+        }
+        const Conserved<float> m0 = conserved<float>(d, g);
+        // the fields a residual point compares, used after the stores
+        const float th = m0.Tu, ux = m0.vx, uy = m0.vy, uz = m0.vz;
+        collide_from<float>(C, d, g, m0);
+        unsigned base = 0;
+        if constexpr (SR) {
+            unsigned *ctr = reinterpret_cast<unsigned *>(A + static_cast<size_t>(kPlanes) * S.plane);
+            const unsigned step = ctr[PHASE];
+            if (self == 0) ctr[PHASE ^ 1] = step + 1u;
+            base = pcg_hash(self ^ pcg_hash(step));
+        }
+        if constexpr (PHASE == 1) {
+            store_cell_to<T, SR>(A, d, g, base, [&](auto I) -> unsigned {
+                constexpr int q = decltype(I)::value;
+                constexpr int opp = q < 19 ? q19_opp(q) : 19 + q7_opp(q - 19);
+                return self + opp * S.plane;
+            });
+        } else if constexpr (WALL == 0) {
+            store_cell_to<T, SR>(A, d, g, base, [&](auto I) -> unsigned {
+                constexpr int q = decltype(I)::value;
+                constexpr int ex = q < 19 ? q19_ex(q) : q7_ex(q - 19);
+                constexpr int ey = q < 19 ? q19_ey(q) : q7_ey(q - 19);
+                constexpr int ez = q < 19 ? q19_ez(q) : q7_ez(q - 19);
+                return q * S.plane + wrapped_cell(S, x + ex, y + ey, z + ez);
+            });
+        } else {
+            const unsigned edge = face_bits(x, y, z, S.nx, S.ny, S.nz);
+            store_cell_to<T, SR>(A, d, g, base, [&](auto I) -> unsigned {
+                constexpr int q = decltype(I)::value;
+                constexpr unsigned faces = leaving_faces<q>();
+                if constexpr (faces == 0) return self + static_cast<unsigned>(SI.sn[q]);
+                else return self + static_cast<unsigned>((edge & faces) ? SI.sb[q] : SI.sn[q]);
+            });
+        }
+        if constexpr (RES) residual_cell(R, self, prev, th, ux, uy, uz, acc);
     }
-    collide_cell(C, d, g);
-    unsigned base = 0;
-    if constexpr (SR) {
-        unsigned *ctr = reinterpret_cast<unsigned *>(A + static_cast<size_t>(kPlanes) * S.plane);
-        const unsigned step = ctr[PHASE];
-        if (self == 0) ctr[PHASE ^ 1] = step + 1u;
-        base = pcg_hash(self ^ pcg_hash(step));
-    }
-    if constexpr (PHASE == 1) {
-        store_cell_to<T, SR>(A, d, g, base, [&](auto I) -> unsigned {
-            constexpr int q = decltype(I)::value;
-            constexpr int opp = q < 19 ? q19_opp(q) : 19 + q7_opp(q - 19);
-            return self + opp * S.plane;
-        });
-    } else if constexpr (WALL == 0) {
-        store_cell_to<T, SR>(A, d, g, base, [&](auto I) -> unsigned {
-            constexpr int q = decltype(I)::value;
-            constexpr int ex = q < 19 ? q19_ex(q) : q7_ex(q - 19);
-            constexpr int ey = q < 19 ? q19_ey(q) : q7_ey(q - 19);
-            constexpr int ez = q < 19 ? q19_ez(q) : q7_ez(q - 19);
-            return q * S.plane + wrapped_cell(S, x + ex, y + ey, z + ez);
-        });
-    } else {
-        const unsigned edge = face_bits(x, y, z, S.nx, S.ny, S.nz);
-        store_cell_to<T, SR>(A, d, g, base, [&](auto I) -> unsigned {
-            constexpr int q = decltype(I)::value;
-            constexpr unsigned faces = leaving_faces<q>();
-            if constexpr (faces == 0) return self + static_cast<unsigned>(SI.sn[q]);
-            else return self + static_cast<unsigned>((edge & faces) ? SI.sb[q] : SI.sn[q]);
-        });
-    }
+    if constexpr (RES) residual_block_store(acc, R.partials);
 }
 
 }  // namespace
@@ -163,9 +175,12 @@ void fill_inplace_geometry(const Geometry &G, InplaceGeometry &SI)
 
 cudaError_t launch_step_inplace(int wall, int storage, bool stochastic, void *buf, int phase,
                                 const InplaceGeometry &SI, const Geometry &G,
-                                const CollideParams &C, BlockShape b, cudaStream_t s, bool pdl)
+                                const CollideParams &C, BlockShape b, cudaStream_t s, bool pdl,
+                                const ResidualArgs *res)
 {
     if (phase != 0 && phase != 1) return cudaErrorInvalidValue;
+    // the residual's block reduction works on whole warps
+    if (res && (b.bx * b.by) % 32 != 0) return cudaErrorInvalidValue;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((G.nx + b.bx - 1) / b.bx, (G.ny + b.by - 1) / b.by, G.nz);
     cfg.blockDim = dim3(b.bx, b.by, 1);
@@ -176,18 +191,23 @@ cudaError_t launch_step_inplace(int wall, int storage, bool stochastic, void *bu
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = pdl ? 1 : 0;
+    const ResidualArgs R = res ? *res : ResidualArgs{};
     cudaError_t e = dispatch(wall, storage, [&](auto W, auto *tp) {
         using T = std::remove_pointer_t<decltype(tp)>;
         constexpr int WL = decltype(W)::value;
         T *A = static_cast<T *>(buf);
+        auto go = [&](auto sr) {
+            constexpr bool SRv = decltype(sr)::value;
+            if (res)
+                return phase == 0 ? cudaLaunchKernelEx(&cfg, step_inplace_kernel<WL, T, SRv, 0, true>, A, SI, C, R)
+                                  : cudaLaunchKernelEx(&cfg, step_inplace_kernel<WL, T, SRv, 1, true>, A, SI, C, R);
+            return phase == 0 ? cudaLaunchKernelEx(&cfg, step_inplace_kernel<WL, T, SRv, 0, false>, A, SI, C, R)
+                              : cudaLaunchKernelEx(&cfg, step_inplace_kernel<WL, T, SRv, 1, false>, A, SI, C, R);
+        };
         if constexpr (!std::is_same_v<T, float>) {
-            if (stochastic)
-                return phase == 0
-                           ? cudaLaunchKernelEx(&cfg, step_inplace_kernel<WL, T, true, 0>, A, SI, C)
-                           : cudaLaunchKernelEx(&cfg, step_inplace_kernel<WL, T, true, 1>, A, SI, C);
+            if (stochastic) return go(std::true_type{});
         }
-        return phase == 0 ? cudaLaunchKernelEx(&cfg, step_inplace_kernel<WL, T, false, 0>, A, SI, C)
-                          : cudaLaunchKernelEx(&cfg, step_inplace_kernel<WL, T, false, 1>, A, SI, C);
+        return go(std::false_type{});
     });
     if (e != cudaSuccess) return e;
     return cudaGetLastError();

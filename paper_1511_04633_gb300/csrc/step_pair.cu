@@ -23,6 +23,7 @@
 #include <cudaTypedefs.h>
 
 #include "pair_body.cuh"
+#include "residual.cuh"
 #include "umma.cuh"
 
 namespace lbm {
@@ -67,33 +68,58 @@ __device__ __forceinline__ PairCoords pair_coords(const StepGeometry &S)
     return c;
 }
 
-template <int WALL, typename T, bool SR>
-__global__ void __launch_bounds__(kPairThreads, kPairBlocks)
+// The fields of a pulled pair that a residual point compares (unscaled):
+// theta, u_x, u_y, u_z, kept from the moments until the stores are done.
+// The snapshot is loaded with the populations and compared after the
+// stores: measured on GB300 (128^3 FP32), a residual step then costs 27 us
+// more than a plain one, against 44 us with the snapshot only prefetched to
+// L2 early and 177 us with its loads after the stores.
+struct PairFields {
+    F2 th, ux, uy, uz;
+};
+
+// Blocks per SM of the kernels that take a residual point: 4 (128
+// registers), so that the snapshot and the kept fields do not spill; the
+// other steps keep kPairBlocks.
+constexpr int kPairBlocksRes = 4;
+
+// RES: this step also takes a residual point of the state it pulls (the
+// fields of the pulled populations against the snapshot, residual.cuh).
+template <int WALL, typename T, bool SR, bool RES>
+__global__ void __launch_bounds__(kPairThreads, RES ? kPairBlocksRes : kPairBlocks)
     step_pair_kernel(const T *__restrict__ src, T *__restrict__ dst, const StepGeometry S,
-                     const CollideParams C)
+                     const CollideParams C, const ResidualArgs R)
 {
     // programmatic dependent launch, as in the one-cell kernel
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;");
     const PairCoords c = pair_coords(S);
-    if (!c.valid) return;
-    F2 d[19], g[7];
-    pull_pair<WALL, T>(src + c.self, TableOffsets{S}, c.faces, c.th_lin, d, g);
-    collide_stored<T>(C, d, g);
-    // every plane of the pair: one 2-element store at the cells' own slots
-    unsigned r01 = 0;
-    if constexpr (SR) {
-        const size_t counter_at = static_cast<size_t>(kPlanes) * S.plane;
-        const unsigned step = *reinterpret_cast<const unsigned *>(src + counter_at);
-        if (c.self == 0) *reinterpret_cast<unsigned *>(dst + counter_at) = step + 1u;
-        r01 = pair_bits(c.self, step);
+    DF acc[4] = {};
+    if (c.valid) {
+        F2 d[19], g[7];
+        float2 prev[4];
+        if constexpr (RES) residual_pair_load(R, c.self, prev);
+        pull_pair<WALL, T>(src + c.self, TableOffsets{S}, c.faces, c.th_lin, d, g);
+        const Conserved<F2> m0 = conserved<F2, Pair<T>::kShift>(d, g);
+        const PairFields fl{m0.Tu, m0.vx, m0.vy, m0.vz};
+        collide_from<F2, Pair<T>::kShift>(C, d, g, m0);
+        // every plane of the pair: one 2-element store at the cells' own slots
+        unsigned r01 = 0;
+        if constexpr (SR) {
+            const size_t counter_at = static_cast<size_t>(kPlanes) * S.plane;
+            const unsigned step = *reinterpret_cast<const unsigned *>(src + counter_at);
+            if (c.self == 0) *reinterpret_cast<unsigned *>(dst + counter_at) = step + 1u;
+            r01 = pair_bits(c.self, step);
+        }
+        T *Dp = dst + c.self;
+        const unsigned plane = opaque(S.plane);
+        static_for<0, 26>([&](auto I) {
+            constexpr int q = decltype(I)::value;
+            store2<T, SR>(Dp + q * plane, plane_value<q>(d, g), SR ? plane_bits<q>(r01) : 0u);
+        });
+        if constexpr (RES) residual_pair(R, c.self, prev, fl.th.v, fl.ux.v, fl.uy.v, fl.uz.v, acc);
     }
-    T *Dp = dst + c.self;
-    const unsigned plane = opaque(S.plane);
-    static_for<0, 26>([&](auto I) {
-        constexpr int q = decltype(I)::value;
-        store2<T, SR>(Dp + q * plane, plane_value<q>(d, g), SR ? plane_bits<q>(r01) : 0u);
-    });
+    if constexpr (RES) residual_block_store(acc, R.partials);
 }
 
 // In-place streaming with two cells per thread: the two phases of
@@ -102,52 +128,61 @@ __global__ void __launch_bounds__(kPairThreads, kPairBlocks)
 // pair; phase 0 pulls like the two-buffer step and writes S*_q to x + e_q,
 // an aligned pair for the planes with e_x = 0 and one element per cell for
 // the others (or, where the link leaves the box, plane opp(q) at the cell).
-template <int WALL, typename T, bool SR, int PHASE>
-__global__ void __launch_bounds__(kPairThreads, kPairBlocks)
-    step_inplace_pair_kernel(T *__restrict__ A, const InplaceGeometry SI, const CollideParams C)
+template <int WALL, typename T, bool SR, int PHASE, bool RES>
+__global__ void __launch_bounds__(kPairThreads, RES ? kPairBlocksRes : kPairBlocks)
+    step_inplace_pair_kernel(T *__restrict__ A, const InplaceGeometry SI, const CollideParams C,
+                             const ResidualArgs R)
 {
     const StepGeometry &S = SI.load;
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;");
     const PairCoords c = pair_coords(S);
-    if (!c.valid) return;
-    F2 d[19], g[7];
-    if constexpr (PHASE == 0) pull_pair<WALL, T>(A + c.self, TableOffsets{S}, c.faces, c.th_lin, d, g);
-    else pull_pair<WALL, T>(A + c.self, LocalOffsets{S.plane}, c.faces, c.th_lin, d, g);
-    collide_stored<T>(C, d, g);
-    unsigned r01 = 0;
-    if constexpr (SR) {
-        unsigned *ctr = reinterpret_cast<unsigned *>(A + static_cast<size_t>(kPlanes) * S.plane);
-        const unsigned step = ctr[PHASE];
-        if (c.self == 0) ctr[PHASE ^ 1] = step + 1u;
-        r01 = pair_bits(c.self, step);
-    }
-    T *Dp = A + c.self;
-    const PairFaces &P = c.faces;
-    const unsigned plane = opaque(S.plane);
-    static_for<0, 26>([&](auto I) {
-        constexpr int q = decltype(I)::value;
-        const F2 v = plane_value<q>(d, g);
-        const unsigned r = SR ? plane_bits<q>(r01) : 0u;
-        if constexpr (PHASE == 1) {
-            store2<T, SR>(Dp + plane_opp<q>() * plane, v, r);
-        } else {
-            constexpr int ex = plane_ex<q>(), ey = plane_ey<q>(), ez = plane_ez<q>();
-            bool lyz = false;  // the link leaves through a y or z face
-            if constexpr (ey == 1) lyz = lyz || P.yhi;
-            if constexpr (ey == -1) lyz = lyz || P.ylo;
-            if constexpr (ez == 1) lyz = lyz || P.zhi;
-            if constexpr (ez == -1) lyz = lyz || P.zlo;
-            const unsigned sn = static_cast<unsigned>(SI.sn[q]), sb = static_cast<unsigned>(SI.sb[q]);
-            if constexpr (ex == 0) {
-                store2<T, SR>(Dp + (lyz ? sb : sn), v, r);
-            } else {
-                const bool l0 = lyz || (ex == -1 && P.xlo);
-                const bool l1 = lyz || (ex == 1 && P.xhi);
-                store_split<T, SR>(Dp + (l0 ? sb : sn), (Dp + (l1 ? sb : sn)) + 1, v, r);
-            }
+    DF acc[4] = {};
+    if (c.valid) {
+        F2 d[19], g[7];
+        float2 prev[4];
+        if constexpr (RES) residual_pair_load(R, c.self, prev);
+        if constexpr (PHASE == 0) pull_pair<WALL, T>(A + c.self, TableOffsets{S}, c.faces, c.th_lin, d, g);
+        else pull_pair<WALL, T>(A + c.self, LocalOffsets{S.plane}, c.faces, c.th_lin, d, g);
+        const Conserved<F2> m0 = conserved<F2, Pair<T>::kShift>(d, g);
+        const PairFields fl{m0.Tu, m0.vx, m0.vy, m0.vz};
+        collide_from<F2, Pair<T>::kShift>(C, d, g, m0);
+        unsigned r01 = 0;
+        if constexpr (SR) {
+            unsigned *ctr = reinterpret_cast<unsigned *>(A + static_cast<size_t>(kPlanes) * S.plane);
+            const unsigned step = ctr[PHASE];
+            if (c.self == 0) ctr[PHASE ^ 1] = step + 1u;
+            r01 = pair_bits(c.self, step);
         }
-    });
+        T *Dp = A + c.self;
+        const PairFaces &P = c.faces;
+        const unsigned plane = opaque(S.plane);
+        static_for<0, 26>([&](auto I) {
+            constexpr int q = decltype(I)::value;
+            const F2 v = plane_value<q>(d, g);
+            const unsigned r = SR ? plane_bits<q>(r01) : 0u;
+            if constexpr (PHASE == 1) {
+                store2<T, SR>(Dp + plane_opp<q>() * plane, v, r);
+            } else {
+                constexpr int ex = plane_ex<q>(), ey = plane_ey<q>(), ez = plane_ez<q>();
+                bool lyz = false;  // the link leaves through a y or z face
+                if constexpr (ey == 1) lyz = lyz || P.yhi;
+                if constexpr (ey == -1) lyz = lyz || P.ylo;
+                if constexpr (ez == 1) lyz = lyz || P.zhi;
+                if constexpr (ez == -1) lyz = lyz || P.zlo;
+                const unsigned sn = static_cast<unsigned>(SI.sn[q]), sb = static_cast<unsigned>(SI.sb[q]);
+                if constexpr (ex == 0) {
+                    store2<T, SR>(Dp + (lyz ? sb : sn), v, r);
+                } else {
+                    const bool l0 = lyz || (ex == -1 && P.xlo);
+                    const bool l1 = lyz || (ex == 1 && P.xhi);
+                    store_split<T, SR>(Dp + (l0 ? sb : sn), (Dp + (l1 ? sb : sn)) + 1, v, r);
+                }
+            }
+        });
+        if constexpr (RES) residual_pair(R, c.self, prev, fl.th.v, fl.ux.v, fl.uy.v, fl.uz.v, acc);
+    }
+    if constexpr (RES) residual_block_store(acc, R.partials);
 }
 
 
@@ -411,13 +446,21 @@ cudaLaunchConfig_t pair_config(const Geometry &G, cudaStream_t s, cudaLaunchAttr
 
 }  // namespace
 
+size_t pair_blocks(const Geometry &G)
+{
+    cudaLaunchAttribute attr[1];
+    const cudaLaunchConfig_t cfg = pair_config(G, nullptr, attr, false);
+    return static_cast<size_t>(cfg.gridDim.x) * cfg.gridDim.y * cfg.gridDim.z;
+}
+
 cudaError_t launch_step_pair(int wall, int storage, bool stochastic, const void *src, void *dst,
                              const StepGeometry &S, const Geometry &G, const CollideParams &C,
-                             cudaStream_t s, bool pdl)
+                             cudaStream_t s, bool pdl, const ResidualArgs *res)
 {
     if (!step_pair_supported(wall, G)) return cudaErrorInvalidValue;
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = pair_config(G, s, attr, pdl);
+    const ResidualArgs R = res ? *res : ResidualArgs{};
     cudaError_t e = dispatch(wall, storage, [&](auto W, auto *tp) {
         using T = std::remove_pointer_t<decltype(tp)>;
         constexpr int WL = decltype(W)::value;
@@ -426,10 +469,15 @@ cudaError_t launch_step_pair(int wall, int storage, bool stochastic, const void 
         } else {
             const T *a = static_cast<const T *>(src);
             T *b = static_cast<T *>(dst);
+            auto go = [&](auto sr) {
+                constexpr bool SRv = decltype(sr)::value;
+                if (res) return cudaLaunchKernelEx(&cfg, step_pair_kernel<WL, T, SRv, true>, a, b, S, C, R);
+                return cudaLaunchKernelEx(&cfg, step_pair_kernel<WL, T, SRv, false>, a, b, S, C, R);
+            };
             if constexpr (!std::is_same_v<T, float>) {
-                if (stochastic) return cudaLaunchKernelEx(&cfg, step_pair_kernel<WL, T, true>, a, b, S, C);
+                if (stochastic) return go(std::true_type{});
             }
-            return cudaLaunchKernelEx(&cfg, step_pair_kernel<WL, T, false>, a, b, S, C);
+            return go(std::false_type{});
         }
     });
     if (e != cudaSuccess) return e;
@@ -534,11 +582,13 @@ cudaError_t launch_step_pair_tma(int wall, int storage, bool stochastic, const v
 
 cudaError_t launch_step_inplace_pair(int wall, int storage, bool stochastic, void *buf, int phase,
                                      const InplaceGeometry &SI, const Geometry &G,
-                                     const CollideParams &C, cudaStream_t s, bool pdl)
+                                     const CollideParams &C, cudaStream_t s, bool pdl,
+                                     const ResidualArgs *res)
 {
     if (!step_pair_supported(wall, G) || (phase != 0 && phase != 1)) return cudaErrorInvalidValue;
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = pair_config(G, s, attr, pdl);
+    const ResidualArgs R = res ? *res : ResidualArgs{};
     cudaError_t e = dispatch(wall, storage, [&](auto W, auto *tp) {
         using T = std::remove_pointer_t<decltype(tp)>;
         constexpr int WL = decltype(W)::value;
@@ -546,14 +596,20 @@ cudaError_t launch_step_inplace_pair(int wall, int storage, bool stochastic, voi
             return cudaErrorInvalidValue;
         } else {
             T *A = static_cast<T *>(buf);
-            if constexpr (!std::is_same_v<T, float>) {
-                if (stochastic)
+            auto go = [&](auto sr) {
+                constexpr bool SRv = decltype(sr)::value;
+                if (res)
                     return phase == 0
-                               ? cudaLaunchKernelEx(&cfg, step_inplace_pair_kernel<WL, T, true, 0>, A, SI, C)
-                               : cudaLaunchKernelEx(&cfg, step_inplace_pair_kernel<WL, T, true, 1>, A, SI, C);
+                               ? cudaLaunchKernelEx(&cfg, step_inplace_pair_kernel<WL, T, SRv, 0, true>, A, SI, C, R)
+                               : cudaLaunchKernelEx(&cfg, step_inplace_pair_kernel<WL, T, SRv, 1, true>, A, SI, C, R);
+                return phase == 0
+                           ? cudaLaunchKernelEx(&cfg, step_inplace_pair_kernel<WL, T, SRv, 0, false>, A, SI, C, R)
+                           : cudaLaunchKernelEx(&cfg, step_inplace_pair_kernel<WL, T, SRv, 1, false>, A, SI, C, R);
+            };
+            if constexpr (!std::is_same_v<T, float>) {
+                if (stochastic) return go(std::true_type{});
             }
-            return phase == 0 ? cudaLaunchKernelEx(&cfg, step_inplace_pair_kernel<WL, T, false, 0>, A, SI, C)
-                              : cudaLaunchKernelEx(&cfg, step_inplace_pair_kernel<WL, T, false, 1>, A, SI, C);
+            return go(std::false_type{});
         }
     });
     if (e != cudaSuccess) return e;

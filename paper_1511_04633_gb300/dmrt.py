@@ -273,13 +273,19 @@ def dmrt_nusselt_local(h, wall, local):
 def dmrt_nusselt_noalloc(theta, wall: int = 0, stream=None):
     """Nusselt numbers of a CUDA float32 tensor theta[z][y][x], computed
     without any device allocation (see include/dmrt.h)."""
+    import torch
+
     p, side = _ptr(theta)
     if side != 1:
         raise TypeError("theta must be a CUDA tensor")
+    if theta.dim() != 3:
+        raise ValueError("theta must be a 3-D tensor [z][y][x]")
     nz, ny, nx = theta.shape
     raw = getattr(stream, "cuda_stream", stream)
     out = (ctypes.c_double * 3)()
-    check(None, load().dmrt_nusselt_noalloc(p, nx, ny, nz, wall, raw, out), "dmrt_nusselt_noalloc")
+    # the entry point works on the current device: make it theta's
+    with torch.cuda.device(theta.device):
+        check(None, load().dmrt_nusselt_noalloc(p, nx, ny, nz, wall, raw, out), "dmrt_nusselt_noalloc")
     return tuple(out)
 
 

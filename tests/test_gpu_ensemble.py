@@ -61,6 +61,9 @@ def test_members_match_the_oracle(dm):
 
 
 def test_member_residuals_equal_single_residuals(dm):
+    """The same per-cell terms (members evolve bitwise like single handles),
+    summed over other blocks: equal up to the last bits of the double-float
+    sums."""
     K = 50
     ens = dm.Ensemble(MEMBERS, residual_interval=K)
     ens.step(3 * K)
@@ -68,7 +71,7 @@ def test_member_residuals_equal_single_residuals(dm):
     for k, m in enumerate(MEMBERS):
         single = dm.Cavity(m["grid"], m["Ra"], wall_type=m["wall"], residual_interval=K)
         single.step(3 * K)
-        assert r[k] == pytest.approx(single.residual(), rel=1e-12)
+        assert r[k] == pytest.approx(single.residual(), rel=1e-11)
 
 
 def test_autotune_keeps_the_state_and_reports(dm):

@@ -115,7 +115,9 @@ def test_graph_replayed_intervals_from_rest(dm, storage, loads):
         h.step(7)
         h.step(400)
     _assert_same(two, one)
-    assert two.residual() == one.residual()
+    # the same fields, summed over different block shapes: the residuals'
+    # double-float sums may differ in their last bits only
+    assert two.residual() == pytest.approx(one.residual(), rel=1e-11)
     assert dm.dmrt_get_stats(two.h)["step_launches"] == 407
 
 

@@ -4,6 +4,7 @@ FP64 numpy oracle of the same network, its training, and its warm start."""
 import numpy as np
 import pytest
 
+import oracle
 from oracle import surrogate as S
 from paper_1511_04633_gb300 import inputs
 
@@ -22,11 +23,11 @@ def env():
     return torch, dmrt
 
 
-def _setup(dm, storage, seed=5):
+def _setup(dm, storage, seed=5, scale=0.3):
     sur = dm.Surrogate(CFG["grid"], CFG["depth"], CFG["channels"], storage=storage, max_batch=2)
     net = S.UNet(CFG["grid"], CFG["depth"], CFG["channels"])
     assert sur.param_count == net.count
-    p = inputs.random_weights(net.count, seed=seed, scale=0.3)
+    p = inputs.random_weights(net.count, seed=seed, scale=scale)
     sur.set_params(p)
     return sur, net, p
 
@@ -116,25 +117,36 @@ def test_training_overfits_a_batch_and_is_repeatable(env):
     assert np.array_equal(runs[0][1], runs[1][1])
 
 
-def test_warm_start_resamples_and_scales_the_prediction(env):
-    """A network whose output is the constant (0, 0, 0, 0.2, 0.5) warm-starts a
-    cavity to u = 0, theta = 0.2 away from the Dirichlet walls and rho =
-    1 + 0.5 * 3 u_c^2."""
+@pytest.mark.parametrize("N,wall,Ra", [(24, 1, 3e4), (12, 3, 5e5), (16, 2, 2e3)])
+def test_warm_start_matches_the_oracle_mapping(env, N, wall, Ra):
+    """dmrt_warm_start against the oracle's chain on a network with random
+    weights (so the prediction varies along every axis and channel): the
+    FP64 network forward, trilinear resampling between the cell-centred grids
+    (16^3 to N^3: up by 3/2, down by 3/4, and the identity), the channel
+    scalings and the equilibrium initialisation, compared through the
+    fields of the pulled populations.  A wrong interpolation weight, axis
+    order, cell-centre offset or channel-to-field assignment fails."""
     torch, dm = env
-    sur = dm.Surrogate(CFG["grid"], CFG["depth"], CFG["channels"], storage=dm.STORE_F32)
-    net = S.UNet(CFG["grid"], CFG["depth"], CFG["channels"])
-    p = np.zeros(net.count, np.float32)
-    wo, bo = net.offsets[-1]
-    p[bo + 3] = 0.2  # head bias of theta
-    p[bo + 4] = 0.5  # head bias of (rho - 1) / (3 u_c^2)
-    sur.set_params(p)
-    cav = dm.Cavity((24, 24, 24), 1e4, wall_type=1)
-    sur.warm_start(cav, 1e4, 1)
+    # weights of scale 0.12 give outputs of order 0.1-0.3: velocities near
+    # 0.01, as in a converged cavity
+    sur, net, p = _setup(dm, dm.STORE_F32, seed=17, scale=0.12)
+    cav = dm.Cavity((N, N, N), Ra, wall_type=wall)
+    sur.warm_start(cav, Ra, wall)
     rho, u, th = cav.fields()
-    uc = np.sqrt(cav.params["gbeta"] * 24)
-    assert np.abs(u).max() == 0.0
-    assert np.abs(rho - (1 + 0.5 * 3 * uc * uc)).max() < 1e-6
-    assert np.abs(th[:, 1:-1, :] - 0.2).max() < 1e-6
+    pred, _ = net.forward(p.astype(np.float64), S.features([Ra], [wall], CFG["grid"]))
+    uc = np.sqrt(cav.params["gbeta"] * N)
+    r0, u0, t0 = S.warm_start_fields(pred[0], N, uc)
+    # the prediction must vary, or the comparison could not see a resampling error
+    assert np.ptp(t0) > 0.1 * np.abs(t0).max() and np.ptp(u0[0]) > 0.1 * np.abs(u0[0]).max()
+    o = oracle.Oracle.physical((N, N, N), wall, Ra)
+    o.init_fields(r0, u0, t0)
+    ro, uo, to = o.fields()
+    o.close()
+    # FP32 network (checked to 1e-4 of its output scale above) and FP32 fields
+    tol = 2e-4
+    assert np.abs(th - to).max() <= tol * np.abs(to).max()
+    assert np.abs(u - uo).max() <= tol * np.abs(uo).max()
+    assert np.abs(rho - ro).max() <= tol * np.abs(ro - 1).max() + 1e-6
 
 
 def test_surrogate_rejects_bad_configurations(env):

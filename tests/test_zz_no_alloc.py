@@ -66,3 +66,28 @@ def test_noalloc_rejects_sizes_beyond_its_limit(env):
     assert lib.dmrt_nusselt_noalloc(fake, 8, 1, 8, 0, None, out) == dmrt.ERR_ARG
     assert lib.dmrt_nusselt_noalloc(fake, 8, 8, 8, 2, None, out) == dmrt.ERR_ARG
     assert lib.dmrt_nusselt_noalloc(None, 8, 8, 8, 0, None, out) == dmrt.ERR_ARG
+
+
+@pytest.mark.parametrize("nz,ny,nx,wall,on_stream", [(18, 12, 24, 0, False), (301, 4, 300, 1, True),
+                                                     (9, 5, 257, 0, False)])
+def test_noalloc_matches_the_oracle_on_a_seeded_field(env, nz, ny, nx, wall, on_stream):
+    """The same seeded temperature field (rounded to float32, as the call
+    reads it) through the allocation-free call and through the FP64 oracle's
+    Nusselt numbers of a field: rows wider than one block's threads (nx >
+    256) and more rows than the finishing block has threads (nz > 256) take
+    the strided loops of both kernels; one case runs on a caller's stream."""
+    import numpy as np
+
+    import oracle
+    from paper_1511_04633_gb300 import inputs
+
+    torch, dmrt = env
+    _, _, th = inputs.random_fields((nx, ny, nz), seed=70 + nz, dtheta=0.4)
+    th32 = np.ascontiguousarray(th, dtype=np.float32)
+    (r3, r2, rmax), _ = oracle.nusselt_from_theta(th32.astype(np.float64), wall)
+    theta = torch.from_numpy(th32).cuda()
+    stream = torch.cuda.Stream() if on_stream else None
+    got = dmrt.dmrt_nusselt_noalloc(theta, wall, stream=stream)
+    # FP64 local values of the same float32 inputs, summed in another order
+    for x, y in zip(got, (r3, r2, rmax)):
+        assert abs(x - y) <= 1e-12 * max(1.0, abs(y)), (got, (r3, r2, rmax))
