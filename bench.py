@@ -60,7 +60,7 @@ def workload(args) -> str:
 
 
 _BODY = ["paper_1511_04633_gb300/csrc/step_body.cuh", "paper_1511_04633_gb300/csrc/lattice.cuh",
-         "paper_1511_04633_gb300/csrc/vec2.cuh"]
+         "paper_1511_04633_gb300/csrc/vec2.cuh", "paper_1511_04633_gb300/csrc/residual.cuh"]
 # sources of each step kernel: one cell per thread (two buffers), two cells
 # per thread (two buffers; direct or TMA-staged loads), in place
 KERNEL_SOURCES = {"ab": ["paper_1511_04633_gb300/csrc/step.cu"] + _BODY,
@@ -366,6 +366,8 @@ def run_dmrt(args, rank, local, world):
 
     nbuf = 2 if args.streaming == "ab" else 1
     steady = None if args.no_steady else run_to_steady(dmrt, torch, stream, grid, storage, args, launch_s)
+    warm = None if args.warm_start_cases <= 0 else run_warm_start(args.warm_start_cases)
+    configs = None if args.no_configs else run_configs(dmrt, torch, stream, local)
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         mlups, cores, n = oracle_sample(grid, args.wall, args.ra, args.cpu_seconds)
@@ -406,6 +408,8 @@ def run_dmrt(args, rank, local, world):
         "gpu_launches": stats["total_launches"],
         "clocks": clocks.summary(),
         "steady": steady,
+        "warm_start": warm,
+        "configs": configs,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:
@@ -448,10 +452,199 @@ def run_to_steady(dmrt, torch, stream, grid, storage, args, launch_s, seconds=40
             "window_mlups": cells * 1000 / (ms / 1e3) / 1e6}
 
 
+WARM_GRID = 128  # the warm-started cavities of the learned warm start (64^3 network, resampled)
+
+
+def run_warm_start(count):
+    """Outside the timed region: the learned warm start on `count` cavities
+    of the network's seeded draws that it was not trained on, at 128^3.  The
+    network is read from the parameters file that
+    ``python -m paper_1511_04633_gb300.surrogate --save-params`` wrote (no
+    training here).  Each cavity is solved from rest to the convergence
+    residual and on to 1e-9 for the reference Nu, and from the network's
+    prediction to the convergence residual; steps and wall-clock seconds
+    until the hot-wall Nu_3D stays within 1e-3 of the reference, and until
+    the residual falls below 1e-7, are reported for both."""
+    from paper_1511_04633_gb300 import surrogate as S
+
+    sur, info = S.load_surrogate()
+    cases = []
+    t0 = time.perf_counter()
+    for d in S.held_out_draws(count):
+        r = S.compare_warm_start(sur, WARM_GRID, d["Ra"], d["wall"], tol=1e-7, nu_rtol=1e-3)
+        cold, warm = r["from_rest"], r["warm"]
+
+        def ratio(a, b):
+            return None if a is None or b is None or b <= 0 else a / b
+
+        cases.append({"Ra": d["Ra"], "wall": d["wall"], "nu_reference": r["nu_reference"],
+                      "nu_warm_rel_err": r["nu_rel_diff"],
+                      "from_rest": {k: cold[k] for k in ("steps_to_nu", "seconds_to_nu",
+                                                         "steps_to_residual", "seconds_to_residual")},
+                      "warm": {k: warm[k] for k in ("steps_to_nu", "seconds_to_nu", "steps_to_residual",
+                                                    "seconds_to_residual", "predict_seconds")},
+                      "gain_steps_to_nu": ratio(cold["steps_to_nu"], warm["steps_to_nu"]),
+                      "gain_seconds_to_nu": ratio(cold["seconds_to_nu"], warm["seconds_to_nu"]),
+                      "gain_seconds_to_residual": ratio(cold["seconds_to_residual"], warm["seconds_to_residual"])})
+    sur.close()
+    gains = [c["gain_seconds_to_nu"] for c in cases if c["gain_seconds_to_nu"] is not None]
+    return {"grid": WARM_GRID, "network": {"grid": info.get("grid"), "channels": info.get("channels"),
+                                           "trained_on": info.get("train"), "seed": info.get("seed")},
+            "nu_rtol": 1e-3, "residual_tol": 1e-7, "nu_reference": "from-rest solve continued to r < 1e-9",
+            "cases": cases, "min_gain_seconds_to_nu": min(gains) if gains else None,
+            "max_nu_warm_rel_err": max(c["nu_warm_rel_err"] for c in cases),
+            "seconds": time.perf_counter() - t0}
+
+
+def measure_ensemble(dmrt, inputs, torch, stream, gpu, *, members, seed, storage, streaming, inner, steps,
+                     warmup, dist=None, device=None, world=1):
+    """The batched ensemble of seeded cavities (one launch per time step over
+    all of them, autotuned) timed with CUDA events on `stream`, and the same
+    cavities as separate handles stepped one after another.  Returns the
+    measurement as a dict (MLUPS over all ranks)."""
+    draws = inputs.ensemble_draws(members, seed=seed)
+    cav = [{"grid": (d["n"],) * 3, "Ra": d["Ra"], "wall": d["wall"]} for d in draws]
+    ens = dmrt.Ensemble(cav, storage=storage, streaming=streaming)
+    ens_kernel = ("ensemble_pair_kernel" if ens.params(0)["cells_per_thread"] == 2
+                  else "ensemble_step_kernel") + (" (in place, both phases)" if streaming else "")
+    dmrt.dmrt_ensemble_set_stream(ens.e, stream)
+    report = ens.autotune(trials=3)
+    cells = ens.cells
+
+    def one_step():
+        ens.step(inner)
+        return ens.nusselt(0)
+
+    for _ in range(warmup):
+        one_step()
+    dmrt.dmrt_ensemble_get_stats(ens.e, reset=True)
+    dmrt.dmrt_ensemble_set_timing(ens.e, True)
+    barrier(dist)
+    torch.cuda.synchronize()
+    with ClockSampler(gpu) as clocks:
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(steps):
+            one_step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier(dist)
+    secs = reduce_max(dist, ev0.elapsed_time(ev1) / 1e3, device)
+    stats = dmrt.dmrt_ensemble_get_stats(ens.e, reset=True)
+    value = aggregate(cells * inner * steps, world, secs)
+    launch_s = stats["step_ms"] / 1e3 / max(stats["timed_steps"], 1)
+    achieved = stats["bytes_per_cell"] * cells / launch_s / 1e9
+    peak, peak_src = measured_peaks()
+    taus = [ens.params(k)["tau_nu"] for k in range(len(cav))]
+    ens.close()
+
+    # the same cavities as separate handles, stepped one after another
+    singles = [dmrt.Cavity(c["grid"], c["Ra"], wall_type=c["wall"], storage=storage, streaming=streaming)
+               for c in cav]
+    for h in singles:
+        dmrt.dmrt_set_stream(h.h, stream)
+        h.step(inner)
+        h.nusselt(0)
+    sep_steps = max(2, steps // 4)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(sep_steps):
+        for h in singles:
+            h.step(inner)
+            h.nusselt(0)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    sep_secs = reduce_max(dist, ev0.elapsed_time(ev1) / 1e3, device)
+    separate = aggregate(cells * inner * sep_steps, world, sep_secs)
+    for h in singles:
+        h.close()
+    names = {v: k for k, v in STORAGES.items()}
+    return {
+        "value": value, "unit": "MLUPS", "steps": steps, "warmup": warmup, "ms_per_step": secs / steps * 1e3,
+        "workload": f"ensemble of {len(cav)} seeded cavities (edge in 32/48/64/96, log10 Ra in [3, 6], "
+                    f"types 1-3, seed {seed}), {names[storage]} storage"
+                    + ("" if streaming == 0 else ", in-place streaming")
+                    + f"; one step = {inner} LBM steps of all members + residuals + hot-wall Nu of all",
+        "cells": cells, "min_tau_nu": min(taus), "autotune": report,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
+                     "nominal_peak": NOMINAL_HBM_GBS, "frac_nominal": achieved / NOMINAL_HBM_GBS,
+                     "kernel": ens_kernel, "bytes_per_cell": stats["bytes_per_cell"],
+                     "launch_us": launch_s * 1e6},
+        "separate_runs": {"value": separate, "unit": "MLUPS",
+                          "what": f"the same {len(cav)} cavities as separate handles, stepped one after another"},
+        "gpu_launches": stats["total_launches"], "clocks": clocks.summary(),
+    }
+
+
+def measure_cavity(dmrt, torch, stream, gpu, *, grid, wall, ra, storage, inner, steps, warmup):
+    """One cavity from rest: `steps` benchmark steps of `inner` LBM steps,
+    a residual and a hot-wall Nu each, timed with CUDA events on `stream`;
+    the step kernels' own events give the roofline."""
+    cav = dmrt.Cavity(grid, ra, PR, MA, wall, storage=storage)
+    dmrt.dmrt_set_stream(cav.h, stream)
+    for _ in range(warmup):
+        cav.step(inner)
+        cav.nusselt(0)
+    dmrt.dmrt_get_stats(cav.h, reset=True)
+    dmrt.dmrt_set_timing(cav.h, True)
+    torch.cuda.synchronize()
+    with ClockSampler(gpu) as clocks:
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(steps):
+            dmrt.dmrt_step(cav.h, inner)
+            dmrt.dmrt_nusselt(cav.h, 0)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    secs = ev0.elapsed_time(ev1) / 1e3
+    stats = dmrt.dmrt_get_stats(cav.h, reset=True)
+    cells = grid[0] * grid[1] * grid[2]
+    launch_s = stats["step_ms"] / 1e3 / max(stats["timed_steps"], 1)
+    achieved = stats["bytes_per_cell"] * cells / launch_s / 1e9
+    peak, peak_src = measured_peaks()
+    params = cav.params
+    cav.close()
+    names = {v: k for k, v in STORAGES.items()}
+    kernel = "step_pair_kernel" if params["cells_per_thread"] == 2 else "step_kernel"
+    return {
+        "value": cells * inner * steps / secs / 1e6, "unit": "MLUPS", "steps": steps, "warmup": warmup,
+        "ms_per_step": secs / steps * 1e3,
+        "workload": f"{grid[0]}^3 cavity, {WALL_NAMES[wall]}, Ra={ra:g}, Pr={PR}, Ma={MA}, from rest, "
+                    f"{names[storage]} population storage" + ("" if storage == 0 else ", stochastic rounding")
+                    + f"; one step = {inner} fused LBM steps + residual + hot-wall Nu",
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
+                     "nominal_peak": NOMINAL_HBM_GBS, "frac_nominal": achieved / NOMINAL_HBM_GBS,
+                     "kernel": f"{kernel}<{wall}, {names[storage]}>", "bytes_per_cell": stats["bytes_per_cell"],
+                     "launch_us": launch_s * 1e6},
+        "gpu_launches": stats["total_launches"], "clocks": clocks.summary(),
+    }
+
+
+def run_configs(dmrt, torch, stream, gpu, steps=5, warmup=3):
+    """Outside the timed region: short CUDA-event-timed measurements of the
+    reduced-storage 256^3 cavity (Type 3, Ra = 1e6, BF16 and FP16) and of the
+    64-member seeded ensemble (FP32 and BF16, against the same cavities as
+    separate handles), each with its own clock samples."""
+    from paper_1511_04633_gb300 import inputs
+
+    out = {}
+    for name in ("bf16", "f16"):
+        out[f"256cube_type3_ra1e6_{name}"] = measure_cavity(
+            dmrt, torch, stream, gpu, grid=(256,) * 3, wall=3, ra=1e6, storage=STORAGES[name],
+            inner=LBM_STEPS_PER_STEP, steps=steps, warmup=warmup)
+    for name in ("f32", "bf16"):
+        out[f"ensemble64_{name}"] = measure_ensemble(
+            dmrt, inputs, torch, stream, gpu, members=64, seed=1234, storage=STORAGES[name], streaming=0,
+            inner=LBM_STEPS_PER_STEP, steps=steps, warmup=warmup)
+    return out
+
+
 def run_ensemble(args, rank, local, world):
-    """The batched ensemble of seeded cavities: one launch per time step over
-    all of them, against the same cavities as separate handles run one after
-    another."""
+    """The batched ensemble of seeded cavities as the benchmark line."""
     import torch
     from paper_1511_04633_gb300 import dmrt, inputs
 
@@ -460,89 +653,20 @@ def run_ensemble(args, rank, local, world):
     device = torch.device("cuda", local)
     stream = torch.cuda.Stream(device)
     torch.cuda.set_stream(stream)
-    draws = inputs.ensemble_draws(args.members, seed=args.seed)
-    cav = [{"grid": (d["n"],) * 3, "Ra": d["Ra"], "wall": d["wall"]} for d in draws]
-    storage = STORAGES[args.storage]
-    streaming = STREAMINGS[args.streaming]
-    ens = dmrt.Ensemble(cav, storage=storage, streaming=streaming)
-    ens_kernel = ("ensemble_pair_kernel" if ens.params(0)["cells_per_thread"] == 2
-                  else "ensemble_step_kernel") + (" (in place, both phases)" if streaming else "")
-    dmrt.dmrt_ensemble_set_stream(ens.e, stream)
-    report = ens.autotune(trials=3)
-    cells = ens.cells
-    inner = args.inner
-
-    def one_step():
-        ens.step(inner)
-        return ens.nusselt(0)
-
-    for _ in range(args.warmup):
-        one_step()
-    dmrt.dmrt_ensemble_get_stats(ens.e, reset=True)
-    dmrt.dmrt_ensemble_set_timing(ens.e, True)
-    barrier(dist)
-    torch.cuda.synchronize()
-    with ClockSampler(local) as clocks:
-        ev0 = torch.cuda.Event(enable_timing=True)
-        ev1 = torch.cuda.Event(enable_timing=True)
-        ev0.record(stream)
-        for _ in range(args.steps):
-            one_step()
-        ev1.record(stream)
-        torch.cuda.synchronize()
-    barrier(dist)
-    secs = reduce_max(dist, ev0.elapsed_time(ev1) / 1e3, device)
-    stats = dmrt.dmrt_ensemble_get_stats(ens.e, reset=True)
-    value = aggregate(cells * inner * args.steps, world, secs)
-    launch_s = stats["step_ms"] / 1e3 / max(stats["timed_steps"], 1)
-    achieved = stats["bytes_per_cell"] * cells / launch_s / 1e9
-    peak, peak_src = measured_peaks()
-    taus = [ens.params(k)["tau_nu"] for k in range(len(cav))]
-    ens.close()
-
-    # the same cavities as 64 separate handles, stepped one after another
-    singles = [dmrt.Cavity(c["grid"], c["Ra"], wall_type=c["wall"], storage=storage, streaming=streaming)
-               for c in cav]
-    for s in singles:
-        dmrt.dmrt_set_stream(s.h, stream)
-        s.step(inner)
-        s.nusselt(0)
-    sep_steps = max(2, args.steps // 4)
-    torch.cuda.synchronize()
-    ev0.record(stream)
-    for _ in range(sep_steps):
-        for s in singles:
-            s.step(inner)
-            s.nusselt(0)
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    sep_secs = reduce_max(dist, ev0.elapsed_time(ev1) / 1e3, device)
-    separate = aggregate(cells * inner * sep_steps, world, sep_secs)
-    for s in singles:
-        s.close()
+    m = measure_ensemble(dmrt, inputs, torch, stream, local, members=args.members, seed=args.seed,
+                         storage=STORAGES[args.storage], streaming=STREAMINGS[args.streaming],
+                         inner=args.inner, steps=args.steps, warmup=args.warmup, dist=dist, device=device,
+                         world=world)
     if rank == 0:
         line = {
-            "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
+            "metric": METRIC, "value": m["value"], "unit": "MLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": m["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": f"ensemble of {len(cav)} seeded cavities (edge in 32/48/64/96, "
-                                   f"log10 Ra in [3, 6], types 1-3, seed {args.seed}), "
-                                   f"{args.storage} storage"
-                                   + ("" if args.streaming == "ab" else ", in-place streaming")
-                                   + f"; one step = {inner} LBM steps of all "
-                                   f"members + residuals + hot-wall Nu of all",
-                       "cells": cells, "min_tau_nu": min(taus), "autotune": report,
-                       "parallelism": f"replicas x{world}"},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
-                         "nominal_peak": NOMINAL_HBM_GBS, "frac_nominal": achieved / NOMINAL_HBM_GBS,
-                         "kernel": ens_kernel, "bytes_per_cell": stats["bytes_per_cell"],
-                         "launch_us": launch_s * 1e6},
-            "separate_runs": {"value": separate, "unit": "MLUPS",
-                              "what": f"the same {len(cav)} cavities as separate handles, "
-                                      f"stepped one after another"},
-            "gpu_launches": stats["total_launches"], "clocks": clocks.summary(),
+            "config": {"workload": m["workload"], "cells": m["cells"], "min_tau_nu": m["min_tau_nu"],
+                       "autotune": m["autotune"], "parallelism": f"replicas x{world}"},
+            "roofline": m["roofline"], "separate_runs": m["separate_runs"],
+            "gpu_launches": m["gpu_launches"], "clocks": m["clocks"],
         }
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -578,6 +702,11 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-steady", action="store_true",
                     help="skip the run to steady state after the timed region")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the 256^3 16-bit and 64-member ensemble measurements after the timed region")
+    ap.add_argument("--warm-start-cases", type=int, default=3,
+                    help="held-out 128^3 cavities of the learned warm start measured after the timed "
+                         "region (0: none)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

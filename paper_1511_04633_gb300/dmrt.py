@@ -777,6 +777,7 @@ class Surrogate:
     def __init__(self, grid=64, depth=3, channels=(16, 32, 64, 128), storage=STORE_BF16, max_batch=1,
                  seed=1):
         self.grid, self.depth, self.channels = grid, depth, tuple(channels)
+        self.storage = storage
         self.max_batch = max_batch
         self.s = dmrt_surrogate_create(grid, depth, channels, storage, max_batch, seed)
 

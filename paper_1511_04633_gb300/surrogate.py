@@ -15,8 +15,13 @@ cavity's (Ra, wall type) to an approximate steady state.  This module
 Orchestration only: every arithmetic step runs in the library's kernels;
 torch provides device memory.
 
+The trained parameters ship with the package (``weights/``); this module
+writes them (``--save-params``) and reads them back (``load_surrogate``).
+
     python -m paper_1511_04633_gb300.surrogate --grid 32 --train 48 --epochs 30
     python -m paper_1511_04633_gb300.surrogate --time-steps 3     # time the training step
+    python -m paper_1511_04633_gb300.surrogate --test 0 --epochs 60 \
+        --save-params paper_1511_04633_gb300/weights/warm_start_64cube.npz
 """
 
 from __future__ import annotations
@@ -24,11 +29,87 @@ from __future__ import annotations
 import argparse
 import json
 import math
+import os
 import time
 
 import numpy as np
 
 from . import dmrt, inputs
+
+WEIGHTS_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights")
+# the network trained on 512 steady states of 64^3 cavities (log10 Ra in [3, 6],
+# wall types 1-3, draws of seed 2024), written by main() with --save-params
+DEFAULT_PARAMS = os.path.join(WEIGHTS_DIR, "warm_start_64cube.npz")
+# the seeded draws of that training run: the first 512 trained it, the rest
+# are held out
+TRAIN_SEED, TRAIN_COUNT = 2024, 512
+
+
+def held_out_draws(count, grid=64):
+    """The cavities (Ra, wall) of the training run's seeded draws that it
+    did not train on."""
+    draws = inputs.ensemble_draws(TRAIN_COUNT + count, seed=TRAIN_SEED, edges=(grid,), log10_ra=(3.0, 6.0))
+    return draws[TRAIN_COUNT:]
+
+
+def _to_bf16_bits(p):
+    """float32 -> bfloat16 bit patterns, rounded to nearest even (the
+    conversion the BF16 network applies to its master weights)."""
+    b = np.ascontiguousarray(p, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    return ((b + 0x7FFF + ((b >> 16) & 1)) >> 16).astype(np.uint16)
+
+
+def bias_mask(depth, channels, features=8, out=5):
+    """Which entries of the flat parameter vector are biases, from the
+    layout include/dmrt.h states: layer by layer (a_0, s_0, then a_l, s_l
+    for l = 1..D, then d_l, h_l for l = D-1..0, then the 1x1 head), each
+    layer's weights [tap][cout][cin] followed by its cout biases."""
+    c = list(channels)[:depth + 1]
+    layers = [(features, c[0], 27), (c[0], c[0], 27)]
+    for l in range(1, depth + 1):
+        layers += [(c[l - 1], c[l], 27), (c[l], c[l], 27)]
+    for l in range(depth - 1, -1, -1):
+        layers += [(c[l + 1], c[l], 27), (c[l], c[l], 27)]
+    layers.append((c[0], out, 1))
+    mask = []
+    for cin, cout, taps in layers:
+        mask += [False] * (taps * cout * cin) + [True] * cout
+    return np.array(mask)
+
+
+def save_params(sur, path, info=None):
+    """Write a BF16 network's configuration and parameters.  The BF16
+    network multiplies with its weights rounded to bfloat16 and adds its
+    biases in FP32, so the file holds the weights rounded the same way and
+    the biases as they are (about half the bytes of FP32): a network loaded
+    from it predicts exactly what the saved one did."""
+    if sur.storage != dmrt.STORE_BF16:
+        raise ValueError("save_params stores the weights of a BF16 network")
+    p = sur.params()
+    mask = bias_mask(sur.depth, sur.channels)
+    if mask.size != p.size:
+        raise ValueError(f"layout of {mask.size} parameters for a network of {p.size}")
+    os.makedirs(os.path.dirname(os.path.abspath(path)), exist_ok=True)
+    np.savez_compressed(path, weights_bf16=_to_bf16_bits(p[~mask]), biases=p[mask].astype(np.float32),
+                        grid=sur.grid, depth=sur.depth, channels=np.array(sur.channels),
+                        info=json.dumps(info or {}))
+
+
+def load_surrogate(path=DEFAULT_PARAMS, max_batch=1):
+    """A BF16 surrogate with the parameters of a file written by save_params.
+    Returns (surrogate, info dict)."""
+    with np.load(path) as z:
+        depth, channels = int(z["depth"]), tuple(int(c) for c in z["channels"])
+        sur = dmrt.Surrogate(int(z["grid"]), depth, channels, dmrt.STORE_BF16, max_batch=max_batch)
+        mask = bias_mask(depth, channels)
+        if mask.size != sur.param_count:
+            raise ValueError(f"{path}: layout of {mask.size} parameters for a network of {sur.param_count}")
+        p = np.empty(mask.size, np.float32)
+        p[~mask] = (z["weights_bf16"].astype(np.uint32) << 16).view(np.float32)
+        p[mask] = z["biases"]
+        sur.set_params(p)
+        info = json.loads(str(z["info"]))
+    return sur, info
 
 
 def steady_dataset(n, draws, tol=1e-6, max_steps=200_000, group=64, storage=dmrt.STORE_F32):
@@ -221,6 +302,8 @@ def main(argv=None):
     ap.add_argument("--max-steps", type=int, default=200_000)
     ap.add_argument("--seed", type=int, default=2024)
     ap.add_argument("--out", type=str, default="")
+    ap.add_argument("--save-params", type=str, default="",
+                    help="write the trained parameters (BF16 network) to this .npz file")
     ap.add_argument("--time-steps", type=int, default=0,
                     help="only time this many training steps (zero targets) and predictions")
     args = ap.parse_args(argv)
@@ -250,6 +333,17 @@ def main(argv=None):
     if not math.isfinite(hist[-1]) or len(hist) < args.epochs:
         print(json.dumps({"error": "training diverged", "history": hist}), flush=True)
         return results
+    if args.save_params:
+        info = {"grid": args.grid, "depth": args.depth, "channels": ch, "train": args.train,
+                "seed": args.seed, "log10_ra": [lo, hi], "epochs": args.epochs, "batch": args.batch,
+                "lr": args.lr, "data_tol": args.data_tol, "loss_first": hist[0], "loss_last": hist[-1],
+                "dataset_seconds": info["seconds"], "train_seconds": t_train}
+        save_params(sur, args.save_params, info)
+        loaded, _ = load_surrogate(args.save_params)
+        probe_ra, probe_wall = [float(train_draws[0]["Ra"])], [int(train_draws[0]["wall"])]
+        same = np.array_equal(loaded.predict(probe_ra, probe_wall), sur.predict(probe_ra, probe_wall))
+        print(json.dumps({"saved": args.save_params, "reloaded_predicts_the_same": bool(same)}), flush=True)
+        loaded.close()
     for d in test_draws:
         r = compare_warm_start(sur, args.target_grid, d["Ra"], d["wall"], max_steps=args.max_steps * 8)
         results["cases"].append(r)

@@ -35,7 +35,7 @@ def _run(*args):
 @pytest.mark.parametrize("streaming", ["ab", "inplace"])
 def test_bench_line_has_the_contract_keys(torch, streaming):
     d = _run("--steps", "3", "--warmup", "3", "--inner", "20", "--grid", "64", "--no-cpu-baseline",
-             "--no-steady", "--streaming", streaming)
+             "--no-steady", "--warm-start-cases", "0", "--no-configs", "--streaming", streaming)
     for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
               "scaling", "vs_baseline", "dtype", "data", "config", "roofline", "e2e", "gpu_launches", "clocks"):
         assert k in d, k
