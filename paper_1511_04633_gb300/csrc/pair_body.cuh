@@ -249,6 +249,24 @@ __device__ __forceinline__ unsigned opaque(unsigned v)
     return r;
 }
 
+// A collision sink (collide_from) that hands each post-collision value of
+// plane q (0..18 flow, 19..25 energy) to store(std::integral_constant<int,
+// q>, value) as soon as it is final.
+template <typename F>
+struct PlaneSink {
+    F store;
+    template <int I>
+    __device__ __forceinline__ void put_f(F2 v) const { store(std::integral_constant<int, I>{}, v); }
+    template <int I>
+    __device__ __forceinline__ void put_g(F2 v) const { store(std::integral_constant<int, 19 + I>{}, v); }
+};
+
+template <typename F>
+__device__ __forceinline__ PlaneSink<F> plane_sink(F f)
+{
+    return PlaneSink<F>{f};
+}
+
 // Value of plane q (0..25) of a collided pair.
 template <int Q>
 __device__ __forceinline__ F2 plane_value(const F2 d[19], const F2 g[7])

@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(256, DMRT_STEP_MIN_BLOCKS)
         const Conserved<float> m0 = conserved<float>(d, g);
         // the fields a residual point compares, used after the stores
         const float th = m0.Tu, ux = m0.vx, uy = m0.vy, uz = m0.vz;
-        collide_from<float>(C, d, g, m0);
+        collide_from<float, 0>(C, d, g, m0, InPlace<float>{d, g});
         unsigned base = 0;
         if constexpr (SR) {
             const size_t counter_at = static_cast<size_t>(kPlanes) * S.plane;

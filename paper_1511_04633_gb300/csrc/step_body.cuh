@@ -84,6 +84,20 @@ __device__ __forceinline__ Conserved<V> conserved(const V d[19], const V g[7])
                         tsx, tax, tsy, tay, tsz, taz, tsm, T, Tu, rho, ir, vx, vy, vz};
 }
 
+// Where collide_from puts each post-collision value: put_f<i>(v) for the 19
+// flow populations, put_g<i>(v) for the 7 energy populations, each as soon as
+// it is final (the energy populations first), so a sink that stores them
+// lets their registers go at once.  InPlace writes them back over the pulled
+// values.
+template <typename V>
+struct InPlace {
+    V *d, *g;
+    template <int I>
+    __device__ __forceinline__ void put_f(V v) const { d[I] = v; }
+    template <int I>
+    __device__ __forceinline__ void put_g(V v) const { g[I] = v; }
+};
+
 // Collision of one cell (V = float) or of two cells at once (V = F2), in
 // place: d holds f - w, g the energy populations (pulled); on return both
 // hold the post-collision values of Eqs. (14), (29).  Both forms give the same
@@ -103,8 +117,9 @@ __device__ __forceinline__ Conserved<V> conserved(const V d[19], const V g[7])
 // or one multiply; the force terms take S in their constant factors.
 // Multiplying by a power of two commutes with rounding, so every value is
 // exactly S times its value at kShift = 0.
-template <typename V, int kShift = 0>
-__device__ __forceinline__ void collide_from(const CollideParams &C, V d[19], V g[7], const Conserved<V> &m0)
+template <typename V, int kShift, typename Sink>
+__device__ __forceinline__ void collide_from(const CollideParams &C, const V d[19], const V g[7],
+                                             const Conserved<V> &m0, Sink out)
 {
     constexpr bool kScaled = kShift != 0;
     constexpr float kS = static_cast<float>(1u << kShift), kU = 1.0f / kS;
@@ -125,6 +140,43 @@ __device__ __forceinline__ void collide_from(const CollideParams &C, V d[19], V 
         if constexpr (kScaled) return p * V(kU);
         else return p;
     };
+
+    // ---- energy: n - n^eq with n^eq = (T, V T, 3/4 T, 0, 0) (Eqs. (33),(34)).
+    // The flux parts e = (ta - V T) relax with Q's flux block; with
+    // T = g0 + tsm the even parts are t4 = q4 (21/4 g0 - 7/4 tsm),
+    // t5 = q5 (3 tsx - tsm), t6 = q6 (tsy - tsz) (rates divided by the norms),
+    // and the back-transform subtracts, per pair, an even part (2 t5 - t4 for
+    // x, t6 - t4 - t5 for y, -(t4 + t5 + t6) for z) and +-the relaxed flux.
+    const V nT = T * V(-1.0f);
+    const V e1 = fma(vx, nT, tax), e2 = fma(vy, nT, tay), e3 = fma(vz, nT, taz);
+    const V u4 = fma(V(5.25f), g[0], V(-1.75f) * tsm);
+    const V u5 = fma(V(3.0f), tsx, tsm * V(-1.0f));
+    const V u6 = tsy - tsz;
+    const V t4 = V(C.rq[4]) * u4, nt4 = V(-C.rq[4]) * u4;
+    out.template put_g<0>(fma(V(-6.0f), t4, g[0]));
+    const V Etx = fma(V(2.0f * C.rq[5]), u5, nt4);     // 2 t5 - t4
+    const V t45 = fma(V(C.rq[5]), u5, t4);             // t4 + t5
+    const V nt45 = fma(V(-C.rq[5]), u5, nt4);          // -(t4 + t5)
+    const V Ety = fma(V(C.rq[6]), u6, nt45);           // t6 - t4 - t5
+    const V P = fma(V(C.rq[6]), u6, t45);              // t4 + t5 + t6
+    if (C.aniso) {  // uniform: the full flux block of Q (Eq. (35))
+        const V t1 = fma(V(C.qa[0]), e1, fma(V(C.qa[1]), e2, V(C.qa[2]) * e3));
+        const V t2 = fma(V(C.qa[3]), e1, fma(V(C.qa[4]), e2, V(C.qa[5]) * e3));
+        const V t3 = fma(V(C.qa[6]), e1, fma(V(C.qa[7]), e2, V(C.qa[8]) * e3));
+        out.template put_g<1>((g[1] - Etx) - t1);
+        out.template put_g<2>((g[2] - Etx) + t1);
+        out.template put_g<3>((g[3] - Ety) - t2);
+        out.template put_g<4>((g[4] - Ety) + t2);
+        out.template put_g<5>((g[5] + P) - t3);
+        out.template put_g<6>((g[6] + P) + t3);
+    } else {
+        out.template put_g<1>(fma(V(-C.rq[1]), e1, g[1] - Etx));
+        out.template put_g<2>(fma(V(C.rq[1]), e1, g[2] - Etx));
+        out.template put_g<3>(fma(V(-C.rq[2]), e2, g[3] - Ety));
+        out.template put_g<4>(fma(V(C.rq[2]), e2, g[4] - Ety));
+        out.template put_g<5>(fma(V(-C.rq[3]), e3, g[5] + P));
+        out.template put_g<6>(fma(V(C.rq[3]), e3, g[6] + P));
+    }
 
     // ---- moments m_k of the deviations (Eqs. (21), (22)): the moments of w
     // are the rest equilibrium moments and cancel against those of m^eq.
@@ -206,7 +258,7 @@ __device__ __forceinline__ void collide_from(const CollideParams &C, V d[19], V 
     // ---- back-transform f* = M^T c (M^-1 = M^T diag(1/|M_k|^2)), one even (E)
     // and one odd (O) partial sum per pair: f*_i = E + O, f*_opp = E - O.
     // c0 = drho/19, c3 = jx/10, c5 = jy/10, c7 = (jz + g)/10 enter through fma.
-    d[0] = fma(V(-30.0f), c1, fma(V(12.0f), c2, drho * V(1.0f / 19.0f)));
+    out.template put_f<0>(fma(V(-30.0f), c1, fma(V(12.0f), c2, drho * V(1.0f / 19.0f))));
     const V Fc = fma(V(-11.0f), c1, fma(V(-4.0f), c2, drho * V(1.0f / 19.0f)));  // every face
     const V Gc = fma(V(8.0f), c1, fma(drho, V(1.0f / 19.0f), c2));                // every edge
     const V Efx = fma(V(2.0f), c9, fma(V(-4.0f), c10, Fc));
@@ -219,12 +271,12 @@ __device__ __forceinline__ void collide_from(const CollideParams &C, V d[19], V 
     const V Ofx = fma(V(-4.0f), c4, jx * V(0.1f));
     const V Ofy = fma(V(-4.0f), c6, jy * V(0.1f));
     const V Ofz = fma(V(-4.0f), c8, jzg * V(0.1f));
-    d[1] = Efx + Ofx;
-    d[2] = Efx - Ofx;
-    d[3] = Efy + Ofy;
-    d[4] = Efy - Ofy;
-    d[5] = Efz + Ofz;
-    d[6] = Efz - Ofz;
+    out.template put_f<1>(Efx + Ofx);
+    out.template put_f<2>(Efx - Ofx);
+    out.template put_f<3>(Efy + Ofy);
+    out.template put_f<4>(Efy - Ofy);
+    out.template put_f<5>(Efz + Ofz);
+    out.template put_f<6>(Efz - Ofz);
 
     const V H = c9 + c10, K = c11 + c12;
     const V GH = Gc + H;
@@ -236,62 +288,27 @@ __device__ __forceinline__ void collide_from(const CollideParams &C, V d[19], V 
     const V E12 = Exz - c15, O12 = (cz - cx) + (c16 + c18);      // (-1,0,1)
     const V E15 = Eyz + c14, O15 = (cy + cz) + (c17 - c18);      // (0,1,1)
     const V E16 = Eyz - c14, O16 = (cz - cy) - (c17 + c18);      // (0,-1,1)
-    d[7] = E7 + O7;
-    d[10] = E7 - O7;
-    d[8] = E8 + O8;
-    d[9] = E8 - O8;
-    d[11] = E11 + O11;
-    d[14] = E11 - O11;
-    d[12] = E12 + O12;
-    d[13] = E12 - O12;
-    d[15] = E15 + O15;
-    d[18] = E15 - O15;
-    d[16] = E16 + O16;
-    d[17] = E16 - O16;
+    out.template put_f<7>(E7 + O7);
+    out.template put_f<10>(E7 - O7);
+    out.template put_f<8>(E8 + O8);
+    out.template put_f<9>(E8 - O8);
+    out.template put_f<11>(E11 + O11);
+    out.template put_f<14>(E11 - O11);
+    out.template put_f<12>(E12 + O12);
+    out.template put_f<13>(E12 - O12);
+    out.template put_f<15>(E15 + O15);
+    out.template put_f<18>(E15 - O15);
+    out.template put_f<16>(E16 + O16);
+    out.template put_f<17>(E16 - O16);
 
-    // ---- energy: n - n^eq with n^eq = (T, V T, 3/4 T, 0, 0) (Eqs. (33),(34)).
-    // The flux parts e = (ta - V T) relax with Q's flux block; with
-    // T = g0 + tsm the even parts are t4 = q4 (21/4 g0 - 7/4 tsm),
-    // t5 = q5 (3 tsx - tsm), t6 = q6 (tsy - tsz) (rates divided by the norms),
-    // and the back-transform subtracts, per pair, an even part (2 t5 - t4 for
-    // x, t6 - t4 - t5 for y, -(t4 + t5 + t6) for z) and +-the relaxed flux.
-    const V nT = T * V(-1.0f);
-    const V e1 = fma(vx, nT, tax), e2 = fma(vy, nT, tay), e3 = fma(vz, nT, taz);
-    const V u4 = fma(V(5.25f), g[0], V(-1.75f) * tsm);
-    const V u5 = fma(V(3.0f), tsx, tsm * V(-1.0f));
-    const V u6 = tsy - tsz;
-    const V t4 = V(C.rq[4]) * u4, nt4 = V(-C.rq[4]) * u4;
-    g[0] = fma(V(-6.0f), t4, g[0]);
-    const V Etx = fma(V(2.0f * C.rq[5]), u5, nt4);     // 2 t5 - t4
-    const V t45 = fma(V(C.rq[5]), u5, t4);             // t4 + t5
-    const V nt45 = fma(V(-C.rq[5]), u5, nt4);          // -(t4 + t5)
-    const V Ety = fma(V(C.rq[6]), u6, nt45);           // t6 - t4 - t5
-    const V P = fma(V(C.rq[6]), u6, t45);              // t4 + t5 + t6
-    if (C.aniso) {  // uniform: the full flux block of Q (Eq. (35))
-        const V t1 = fma(V(C.qa[0]), e1, fma(V(C.qa[1]), e2, V(C.qa[2]) * e3));
-        const V t2 = fma(V(C.qa[3]), e1, fma(V(C.qa[4]), e2, V(C.qa[5]) * e3));
-        const V t3 = fma(V(C.qa[6]), e1, fma(V(C.qa[7]), e2, V(C.qa[8]) * e3));
-        g[1] = (g[1] - Etx) - t1;
-        g[2] = (g[2] - Etx) + t1;
-        g[3] = (g[3] - Ety) - t2;
-        g[4] = (g[4] - Ety) + t2;
-        g[5] = (g[5] + P) - t3;
-        g[6] = (g[6] + P) + t3;
-    } else {
-        g[1] = fma(V(-C.rq[1]), e1, g[1] - Etx);
-        g[2] = fma(V(C.rq[1]), e1, g[2] - Etx);
-        g[3] = fma(V(-C.rq[2]), e2, g[3] - Ety);
-        g[4] = fma(V(C.rq[2]), e2, g[4] - Ety);
-        g[5] = fma(V(-C.rq[3]), e3, g[5] + P);
-        g[6] = fma(V(C.rq[3]), e3, g[6] + P);
-    }
 }
 
-// Collision of the pulled populations d, g (see collide_from).
+// Collision of the pulled populations d, g, the results written back over
+// them (see collide_from).
 template <typename V, int kShift = 0>
 __device__ __forceinline__ void collide(const CollideParams &C, V d[19], V g[7])
 {
-    collide_from<V, kShift>(C, d, g, conserved<V, kShift>(d, g));
+    collide_from<V, kShift>(C, d, g, conserved<V, kShift>(d, g), InPlace<V>{d, g});
 }
 
 // One cell per thread: the float form of collide().

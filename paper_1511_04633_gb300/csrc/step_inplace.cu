@@ -112,7 +112,7 @@ __global__ void DMRT_INPLACE_BOUNDS(PHASE, T)
         const Conserved<float> m0 = conserved<float>(d, g);
         // the fields a residual point compares, used after the stores
         const float th = m0.Tu, ux = m0.vx, uy = m0.vy, uz = m0.vz;
-        collide_from<float>(C, d, g, m0);
+        collide_from<float, 0>(C, d, g, m0, InPlace<float>{d, g});
         unsigned base = 0;
         if constexpr (SR) {
             unsigned *ctr = reinterpret_cast<unsigned *>(A + static_cast<size_t>(kPlanes) * S.plane);

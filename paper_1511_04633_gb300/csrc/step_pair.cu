@@ -102,8 +102,6 @@ __global__ void __launch_bounds__(kPairThreads, RES ? kPairBlocksRes : kPairBloc
         pull_pair<WALL, T>(src + c.self, TableOffsets{S}, c.faces, c.th_lin, d, g);
         const Conserved<F2> m0 = conserved<F2, Pair<T>::kShift>(d, g);
         const PairFields fl{m0.Tu, m0.vx, m0.vy, m0.vz};
-        collide_from<F2, Pair<T>::kShift>(C, d, g, m0);
-        // every plane of the pair: one 2-element store at the cells' own slots
         unsigned r01 = 0;
         if constexpr (SR) {
             const size_t counter_at = static_cast<size_t>(kPlanes) * S.plane;
@@ -111,12 +109,14 @@ __global__ void __launch_bounds__(kPairThreads, RES ? kPairBlocksRes : kPairBloc
             if (c.self == 0) *reinterpret_cast<unsigned *>(dst + counter_at) = step + 1u;
             r01 = pair_bits(c.self, step);
         }
+        // every plane of the pair: one 2-element store at the cells' own
+        // slots, as soon as the collision has its value
         T *Dp = dst + c.self;
         const unsigned plane = opaque(S.plane);
-        static_for<0, 26>([&](auto I) {
+        collide_from<F2, Pair<T>::kShift>(C, d, g, m0, plane_sink([&](auto I, F2 v) {
             constexpr int q = decltype(I)::value;
-            store2<T, SR>(Dp + q * plane, plane_value<q>(d, g), SR ? plane_bits<q>(r01) : 0u);
-        });
+            store2<T, SR>(Dp + q * plane, v, SR ? plane_bits<q>(r01) : 0u);
+        }));
         if constexpr (RES) residual_pair(R, c.self, prev, fl.th.v, fl.ux.v, fl.uy.v, fl.uz.v, acc);
     }
     if constexpr (RES) residual_block_store(acc, R.partials);
@@ -146,7 +146,6 @@ __global__ void __launch_bounds__(kPairThreads, RES ? kPairBlocksRes : kPairBloc
         else pull_pair<WALL, T>(A + c.self, LocalOffsets{S.plane}, c.faces, c.th_lin, d, g);
         const Conserved<F2> m0 = conserved<F2, Pair<T>::kShift>(d, g);
         const PairFields fl{m0.Tu, m0.vx, m0.vy, m0.vz};
-        collide_from<F2, Pair<T>::kShift>(C, d, g, m0);
         unsigned r01 = 0;
         if constexpr (SR) {
             unsigned *ctr = reinterpret_cast<unsigned *>(A + static_cast<size_t>(kPlanes) * S.plane);
@@ -157,9 +156,8 @@ __global__ void __launch_bounds__(kPairThreads, RES ? kPairBlocksRes : kPairBloc
         T *Dp = A + c.self;
         const PairFaces &P = c.faces;
         const unsigned plane = opaque(S.plane);
-        static_for<0, 26>([&](auto I) {
+        collide_from<F2, Pair<T>::kShift>(C, d, g, m0, plane_sink([&](auto I, F2 v) {
             constexpr int q = decltype(I)::value;
-            const F2 v = plane_value<q>(d, g);
             const unsigned r = SR ? plane_bits<q>(r01) : 0u;
             if constexpr (PHASE == 1) {
                 store2<T, SR>(Dp + plane_opp<q>() * plane, v, r);
@@ -179,7 +177,7 @@ __global__ void __launch_bounds__(kPairThreads, RES ? kPairBlocksRes : kPairBloc
                     store_split<T, SR>(Dp + (l0 ? sb : sn), (Dp + (l1 ? sb : sn)) + 1, v, r);
                 }
             }
-        });
+        }));
         if constexpr (RES) residual_pair(R, c.self, prev, fl.th.v, fl.ux.v, fl.uy.v, fl.uz.v, acc);
     }
     if constexpr (RES) residual_block_store(acc, R.partials);
