@@ -228,6 +228,31 @@ __device__ __forceinline__ PairFaces pair_faces(const CavityDesc &D, int x0, int
     return PairFaces{x0 == 0, x0 + 2 == D.nx, y == 0, y == D.ny - 1, z == 0, z == D.nz - 1};
 }
 
+// One pair of a member: pull (the wall type, which only sets the thermal
+// rule of the x and z walls, is a runtime value: taken at compile time per
+// block, the three bodies spilled 300-400 bytes), collide, and store each
+// plane as soon as the collision has its value.
+template <typename T, bool SR>
+__device__ __forceinline__ void ensemble_pair_body(const T *__restrict__ src, T *__restrict__ dst,
+                                                   const CavityDesc &D, int x0, int y, int z, unsigned salt)
+{
+    const unsigned self = (static_cast<unsigned>(z) * D.ny + y) * D.nx + x0;
+    F2 d[19], g[7];
+    pull_pair<kRuntimeWall, T>(src + self, ComputedOffsets{D.plane, static_cast<unsigned>(D.nx), D.nxy},
+                               pair_faces(D, x0, y, z), theta_linear(y, D.inv_ny), d, g, D.wall != 1,
+                               D.wall == 2);
+    const unsigned r01 = SR ? pair_bits_salted(self, salt) : 0u;
+    // re-read the plane stride after a compiler barrier (see ensemble_cell)
+    asm volatile("" ::: "memory");
+    T *Dp = dst + self;
+    const unsigned plane = D.plane;
+    collide_from<F2, Pair<T>::kShift>(D.C, d, g, conserved<F2, Pair<T>::kShift>(d, g),
+                                      plane_sink([&](auto I, F2 v) {
+                                          constexpr int q = decltype(I)::value;
+                                          store2<T, SR>(Dp + q * plane, v, SR ? plane_bits<q>(r01) : 0u);
+                                      }));
+}
+
 template <typename T, bool SR>
 __global__ void __launch_bounds__(128, kEnsPairBlocks)
     ensemble_pair_kernel(const T *__restrict__ srcb, T *__restrict__ dstb, const CavityDesc *__restrict__ descs,
@@ -245,43 +270,14 @@ __global__ void __launch_bounds__(128, kEnsPairBlocks)
     __shared__ CavityDesc D;
     int x0, y, z;
     if (!locate_pair(D, descs, blockmap, x0, y, z)) return;
-    const unsigned self = (static_cast<unsigned>(z) * D.ny + y) * D.nx + x0;
-    F2 d[19], g[7];
-    pull_pair<kRuntimeWall, T>(srcb + D.offset + self,
-                               ComputedOffsets{D.plane, static_cast<unsigned>(D.nx), D.nxy},
-                               pair_faces(D, x0, y, z), theta_linear(y, D.inv_ny), d, g, D.wall != 1,
-                               D.wall == 2);
-    collide_stored<T>(D.C, d, g);
-    // re-read the plane stride after a compiler barrier (see ensemble_cell)
-    asm volatile("" ::: "memory");
-    const unsigned r01 = SR ? pair_bits_salted(self, salt) : 0u;
-    T *Dp = dstb + D.offset + self;
-    const unsigned plane = D.plane;
-    static_for<0, 26>([&](auto I) {
-        constexpr int q = decltype(I)::value;
-        store2<T, SR>(Dp + q * plane, plane_value<q>(d, g), SR ? plane_bits<q>(r01) : 0u);
-    });
+    ensemble_pair_body<T, SR>(srcb + D.offset, dstb + D.offset, D, x0, y, z, salt);
 }
 
 // In-place scheme with two cells per thread (see step_inplace_pair_kernel).
 template <typename T, bool SR, int PHASE>
-__global__ void __launch_bounds__(128, kEnsPairBlocks)
-    ensemble_inplace_pair_kernel(T *__restrict__ buf, const CavityDesc *__restrict__ descs,
-                                 const BlockTile *__restrict__ blockmap, long long counter_at)
+__device__ __forceinline__ void ensemble_inplace_pair_body(T *__restrict__ A, const CavityDesc &D, int x0, int y,
+                                                           int z, unsigned salt)
 {
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    asm volatile("griddepcontrol.launch_dependents;");
-    unsigned salt = 0;
-    if constexpr (SR) {
-        unsigned *ctr = reinterpret_cast<unsigned *>(buf + counter_at);
-        const unsigned step = ctr[PHASE];
-        if (blockIdx.x == 0 && threadIdx.x == 0) ctr[PHASE ^ 1] = step + 1u;
-        salt = pcg_hash(step);
-    }
-    __shared__ CavityDesc D;
-    int x0, y, z;
-    if (!locate_pair(D, descs, blockmap, x0, y, z)) return;
-    T *A = buf + D.offset;
     const unsigned self = (static_cast<unsigned>(z) * D.ny + y) * D.nx + x0;
     const PairFaces P = pair_faces(D, x0, y, z);
     F2 d[19], g[7];
@@ -291,14 +287,12 @@ __global__ void __launch_bounds__(128, kEnsPairBlocks)
     else
         pull_pair<kRuntimeWall, T>(A + self, LocalOffsets{D.plane}, P, theta_linear(y, D.inv_ny), d, g,
                                    D.wall != 1, D.wall == 2);
-    collide_stored<T>(D.C, d, g);
-    asm volatile("" ::: "memory");
     const unsigned r01 = SR ? pair_bits_salted(self, salt) : 0u;
+    asm volatile("" ::: "memory");
     T *Dp = A + self;
     const SwappedOffsets SO{D.plane, static_cast<unsigned>(D.nx), D.nxy};
-    static_for<0, 26>([&](auto I) {
+    collide_from<F2, Pair<T>::kShift>(D.C, d, g, conserved<F2, Pair<T>::kShift>(d, g), plane_sink([&](auto I, F2 v) {
         constexpr int q = decltype(I)::value;
-        const F2 v = plane_value<q>(d, g);
         const unsigned r = SR ? plane_bits<q>(r01) : 0u;
         if constexpr (PHASE == 1) {
             store2<T, SR>(Dp + plane_opp<q>() * SO.plane, v, r);
@@ -318,7 +312,27 @@ __global__ void __launch_bounds__(128, kEnsPairBlocks)
                 store_split<T, SR>(Dp + (l0 ? sb : sn), (Dp + (l1 ? sb : sn)) + 1, v, r);
             }
         }
-    });
+    }));
+}
+
+template <typename T, bool SR, int PHASE>
+__global__ void __launch_bounds__(128, kEnsPairBlocks)
+    ensemble_inplace_pair_kernel(T *__restrict__ buf, const CavityDesc *__restrict__ descs,
+                                 const BlockTile *__restrict__ blockmap, long long counter_at)
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;");
+    unsigned salt = 0;
+    if constexpr (SR) {
+        unsigned *ctr = reinterpret_cast<unsigned *>(buf + counter_at);
+        const unsigned step = ctr[PHASE];
+        if (blockIdx.x == 0 && threadIdx.x == 0) ctr[PHASE ^ 1] = step + 1u;
+        salt = pcg_hash(step);
+    }
+    __shared__ CavityDesc D;
+    int x0, y, z;
+    if (!locate_pair(D, descs, blockmap, x0, y, z)) return;
+    ensemble_inplace_pair_body<T, SR, PHASE>(buf + D.offset, D, x0, y, z, salt);
 }
 
 // ---------------------------------------------------------------- residual
