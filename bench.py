@@ -609,6 +609,7 @@ def measure_cavity(dmrt, torch, stream, gpu, *, grid, wall, ra, storage, inner, 
     cav.close()
     names = {v: k for k, v in STORAGES.items()}
     kernel = "step_pair_kernel" if params["cells_per_thread"] == 2 else "step_kernel"
+    traffic = profiled_traffic(names[storage], wall, "pair" if params["cells_per_thread"] == 2 else "ab")
     return {
         "value": cells * inner * steps / secs / 1e6, "unit": "MLUPS", "steps": steps, "warmup": warmup,
         "ms_per_step": secs / steps * 1e3,
@@ -616,7 +617,7 @@ def measure_cavity(dmrt, torch, stream, gpu, *, grid, wall, ra, storage, inner, 
                     f"{names[storage]} population storage" + ("" if storage == 0 else ", stochastic rounding")
                     + f"; one step = {inner} fused LBM steps + residual + hot-wall Nu",
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
+                     "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
                      "nominal_peak": NOMINAL_HBM_GBS, "frac_nominal": achieved / NOMINAL_HBM_GBS,
                      "kernel": f"{kernel}<{wall}, {names[storage]}>", "bytes_per_cell": stats["bytes_per_cell"],
                      "launch_us": launch_s * 1e6},
