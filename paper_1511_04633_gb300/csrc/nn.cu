@@ -10,10 +10,13 @@
 // sum accumulates in FP32; gradients are FP32.  Every reduction runs in a
 // fixed order (per-block partials, then an ordered finishing pass), so the
 // training is bitwise repeatable.
+#include <cuda.h>
 #include <cuda_bf16.h>
+#include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <cstdlib>
+#include <cstring>
 #include <type_traits>
 
 #include "internal.h"
@@ -569,6 +572,25 @@ __device__ __forceinline__ void st2<__nv_bfloat16>(__nv_bfloat16 *p, float a, fl
     *reinterpret_cast<__nv_bfloat162 *>(p) = __floats2bfloat162_rn(a, b);
 }
 
+// Eight consecutive channels in one or two 16-byte stores (p 16-byte aligned).
+template <typename T>
+__device__ __forceinline__ void st8(T *p, const float *v);
+template <>
+__device__ __forceinline__ void st8<float>(float *p, const float *v)
+{
+    reinterpret_cast<float4 *>(p)[0] = make_float4(v[0], v[1], v[2], v[3]);
+    reinterpret_cast<float4 *>(p)[1] = make_float4(v[4], v[5], v[6], v[7]);
+}
+template <>
+__device__ __forceinline__ void st8<__nv_bfloat16>(__nv_bfloat16 *p, const float *v)
+{
+    uint4 u;
+    __nv_bfloat162 h[4];
+    for (int i = 0; i < 4; ++i) h[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+    memcpy(&u, h, sizeof u);
+    *reinterpret_cast<uint4 *>(p) = u;
+}
+
 // Tensor-core 3^3 convolution (implicit GEMM, mma.m16n8k16, FP32
 // accumulation) over 8 x 8 x 4 voxel tiles: a block owns one tile of one
 // sample and 8 NT output channels.  For every 16 input channels it stages
@@ -853,40 +875,70 @@ __global__ void __launch_bounds__(128, 1) conv3d_umma_kernel(const __nv_bfloat16
     if (warp == 0) umma::tmem_dealloc(tmem, kCols);
 }
 
-// The same tcgen05 convolution streamed along z for few channels (cin <= 32,
-// cout <= 32): a CTA keeps the weights of all taps and a ring of four halo
-// planes (10 x 18 voxels, all input channels) resident and walks a run of
-// z-planes of its 8 x 16 tile.  The MMAs of plane z go to one of two TMEM
-// accumulators while the threads write out plane z - 1 from the other and
-// stage halo plane z + 2 into the ring slot plane z - 2 left free, so the
-// tensor cores, the epilogue and the loads overlap.  Ring slot of grid plane
-// g: g mod 4 (planes outside the grid hold zeros).
+// 3^3 convolution on the tcgen05 tensor cores for few channels (cin <= 32,
+// cout <= 32), streamed along z with its halo planes brought in by TMA and
+// its roles split among warps.  A CTA owns an 8 x 16 tile (M = 128 GEMM
+// rows, one per voxel) over a run of z-planes and keeps the weights of all
+// taps resident in the layout of conv3d_umma_kernel ([tap][kg][co] x 16 B);
+// tap (dz, dy, dx) of plane z is the halo descriptor of plane z - 1 + dz
+// shifted by (dy * 10 + dx) * 16 bytes.
+//  - the halo planes (10 x 18 voxels, 8 channels per k-group) arrive by
+//    tiled TMA copies of the channels-last activations, viewed as the 5-D
+//    tensor (c, x, y, z, sample): one box of 8 x 10 x 18 x 1 x 1 per k-group,
+//    zero-filled outside the grid, into a ring of kUtRing plane slots with
+//    one mbarrier each;
+//  - warp 4 is the producer: one lane issues the copies and the 27 MMAs of a
+//    plane into one of kUtAcc TMEM accumulators, and refills a ring slot as
+//    soon as the MMAs that read it have completed;
+//  - warps 0-3 are the epilogue (TMEM lanes 32 w .. 32 w + 31, one voxel
+//    each): they wait for a plane's MMAs, read its accumulator, hand it back
+//    on an mbarrier and write bias + activation.
+// No thread waits at a block barrier inside the loop: the tensor cores, the
+// copies and the epilogue run concurrently.  What bounds the narrow layers
+// then is the tensor core's operand traffic: each of the 27 MMAs of a plane
+// reads its 128 x 16 A tile (4 KB) from shared memory for only 16 or 32
+// output channels.  Each k-group of a plane starts on a 128-byte boundary
+// (2944 bytes apart), which the MMA descriptors take as the leading byte
+// offset.  Every wait is bounded; one that runs out sets *err and ends its
+// warp's loop, and the CTA waits (bounded) for its copies in flight before it
+// releases its TMEM and exits.
+constexpr int kUtRing = 6;
+constexpr int kUtAcc = 4;  // TMEM accumulators
+constexpr int kUtThreads = 160;
+constexpr unsigned kUtKgBytes = (kUmHX * kUmHY * 16u + 127u) / 128u * 128u;  // 2944
+constexpr unsigned kUtHead = 256;  // mbarriers and the TMEM slot
 template <int KG>
-constexpr unsigned up_plane_bytes()
+constexpr unsigned ut_plane_bytes()
 {
-    return static_cast<unsigned>(KG) * kUmHX * kUmHY * 16u;
+    return static_cast<unsigned>(KG) * kUtKgBytes;
 }
 template <int CO, int KG>
-constexpr unsigned up_smem_bytes()
+constexpr unsigned ut_smem_bytes()
 {
-    return 128u + 4u * up_plane_bytes<KG>() + 27u * KG * CO * 16u;
+    return 128u + kUtHead + kUtRing * ut_plane_bytes<KG>() + 27u * KG * CO * 16u;  // + alignment slack
 }
 
 template <int CO, int KG, typename TO>
-__global__ void __launch_bounds__(128) conv3d_umma_stream_kernel(const __nv_bfloat16 *__restrict__ x,
-                                                                 const __nv_bfloat16 *__restrict__ w,
-                                                                 const float *__restrict__ bias,
-                                                                 TO *__restrict__ y, int n, int cin, int cout,
-                                                                 int act, int zrun, int *err)
+__global__ void __launch_bounds__(kUtThreads, 4) conv3d_umma_tma_kernel(const __grid_constant__ CUtensorMap xmap,
+                                                                     const __nv_bfloat16 *__restrict__ w,
+                                                                     const float *__restrict__ bias,
+                                                                     TO *__restrict__ y, int n, int cin, int cout,
+                                                                     int act, int zrun, int *err)
 {
-    extern __shared__ __align__(1024) unsigned char up_smem[];
-    uint64_t *bar = reinterpret_cast<uint64_t *>(up_smem);  // [2]
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(up_smem + 16);
-    unsigned char *ring = up_smem + 128;
-    unsigned char *wsm = ring + 4 * up_plane_bytes<KG>();
-    constexpr unsigned kPlane = up_plane_bytes<KG>();
+    extern __shared__ __align__(1024) unsigned char ut_smem_raw[];
+    // TMA destinations start on 128-byte boundaries whatever the base alignment
+    unsigned char *ut_smem = ut_smem_raw + ((128u - (umma::smem_u32(ut_smem_raw) & 127u)) & 127u);
+    uint64_t *full = reinterpret_cast<uint64_t *>(ut_smem);  // [kUtRing]: a slot holds its plane
+    uint64_t *acc_full = full + kUtRing;                      // [kUtAcc]: a plane's MMAs are done
+    uint64_t *acc_empty = acc_full + kUtAcc;                  // [kUtAcc]: its accumulator was read
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(acc_empty + kUtAcc);
+    unsigned char *ring = ut_smem + kUtHead;
+    constexpr unsigned kPlane = ut_plane_bytes<KG>();
+    unsigned char *wsm = ring + kUtRing * kPlane;
     constexpr int kRow = kUmHX * kUmHY;  // 180 voxels of a halo plane
-    constexpr uint32_t kCols = 2 * CO < 32 ? 32 : 2 * CO;
+    constexpr uint32_t kPlaneTx = static_cast<uint32_t>(KG) * kRow * 16u;
+    constexpr uint32_t kCols = kUtAcc * CO < 32 ? 32 : kUtAcc * CO;
+    static_assert(kUtHead >= 8 * (kUtRing + 2 * kUtAcc) + 4, "mbarriers and TMEM slot");
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     const int tx_n = n / kUmX, ty_n = n / kUmY, zs_n = (n + zrun - 1) / zrun;
     int r = blockIdx.x;
@@ -898,14 +950,18 @@ __global__ void __launch_bounds__(128) conv3d_umma_stream_kernel(const __nv_bflo
     const int b = r / zs_n;
     const int z_end = min(z_begin + zrun, n);
     const long long sample = static_cast<long long>(b) * n * n * n;
+    const int p0 = z_begin - 1;  // the first halo plane; the last one is z_end
     const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
     if (t == 0) {
-        umma::mbar_init(&bar[0], 1);
-        umma::mbar_init(&bar[1], 1);
+        for (int k = 0; k < kUtRing; ++k) umma::mbar_init(&full[k], 1);
+        for (int k = 0; k < kUtAcc; ++k) {
+            umma::mbar_init(&acc_full[k], 1);
+            umma::mbar_init(&acc_empty[k], 4);  // one arrival per epilogue warp
+        }
     }
     if (warp == 0) umma::tmem_alloc(tslot, kCols);
     // weights of all taps: [tap][kg][co] x 16 B
-    for (int e = t; e < 27 * KG * CO; e += 128) {
+    for (int e = t; e < 27 * KG * CO; e += kUtThreads) {
         const int co = e % CO, kg = (e / CO) % KG, tap = e / (KG * CO);
         const int c = 8 * kg;
         uint4 v = zero4;
@@ -913,88 +969,111 @@ __global__ void __launch_bounds__(128) conv3d_umma_stream_kernel(const __nv_bflo
             v = *reinterpret_cast<const uint4 *>(w + (static_cast<long long>(tap) * cout + co) * cin + c);
         *reinterpret_cast<uint4 *>(wsm + ((tap * KG + kg) * CO + co) * 16) = v;
     }
-    auto stage = [&](int g) {  // grid plane g into ring slot g mod 4
-        unsigned char *dst = ring + static_cast<unsigned>((g + 4) & 3) * kPlane;
-        for (int e = t; e < KG * kRow; e += 128) {
-            const int kg = e / kRow, h = e % kRow;
-            const int gx = x0 + h % kUmHX - 1, gy = y0 + h / kUmHX - 1;
-            const int c = 8 * kg;
-            uint4 v = zero4;
-            if (g >= 0 && g < n && gx >= 0 && gx < n && gy >= 0 && gy < n && c < cin)
-                v = *reinterpret_cast<const uint4 *>(
-                    x + (sample + (static_cast<long long>(g) * n + gy) * n + gx) * cin + c);
-            *reinterpret_cast<uint4 *>(dst + (kg * kRow + h) * 16) = v;
-        }
-    };
-    stage(z_begin - 1);
-    stage(z_begin);
-    stage(z_begin + 1);
     umma::fence_proxy_async_smem();
     umma::fence_before_sync();
     __syncthreads();
     umma::fence_after_sync();
     const uint32_t tmem = *tslot;
-    constexpr uint32_t idesc = umma::idesc_bf16_f32(128, CO);
-    const uint32_t ring_s = umma::smem_u32(ring), w_s = umma::smem_u32(wsm);
-    uint32_t uses0 = 0u, uses1 = 0u;  // completed phases of each accumulator's barrier
     bool ok = true;
-    auto epilogue = [&](int zz, int buf) {
-        const int m = 32 * warp + lane;  // TMEM lane = GEMM row = voxel (x fastest)
-        const long long vox = sample + (static_cast<long long>(zz) * n + y0 + m / kUmX) * n + x0 + m % kUmX;
-        TO *yo = y + vox * cout;
+    if (warp == 4) {
+        // ---- producer: copies and MMAs (one lane)
+        if (lane == 0) {
+            constexpr uint32_t idesc = umma::idesc_bf16_f32(128, CO);
+            const uint64_t a_base = umma::smem_desc(umma::smem_u32(ring), kUtKgBytes, kUmHX * 16);
+            const uint64_t b_base = umma::smem_desc(umma::smem_u32(wsm), CO * 16, 128);
+            // plane p (p0 <= p <= z_end) is load number (p - p0) / kUtRing of slot (p - p0) % kUtRing
+            auto issue = [&](int p) {
+                const int k = p - p0, slot = k % kUtRing;
+                umma::mbar_arrive_expect_tx(&full[slot], kPlaneTx);
 #pragma unroll
-        for (int c16 = 0; c16 < CO; c16 += 16) {
-            float v[16];
-            umma::ld_32x32b_x16(tmem + (static_cast<uint32_t>(32 * warp) << 16) + buf * CO + c16, v);
+                for (int kg = 0; kg < KG; ++kg)
+                    umma::tma_load_5d(&xmap, ring + slot * kPlane + kg * kUtKgBytes, &full[slot], 8 * kg, x0 - 1,
+                                      y0 - 1, p, b);
+            };
+            auto wait_plane = [&](int p) {
+                const int k = p - p0;
+                return umma::mbar_wait(&full[k % kUtRing], static_cast<uint32_t>(k / kUtRing) & 1u, kUmWaitPolls);
+            };
+            int issued = p0 - 1;  // the last plane whose copies went out
+            while (issued < z_end && issued + 1 - p0 < kUtRing) issue(++issued);
+            for (int z = z_begin; z < z_end && ok; ++z) {
+                const int j = z - z_begin, buf = j % kUtAcc;
+                // the accumulator's previous plane has been read out
+                if (j >= kUtAcc)
+                    ok = umma::mbar_wait(&acc_empty[buf], static_cast<uint32_t>(j / kUtAcc - 1) & 1u, kUmWaitPolls);
+                ok = ok && wait_plane(z - 1) && wait_plane(z) && wait_plane(z + 1);
+                if (!ok) break;
+                umma::fence_after_sync();
+                // descriptors: the base ones plus each operand's offset / 16 in
+                // the start-address field (shared addresses stay below 2^18)
+                uint64_t a_plane[3];
 #pragma unroll
-            for (int j = 0; j < 16; j += 2) {
-                const int co = c16 + j;
-                float a = v[j] + (bias ? bias[co] : 0.f), bb = v[j + 1] + (bias ? bias[co + 1] : 0.f);
-                if (act) {
-                    a = a > 0.f ? a : kSlope * a;
-                    bb = bb > 0.f ? bb : kSlope * bb;
+                for (int dz = 0; dz < 3; ++dz)
+                    a_plane[dz] = a_base + static_cast<uint64_t>((((z - 1 + dz - p0) % kUtRing) * kPlane) >> 4);
+                const uint32_t dacc = tmem + buf * CO;
+#pragma unroll
+                for (int tap = 0; tap < 27; ++tap) {
+                    const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
+#pragma unroll
+                    for (int kc = 0; kc < KG / 2; ++kc) {
+                        const uint64_t ad =
+                            a_plane[dz] + static_cast<uint64_t>(((dy * kUmHX + dx) * 16 + 2 * kc * kUtKgBytes) >> 4);
+                        const uint64_t bd = b_base + static_cast<uint64_t>(((tap * KG + 2 * kc) * CO * 16) >> 4);
+                        umma::mma_bf16(dacc, ad, bd, idesc, (tap > 0 || kc > 0) ? 1u : 0u);
+                    }
                 }
-                st2(yo + co, a, bb);
+                umma::commit(&acc_full[buf]);
+                // plane z - 1's MMAs were the last to read the slot of plane z - 2
+                if (j >= 1 && issued < z_end) {
+                    const int jp = j - 1;
+                    ok = umma::mbar_wait(&acc_full[jp % kUtAcc], static_cast<uint32_t>(jp / kUtAcc) & 1u,
+                                         kUmWaitPolls);
+                    if (ok) issue(++issued);
+                }
+            }
+            if (!ok) {
+                atomicExch(err, 1);
+                // copies still in flight land before the CTA's shared memory is released
+                for (int p = max(p0, issued - kUtRing + 1); p <= issued; ++p) (void)wait_plane(p);
             }
         }
-    };
-    for (int z = z_begin; z < z_end && ok; ++z) {
-        const int buf = z & 1;
-        if (t == 0) {
-            for (int tap = 0; tap < 27; ++tap) {
-                const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
-                const uint32_t plane = ring_s + static_cast<uint32_t>((z - 1 + dz + 4) & 3) * kPlane +
-                                       (dy * kUmHX + dx) * 16;
+    } else {
+        // ---- epilogue: warp w holds TMEM lanes 32 w .. 32 w + 31 (voxel m, x fastest)
+        const int m = 32 * warp + lane;
+        float bv[CO];  // the biases, read once
 #pragma unroll
-                for (int kc = 0; kc < KG / 2; ++kc) {
-                    const uint64_t ad = umma::smem_desc(plane + 2 * kc * kRow * 16, kRow * 16, kUmHX * 16);
-                    const uint64_t bd = umma::smem_desc(w_s + (tap * KG + 2 * kc) * CO * 16, CO * 16, 128);
-                    umma::mma_bf16(tmem + buf * CO, ad, bd, idesc, (tap > 0 || kc > 0) ? 1u : 0u);
-                }
-            }
-            umma::commit(&bar[buf]);
-        }
-        if (z > z_begin) {
-            // plane z - 1: its MMAs read the slot plane z + 2 goes to
-            uint32_t &u = buf ? uses0 : uses1;  // the barrier of plane z - 1
-            if (!umma::mbar_wait(&bar[buf ^ 1], u & 1u, kUmWaitPolls)) ok = false;
-            ++u;
+        for (int co = 0; co < CO; ++co) bv[co] = bias ? bias[co] : 0.f;
+        for (int z = z_begin; z < z_end && ok; ++z) {
+            const int j = z - z_begin, buf = j % kUtAcc;
+            ok = umma::mbar_wait(&acc_full[buf], static_cast<uint32_t>(j / kUtAcc) & 1u, kUmWaitPolls);
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok) break;
             umma::fence_after_sync();
-            if (ok) epilogue(z - 1, buf ^ 1);
+            float v[CO];
+#pragma unroll
+            for (int c16 = 0; c16 < CO; c16 += 16) {
+                float part[16];
+                umma::ld_32x32b_x16(tmem + (static_cast<uint32_t>(32 * warp) << 16) + buf * CO + c16, part);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) v[c16 + i] = part[i];
+            }
+            // the accumulator may take the next plane's MMAs
+            umma::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(umma::smem_u32(&acc_empty[buf]))
+                                        : "memory");
+            const long long vox = sample + (static_cast<long long>(z) * n + y0 + m / kUmX) * n + x0 + m % kUmX;
+            TO *yo = y + vox * cout;
+#pragma unroll
+            for (int co = 0; co < CO; ++co) {
+                const float a = v[co] + bv[co];
+                v[co] = act && a <= 0.f ? kSlope * a : a;
+            }
+#pragma unroll
+            for (int co = 0; co < CO; co += 8) st8(yo + co, v + co);
         }
-        if (ok && z + 1 < z_end) stage(z + 2);
-        umma::fence_proxy_async_smem();
-        umma::fence_before_sync();
-        __syncthreads();
-        umma::fence_after_sync();
+        if (!ok && lane == 0) atomicExch(err, 1);
     }
-    if (ok) {
-        const int zl = z_end - 1, buf = zl & 1;
-        if (!umma::mbar_wait(&bar[buf], (buf ? uses1 : uses0) & 1u, kUmWaitPolls)) ok = false;
-        umma::fence_after_sync();
-        if (ok) epilogue(zl, buf);
-    }
-    if (!ok && t == 0) atomicExch(err, 1);
     umma::fence_before_sync();
     __syncthreads();
     if (warp == 0) umma::tmem_dealloc(tmem, kCols);
@@ -1633,6 +1712,32 @@ unsigned flat_blocks(long long len)
     return static_cast<unsigned>(b);
 }
 
+// Tensor map of a channels-last bf16 activation tensor [batch][n][n][n][cin]
+// as the 5-D (c, x, y, z, sample) tensor conv3d_umma_tma_kernel loads its
+// halo planes from: boxes of 8 channels x 10 x 18 x 1 x 1, zeros outside.
+// False if the driver's encoder is missing or rejects the shape.
+bool encode_act_map(const void *x, int batch, int n, int cin, CUtensorMap *map)
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn)
+            return false;
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    const cuuint64_t N = static_cast<cuuint64_t>(n), C = static_cast<cuuint64_t>(cin);
+    const cuuint64_t dims[5] = {C, N, N, N, static_cast<cuuint64_t>(batch)};
+    const cuuint64_t strides[4] = {C * 2, N * C * 2, N * N * C * 2, N * N * N * C * 2};
+    const cuuint32_t box[5] = {8, static_cast<cuuint32_t>(kUmHX), static_cast<cuuint32_t>(kUmHY), 1, 1};
+    const cuuint32_t unit[5] = {1, 1, 1, 1, 1};
+    return encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void *>(x), dims, strides, box, unit,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------- launchers
@@ -1677,16 +1782,22 @@ cudaError_t conv3d(const TI *x, const TW *w, const float *bias, TO *y, int batch
             int *err = umma_error_word();
             if (!err) return cudaErrorInvalidValue;
             cudaError_t e = cudaSuccess;
-            auto go = [&](auto kernel, unsigned smem) {
-                e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-                if (e == cudaSuccess) kernel<<<grid, 128, smem, s>>>(x, w, bias, y, n, cin, cout, act, zrun, err);
-            };
-            if (cout == 16 && cin <= 16) go(conv3d_umma_stream_kernel<16, 2, TO>, up_smem_bytes<16, 2>());
-            else if (cout == 16) go(conv3d_umma_stream_kernel<16, 4, TO>, up_smem_bytes<16, 4>());
-            else if (cin <= 16) go(conv3d_umma_stream_kernel<32, 2, TO>, up_smem_bytes<32, 2>());
-            else go(conv3d_umma_stream_kernel<32, 4, TO>, up_smem_bytes<32, 4>());
-            if (e != cudaSuccess) return e;
-            return cudaGetLastError();
+            CUtensorMap xmap;
+            if (encode_act_map(x, batch, n, cin, &xmap)) {
+                // halo planes by TMA
+                auto go_tma = [&](auto kernel, unsigned smem) {
+                    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+                    if (e == cudaSuccess)
+                        kernel<<<grid, kUtThreads, smem, s>>>(xmap, w, bias, y, n, cin, cout, act, zrun, err);
+                };
+                if (cout == 16 && cin <= 16) go_tma(conv3d_umma_tma_kernel<16, 2, TO>, ut_smem_bytes<16, 2>());
+                else if (cout == 16) go_tma(conv3d_umma_tma_kernel<16, 4, TO>, ut_smem_bytes<16, 4>());
+                else if (cin <= 16) go_tma(conv3d_umma_tma_kernel<32, 2, TO>, ut_smem_bytes<32, 2>());
+                else go_tma(conv3d_umma_tma_kernel<32, 4, TO>, ut_smem_bytes<32, 4>());
+                if (e != cudaSuccess) return e;
+                return cudaGetLastError();
+            }
+            // the driver's encoder rejected the shape: the plane-at-a-time kernel below
         }
         if (k == 3 && aligned && (cin == 8 || cin % 16 == 0) && cout % 16 == 0 && n % kUmY == 0 &&
             umma_enabled()) {

@@ -78,6 +78,31 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32
     return false;
 }
 
+// Arrive on the mbarrier (one of its expected arrivals) and add `bytes` to
+// the transaction count the current phase waits for.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// ---------------------------------------------------------------- TMA
+
+// One tiled TMA copy of a 5-D box at coordinates (c0 .. c4) of the tensor map
+// `map` (the address of a __grid_constant__ CUtensorMap parameter) into
+// shared memory at `dst` (128-byte aligned), completing on `bar`.  c0, the
+// innermost coordinate, times the element size must be a multiple of 16
+// bytes; the others may lie outside the tensor (the box reads zeros there).
+__device__ __forceinline__ void tma_load_5d(const void *map, void *dst, uint64_t *bar, int c0, int c1, int c2,
+                                            int c3, int c4)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_u32(bar))
+        : "memory");
+}
+
 // ---------------------------------------------------------------- TMEM
 
 // Allocate `ncols` TMEM columns (a power of two >= 32) for this CTA; the
