@@ -20,6 +20,7 @@ writes them (``--save-params``) and reads them back (``load_surrogate``).
 
     python -m paper_1511_04633_gb300.surrogate --grid 32 --train 48 --epochs 30
     python -m paper_1511_04633_gb300.surrogate --time-steps 3     # time the training step
+    python -m paper_1511_04633_gb300.surrogate --time-steps 3 --layer 16,16   # one conv layer
     python -m paper_1511_04633_gb300.surrogate --test 0 --epochs 60 \
         --save-params paper_1511_04633_gb300/weights/warm_start_64cube.npz
 """
@@ -285,6 +286,30 @@ def time_steps(args):
     return res
 
 
+def time_layer(args):
+    """Calls of one 3^3 convolution layer of the network (dmrt_nn_conv3d,
+    bf16, leaky ReLU) on seeded random activations and weights at the
+    configured grid and batch: one warm-up call, then --time-steps timed
+    calls (each synchronises)."""
+    import torch
+
+    cin, cout = (int(c) for c in args.layer.split(","))
+    n, batch = args.grid, args.batch
+    x = torch.from_numpy(inputs.random_targets((batch, n, n, n, cin), seed=1)).to(torch.bfloat16).cuda()
+    w = torch.from_numpy(inputs.random_weights(27 * cout * cin, seed=2, scale=0.2)).to(torch.bfloat16).cuda()
+    b = torch.from_numpy(inputs.random_weights(cout, seed=3, scale=0.5)).cuda()
+    y = torch.empty((batch, n, n, n, cout), dtype=torch.bfloat16, device="cuda")
+    dmrt.dmrt_nn_conv3d(x, w, b, y, batch, n, cin, cout, 3, act=1)
+    t0 = time.perf_counter()
+    for _ in range(args.time_steps):
+        dmrt.dmrt_nn_conv3d(x, w, b, y, batch, n, cin, cout, 3, act=1)
+    per_call = (time.perf_counter() - t0) / args.time_steps
+    res = {"layer": [cin, cout], "grid": n, "batch": batch, "call_ms": per_call * 1e3,
+           "tensor_core_errors": dmrt.dmrt_nn_tensor_core_errors(reset=True)}
+    print(json.dumps(res), flush=True)
+    return res
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description="train the warm-start surrogate and measure its gain")
     ap.add_argument("--grid", type=int, default=64, help="network (and training cavity) grid")
@@ -306,11 +331,13 @@ def main(argv=None):
                     help="write the trained parameters (BF16 network) to this .npz file")
     ap.add_argument("--time-steps", type=int, default=0,
                     help="only time this many training steps (zero targets) and predictions")
+    ap.add_argument("--layer", type=str, default="",
+                    help="with --time-steps: time one 3^3 convolution layer CIN,COUT instead")
     args = ap.parse_args(argv)
     import torch
 
     if args.time_steps > 0:
-        return time_steps(args)
+        return time_layer(args) if args.layer else time_steps(args)
 
     lo, hi = (float(v) for v in args.ra.split(","))
     draws = inputs.ensemble_draws(args.train + args.test, seed=args.seed, edges=(args.grid,),
