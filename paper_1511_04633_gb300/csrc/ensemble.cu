@@ -1,23 +1,26 @@
 // ensemble.cu -- many independent cavities advanced together: one kernel
-// launch per time step covers every cavity of the ensemble, and a residual
+// launch per time step covers up to 64 cavities of the ensemble, and a residual
 // interval of K steps replays one captured CUDA graph.
 //
 // Each cavity keeps its own 26-plane population slab inside two shared
 // ping-pong buffers (A-B scheme, as for a single cavity), or inside one
 // buffer updated in place by two alternating kernels (the in-place scheme of
-// step_inplace.cu, half the population memory).  A table of cavity
-// descriptors (sizes, strides, tile shape, relaxation rates, wall type) lives
-// in device memory, and a block map gives every thread block of the launch
-// its cavity; the block's position inside that cavity follows from the
-// cavity's first block index.  The per-cell arithmetic is the single-cavity
-// body (step_body.cuh), and stochastic rounding draws the same bits from the
-// cell index and step number, so a member evolves bitwise like a single
-// handle of the same cavity.  When every member has an even row length the
-// kernels take two cells per thread (pair_body.cuh), as a single cavity does.
+// step_inplace.cu, half the population memory).  Each step launch carries
+// the descriptors of its members (sizes, strides, tile shape, relaxation
+// rates, wall type; up to 64 members, more take several launches) in its
+// parameters, so that a block finds its member from its index alone; a
+// block map in device memory gives the block's tile.  The residual and
+// Nusselt kernels read the same descriptors from device memory.  The
+// per-cell arithmetic is the single-cavity body (step_body.cuh), and
+// stochastic rounding draws the same bits from the cell index and step
+// number, so a member evolves bitwise like a single handle of the same
+// cavity.  When every member has an even row length the kernels take two
+// cells per thread (pair_body.cuh), as a single cavity does.
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstring>
 #include <map>
 #include <new>
 #include <string>
@@ -48,6 +51,30 @@ struct __align__(16) BlockTile {
     int member, tx, ty, z;
 };
 
+// What a step kernel needs of one member.  A launch carries the members it
+// covers by value in its parameters (StepTable, at most kStepTableMembers):
+// the block's member then follows from the block index alone, so every field
+// is the same for the whole block and lives in the constant bank; the
+// kernels read them as operands there instead of holding them in registers
+// or re-reading them from shared memory.
+struct MemberStep {
+    int nx, ny, nz, wall;
+    unsigned plane, nxy;
+    float inv_ny;
+    int bx, by;              // step tile shape (see CavityDesc)
+    long long offset;        // element offset of the member's slab in each buffer
+    CollideParams C;
+};
+
+constexpr int kStepTableMembers = 64;
+
+struct StepTable {
+    int count;                                // members of this launch
+    int first_block[kStepTableMembers + 1];   // their first blocks in the launch's grid, then its size
+    MemberStep m[kStepTableMembers];
+};
+static_assert(sizeof(StepTable) <= 32000, "a launch's parameters hold at most 32764 bytes");
+
 namespace {
 
 constexpr int kEnsRedThreads = 256;
@@ -76,36 +103,37 @@ constexpr int kMinBlocksEns = 4;
 
 // ---------------------------------------------------------------- step
 
-// Stage the descriptor of the block's cavity in shared memory and locate the
-// block's cell: false if the thread lies outside the cavity.
-__device__ __forceinline__ bool locate_cell(CavityDesc &D, const CavityDesc *__restrict__ descs,
-                                            const BlockTile *__restrict__ blockmap, int &x, int &y,
-                                            int &z)
+// The member of this block in a launch's table: the last whose first block
+// is not above the block index (a search over block-uniform values).
+__device__ __forceinline__ const MemberStep &member_of_block(const StepTable &P)
 {
-    __shared__ BlockTile t;
-    {
-        const BlockTile *bt = blockmap + blockIdx.x;
-        const unsigned *g = reinterpret_cast<const unsigned *>(descs + bt->member);
-        unsigned *sdst = reinterpret_cast<unsigned *>(&D);
-        for (int w = threadIdx.x; w < static_cast<int>(sizeof(CavityDesc) / 4); w += blockDim.x)
-            sdst[w] = g[w];
-        if (threadIdx.x == 0) t = *bt;
+    const int b = static_cast<int>(blockIdx.x);
+    int lo = 0, hi = P.count;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (P.first_block[mid] <= b) lo = mid;
+        else hi = mid;
     }
-    __syncthreads();
-    // bx is a power of two, but a shift and mask here made ptxas spill about
-    // 50 bytes more in the paired kernels than this division does
+    return P.m[lo];
+}
+
+// The thread's cell (x, or the pair index along x) in the block's tile of
+// member D: false if it lies outside the member.
+__device__ __forceinline__ void tile_position(const MemberStep &D, const BlockTile *__restrict__ blockmap, int &x,
+                                              int &y, int &z)
+{
+    const BlockTile t = blockmap[blockIdx.x];
     const int bx = D.bx;
     x = t.tx * bx + static_cast<int>(threadIdx.x) % bx;
     y = t.ty * D.by + static_cast<int>(threadIdx.x) / bx;
     z = t.z;
-    return x < D.nx && y < D.ny;
 }
 
 // One cell of a walled cavity (Types 1-3; the wall type is a per-cavity
 // runtime value, which only changes the thermal rule on the x and z walls).
 template <typename T, bool SR>
 __device__ __forceinline__ void ensemble_cell(const T *__restrict__ src, T *__restrict__ dst,
-                                              const CavityDesc &D, int x, int y, int z,
+                                              const MemberStep &D, int x, int y, int z,
                                               unsigned salt)
 {
     const int nx = D.nx, ny = D.ny, nz = D.nz;
@@ -117,19 +145,16 @@ __device__ __forceinline__ void ensemble_cell(const T *__restrict__ src, T *__re
     pull_offsets<kRuntimeWall, T>(src, ComputedOffsets{plane, static_cast<unsigned>(nx), D.nxy}, nx,
                                   ny, nz, D.inv_ny, self, x, y, z, d, g, dir_x, dir_z);
     collide_cell(D.C, d, g);
-    // re-read the plane stride after a compiler barrier: otherwise the
-    // compiler keeps the load offsets live through the collision for the
-    // stores and spills (see ensemble_inplace_kernel)
-    asm volatile("" ::: "memory");
-    // same random word as a single cavity (step.cu) at the same step
-    store_cell<T, SR>(dst, self, D.plane, d, g, SR ? pcg_hash(self ^ salt) : 0u);
+    // the store offsets from a stride the compiler cannot see through
+    // (see ensemble_inplace_kernel); the same random word as a single
+    // cavity (step.cu) at the same step
+    store_cell<T, SR>(dst, self, opaque(D.plane), d, g, SR ? pcg_hash(self ^ salt) : 0u);
 }
 
 template <typename T, bool SR>
 __global__ void __launch_bounds__(256, kMinBlocksEns)
-    ensemble_step_kernel(const T *__restrict__ srcb, T *__restrict__ dstb,
-                         const CavityDesc *__restrict__ descs, const BlockTile *__restrict__ blockmap,
-                         long long counter_at)
+    ensemble_step_kernel(const T *__restrict__ srcb, T *__restrict__ dstb, const BlockTile *__restrict__ blockmap,
+                         long long counter_at, const __grid_constant__ StepTable P)
 {
     // programmatic dependent launch (see step.cu)
     asm volatile("griddepcontrol.wait;" ::: "memory");
@@ -141,11 +166,10 @@ __global__ void __launch_bounds__(256, kMinBlocksEns)
             *reinterpret_cast<unsigned *>(dstb + counter_at) = step + 1u;
         salt = pcg_hash(step);
     }
-    // the block's cavity descriptor, staged in shared memory: its fields are
-    // then re-read cheaply instead of occupying registers through the step
-    __shared__ CavityDesc D;
+    const MemberStep &D = member_of_block(P);
     int x, y, z;
-    if (!locate_cell(D, descs, blockmap, x, y, z)) return;
+    tile_position(D, blockmap, x, y, z);
+    if (x >= D.nx || y >= D.ny) return;
     ensemble_cell<T, SR>(srcb + D.offset, dstb + D.offset, D, x, y, z, salt);
 }
 
@@ -155,8 +179,8 @@ __global__ void __launch_bounds__(256, kMinBlocksEns)
 // word p ^ 1.
 template <typename T, bool SR, int PHASE>
 __global__ void DMRT_ENS_INPLACE_BOUNDS(PHASE)
-    ensemble_inplace_kernel(T *__restrict__ buf, const CavityDesc *__restrict__ descs,
-                            const BlockTile *__restrict__ blockmap, long long counter_at)
+    ensemble_inplace_kernel(T *__restrict__ buf, const BlockTile *__restrict__ blockmap, long long counter_at,
+                            const __grid_constant__ StepTable P)
 {
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;");
@@ -167,9 +191,10 @@ __global__ void DMRT_ENS_INPLACE_BOUNDS(PHASE)
         if (blockIdx.x == 0 && threadIdx.x == 0) ctr[PHASE ^ 1] = step + 1u;
         salt = pcg_hash(step);
     }
-    __shared__ CavityDesc D;
+    const MemberStep &D = member_of_block(P);
     int x, y, z;
-    if (!locate_cell(D, descs, blockmap, x, y, z)) return;
+    tile_position(D, blockmap, x, y, z);
+    if (x >= D.nx || y >= D.ny) return;
     T *A = buf + D.offset;
     const int nx = D.nx, ny = D.ny, nz = D.nz;
     const unsigned plane = D.plane;
@@ -186,10 +211,9 @@ __global__ void DMRT_ENS_INPLACE_BOUNDS(PHASE)
     const unsigned base = SR ? pcg_hash(self ^ salt) : 0u;
     // The store offsets equal the load offsets (each cell writes the slots it
     // read); left to itself the compiler keeps all 26 of them live through the
-    // collision and spills.  Re-reading the strides from shared memory after
-    // a compiler barrier makes it recompute them at the stores instead.
-    asm volatile("" ::: "memory");
-    const unsigned splane = D.plane;
+    // collision and spills.  A stride it cannot see through (opaque) makes it
+    // recompute them at the stores instead.
+    const unsigned splane = opaque(D.plane);
     if constexpr (PHASE == 1) {
         store_cell_to<T, SR>(A, d, g, base, [&](auto I) -> unsigned {
             return self + plane_opp<decltype(I)::value>() * splane;
@@ -212,18 +236,18 @@ __global__ void DMRT_ENS_INPLACE_BOUNDS(PHASE)
 // paired kernels of BF16 storage.
 constexpr int kEnsPairBlocks = 5;
 
-// As locate_cell, for tiles of pairs: the thread holds the cells x0, x0 + 1
-// with x0 = 2 (tile x * bx + thread x).
-__device__ __forceinline__ bool locate_pair(CavityDesc &D, const CavityDesc *__restrict__ descs,
-                                            const BlockTile *__restrict__ blockmap, int &x0, int &y, int &z)
+// The pair of the thread (tiles of pairs): the cells x0, x0 + 1 with x0 =
+// 2 (tile x * bx + thread x); false if it lies outside the member.
+__device__ __forceinline__ bool locate_pair(const MemberStep &D, const BlockTile *__restrict__ blockmap, int &x0,
+                                            int &y, int &z)
 {
     int xp;
-    (void)locate_cell(D, descs, blockmap, xp, y, z);  // its bound is for one cell per thread
+    tile_position(D, blockmap, xp, y, z);
     x0 = 2 * xp;
     return x0 < D.nx && y < D.ny;
 }
 
-__device__ __forceinline__ PairFaces pair_faces(const CavityDesc &D, int x0, int y, int z)
+__device__ __forceinline__ PairFaces pair_faces(const MemberStep &D, int x0, int y, int z)
 {
     return PairFaces{x0 == 0, x0 + 2 == D.nx, y == 0, y == D.ny - 1, z == 0, z == D.nz - 1};
 }
@@ -234,7 +258,7 @@ __device__ __forceinline__ PairFaces pair_faces(const CavityDesc &D, int x0, int
 // plane as soon as the collision has its value.
 template <typename T, bool SR>
 __device__ __forceinline__ void ensemble_pair_body(const T *__restrict__ src, T *__restrict__ dst,
-                                                   const CavityDesc &D, int x0, int y, int z, unsigned salt)
+                                                   const MemberStep &D, int x0, int y, int z, unsigned salt)
 {
     const unsigned self = (static_cast<unsigned>(z) * D.ny + y) * D.nx + x0;
     F2 d[19], g[7];
@@ -242,10 +266,8 @@ __device__ __forceinline__ void ensemble_pair_body(const T *__restrict__ src, T 
                                pair_faces(D, x0, y, z), theta_linear(y, D.inv_ny), d, g, D.wall != 1,
                                D.wall == 2);
     const unsigned r01 = SR ? pair_bits_salted(self, salt) : 0u;
-    // re-read the plane stride after a compiler barrier (see ensemble_cell)
-    asm volatile("" ::: "memory");
     T *Dp = dst + self;
-    const unsigned plane = D.plane;
+    const unsigned plane = opaque(D.plane);  // (see ensemble_inplace_pair_body)
     collide_from<F2, Pair<T>::kShift>(D.C, d, g, conserved<F2, Pair<T>::kShift>(d, g),
                                       plane_sink([&](auto I, F2 v) {
                                           constexpr int q = decltype(I)::value;
@@ -255,8 +277,8 @@ __device__ __forceinline__ void ensemble_pair_body(const T *__restrict__ src, T 
 
 template <typename T, bool SR>
 __global__ void __launch_bounds__(128, kEnsPairBlocks)
-    ensemble_pair_kernel(const T *__restrict__ srcb, T *__restrict__ dstb, const CavityDesc *__restrict__ descs,
-                         const BlockTile *__restrict__ blockmap, long long counter_at)
+    ensemble_pair_kernel(const T *__restrict__ srcb, T *__restrict__ dstb, const BlockTile *__restrict__ blockmap,
+                         long long counter_at, const __grid_constant__ StepTable P)
 {
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;");
@@ -267,15 +289,15 @@ __global__ void __launch_bounds__(128, kEnsPairBlocks)
             *reinterpret_cast<unsigned *>(dstb + counter_at) = step + 1u;
         salt = pcg_hash(step);
     }
-    __shared__ CavityDesc D;
+    const MemberStep &D = member_of_block(P);
     int x0, y, z;
-    if (!locate_pair(D, descs, blockmap, x0, y, z)) return;
+    if (!locate_pair(D, blockmap, x0, y, z)) return;
     ensemble_pair_body<T, SR>(srcb + D.offset, dstb + D.offset, D, x0, y, z, salt);
 }
 
 // In-place scheme with two cells per thread (see step_inplace_pair_kernel).
 template <typename T, bool SR, int PHASE>
-__device__ __forceinline__ void ensemble_inplace_pair_body(T *__restrict__ A, const CavityDesc &D, int x0, int y,
+__device__ __forceinline__ void ensemble_inplace_pair_body(T *__restrict__ A, const MemberStep &D, int x0, int y,
                                                            int z, unsigned salt)
 {
     const unsigned self = (static_cast<unsigned>(z) * D.ny + y) * D.nx + x0;
@@ -288,9 +310,11 @@ __device__ __forceinline__ void ensemble_inplace_pair_body(T *__restrict__ A, co
         pull_pair<kRuntimeWall, T>(A + self, LocalOffsets{D.plane}, P, theta_linear(y, D.inv_ny), d, g,
                                    D.wall != 1, D.wall == 2);
     const unsigned r01 = SR ? pair_bits_salted(self, salt) : 0u;
-    asm volatile("" ::: "memory");
+    // phase 0: store addresses from a stride the compiler cannot see
+    // through, so that it recomputes them instead of keeping the load
+    // addresses live (phase 1 spills less without)
     T *Dp = A + self;
-    const SwappedOffsets SO{D.plane, static_cast<unsigned>(D.nx), D.nxy};
+    const SwappedOffsets SO{PHASE == 0 ? opaque(D.plane) : D.plane, static_cast<unsigned>(D.nx), D.nxy};
     collide_from<F2, Pair<T>::kShift>(D.C, d, g, conserved<F2, Pair<T>::kShift>(d, g), plane_sink([&](auto I, F2 v) {
         constexpr int q = decltype(I)::value;
         const unsigned r = SR ? plane_bits<q>(r01) : 0u;
@@ -317,8 +341,8 @@ __device__ __forceinline__ void ensemble_inplace_pair_body(T *__restrict__ A, co
 
 template <typename T, bool SR, int PHASE>
 __global__ void __launch_bounds__(128, kEnsPairBlocks)
-    ensemble_inplace_pair_kernel(T *__restrict__ buf, const CavityDesc *__restrict__ descs,
-                                 const BlockTile *__restrict__ blockmap, long long counter_at)
+    ensemble_inplace_pair_kernel(T *__restrict__ buf, const BlockTile *__restrict__ blockmap, long long counter_at,
+                                 const __grid_constant__ StepTable P)
 {
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;");
@@ -329,9 +353,9 @@ __global__ void __launch_bounds__(128, kEnsPairBlocks)
         if (blockIdx.x == 0 && threadIdx.x == 0) ctr[PHASE ^ 1] = step + 1u;
         salt = pcg_hash(step);
     }
-    __shared__ CavityDesc D;
+    const MemberStep &D = member_of_block(P);
     int x0, y, z;
-    if (!locate_pair(D, descs, blockmap, x0, y, z)) return;
+    if (!locate_pair(D, blockmap, x0, y, z)) return;
     ensemble_inplace_pair_body<T, SR, PHASE>(buf + D.offset, D, x0, y, z, salt);
 }
 
@@ -555,9 +579,9 @@ __global__ void __launch_bounds__(kEnsRedThreads)
 
 // ---------------------------------------------------------------- launchers
 
-cudaError_t launch_ensemble_step(int storage, bool stochastic, const void *src, void *dst,
-                                 const CavityDesc *descs, const BlockTile *blockmap, long long blocks,
-                                 int threads, long long counter_at, cudaStream_t s, bool pdl, bool pairs)
+cudaError_t launch_ensemble_step(int storage, bool stochastic, const void *src, void *dst, const StepTable &P,
+                                 const BlockTile *blockmap, long long blocks, int threads, long long counter_at,
+                                 cudaStream_t s, bool pdl, bool pairs)
 {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(static_cast<unsigned>(blocks));
@@ -575,23 +599,23 @@ cudaError_t launch_ensemble_step(int storage, bool stochastic, const void *src, 
         if (pairs) {
             if constexpr (!std::is_same_v<T, float>) {
                 if (stochastic)
-                    return cudaLaunchKernelEx(&cfg, ensemble_pair_kernel<T, true>, a, b, descs, blockmap, counter_at);
+                    return cudaLaunchKernelEx(&cfg, ensemble_pair_kernel<T, true>, a, b, blockmap, counter_at, P);
             }
-            return cudaLaunchKernelEx(&cfg, ensemble_pair_kernel<T, false>, a, b, descs, blockmap, counter_at);
+            return cudaLaunchKernelEx(&cfg, ensemble_pair_kernel<T, false>, a, b, blockmap, counter_at, P);
         }
         if constexpr (!std::is_same_v<T, float>) {
             if (stochastic)
-                return cudaLaunchKernelEx(&cfg, ensemble_step_kernel<T, true>, a, b, descs, blockmap, counter_at);
+                return cudaLaunchKernelEx(&cfg, ensemble_step_kernel<T, true>, a, b, blockmap, counter_at, P);
         }
-        return cudaLaunchKernelEx(&cfg, ensemble_step_kernel<T, false>, a, b, descs, blockmap, counter_at);
+        return cudaLaunchKernelEx(&cfg, ensemble_step_kernel<T, false>, a, b, blockmap, counter_at, P);
     });
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
-cudaError_t launch_ensemble_inplace(int storage, bool stochastic, void *buf, int phase,
-                                    const CavityDesc *descs, const BlockTile *blockmap, long long blocks,
-                                    int threads, long long counter_at, cudaStream_t s, bool pdl, bool pairs)
+cudaError_t launch_ensemble_inplace(int storage, bool stochastic, void *buf, int phase, const StepTable &P,
+                                    const BlockTile *blockmap, long long blocks, int threads, long long counter_at,
+                                    cudaStream_t s, bool pdl, bool pairs)
 {
     if (phase != 0 && phase != 1) return cudaErrorInvalidValue;
     cudaLaunchConfig_t cfg = {};
@@ -606,30 +630,21 @@ cudaError_t launch_ensemble_inplace(int storage, bool stochastic, void *buf, int
     cudaError_t e = dispatch(1, storage, [&](auto, auto *tp) {
         using T = std::remove_pointer_t<decltype(tp)>;
         T *A = static_cast<T *>(buf);
+        auto go = [&](auto kernel) { return cudaLaunchKernelEx(&cfg, kernel, A, blockmap, counter_at, P); };
         if (pairs) {
             if constexpr (!std::is_same_v<T, float>) {
                 if (stochastic)
-                    return phase == 0 ? cudaLaunchKernelEx(&cfg, ensemble_inplace_pair_kernel<T, true, 0>, A,
-                                                           descs, blockmap, counter_at)
-                                      : cudaLaunchKernelEx(&cfg, ensemble_inplace_pair_kernel<T, true, 1>, A,
-                                                           descs, blockmap, counter_at);
+                    return phase == 0 ? go(ensemble_inplace_pair_kernel<T, true, 0>)
+                                      : go(ensemble_inplace_pair_kernel<T, true, 1>);
             }
-            return phase == 0 ? cudaLaunchKernelEx(&cfg, ensemble_inplace_pair_kernel<T, false, 0>, A, descs,
-                                                   blockmap, counter_at)
-                              : cudaLaunchKernelEx(&cfg, ensemble_inplace_pair_kernel<T, false, 1>, A, descs,
-                                                   blockmap, counter_at);
+            return phase == 0 ? go(ensemble_inplace_pair_kernel<T, false, 0>)
+                              : go(ensemble_inplace_pair_kernel<T, false, 1>);
         }
         if constexpr (!std::is_same_v<T, float>) {
             if (stochastic)
-                return phase == 0 ? cudaLaunchKernelEx(&cfg, ensemble_inplace_kernel<T, true, 0>, A,
-                                                       descs, blockmap, counter_at)
-                                  : cudaLaunchKernelEx(&cfg, ensemble_inplace_kernel<T, true, 1>, A,
-                                                       descs, blockmap, counter_at);
+                return phase == 0 ? go(ensemble_inplace_kernel<T, true, 0>) : go(ensemble_inplace_kernel<T, true, 1>);
         }
-        return phase == 0 ? cudaLaunchKernelEx(&cfg, ensemble_inplace_kernel<T, false, 0>, A, descs,
-                                               blockmap, counter_at)
-                          : cudaLaunchKernelEx(&cfg, ensemble_inplace_kernel<T, false, 1>, A, descs,
-                                               blockmap, counter_at);
+        return phase == 0 ? go(ensemble_inplace_kernel<T, false, 0>) : go(ensemble_inplace_kernel<T, false, 1>);
     });
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
@@ -690,6 +705,10 @@ struct dmrt_ensemble {
     lbm::BlockTile *d_blockmap = nullptr;
     long long step_blocks = 0;
     size_t blockmap_cap = 0;
+    // The step launches: the members of each, by value (its parameters), and
+    // its range of the block map.
+    std::vector<lbm::StepTable> tables;
+    std::vector<long long> table_first, table_blocks;
     int *d_redmap = nullptr;
     long long red_blocks = 0;
     int threads = 128;
@@ -821,8 +840,66 @@ std::vector<lbm::BlockTile> layout_step(dmrt_ensemble_t *e, const std::vector<in
     return map;
 }
 
+void drop_graphs(dmrt_ensemble_t *e)
+{
+    for (auto &g : e->graph)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+}
+
+lbm::MemberStep member_step(const lbm::CavityDesc &D)
+{
+    lbm::MemberStep M;
+    std::memset(&M, 0, sizeof M);
+    M.nx = D.nx;
+    M.ny = D.ny;
+    M.nz = D.nz;
+    M.wall = D.wall;
+    M.plane = D.plane;
+    M.nxy = D.nxy;
+    M.inv_ny = D.inv_ny;
+    M.bx = D.bx;
+    M.by = D.by;
+    M.offset = D.offset;
+    M.C = D.C;
+    return M;
+}
+
+// Split a block map (each member's blocks contiguous) into step launches of
+// at most kStepTableMembers members each.
+void build_step_tables(dmrt_ensemble_t *e, const std::vector<lbm::BlockTile> &map)
+{
+    e->tables.clear();
+    e->table_first.clear();
+    e->table_blocks.clear();
+    size_t b = 0;
+    while (b < map.size()) {
+        e->tables.emplace_back();
+        lbm::StepTable &T = e->tables.back();
+        std::memset(&T, 0, sizeof T);
+        const size_t first = b;
+        int count = 0;
+        while (b < map.size() && count < lbm::kStepTableMembers) {
+            const int c = map[b].member;
+            T.first_block[count] = static_cast<int>(b - first);
+            T.m[count] = member_step(e->desc[c]);
+            ++count;
+            while (b < map.size() && map[b].member == c) ++b;
+        }
+        T.count = count;
+        T.first_block[count] = static_cast<int>(b - first);
+        e->table_first.push_back(static_cast<long long>(first));
+        e->table_blocks.push_back(static_cast<long long>(b - first));
+    }
+}
+
 dmrt_status upload_layout(dmrt_ensemble_t *e, const std::vector<lbm::BlockTile> &map)
 {
+    // captured graphs hold the previous launches' tables
+    drop_graphs(e);
+    build_step_tables(e, map);
     if (map.size() > e->blockmap_cap) {
         if (e->d_blockmap) cudaFree(e->d_blockmap);
         e->d_blockmap = nullptr;
@@ -841,14 +918,6 @@ dmrt_status upload_layout(dmrt_ensemble_t *e, const std::vector<lbm::BlockTile> 
     return DMRT_OK;
 }
 
-void drop_graphs(dmrt_ensemble_t *e)
-{
-    for (auto &g : e->graph)
-        if (g) {
-            cudaGraphExecDestroy(g);
-            g = nullptr;
-        }
-}
 
 // The alternating state of the ensemble: the current buffer (A-B) or the
 // layout parity (in-place).
@@ -879,13 +948,18 @@ cudaError_t launch_one_step(dmrt_ensemble_t *e, int from, bool res = false)
         const cudaError_t c = launch_residual_point(e, from);
         if (c != cudaSuccess) return c;
     }
-    if (e->inplace)
-        return lbm::launch_ensemble_inplace(e->storage, e->stochastic, e->buf[0], from, e->d_desc,
-                                            e->d_blockmap, e->step_blocks, e->threads,
-                                            e->total_elems, e->stream, e->use_pdl, e->pairs);
-    return lbm::launch_ensemble_step(e->storage, e->stochastic, e->buf[from], e->buf[from ^ 1],
-                                     e->d_desc, e->d_blockmap, e->step_blocks, e->threads,
-                                     e->total_elems, e->stream, e->use_pdl, e->pairs);
+    for (size_t i = 0; i < e->tables.size(); ++i) {
+        const lbm::BlockTile *map = e->d_blockmap + e->table_first[i];
+        const cudaError_t c =
+            e->inplace ? lbm::launch_ensemble_inplace(e->storage, e->stochastic, e->buf[0], from, e->tables[i], map,
+                                                      e->table_blocks[i], e->threads, e->total_elems, e->stream,
+                                                      e->use_pdl, e->pairs)
+                       : lbm::launch_ensemble_step(e->storage, e->stochastic, e->buf[from], e->buf[from ^ 1],
+                                                   e->tables[i], map, e->table_blocks[i], e->threads,
+                                                   e->total_elems, e->stream, e->use_pdl, e->pairs);
+        if (c != cudaSuccess) return c;
+    }
+    return cudaSuccess;
 }
 
 bool capture_interval(dmrt_ensemble_t *e, int start)
@@ -944,8 +1018,9 @@ dmrt_status run_steps(dmrt_ensemble_t *e, long n)
             ph ^= 1;
         }
         e->steps += chunk;
-        e->step_launches += chunk;
-        e->total_launches += chunk + (took ? 2 : 0);
+        const long per_step = static_cast<long>(e->tables.size());  // launches per step
+        e->step_launches += chunk * per_step;
+        e->total_launches += chunk * per_step + (took ? 2 : 0);
         if (took && e->snaps < 2) e->snaps++;
         if (e->timing) {
             ECK(e, cudaEventRecord(e1, e->stream), "cudaEventRecord");

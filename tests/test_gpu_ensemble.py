@@ -284,3 +284,42 @@ def test_paired_ensemble_autotune_and_requests(dm):
     assert dm.Ensemble(MEMBERS).params(0)["cells_per_thread"] == 1
     with pytest.raises(dm.DmrtError):
         dm.Ensemble(MEMBERS, cells_per_thread=2)
+
+
+# ------------------------------------------------------------------ more members than one launch holds
+
+def _many(count, even):
+    """`count` small seeded cavities (edges 6..13, all wall types)."""
+    rng = np.random.default_rng(99 if even else 98)
+    out = []
+    for k in range(count):
+        nx, ny, nz = (int(v) for v in rng.integers(6, 14, size=3))
+        if even:
+            nx += nx & 1
+        out.append({"grid": (nx, ny, nz), "Ra": float(10 ** rng.uniform(3, 5)), "wall": 1 + k % 3})
+    return out
+
+
+@pytest.mark.parametrize("even", [False, True], ids=["one_cell", "pairs"])
+@pytest.mark.parametrize("streaming", [0, 1], ids=["ab", "inplace"])
+def test_ensemble_of_more_members_than_one_launch_holds(dm, streaming, even):
+    """A step launch carries at most 64 members' descriptors in its
+    parameters; 150 members take three launches per step.  Members in every
+    launch (first, last and boundary members) stay bitwise equal to single
+    handles, through graph-replayed intervals, and the step count is three
+    launches per step."""
+    cav = _many(150, even)
+    ens = dm.Ensemble(cav, storage=1, streaming=streaming, residual_interval=5)
+    assert ens.params(0)["cells_per_thread"] == (2 if even else 1)
+    dm.dmrt_ensemble_get_stats(ens.e, reset=True)
+    ens.step(23)
+    assert dm.dmrt_ensemble_get_stats(ens.e)["step_launches"] == 3 * 23
+    for k in (0, 1, 63, 64, 65, 127, 128, 149):
+        m = cav[k]
+        single = dm.Cavity(m["grid"], m["Ra"], wall_type=m["wall"], storage=1, streaming=streaming)
+        single.step(23)
+        fe, ge = ens.populations(k)
+        fs, gs = single.populations()
+        assert np.array_equal(fe, fs) and np.array_equal(ge, gs), k
+    r = np.asarray(ens.residual())
+    assert np.all(np.isfinite(r))
