@@ -203,26 +203,7 @@ dmrt_status check_stage_errors(dmrt_t *h)
 
 // Relaxation rates of Eq. (26) (flow) and Eqs. (35),(36) (energy), folded with
 // the squared norms of the moment basis.
-void fill_rates(dmrt_t *h)
-{
-    const double s_nu = 1.0 / (3.0 * h->nu + 0.5);
-    double s[19];
-    for (int k = 0; k < 19; ++k) s[k] = 1.0;
-    s[1] = 1.19;
-    s[2] = s[10] = s[12] = 1.4;
-    s[4] = s[6] = s[8] = 1.2;
-    s[16] = s[17] = s[18] = 1.98;
-    s[9] = s[11] = s[13] = s[14] = s[15] = s_nu;
-    for (int k = 0; k < 19; ++k) {
-        h->C.rs[k] = static_cast<float>(s[k] / lbm::m19_norm2(k));
-        h->C.ws[k] = static_cast<float>((1.0 - s[k]) / lbm::m19_norm2(k));
-    }
-    const double tau_a = 0.5 + 4.0 * h->alpha;  // eps = 1/4, dt = dx = 1
-    double q[7] = {1.0, 1.0 / tau_a, 1.0 / tau_a, 1.0 / tau_a, 1.0, 1.0, 1.0};
-    for (int k = 0; k < 7; ++k) h->C.rq[k] = static_cast<float>(q[k] / lbm::m7_norm2(k));
-    h->C.gbeta = static_cast<float>(h->gbeta);
-    h->C.theta_ref = 0.0f;  // T_l = (T_h + T_c)/2
-}
+void fill_rates(dmrt_t *h) { lbm::fill_collide_params(h->C, h->nu, h->alpha, h->gbeta); }
 
 dmrt_status ensure_staging(dmrt_t *h, size_t floats)
 {

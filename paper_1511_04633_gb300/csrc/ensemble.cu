@@ -51,6 +51,81 @@ struct __align__(16) BlockTile {
     int member, tx, ty, z;
 };
 
+// The collision parameters that differ between members.  The others (the
+// rates of Eq. (26) not set by the viscosity, q_0 and q_4..6, theta_ref = 0,
+// isotropic diffusion) are the same for every cavity and come from a
+// constant table (kFixedRates); fill_collide_params computes both.
+struct MemberRates {
+    float rs9, rs11, rs13;  // s_nu / |M_k|^2 for k = 9, 11 and 13..15 (equal norms)
+    float ws9, ws11, ws13;  // (1 - s_nu) / |M_k|^2, likewise
+    float rq1;              // q_k / |N_k|^2, k = 1, 2, 3 (Eq. (36); equal rates and norms)
+    float gbeta;
+    // always 0 (isotropic diffusion), but read at run time: the collision's
+    // branch on it splits the energy part for the scheduler, and with a
+    // constant 0 the in-place kernels spilled about 100 bytes
+    int aniso;
+};
+static_assert(m19_norm2(13) == m19_norm2(14) && m19_norm2(13) == m19_norm2(15),
+              "one rate entry serves moments 13, 14 and 15");
+static_assert(m7_norm2(1) == m7_norm2(2) && m7_norm2(1) == m7_norm2(3), "one entry serves q_1..3");
+
+struct FixedRates {
+    float rs[19], ws[19], rq[7];
+};
+__host__ __device__ constexpr FixedRates fixed_rates()
+{
+    FixedRates r{};
+    for (int k = 0; k < 19; ++k) {
+        r.rs[k] = static_cast<float>(mrt_rate(k) / m19_norm2(k));
+        r.ws[k] = static_cast<float>((1.0 - mrt_rate(k)) / m19_norm2(k));
+    }
+    for (int k = 0; k < 7; ++k) r.rq[k] = static_cast<float>(1.0 / m7_norm2(k));
+    return r;
+}
+// in the constant bank at fixed addresses, so that the collision reads them
+// as instruction operands (the entries of the member-dependent rates unused)
+__constant__ FixedRates kFixedRates = fixed_rates();
+
+// The parameter set collide_from reads, for one member: the member's rates
+// from the launch's parameters, the rest from kFixedRates.
+struct MemberCollide {
+    struct Rs {
+        float r9, r11, r13;
+        __device__ __forceinline__ float operator[](int k) const
+        {
+            return k == 9 ? r9 : k == 11 ? r11 : viscous_moment(k) ? r13 : kFixedRates.rs[k];
+        }
+    };
+    struct Ws {
+        float r9, r11, r13;
+        __device__ __forceinline__ float operator[](int k) const
+        {
+            return k == 9 ? r9 : k == 11 ? r11 : viscous_moment(k) ? r13 : kFixedRates.ws[k];
+        }
+    };
+    struct Rq {
+        float r1;
+        __device__ __forceinline__ float operator[](int k) const
+        {
+            return (k >= 1 && k <= 3) ? r1 : kFixedRates.rq[k];
+        }
+    };
+    struct Qa {
+        __device__ __forceinline__ float operator[](int) const { return 0.0f; }
+    };
+    Rs rs;
+    Ws ws;
+    Rq rq;
+    Qa qa;
+    float gbeta;
+    static constexpr float theta_ref = 0.0f;
+    int aniso;
+    __device__ __forceinline__ explicit MemberCollide(const MemberRates &r)
+        : rs{r.rs9, r.rs11, r.rs13}, ws{r.ws9, r.ws11, r.ws13}, rq{r.rq1}, qa{}, gbeta(r.gbeta), aniso(r.aniso)
+    {
+    }
+};
+
 // What a step kernel needs of one member.  A launch carries the members it
 // covers by value in its parameters (StepTable, at most kStepTableMembers):
 // the block's member then follows from the block index alone, so every field
@@ -61,9 +136,9 @@ struct MemberStep {
     int nx, ny, nz, wall;
     unsigned plane, nxy;
     float inv_ny;
-    int bx, by;              // step tile shape (see CavityDesc)
+    int bx_log2, by;         // step tile shape (see CavityDesc; bx = 2^bx_log2)
     long long offset;        // element offset of the member's slab in each buffer
-    CollideParams C;
+    MemberRates r;
 };
 
 constexpr int kStepTableMembers = 64;
@@ -123,9 +198,9 @@ __device__ __forceinline__ void tile_position(const MemberStep &D, const BlockTi
                                               int &y, int &z)
 {
     const BlockTile t = blockmap[blockIdx.x];
-    const int bx = D.bx;
-    x = t.tx * bx + static_cast<int>(threadIdx.x) % bx;
-    y = t.ty * D.by + static_cast<int>(threadIdx.x) / bx;
+    const int tid = static_cast<int>(threadIdx.x);
+    x = (t.tx << D.bx_log2) + (tid & ((1 << D.bx_log2) - 1));
+    y = t.ty * D.by + (tid >> D.bx_log2);
     z = t.z;
 }
 
@@ -144,7 +219,7 @@ __device__ __forceinline__ void ensemble_cell(const T *__restrict__ src, T *__re
     const bool dir_z = D.wall == 2;  // Type 2: linear z walls
     pull_offsets<kRuntimeWall, T>(src, ComputedOffsets{plane, static_cast<unsigned>(nx), D.nxy}, nx,
                                   ny, nz, D.inv_ny, self, x, y, z, d, g, dir_x, dir_z);
-    collide_cell(D.C, d, g);
+    collide_cell(MemberCollide(D.r), d, g);
     // the store offsets from a stride the compiler cannot see through
     // (see ensemble_inplace_kernel); the same random word as a single
     // cavity (step.cu) at the same step
@@ -207,7 +282,7 @@ __global__ void DMRT_ENS_INPLACE_BOUNDS(PHASE)
     else
         pull_offsets<kRuntimeWall, T>(A, LocalOffsets{plane}, nx, ny, nz, D.inv_ny, self, x, y, z, d,
                                       g, dir_x, dir_z);
-    collide_cell(D.C, d, g);
+    collide_cell(MemberCollide(D.r), d, g);
     const unsigned base = SR ? pcg_hash(self ^ salt) : 0u;
     // The store offsets equal the load offsets (each cell writes the slots it
     // read); left to itself the compiler keeps all 26 of them live through the
@@ -268,7 +343,7 @@ __device__ __forceinline__ void ensemble_pair_body(const T *__restrict__ src, T 
     const unsigned r01 = SR ? pair_bits_salted(self, salt) : 0u;
     T *Dp = dst + self;
     const unsigned plane = opaque(D.plane);  // (see ensemble_inplace_pair_body)
-    collide_from<F2, Pair<T>::kShift>(D.C, d, g, conserved<F2, Pair<T>::kShift>(d, g),
+    collide_from<F2, Pair<T>::kShift>(MemberCollide(D.r), d, g, conserved<F2, Pair<T>::kShift>(d, g),
                                       plane_sink([&](auto I, F2 v) {
                                           constexpr int q = decltype(I)::value;
                                           store2<T, SR>(Dp + q * plane, v, SR ? plane_bits<q>(r01) : 0u);
@@ -310,12 +385,11 @@ __device__ __forceinline__ void ensemble_inplace_pair_body(T *__restrict__ A, co
         pull_pair<kRuntimeWall, T>(A + self, LocalOffsets{D.plane}, P, theta_linear(y, D.inv_ny), d, g,
                                    D.wall != 1, D.wall == 2);
     const unsigned r01 = SR ? pair_bits_salted(self, salt) : 0u;
-    // phase 0: store addresses from a stride the compiler cannot see
-    // through, so that it recomputes them instead of keeping the load
-    // addresses live (phase 1 spills less without)
+    // store addresses from a stride the compiler cannot see through, so that
+    // it recomputes them instead of keeping the load addresses live
     T *Dp = A + self;
-    const SwappedOffsets SO{PHASE == 0 ? opaque(D.plane) : D.plane, static_cast<unsigned>(D.nx), D.nxy};
-    collide_from<F2, Pair<T>::kShift>(D.C, d, g, conserved<F2, Pair<T>::kShift>(d, g), plane_sink([&](auto I, F2 v) {
+    const SwappedOffsets SO{opaque(D.plane), static_cast<unsigned>(D.nx), D.nxy};
+    collide_from<F2, Pair<T>::kShift>(MemberCollide(D.r), d, g, conserved<F2, Pair<T>::kShift>(d, g), plane_sink([&](auto I, F2 v) {
         constexpr int q = decltype(I)::value;
         const unsigned r = SR ? plane_bits<q>(r01) : 0u;
         if constexpr (PHASE == 1) {
@@ -789,23 +863,7 @@ struct EDeviceGuard {
 
 void fill_rates_desc(lbm::CavityDesc &D, double nu, double alpha, double gbeta)
 {
-    const double s_nu = 1.0 / (3.0 * nu + 0.5);  // Eq. (26)
-    double s[19];
-    for (int k = 0; k < 19; ++k) s[k] = 1.0;
-    s[1] = 1.19;
-    s[2] = s[10] = s[12] = 1.4;
-    s[4] = s[6] = s[8] = 1.2;
-    s[16] = s[17] = s[18] = 1.98;
-    s[9] = s[11] = s[13] = s[14] = s[15] = s_nu;
-    for (int k = 0; k < 19; ++k) {
-        D.C.rs[k] = static_cast<float>(s[k] / lbm::m19_norm2(k));
-        D.C.ws[k] = static_cast<float>((1.0 - s[k]) / lbm::m19_norm2(k));
-    }
-    const double tau_a = 0.5 + 4.0 * alpha;  // Eq. (36), eps = 1/4
-    const double q[7] = {1.0, 1.0 / tau_a, 1.0 / tau_a, 1.0 / tau_a, 1.0, 1.0, 1.0};
-    for (int k = 0; k < 7; ++k) D.C.rq[k] = static_cast<float>(q[k] / lbm::m7_norm2(k));
-    D.C.gbeta = static_cast<float>(gbeta);
-    D.C.theta_ref = 0.0f;
+    lbm::fill_collide_params(D.C, nu, alpha, gbeta);
 }
 
 // Default tile width in threads: the widest of 128 / 64 / 32 not wider than
@@ -860,11 +918,37 @@ lbm::MemberStep member_step(const lbm::CavityDesc &D)
     M.plane = D.plane;
     M.nxy = D.nxy;
     M.inv_ny = D.inv_ny;
-    M.bx = D.bx;
+    M.bx_log2 = 0;
+    while ((2 << M.bx_log2) <= D.bx) ++M.bx_log2;  // bx is a power of two
     M.by = D.by;
     M.offset = D.offset;
-    M.C = D.C;
+    M.r.rs9 = D.C.rs[9];
+    M.r.rs11 = D.C.rs[11];
+    M.r.rs13 = D.C.rs[13];
+    M.r.ws9 = D.C.ws[9];
+    M.r.ws11 = D.C.ws[11];
+    M.r.ws13 = D.C.ws[13];
+    M.r.rq1 = D.C.rq[1];
+    M.r.gbeta = D.C.gbeta;
+    M.r.aniso = D.C.aniso;
     return M;
+}
+
+// The step kernels take every rate but the member's from kFixedRates; a
+// member whose parameters differ from those (which fill_collide_params rules
+// out) is refused rather than stepped with other rates.
+bool rates_match_the_fixed_table(const lbm::CollideParams &C)
+{
+    constexpr lbm::FixedRates F = lbm::fixed_rates();
+    for (int k = 0; k < 19; ++k) {
+        const int own = k == 9 ? 9 : k == 11 ? 11 : lbm::viscous_moment(k) ? 13 : -1;
+        const float rs = own >= 0 ? C.rs[own] : F.rs[k];
+        const float ws = own >= 0 ? C.ws[own] : F.ws[k];
+        if (rs != C.rs[k] || ws != C.ws[k]) return false;
+    }
+    for (int k = 0; k < 7; ++k)
+        if (((k >= 1 && k <= 3) ? C.rq[1] : F.rq[k]) != C.rq[k]) return false;
+    return C.theta_ref == 0.0f && C.aniso == 0;
 }
 
 // Split a block map (each member's blocks contiguous) into step launches of
@@ -1146,6 +1230,7 @@ dmrt_status dmrt_ensemble_create(dmrt_ensemble_t **out, int count, const dmrt_ca
         redmap.insert(redmap.end(), static_cast<size_t>(nred), c);
         red_start += nred;
         fill_rates_desc(D, nu, al, gb);
+        if (!rates_match_the_fixed_table(D.C)) return bail(DMRT_ERR_ARG);
         offset += plane * lbm::kPlanes;
         snap_off += 4 * cells;
         e->total_cells += cells;

@@ -241,6 +241,41 @@ struct CollideParams {
     int aniso;
 };
 
+// Relaxation rates of Eq. (26): s_k of the D3Q19 moments, except the five
+// set by the viscosity (viscous_moment(k): s_nu = 1/(3 nu + 1/2)); the
+// energy rates q_k of Eqs. (35),(36) are 1 except q_1..3 = 1/tau_a.
+__host__ __device__ constexpr bool viscous_moment(int k)
+{
+    return k == 9 || k == 11 || k == 13 || k == 14 || k == 15;
+}
+__host__ __device__ constexpr double mrt_rate(int k)
+{
+    return k == 1 ? 1.19
+         : (k == 2 || k == 10 || k == 12) ? 1.4
+         : (k == 4 || k == 6 || k == 8) ? 1.2
+         : (k >= 16) ? 1.98
+         : 1.0;  // conserved moments 0, 3, 5, 7 (unused)
+}
+
+// The collision parameters of a cavity with viscosity nu, diffusivity alpha
+// and buoyancy g beta dT (isotropic diffusion; aniso and qa are left alone).
+inline void fill_collide_params(CollideParams &C, double nu, double alpha, double gbeta)
+{
+    const double s_nu = 1.0 / (3.0 * nu + 0.5);  // Eq. (26)
+    for (int k = 0; k < 19; ++k) {
+        const double s = viscous_moment(k) ? s_nu : mrt_rate(k);
+        C.rs[k] = static_cast<float>(s / m19_norm2(k));
+        C.ws[k] = static_cast<float>((1.0 - s) / m19_norm2(k));
+    }
+    const double tau_a = 0.5 + 4.0 * alpha;  // Eq. (36), eps = 1/4, dt = dx = 1
+    for (int k = 0; k < 7; ++k) {
+        const double q = (k >= 1 && k <= 3) ? 1.0 / tau_a : 1.0;
+        C.rq[k] = static_cast<float>(q / m7_norm2(k));
+    }
+    C.gbeta = static_cast<float>(gbeta);
+    C.theta_ref = 0.0f;  // T_l = (T_h + T_c)/2
+}
+
 // Where the stored state sits in a population buffer.  The state S is the
 // set of post-collision populations of the last step, S_i(x) for every cell x
 // and direction i (planes 0..18 D3Q19, 19..25 D3Q7).

@@ -117,9 +117,13 @@ struct InPlace {
 // or one multiply; the force terms take S in their constant factors.
 // Multiplying by a power of two commutes with rounding, so every value is
 // exactly S times its value at kShift = 0.
-template <typename V, int kShift, typename Sink>
-__device__ __forceinline__ void collide_from(const CollideParams &C, const V d[19], const V g[7],
-                                             const Conserved<V> &m0, Sink out)
+//
+// C: a CollideParams, or any type with the same members (rs[k], ws[k],
+// rq[k], qa[k], gbeta, theta_ref, aniso), e.g. one that supplies the rates
+// that do not vary between cavities as constants.
+template <typename V, int kShift, typename Sink, typename Params = CollideParams>
+__device__ __forceinline__ void collide_from(const Params &C, const V d[19], const V g[7], const Conserved<V> &m0,
+                                             Sink out)
 {
     constexpr bool kScaled = kShift != 0;
     constexpr float kS = static_cast<float>(1u << kShift), kU = 1.0f / kS;
@@ -305,16 +309,17 @@ __device__ __forceinline__ void collide_from(const CollideParams &C, const V d[1
 
 // Collision of the pulled populations d, g, the results written back over
 // them (see collide_from).
-template <typename V, int kShift = 0>
-__device__ __forceinline__ void collide(const CollideParams &C, V d[19], V g[7])
+template <typename V, int kShift = 0, typename Params = CollideParams>
+__device__ __forceinline__ void collide(const Params &C, V d[19], V g[7])
 {
     collide_from<V, kShift>(C, d, g, conserved<V, kShift>(d, g), InPlace<V>{d, g});
 }
 
 // One cell per thread: the float form of collide().
-__device__ __forceinline__ void collide_cell(const CollideParams &C, float d[19], float g[7])
+template <typename Params = CollideParams>
+__device__ __forceinline__ void collide_cell(const Params &C, float d[19], float g[7])
 {
-    collide<float>(C, d, g);
+    collide<float, 0>(C, d, g);
 }
 
 // Neighbour / bounce-back offsets of the 26 planes: from the launch-parameter
