@@ -433,6 +433,133 @@ __global__ void __launch_bounds__(128, kEnsPairBlocks)
     ensemble_inplace_pair_body<T, SR, PHASE>(buf + D.offset, D, x0, y, z, salt);
 }
 
+// ---------------------------------------------------------------- shape groups
+
+// The members of one shape (nx, ny, nz) stepped together, two cells per
+// thread: the shape's offset tables are launch parameters, as a single
+// cavity's are (StepGeometry / InplaceGeometry, read as instruction
+// operands), and the grid is that of a single cavity with its z extent
+// repeated once per member, so a block finds its member as blockIdx.z / nz.
+// The member's slab, wall type and rates come from the launch's table.
+struct GroupMember {
+    long long offset;  // element offset of the member's slab in each buffer
+    MemberRates r;
+    int wall;
+};
+
+constexpr int kGroupMembers = 64;
+
+struct GroupTable {
+    int count;
+    GroupMember m[kGroupMembers];
+};
+static_assert(sizeof(GroupTable) + sizeof(InplaceGeometry) + 64 <= 32000, "launch parameters");
+
+// The block's member, z slab and pair (x0 even); false outside the shape.
+__device__ __forceinline__ bool group_pair(const StepGeometry &S, unsigned &m, int &x0, int &y, int &z)
+{
+    m = blockIdx.z / static_cast<unsigned>(S.nz);
+    z = static_cast<int>(blockIdx.z - m * static_cast<unsigned>(S.nz));
+    x0 = 2 * static_cast<int>(blockIdx.x * blockDim.x + threadIdx.x);
+    y = static_cast<int>(blockIdx.y * blockDim.y + threadIdx.y);
+    return x0 < S.nx && y < S.ny;
+}
+
+// srcb is not declared read-only (const __restrict__): through the
+// read-only load path this kernel ran 4 % slower (16 members of 96^3, BF16:
+// 286 against 275 us per step), while the single-cavity kernel's speed did
+// not depend on it.
+template <typename T, bool SR>
+__global__ void __launch_bounds__(128, kEnsPairBlocks)
+    ensemble_group_pair_kernel(const T *srcb, T *dstb, const StepGeometry S, long long counter_at,
+                               const __grid_constant__ GroupTable P)
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;");
+    unsigned salt = 0;
+    if constexpr (SR) {
+        const unsigned step = *reinterpret_cast<const unsigned *>(srcb + counter_at);
+        if ((blockIdx.x | blockIdx.y | blockIdx.z | threadIdx.x | threadIdx.y) == 0)
+            *reinterpret_cast<unsigned *>(dstb + counter_at) = step + 1u;
+        salt = pcg_hash(step);
+    }
+    unsigned m;
+    int x0, y, z;
+    if (!group_pair(S, m, x0, y, z)) return;
+    const GroupMember &M = P.m[m];
+    const unsigned self = (static_cast<unsigned>(z) * S.ny + y) * S.nx + x0;
+    const PairFaces faces{x0 == 0, x0 + 2 == S.nx, y == 0, y == S.ny - 1, z == 0, z == S.nz - 1};
+    F2 d[19], g[7];
+    pull_pair<kRuntimeWall, T>(srcb + M.offset + self, TableOffsets{S}, faces, theta_linear(y, S.inv_ny), d, g,
+                               M.wall != 1, M.wall == 2);
+    const unsigned r01 = SR ? pair_bits_salted(self, salt) : 0u;
+    T *Dp = dstb + M.offset + self;
+    const unsigned plane = opaque(S.plane);  // (see ensemble_inplace_pair_body)
+    collide_from<F2, Pair<T>::kShift>(MemberCollide(M.r), d, g, conserved<F2, Pair<T>::kShift>(d, g),
+                                      plane_sink([&](auto I, F2 v) {
+                                          constexpr int q = decltype(I)::value;
+                                          store2<T, SR>(Dp + q * plane, v, SR ? plane_bits<q>(r01) : 0u);
+                                      }));
+}
+
+// In-place scheme (step_inplace_pair_kernel's two phases) for a shape group.
+template <typename T, bool SR, int PHASE>
+__global__ void __launch_bounds__(128, kEnsPairBlocks)
+    ensemble_group_inplace_pair_kernel(T *__restrict__ buf, const InplaceGeometry SI, long long counter_at,
+                                       const __grid_constant__ GroupTable P)
+{
+    const StepGeometry &S = SI.load;
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;");
+    unsigned salt = 0;
+    if constexpr (SR) {
+        unsigned *ctr = reinterpret_cast<unsigned *>(buf + counter_at);
+        const unsigned step = ctr[PHASE];
+        if ((blockIdx.x | blockIdx.y | blockIdx.z | threadIdx.x | threadIdx.y) == 0) ctr[PHASE ^ 1] = step + 1u;
+        salt = pcg_hash(step);
+    }
+    unsigned m;
+    int x0, y, z;
+    if (!group_pair(S, m, x0, y, z)) return;
+    const GroupMember &M = P.m[m];
+    T *A = buf + M.offset;
+    const unsigned self = (static_cast<unsigned>(z) * S.ny + y) * S.nx + x0;
+    const PairFaces P2{x0 == 0, x0 + 2 == S.nx, y == 0, y == S.ny - 1, z == 0, z == S.nz - 1};
+    F2 d[19], g[7];
+    if constexpr (PHASE == 0)
+        pull_pair<kRuntimeWall, T>(A + self, TableOffsets{S}, P2, theta_linear(y, S.inv_ny), d, g, M.wall != 1,
+                                   M.wall == 2);
+    else
+        pull_pair<kRuntimeWall, T>(A + self, LocalOffsets{S.plane}, P2, theta_linear(y, S.inv_ny), d, g,
+                                   M.wall != 1, M.wall == 2);
+    const unsigned r01 = SR ? pair_bits_salted(self, salt) : 0u;
+    T *Dp = A + self;
+    const unsigned plane = opaque(S.plane);
+    collide_from<F2, Pair<T>::kShift>(MemberCollide(M.r), d, g, conserved<F2, Pair<T>::kShift>(d, g),
+                                      plane_sink([&](auto I, F2 v) {
+        constexpr int q = decltype(I)::value;
+        const unsigned r = SR ? plane_bits<q>(r01) : 0u;
+        if constexpr (PHASE == 1) {
+            store2<T, SR>(Dp + plane_opp<q>() * plane, v, r);
+        } else {
+            constexpr int ex = plane_ex<q>(), ey = plane_ey<q>(), ez = plane_ez<q>();
+            bool lyz = false;  // the link leaves through a y or z face
+            if constexpr (ey == 1) lyz = lyz || P2.yhi;
+            if constexpr (ey == -1) lyz = lyz || P2.ylo;
+            if constexpr (ez == 1) lyz = lyz || P2.zhi;
+            if constexpr (ez == -1) lyz = lyz || P2.zlo;
+            const unsigned sn = static_cast<unsigned>(SI.sn[q]), sb = static_cast<unsigned>(SI.sb[q]);
+            if constexpr (ex == 0) {
+                store2<T, SR>(Dp + (lyz ? sb : sn), v, r);
+            } else {
+                const bool l0 = lyz || (ex == -1 && P2.xlo);
+                const bool l1 = lyz || (ex == 1 && P2.xhi);
+                store_split<T, SR>(Dp + (l0 ? sb : sn), (Dp + (l1 ? sb : sn)) + 1, v, r);
+            }
+        }
+    }));
+}
+
 // ---------------------------------------------------------------- residual
 
 __device__ __forceinline__ Geometry geometry_of(const CavityDesc &D, int layout)
@@ -724,6 +851,50 @@ cudaError_t launch_ensemble_inplace(int storage, bool stochastic, void *buf, int
     return cudaGetLastError();
 }
 
+// One shape group's chunk: grid (tiles along x, tiles along y, nz * members)
+// of bx x (128 / bx) threads; phase < 0: two-buffer step from src to dst,
+// else the in-place phase on src.
+cudaError_t launch_ensemble_group(int storage, bool stochastic, const void *src, void *dst, int phase,
+                                  const InplaceGeometry &SI, const GroupTable &P, int bx, long long counter_at,
+                                  cudaStream_t s, bool pdl)
+{
+    const StepGeometry &S = SI.load;
+    const int by = 128 / bx;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(static_cast<unsigned>((S.nx / 2 + bx - 1) / bx), static_cast<unsigned>((S.ny + by - 1) / by),
+                       static_cast<unsigned>(S.nz) * static_cast<unsigned>(P.count));
+    cfg.blockDim = dim3(bx, by, 1);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    cudaError_t e = dispatch(1, storage, [&](auto, auto *tp) {
+        using T = std::remove_pointer_t<decltype(tp)>;
+        if (phase < 0) {
+            const T *a = static_cast<const T *>(src);
+            T *b = static_cast<T *>(dst);
+            if constexpr (!std::is_same_v<T, float>) {
+                if (stochastic)
+                    return cudaLaunchKernelEx(&cfg, ensemble_group_pair_kernel<T, true>, a, b, S, counter_at, P);
+            }
+            return cudaLaunchKernelEx(&cfg, ensemble_group_pair_kernel<T, false>, a, b, S, counter_at, P);
+        }
+        T *A = static_cast<T *>(const_cast<void *>(src));
+        auto go = [&](auto kernel) { return cudaLaunchKernelEx(&cfg, kernel, A, SI, counter_at, P); };
+        if constexpr (!std::is_same_v<T, float>) {
+            if (stochastic)
+                return phase == 0 ? go(ensemble_group_inplace_pair_kernel<T, true, 0>)
+                                  : go(ensemble_group_inplace_pair_kernel<T, true, 1>);
+        }
+        return phase == 0 ? go(ensemble_group_inplace_pair_kernel<T, false, 0>)
+                          : go(ensemble_group_inplace_pair_kernel<T, false, 1>);
+    });
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
 // points: the count of residual points (device), followed by the finishing
 // kernel's ticket word.
 cudaError_t launch_ensemble_residual(int storage, const void *src, int layout, const CavityDesc *descs,
@@ -779,10 +950,20 @@ struct dmrt_ensemble {
     lbm::BlockTile *d_blockmap = nullptr;
     long long step_blocks = 0;
     size_t blockmap_cap = 0;
-    // The step launches: the members of each, by value (its parameters), and
-    // its range of the block map.
+    // The step launches of one cell per thread: the members of each, by
+    // value (its parameters), and its range of the block map.
     std::vector<lbm::StepTable> tables;
     std::vector<long long> table_first, table_blocks;
+    // Two cells per thread: the members grouped by shape, one launch per
+    // chunk of a group (geometry of the shape, tile width, member table).
+    struct GroupChunk {
+        int group;
+        lbm::GroupTable table;
+    };
+    std::vector<lbm::InplaceGeometry> group_geom;
+    std::vector<int> group_bx;
+    std::vector<GroupChunk> chunks;
+    bool grouped = false;  // steps by shape groups (else by the tables)
     int *d_redmap = nullptr;
     long long red_blocks = 0;
     int threads = 128;
@@ -819,6 +1000,8 @@ struct dmrt_ensemble {
 namespace {
 
 constexpr long kEnsMaxGraphSteps = 1000;
+// Most launches per step for which shape groups replace the tables.
+constexpr size_t kMaxGroupLaunches = 8;
 
 dmrt_status efail(dmrt_ensemble_t *e, dmrt_status st, const char *fmt, ...)
     __attribute__((format(printf, 3, 4)));
@@ -871,7 +1054,18 @@ void fill_rates_desc(lbm::CavityDesc &D, double nu, double alpha, double gbeta)
 // per thread a row holds nx / 2 threads, and tiles of 16 are allowed too.
 int default_bx(int nx, int threads, bool pairs)
 {
-    const int units = pairs ? nx / 2 : nx;
+    if (pairs) {
+        // as a single cavity's paired kernel: the tile width that launches the
+        // fewest idle threads along a row, the widest of equals
+        const int units = nx / 2;
+        int bx = 16, slots = (units + 15) / 16 * 16;
+        for (int cand : {32, 64}) {
+            const int c = (units + cand - 1) / cand * cand;
+            if (c <= slots && cand <= threads) bx = cand, slots = c;
+        }
+        return bx;
+    }
+    const int units = nx;
     const int q = pairs ? 16 : 32;
     const int w = (units + q - 1) / q * q;
     int bx = q;
@@ -907,6 +1101,22 @@ void drop_graphs(dmrt_ensemble_t *e)
         }
 }
 
+lbm::MemberRates member_rates(const lbm::CavityDesc &D)
+{
+    lbm::MemberRates r;
+    std::memset(&r, 0, sizeof r);
+    r.rs9 = D.C.rs[9];
+    r.rs11 = D.C.rs[11];
+    r.rs13 = D.C.rs[13];
+    r.ws9 = D.C.ws[9];
+    r.ws11 = D.C.ws[11];
+    r.ws13 = D.C.ws[13];
+    r.rq1 = D.C.rq[1];
+    r.gbeta = D.C.gbeta;
+    r.aniso = D.C.aniso;
+    return r;
+}
+
 lbm::MemberStep member_step(const lbm::CavityDesc &D)
 {
     lbm::MemberStep M;
@@ -922,15 +1132,7 @@ lbm::MemberStep member_step(const lbm::CavityDesc &D)
     while ((2 << M.bx_log2) <= D.bx) ++M.bx_log2;  // bx is a power of two
     M.by = D.by;
     M.offset = D.offset;
-    M.r.rs9 = D.C.rs[9];
-    M.r.rs11 = D.C.rs[11];
-    M.r.rs13 = D.C.rs[13];
-    M.r.ws9 = D.C.ws[9];
-    M.r.ws11 = D.C.ws[11];
-    M.r.ws13 = D.C.ws[13];
-    M.r.rq1 = D.C.rq[1];
-    M.r.gbeta = D.C.gbeta;
-    M.r.aniso = D.C.aniso;
+    M.r = member_rates(D);
     return M;
 }
 
@@ -979,11 +1181,72 @@ void build_step_tables(dmrt_ensemble_t *e, const std::vector<lbm::BlockTile> &ma
     }
 }
 
+// Group the members of a block map (two cells per thread) by shape, in order
+// of first appearance, and split each group into launches of at most
+// kGroupMembers members (and at most 65535 z blocks).
+void build_groups(dmrt_ensemble_t *e, const std::vector<lbm::BlockTile> &map)
+{
+    e->group_geom.clear();
+    e->group_bx.clear();
+    e->chunks.clear();
+    std::vector<std::vector<int>> lists;
+    std::map<std::vector<int>, int> index;
+    for (size_t b = 0; b < map.size(); ++b) {
+        const int c = map[b].member;
+        if (b > 0 && map[b - 1].member == c) continue;
+        const lbm::CavityDesc &D = e->desc[c];
+        const std::vector<int> key{D.nx, D.ny, D.nz};
+        auto it = index.find(key);
+        if (it == index.end()) {
+            it = index.emplace(key, static_cast<int>(lists.size())).first;
+            lists.emplace_back();
+        }
+        lists[it->second].push_back(c);
+    }
+    for (size_t g = 0; g < lists.size(); ++g) {
+        const lbm::CavityDesc &D = e->desc[lists[g].front()];
+        lbm::Geometry G{};
+        G.nx = D.nx;
+        G.ny = D.ny;
+        G.nz = D.nz;
+        G.plane = D.plane;
+        G.inv_ny = D.inv_ny;
+        lbm::InplaceGeometry SI{};
+        if (e->inplace) lbm::fill_inplace_geometry(G, SI);
+        else lbm::fill_step_geometry(G, SI.load);
+        e->group_geom.push_back(SI);
+        e->group_bx.push_back(D.bx);
+        const size_t per = static_cast<size_t>(std::min(lbm::kGroupMembers, 65535 / D.nz));
+        for (size_t i = 0; i < lists[g].size(); i += per) {
+            e->chunks.emplace_back();
+            auto &ch = e->chunks.back();
+            ch.group = static_cast<int>(g);
+            std::memset(&ch.table, 0, sizeof ch.table);
+            const size_t n = std::min(per, lists[g].size() - i);
+            ch.table.count = static_cast<int>(n);
+            for (size_t k = 0; k < n; ++k) {
+                const lbm::CavityDesc &M = e->desc[lists[g][i + k]];
+                ch.table.m[k].offset = M.offset;
+                ch.table.m[k].r = member_rates(M);
+                ch.table.m[k].wall = M.wall;
+            }
+        }
+    }
+}
+
 dmrt_status upload_layout(dmrt_ensemble_t *e, const std::vector<lbm::BlockTile> &map)
 {
     // captured graphs hold the previous launches' tables
     drop_graphs(e);
     build_step_tables(e, map);
+    // Shape groups where they take few launches: each launch has a ramp and
+    // a drain, so an ensemble of many distinct shapes keeps the tables (one
+    // launch per 64 members, whatever their shapes).
+    e->grouped = false;
+    if (e->pairs) {
+        build_groups(e, map);
+        e->grouped = e->chunks.size() <= kMaxGroupLaunches;
+    }
     if (map.size() > e->blockmap_cap) {
         if (e->d_blockmap) cudaFree(e->d_blockmap);
         e->d_blockmap = nullptr;
@@ -1031,6 +1294,16 @@ cudaError_t launch_one_step(dmrt_ensemble_t *e, int from, bool res = false)
     if (res) {
         const cudaError_t c = launch_residual_point(e, from);
         if (c != cudaSuccess) return c;
+    }
+    if (e->grouped) {
+        for (const auto &ch : e->chunks) {
+            const cudaError_t c = lbm::launch_ensemble_group(
+                e->storage, e->stochastic, e->buf[e->inplace ? 0 : from], e->inplace ? nullptr : e->buf[from ^ 1],
+                e->inplace ? from : -1, e->group_geom[ch.group], ch.table, e->group_bx[ch.group], e->total_elems,
+                e->stream, e->use_pdl);
+            if (c != cudaSuccess) return c;
+        }
+        return cudaSuccess;
     }
     for (size_t i = 0; i < e->tables.size(); ++i) {
         const lbm::BlockTile *map = e->d_blockmap + e->table_first[i];
@@ -1102,7 +1375,7 @@ dmrt_status run_steps(dmrt_ensemble_t *e, long n)
             ph ^= 1;
         }
         e->steps += chunk;
-        const long per_step = static_cast<long>(e->tables.size());  // launches per step
+        const long per_step = static_cast<long>(e->grouped ? e->chunks.size() : e->tables.size());  // launches
         e->step_launches += chunk * per_step;
         e->total_launches += chunk * per_step + (took ? 2 : 0);
         if (took && e->snaps < 2) e->snaps++;
@@ -1423,7 +1696,7 @@ dmrt_status dmrt_ensemble_autotune(dmrt_ensemble_t *e, int trials, char *report,
     int best_threads = e->threads;
     float best_total = INFINITY;
     std::vector<int> best_bx(e->count);
-    std::string rep;
+    std::string rep, cand_rep;
     for (int threads : {128, 256}) {
         if (DMRT_ENS_INPLACE_BLOCK128 && e->inplace && threads != 128) continue;
         if (e->pairs && threads != 128) continue;  // the paired kernels are built for 128
@@ -1439,6 +1712,9 @@ dmrt_status dmrt_ensemble_autotune(dmrt_ensemble_t *e, int trials, char *report,
                 float ms = 0.f;
                 dmrt_status st = time_layout(g.second, &ms);
                 if (st != DMRT_OK) return st;
+                char c_line[64];
+                snprintf(c_line, sizeof c_line, " nx%d/t%d/bx%d:%.1fus", g.first, threads, bx, ms * 1e3f);
+                cand_rep += c_line;
                 if (ms < best_ms) {
                     best_ms = ms;
                     best = bx;
@@ -1470,8 +1746,8 @@ dmrt_status dmrt_ensemble_autotune(dmrt_ensemble_t *e, int trials, char *report,
     cudaEventDestroy(t1);
     if (st != DMRT_OK) return st;
     char line[64];
-    snprintf(line, sizeof line, "chosen threads=%d", best_threads);
-    rep += line;
+    snprintf(line, sizeof line, "chosen threads=%d;", best_threads);
+    rep += line + cand_rep;
     if (report && report_len > 0) snprintf(report, static_cast<size_t>(report_len), "%s", rep.c_str());
     return DMRT_OK;
 }

@@ -323,3 +323,26 @@ def test_ensemble_of_more_members_than_one_launch_holds(dm, streaming, even):
         assert np.array_equal(fe, fs) and np.array_equal(ge, gs), k
     r = np.asarray(ens.residual())
     assert np.all(np.isfinite(r))
+
+
+@pytest.mark.parametrize("storage", [0, 1], ids=["f32", "bf16"])
+@pytest.mark.parametrize("streaming", [0, 1], ids=["ab", "inplace"])
+def test_shape_groups_of_more_members_than_one_launch_holds(dm, streaming, storage):
+    """With few distinct shapes and even rows, members are stepped by shape
+    groups (the shape's offset tables in the launch parameters, the z extent
+    repeated per member).  130 members of two interleaved shapes take two
+    launches per shape and step; members of every launch stay bitwise equal
+    to single handles."""
+    shapes = [(10, 8, 6), (12, 10, 9)]
+    cav = [{"grid": shapes[k % 2], "Ra": 10 ** (3 + 2 * k / 130), "wall": 1 + k % 3} for k in range(130)]
+    ens = dm.Ensemble(cav, storage=storage, streaming=streaming, residual_interval=5)
+    dm.dmrt_ensemble_get_stats(ens.e, reset=True)
+    ens.step(23)
+    assert dm.dmrt_ensemble_get_stats(ens.e)["step_launches"] == 4 * 23
+    for k in (0, 1, 126, 127, 128, 129):
+        m = cav[k]
+        single = dm.Cavity(m["grid"], m["Ra"], wall_type=m["wall"], storage=storage, streaming=streaming)
+        single.step(23)
+        fe, ge = ens.populations(k)
+        fs, gs = single.populations()
+        assert np.array_equal(fe, fs) and np.array_equal(ge, gs), k
