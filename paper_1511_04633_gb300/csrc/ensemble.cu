@@ -455,6 +455,35 @@ struct GroupTable {
 };
 static_assert(sizeof(GroupTable) + sizeof(InplaceGeometry) + 64 <= 32000, "launch parameters");
 
+// Step counters of a group launch (stochastic rounding): the kernel draws
+// its bits from the step number *read and writes that number plus one to
+// *write (and to *tail if not null).  Run one after another, the launches
+// use the buffer's own counters; run as concurrent chains (one per launch
+// of a step, within a captured interval), each chain keeps its own pair and
+// also keeps the buffer's counter current.
+struct GroupCounters {
+    const unsigned *read;
+    unsigned *write;
+    unsigned *tail;
+};
+
+__device__ __forceinline__ unsigned group_step(const GroupCounters &K)
+{
+    const unsigned step = *K.read;
+    if ((blockIdx.x | blockIdx.y | blockIdx.z | threadIdx.x | threadIdx.y) == 0) {
+        *K.write = step + 1u;
+        if (K.tail) *K.tail = step + 1u;
+    }
+    return step;
+}
+
+// Copy a buffer's step counter into word `from` of each chain's pair (the
+// start of a concurrently captured interval).
+__global__ void ensemble_counter_sync(const unsigned *__restrict__ tail, unsigned *__restrict__ pairs, int n, int from)
+{
+    if (threadIdx.x < static_cast<unsigned>(n)) pairs[2 * threadIdx.x + from] = *tail;
+}
+
 // The block's member, z slab and pair (x0 even); false outside the shape.
 __device__ __forceinline__ bool group_pair(const StepGeometry &S, unsigned &m, int &x0, int &y, int &z)
 {
@@ -471,18 +500,13 @@ __device__ __forceinline__ bool group_pair(const StepGeometry &S, unsigned &m, i
 // not depend on it.
 template <typename T, bool SR>
 __global__ void __launch_bounds__(128, kEnsPairBlocks)
-    ensemble_group_pair_kernel(const T *srcb, T *dstb, const StepGeometry S, long long counter_at,
+    ensemble_group_pair_kernel(const T *srcb, T *dstb, const StepGeometry S, const GroupCounters K,
                                const __grid_constant__ GroupTable P)
 {
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;");
     unsigned salt = 0;
-    if constexpr (SR) {
-        const unsigned step = *reinterpret_cast<const unsigned *>(srcb + counter_at);
-        if ((blockIdx.x | blockIdx.y | blockIdx.z | threadIdx.x | threadIdx.y) == 0)
-            *reinterpret_cast<unsigned *>(dstb + counter_at) = step + 1u;
-        salt = pcg_hash(step);
-    }
+    if constexpr (SR) salt = pcg_hash(group_step(K));
     unsigned m;
     int x0, y, z;
     if (!group_pair(S, m, x0, y, z)) return;
@@ -505,19 +529,14 @@ __global__ void __launch_bounds__(128, kEnsPairBlocks)
 // In-place scheme (step_inplace_pair_kernel's two phases) for a shape group.
 template <typename T, bool SR, int PHASE>
 __global__ void __launch_bounds__(128, kEnsPairBlocks)
-    ensemble_group_inplace_pair_kernel(T *__restrict__ buf, const InplaceGeometry SI, long long counter_at,
+    ensemble_group_inplace_pair_kernel(T *__restrict__ buf, const InplaceGeometry SI, const GroupCounters K,
                                        const __grid_constant__ GroupTable P)
 {
     const StepGeometry &S = SI.load;
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;");
     unsigned salt = 0;
-    if constexpr (SR) {
-        unsigned *ctr = reinterpret_cast<unsigned *>(buf + counter_at);
-        const unsigned step = ctr[PHASE];
-        if ((blockIdx.x | blockIdx.y | blockIdx.z | threadIdx.x | threadIdx.y) == 0) ctr[PHASE ^ 1] = step + 1u;
-        salt = pcg_hash(step);
-    }
+    if constexpr (SR) salt = pcg_hash(group_step(K));
     unsigned m;
     int x0, y, z;
     if (!group_pair(S, m, x0, y, z)) return;
@@ -855,7 +874,7 @@ cudaError_t launch_ensemble_inplace(int storage, bool stochastic, void *buf, int
 // of bx x (128 / bx) threads; phase < 0: two-buffer step from src to dst,
 // else the in-place phase on src.
 cudaError_t launch_ensemble_group(int storage, bool stochastic, const void *src, void *dst, int phase,
-                                  const InplaceGeometry &SI, const GroupTable &P, int bx, long long counter_at,
+                                  const InplaceGeometry &SI, const GroupTable &P, int bx, const GroupCounters &K,
                                   cudaStream_t s, bool pdl)
 {
     const StepGeometry &S = SI.load;
@@ -877,12 +896,12 @@ cudaError_t launch_ensemble_group(int storage, bool stochastic, const void *src,
             T *b = static_cast<T *>(dst);
             if constexpr (!std::is_same_v<T, float>) {
                 if (stochastic)
-                    return cudaLaunchKernelEx(&cfg, ensemble_group_pair_kernel<T, true>, a, b, S, counter_at, P);
+                    return cudaLaunchKernelEx(&cfg, ensemble_group_pair_kernel<T, true>, a, b, S, K, P);
             }
-            return cudaLaunchKernelEx(&cfg, ensemble_group_pair_kernel<T, false>, a, b, S, counter_at, P);
+            return cudaLaunchKernelEx(&cfg, ensemble_group_pair_kernel<T, false>, a, b, S, K, P);
         }
         T *A = static_cast<T *>(const_cast<void *>(src));
-        auto go = [&](auto kernel) { return cudaLaunchKernelEx(&cfg, kernel, A, SI, counter_at, P); };
+        auto go = [&](auto kernel) { return cudaLaunchKernelEx(&cfg, kernel, A, SI, K, P); };
         if constexpr (!std::is_same_v<T, float>) {
             if (stochastic)
                 return phase == 0 ? go(ensemble_group_inplace_pair_kernel<T, true, 0>)
@@ -892,6 +911,12 @@ cudaError_t launch_ensemble_group(int storage, bool stochastic, const void *src,
                           : go(ensemble_group_inplace_pair_kernel<T, false, 1>);
     });
     if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_counter_sync(const unsigned *tail, unsigned *pairs, int n, int from, cudaStream_t s)
+{
+    ensemble_counter_sync<<<1, 32, 0, s>>>(tail, pairs, n, from);
     return cudaGetLastError();
 }
 
@@ -964,6 +989,14 @@ struct dmrt_ensemble {
     std::vector<int> group_bx;
     std::vector<GroupChunk> chunks;
     bool grouped = false;  // steps by shape groups (else by the tables)
+    // Captured intervals of shape groups run one chain of launches per
+    // chunk, concurrently (side streams, fork / join events), each with its
+    // own pair of step counters.
+    static constexpr int kMaxChains = 8;
+    cudaStream_t side[kMaxChains] = {};
+    cudaEvent_t fork_ev = nullptr, join_ev[kMaxChains] = {};
+    unsigned *chain_ctr = nullptr;  // 2 words per chain
+    int graph_extra = 0;            // kernels a captured interval adds (counter sync)
     int *d_redmap = nullptr;
     long long red_blocks = 0;
     int threads = 128;
@@ -1001,7 +1034,7 @@ namespace {
 
 constexpr long kEnsMaxGraphSteps = 1000;
 // Most launches per step for which shape groups replace the tables.
-constexpr size_t kMaxGroupLaunches = 8;
+constexpr size_t kMaxGroupLaunches = dmrt_ensemble::kMaxChains;
 
 dmrt_status efail(dmrt_ensemble_t *e, dmrt_status st, const char *fmt, ...)
     __attribute__((format(printf, 3, 4)));
@@ -1286,6 +1319,35 @@ cudaError_t launch_residual_point(dmrt_ensemble_t *e, int from)
                                          e->stream);
 }
 
+// The step counter that a step from state `b` reads (A-B: the tail of
+// buf[b]; in place: word b of the buffer's tail).
+unsigned *step_counter(dmrt_ensemble_t *e, int b)
+{
+    char *base = static_cast<char *>(e->buf[e->inplace ? 0 : b]) +
+                 static_cast<size_t>(e->total_elems) * lbm::storage_bytes(e->storage);
+    return reinterpret_cast<unsigned *>(base) + (e->inplace ? b : 0);
+}
+
+// Chunk i of the shape groups, one step from state `from` on stream s; in a
+// chain (concurrent capture) with the chain's own counters.
+cudaError_t launch_group_chunk(dmrt_ensemble_t *e, size_t i, int from, cudaStream_t s, bool chain)
+{
+    const auto &ch = e->chunks[i];
+    lbm::GroupCounters K;
+    if (chain) {
+        K.read = e->chain_ctr + 2 * i + from;
+        K.write = e->chain_ctr + 2 * i + (from ^ 1);
+        K.tail = step_counter(e, from ^ 1);
+    } else {
+        K.read = step_counter(e, from);
+        K.write = step_counter(e, from ^ 1);
+        K.tail = nullptr;
+    }
+    return lbm::launch_ensemble_group(e->storage, e->stochastic, e->buf[e->inplace ? 0 : from],
+                                      e->inplace ? nullptr : e->buf[from ^ 1], e->inplace ? from : -1,
+                                      e->group_geom[ch.group], ch.table, e->group_bx[ch.group], K, s, e->use_pdl);
+}
+
 // One step of every member from state `from`; with `res` a residual point of
 // that state is taken first (the points are the states that the last step
 // of every K-step interval starts from, as in a single cavity).
@@ -1296,11 +1358,8 @@ cudaError_t launch_one_step(dmrt_ensemble_t *e, int from, bool res = false)
         if (c != cudaSuccess) return c;
     }
     if (e->grouped) {
-        for (const auto &ch : e->chunks) {
-            const cudaError_t c = lbm::launch_ensemble_group(
-                e->storage, e->stochastic, e->buf[e->inplace ? 0 : from], e->inplace ? nullptr : e->buf[from ^ 1],
-                e->inplace ? from : -1, e->group_geom[ch.group], ch.table, e->group_bx[ch.group], e->total_elems,
-                e->stream, e->use_pdl);
+        for (size_t i = 0; i < e->chunks.size(); ++i) {
+            const cudaError_t c = launch_group_chunk(e, i, from, e->stream, false);
             if (c != cudaSuccess) return c;
         }
         return cudaSuccess;
@@ -1319,18 +1378,84 @@ cudaError_t launch_one_step(dmrt_ensemble_t *e, int from, bool res = false)
     return cudaSuccess;
 }
 
+// Side streams, events and chain counters for concurrent chains.
+bool ensure_chains(dmrt_ensemble_t *e)
+{
+    if (!e->chain_ctr) {
+        if (cudaMalloc(&e->chain_ctr, 2 * dmrt_ensemble::kMaxChains * sizeof(unsigned)) != cudaSuccess) {
+            cudaGetLastError();
+            e->chain_ctr = nullptr;
+            return false;
+        }
+        e->device_bytes += 2 * dmrt_ensemble::kMaxChains * sizeof(unsigned);
+    }
+    if (!e->fork_ev && cudaEventCreateWithFlags(&e->fork_ev, cudaEventDisableTiming) != cudaSuccess) return false;
+    for (int i = 0; i < dmrt_ensemble::kMaxChains; ++i) {
+        if (!e->side[i] && cudaStreamCreateWithFlags(&e->side[i], cudaStreamNonBlocking) != cudaSuccess) return false;
+        if (!e->join_ev[i] && cudaEventCreateWithFlags(&e->join_ev[i], cudaEventDisableTiming) != cudaSuccess)
+            return false;
+    }
+    return true;
+}
+
+// A whole interval as concurrent chains: the chunks of the shape groups are
+// independent within a step, so chunk i of step s only waits for chunk i of
+// step s - 1 (its own stream); the chains meet before the residual point
+// (taken before the last step, on the main stream) and at the end.  A chain
+// draws the same step numbers as the one-after-another launches.
+bool capture_chains(dmrt_ensemble_t *e, int start)
+{
+    const int n = static_cast<int>(e->chunks.size());
+    int cur = start;
+    auto fork = [&]() {
+        if (cudaEventRecord(e->fork_ev, e->stream) != cudaSuccess) return false;
+        for (int i = 0; i < n; ++i)
+            if (cudaStreamWaitEvent(e->side[i], e->fork_ev, 0) != cudaSuccess) return false;
+        return true;
+    };
+    auto join = [&]() {
+        for (int i = 0; i < n; ++i) {
+            if (cudaEventRecord(e->join_ev[i], e->side[i]) != cudaSuccess) return false;
+            if (cudaStreamWaitEvent(e->stream, e->join_ev[i], 0) != cudaSuccess) return false;
+        }
+        return true;
+    };
+    e->graph_extra = 0;
+    if (e->stochastic) {
+        if (lbm::launch_counter_sync(step_counter(e, cur), e->chain_ctr, n, cur, e->stream) != cudaSuccess)
+            return false;
+        e->graph_extra = 1;
+    }
+    if (!fork()) return false;
+    for (long s = 0; s < e->K; ++s) {
+        if (s == e->K - 1) {
+            if (!join() || launch_residual_point(e, cur) != cudaSuccess || !fork()) return false;
+        }
+        for (int i = 0; i < n; ++i)
+            if (launch_group_chunk(e, static_cast<size_t>(i), cur, e->side[i], true) != cudaSuccess) return false;
+        cur ^= 1;
+    }
+    return join();
+}
+
 bool capture_interval(dmrt_ensemble_t *e, int start)
 {
     if (e->stream == nullptr) return false;
+    const bool chains = e->grouped && e->chunks.size() > 1 && ensure_chains(e);
     if (cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
     int cur = start;
     bool ok = true;
-    for (long s = 0; s < e->K && ok; ++s) {
-        ok = launch_one_step(e, cur, s == e->K - 1) == cudaSuccess;
-        cur ^= 1;
+    if (chains) {
+        ok = capture_chains(e, start);
+    } else {
+        e->graph_extra = 0;
+        for (long s = 0; s < e->K && ok; ++s) {
+            ok = launch_one_step(e, cur, s == e->K - 1) == cudaSuccess;
+            cur ^= 1;
+        }
     }
     cudaGraph_t graph = nullptr;
     ok = (cudaStreamEndCapture(e->stream, &graph) == cudaSuccess) && ok && graph;
@@ -1377,7 +1502,7 @@ dmrt_status run_steps(dmrt_ensemble_t *e, long n)
         e->steps += chunk;
         const long per_step = static_cast<long>(e->grouped ? e->chunks.size() : e->tables.size());  // launches
         e->step_launches += chunk * per_step;
-        e->total_launches += chunk * per_step + (took ? 2 : 0);
+        e->total_launches += chunk * per_step + (took ? 2 : 0) + (graphed ? e->graph_extra : 0);
         if (took && e->snaps < 2) e->snaps++;
         if (e->timing) {
             ECK(e, cudaEventRecord(e1, e->stream), "cudaEventRecord");
@@ -1575,6 +1700,12 @@ void dmrt_ensemble_destroy(dmrt_ensemble_t *e)
     if (e->d_redmap) cudaFree(e->d_redmap);
     if (e->staging) cudaFree(e->staging);
     if (e->own) cudaStreamDestroy(e->own);
+    for (int i = 0; i < dmrt_ensemble::kMaxChains; ++i) {
+        if (e->side[i]) cudaStreamDestroy(e->side[i]);
+        if (e->join_ev[i]) cudaEventDestroy(e->join_ev[i]);
+    }
+    if (e->fork_ev) cudaEventDestroy(e->fork_ev);
+    if (e->chain_ctr) cudaFree(e->chain_ctr);
     delete e;
 }
 
