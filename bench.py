@@ -628,8 +628,9 @@ def measure_cavity(dmrt, torch, stream, gpu, *, grid, wall, ra, storage, inner, 
 def run_configs(dmrt, torch, stream, gpu, steps=5, warmup=3):
     """Outside the timed region: short CUDA-event-timed measurements of the
     reduced-storage 256^3 cavity (Type 3, Ra = 1e6, BF16 and FP16) and of the
-    64-member seeded ensemble (FP32 and BF16, against the same cavities as
-    separate handles), each with its own clock samples."""
+    64-member seeded ensemble (FP32 and BF16 with two buffers, BF16 in place,
+    against the same cavities as separate handles), each with its own clock
+    samples."""
     from paper_1511_04633_gb300 import inputs
 
     out = {}
@@ -637,10 +638,11 @@ def run_configs(dmrt, torch, stream, gpu, steps=5, warmup=3):
         out[f"256cube_type3_ra1e6_{name}"] = measure_cavity(
             dmrt, torch, stream, gpu, grid=(256,) * 3, wall=3, ra=1e6, storage=STORAGES[name],
             inner=LBM_STEPS_PER_STEP, steps=steps, warmup=warmup)
-    for name in ("f32", "bf16"):
-        out[f"ensemble64_{name}"] = measure_ensemble(
-            dmrt, inputs, torch, stream, gpu, members=64, seed=1234, storage=STORAGES[name], streaming=0,
-            inner=LBM_STEPS_PER_STEP, steps=steps, warmup=warmup)
+    for name, streaming in (("f32", "ab"), ("bf16", "ab"), ("bf16", "inplace")):
+        key = f"ensemble64_{name}" + ("_inplace" if streaming == "inplace" else "")
+        out[key] = measure_ensemble(
+            dmrt, inputs, torch, stream, gpu, members=64, seed=1234, storage=STORAGES[name],
+            streaming=STREAMINGS[streaming], inner=LBM_STEPS_PER_STEP, steps=steps, warmup=warmup)
     return out
 
 
