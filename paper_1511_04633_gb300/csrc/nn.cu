@@ -10,6 +10,7 @@
 // sum accumulates in FP32; gradients are FP32.  Every reduction runs in a
 // fixed order (per-block partials, then an ordered finishing pass), so the
 // training is bitwise repeatable.
+#include <atomic>
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -772,6 +773,46 @@ constexpr unsigned kUmWaitPolls = 1u << 22;  // ~0.3 s of polling before giving 
 #ifndef DMRT_UMMA_TMEM_COLS
 #define DMRT_UMMA_TMEM_COLS 0
 #endif
+
+// Streaming multiprocessors of the current device (152 on GB300), asked once
+// per device.
+int sm_count()
+{
+    static std::atomic<int> cached[64];
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 152;
+    }
+    if (dev >= 0 && dev < 64 && (sms = cached[dev].load(std::memory_order_relaxed)) > 0) return sms;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) {
+        cudaGetLastError();
+        return 152;
+    }
+    if (dev >= 0 && dev < 64) cached[dev].store(sms, std::memory_order_relaxed);
+    return sms;
+}
+
+// The z run of the streaming convolutions: each CTA walks zrun planes of an
+// 8 x 16 column, xy columns in all, `slots` CTAs resident at once.  A run
+// costs about zrun + 3 planes (the CTA's weights, two halo planes, the
+// pipeline fill), and CTAs beyond the resident ones wait for whole runs, so
+// the run minimises waves x (zrun + 3), longer runs among equals.  At 64^3
+// x 4 samples this takes 512 CTAs of 16 planes in one wave; the earlier rule
+// (about 4 CTAs per SM) gave 640 CTAs of 13 planes, 32 of them in a second
+// wave, and the layer took almost two runs' time.
+int conv_zrun(long long xy, int n, int slots)
+{
+    int best = n, best_cost = 0x7fffffff;
+    for (int zs = 1; zs <= std::max(1, n / 2); ++zs) {
+        const int zrun = (n + zs - 1) / zs;
+        const long long ctas = xy * ((n + zrun - 1) / zrun);
+        const long long waves = (ctas + slots - 1) / slots;
+        const long long cost = waves * (zrun + 3);
+        if (cost < best_cost || (cost == best_cost && zrun > best)) best = zrun, best_cost = static_cast<int>(cost);
+    }
+    return best;
+}
 
 template <int CO, typename TO>
 __global__ void __launch_bounds__(128, 1) conv3d_umma_kernel(const __nv_bfloat16 *__restrict__ x,
@@ -1772,13 +1813,9 @@ cudaError_t conv3d(const TI *x, const TW *w, const float *bias, TO *y, int batch
             ((reinterpret_cast<unsigned long long>(x) | reinterpret_cast<unsigned long long>(w)) & 15ull) == 0;
         if (k == 3 && aligned && (cin == 8 || cin == 16 || cin == 32) && (cout == 16 || cout == 32) &&
             n % kUmY == 0 && umma_enabled()) {
-            // stream along z: about DMRT_UMMA_CTAS_PER_SM CTAs per SM, runs of at least 2 planes
+            // stream along z: each CTA walks a run of zrun planes of one 8 x 16
+            // column, the run chosen for the kernel's resident CTAs (conv_zrun)
             const long long xy = static_cast<long long>(batch) * (n / kUmX) * (n / kUmY);
-            int zs = static_cast<int>((DMRT_UMMA_CTAS_PER_SM * 152 + xy - 1) / xy);
-            zs = std::max(1, std::min(zs, n / 2));
-            const int zrun = (n + zs - 1) / zs;
-            zs = (n + zrun - 1) / zrun;
-            const unsigned grid = static_cast<unsigned>(xy * zs);
             int *err = umma_error_word();
             if (!err) return cudaErrorInvalidValue;
             cudaError_t e = cudaSuccess;
@@ -1787,8 +1824,16 @@ cudaError_t conv3d(const TI *x, const TW *w, const float *bias, TO *y, int batch
                 // halo planes by TMA
                 auto go_tma = [&](auto kernel, unsigned smem) {
                     e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-                    if (e == cudaSuccess)
-                        kernel<<<grid, kUtThreads, smem, s>>>(xmap, w, bias, y, n, cin, cout, act, zrun, err);
+                    if (e != cudaSuccess) return;
+                    // resident CTAs per SM of this variant: its shared memory
+                    // (plus the 1 KB the runtime reserves per CTA) against the
+                    // SM's 228 KB, at most DMRT_UMMA_CTAS_PER_SM (the launch
+                    // bounds' minimum)
+                    const int per_sm = std::max(
+                        1, std::min(DMRT_UMMA_CTAS_PER_SM, static_cast<int>((228u * 1024u) / (smem + 1024u))));
+                    const int zrun = conv_zrun(xy, n, per_sm * sm_count());
+                    const unsigned grid = static_cast<unsigned>(xy * ((n + zrun - 1) / zrun));
+                    kernel<<<grid, kUtThreads, smem, s>>>(xmap, w, bias, y, n, cin, cout, act, zrun, err);
                 };
                 if (cout == 16 && cin <= 16) go_tma(conv3d_umma_tma_kernel<16, 2, TO>, ut_smem_bytes<16, 2>());
                 else if (cout == 16) go_tma(conv3d_umma_tma_kernel<16, 4, TO>, ut_smem_bytes<16, 4>());
