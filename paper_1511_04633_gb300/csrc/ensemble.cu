@@ -1,17 +1,21 @@
-// ensemble.cu -- many independent cavities advanced together: one kernel
-// launch per time step covers up to 64 cavities of the ensemble, and a residual
-// interval of K steps replays one captured CUDA graph.
+// ensemble.cu -- many independent cavities advanced together, a few kernel
+// launches per time step for the whole ensemble, and a residual interval of
+// K steps replayed as one captured CUDA graph.
 //
 // Each cavity keeps its own 26-plane population slab inside two shared
 // ping-pong buffers (A-B scheme, as for a single cavity), or inside one
 // buffer updated in place by two alternating kernels (the in-place scheme of
-// step_inplace.cu, half the population memory).  Each step launch carries
-// the descriptors of its members (sizes, strides, tile shape, relaxation
-// rates, wall type; up to 64 members, more take several launches) in its
-// parameters, so that a block finds its member from its index alone; a
-// block map in device memory gives the block's tile.  The residual and
-// Nusselt kernels read the same descriptors from device memory.  The
-// per-cell arithmetic is the single-cavity body (step_body.cuh), and
+// step_inplace.cu, half the population memory).  Two step paths:
+//  - shape groups (two cells per thread, few distinct shapes): one launch
+//    per shape (and per 64 members), the shape's offset tables in the launch
+//    parameters as for a single cavity, the grid a single cavity's with its
+//    z extent repeated per member; in a captured interval each group runs as
+//    its own chain on a side stream;
+//  - tables (otherwise): one launch per 64 members of any shapes, their
+//    sizes, strides and rates in the launch parameters, a block map in device
+//    memory giving each block its tile.
+// The residual and Nusselt kernels read the descriptors from device memory.
+// The per-cell arithmetic is the single-cavity body (step_body.cuh), and
 // stochastic rounding draws the same bits from the cell index and step
 // number, so a member evolves bitwise like a single handle of the same
 // cavity.  When every member has an even row length the kernels take two
