@@ -299,9 +299,11 @@ dmrt_status dmrt_get_stats(dmrt_t *h, dmrt_stats *out, int reset);
 
 /* ------------------------------------------------------------------------
  * Ensembles: many independent cavities advanced together.  Every time step
- * is one kernel launch per 64 cavities (the launch's parameters hold its
- * cavities' sizes and rates, and a block map in device memory gives each
- * thread block its cavity's tile); a whole residual interval of K steps
+ * is a few kernel launches: one per cavity shape when the rows are even and
+ * the shapes few (the shape's offset tables and its cavities' rates in the
+ * launch parameters), else one per 64 cavities (their sizes and rates in the
+ * launch parameters, a block map in device memory giving each thread block
+ * its cavity's tile); a whole residual interval of K steps
  * replays one captured CUDA graph.  Cavities may differ in size, Ra, Pr, Ma
  * and wall type; they share the storage format and K.  Members are numbered
  * 0..count-1 in the order given.  The method per cavity is exactly that of a
