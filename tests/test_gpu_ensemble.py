@@ -325,7 +325,7 @@ def test_ensemble_of_more_members_than_one_launch_holds(dm, streaming, even):
     assert np.all(np.isfinite(r))
 
 
-@pytest.mark.parametrize("storage", [0, 1], ids=["f32", "bf16"])
+@pytest.mark.parametrize("storage", [0, 1, 2], ids=["f32", "bf16", "f16"])
 @pytest.mark.parametrize("streaming", [0, 1], ids=["ab", "inplace"])
 def test_shape_groups_of_more_members_than_one_launch_holds(dm, streaming, storage):
     """With few distinct shapes and even rows, members are stepped by shape
