@@ -339,10 +339,14 @@ dmrt_status dmrt_ensemble_get_stats(dmrt_ensemble_t *e, dmrt_stats *out, int res
  * per thread) and, per distinct cavity width, the tile width along x in
  * threads (32, 64 or 128, and 16 with two cells per thread, where a thread
  * covers two cells of the row) by timing `trials` launches of each candidate
- * on the live buffers (the state is not advanced).  `report` (may be NULL)
- * receives a one-line summary of the choices and times.  Without a call the
- * defaults are 128 threads and the widest tile not wider than the row's
- * threads (rounded up to 32, or to 16 with two cells per thread). */
+ * on the live buffers (in place: on a scratch copy; the state is not
+ * advanced).  `report` (may be NULL) receives a one-line summary: the
+ * choices and the total per thread-block size, "chosen threads=T;", then
+ * every candidate's time as " nxW/tT/bxB:Mus".  Without a call the defaults
+ * are 128 threads and, with one cell per thread, the widest tile not wider
+ * than the row's threads (rounded up to 32); with two cells per thread, the
+ * tile of 16, 32 or 64 pairs that leaves the fewest idle threads along a row
+ * (the widest of equals), as for a single cavity. */
 dmrt_status dmrt_ensemble_autotune(dmrt_ensemble_t *e, int trials, char *report, int report_len);
 
 /* Advance every member n >= 0 steps (residual points as in dmrt_step, per
