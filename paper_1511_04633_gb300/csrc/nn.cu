@@ -1877,7 +1877,11 @@ cudaError_t conv3d(const TI *x, const TW *w, const float *bias, TO *y, int batch
             // the dynamic shared memory exceeds the 48 KB default: opt in (per
             // call, so every device the kernel runs on gets the attribute)
             cudaError_t e;
-            if (cout % 32 == 0) {
+            // 32 output channels per block, unless that leaves most SMs idle
+            // (the 8^3 level: 32 blocks of 32 channels at batch 4): 16 per
+            // block doubles the blocks; every output accumulates the same
+            // MMAs in the same order either way, so the results are the same
+            if (cout % 32 == 0 && vtiles * static_cast<unsigned>(cout / 32) >= 2u * sm_count()) {
                 const int smem = (kWtHalo + 27 * 32) * kWtRow * 2;
                 e = cudaFuncSetAttribute(conv3d_tc_kernel<4, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
                 if (e != cudaSuccess) return e;

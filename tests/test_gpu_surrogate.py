@@ -198,3 +198,26 @@ def test_tensor_core_convolution_on_a_64_grid(env, cin, cout, out_f32):
     got = y.double().cpu().numpy()
     tol = 2e-5 if out_f32 else 8e-3
     assert np.abs(got - ref).max() <= tol * np.abs(ref).max()
+
+
+def test_channel_blocks_of_the_small_grid_convolution_give_the_same_bits(env):
+    """At 8^3 the mma.sync convolution takes 16 output channels per block
+    when 32 per block would leave most SMs idle (a small batch), and 32 per
+    block otherwise (a large batch).  Every output accumulates the same MMAs
+    in the same order either way: the first samples of a large batch come out
+    bitwise equal to the same samples alone, and both match the definition."""
+    torch, dm = env
+    n, cin, cout, big = 8, 64, 128, 64
+    x = torch.from_numpy(inputs.random_targets((big, n, n, n, cin), seed=41)).to(torch.bfloat16).cuda()
+    w = torch.from_numpy(inputs.random_weights(27 * cout * cin, seed=42, scale=0.2)).to(torch.bfloat16).cuda()
+    b = torch.from_numpy(inputs.random_weights(cout, seed=43, scale=0.5)).cuda()
+    y_small = torch.empty((2, n, n, n, cout), dtype=torch.float32, device="cuda")
+    y_big = torch.empty((big, n, n, n, cout), dtype=torch.float32, device="cuda")
+    dm.dmrt_nn_conv3d(x[:2].contiguous(), w, b, y_small, 2, n, cin, cout, 3, act=1)
+    dm.dmrt_nn_conv3d(x, w, b, y_big, big, n, cin, cout, 3, act=1)
+    torch.cuda.synchronize()
+    assert torch.equal(y_small, y_big[:2])
+    xs = x[:2].double().cpu().numpy()
+    ref = S.leaky(S.conv3d(xs, w.double().cpu().numpy().reshape(27, cout, cin), b.double().cpu().numpy(), 3))
+    got = y_small.double().cpu().numpy()
+    assert np.abs(got - ref).max() <= 2e-5 * np.abs(ref).max()
