@@ -498,8 +498,8 @@ def run_warm_start(count):
 
 def measure_ensemble(dmrt, inputs, torch, stream, gpu, *, members, seed, storage, streaming, inner, steps,
                      warmup, dist=None, device=None, world=1):
-    """The batched ensemble of seeded cavities (one launch per time step over
-    all of them, autotuned) timed with CUDA events on `stream`, and the same
+    """The batched ensemble of seeded cavities (a few launches per time step
+    over all of them, autotuned) timed with CUDA events on `stream`, and the same
     cavities as separate handles stepped one after another.  Returns the
     measurement as a dict (MLUPS over all ranks)."""
     draws = inputs.ensemble_draws(members, seed=seed)

@@ -597,7 +597,7 @@ def dmrt_ensemble_member_params(e, member: int) -> dict:
 
 
 class Ensemble:
-    """Many cavities stepped by one launch per time step (per 64 members).  ``cavities`` is a
+    """Many cavities stepped together, a few launches per time step.  ``cavities`` is a
     list of dicts {"grid": (nx, ny, nz), "Ra": .., "wall": 1..3, ["Pr", "Ma"]}."""
 
     def __init__(self, cavities, storage=STORE_F32, residual_interval=0, rounding=ROUND_AUTO,

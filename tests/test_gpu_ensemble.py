@@ -1,4 +1,4 @@
-"""Ensembles: many cavities advanced by one launch per time step.  Each member
+"""Ensembles: many cavities advanced by a few launches per time step.  Each member
 must evolve exactly like a single cavity handle (same per-cell arithmetic)
 and so match the FP64 oracle like one."""
 
